@@ -1,0 +1,325 @@
+"""Plain CPU oracle for OblivGM's masked secure predicate evaluation.
+
+TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may use it.  The
+product package never imports it and it never imports the product package.
+
+The arithmetic lives in ``oracle.c`` (plain byte-oriented FIPS-197 AES, the
+DPF/DCF constructions the paper cites, the token of Sec. V-C, secEval of
+Alg. 3 with the re-share of Sec. III-B and the AND fold of Sec. V-D).  This
+module compiles it with gcc, loads it with ctypes and adds the plaintext
+definitions the results reconstruct to:
+
+* ``plain_pred``  -- Def. 2: ``Att == value`` (equality) or ``Att in range``;
+* ``match``       -- Def. 2 subgraph matching by brute-force backtracking.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_SO = os.path.join(_OUT_DIR, "liboblivgm_oracle.so")
+
+KIND_DPF, KIND_DCF = 1, 2
+PRED_EQ, PRED_RANGE = 1, 2
+BETA_PRIME = 0xAAAAAAAB        # 3^{-1} mod 2^32
+MASK32 = 0xFFFFFFFF
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into a shared library (plain gcc, portable C99)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-Wall", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class _Table(ctypes.Structure):
+    _fields_ = [("n_elems", ctypes.c_uint64), ("n_attrs", ctypes.c_uint32), ("n_bits", ctypes.c_uint32),
+                ("share", ctypes.c_void_p * 3)]
+
+
+class _Pred(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint32) for f in ("kind", "table", "attr", "group", "lo", "hi")]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            l = ctypes.CDLL(build())
+            u8p, u32, u64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+            l.orc_init.restype = None
+            l.orc_aes128.argtypes = [u8p, u8p, u8p]
+            l.orc_prg.argtypes = [ctypes.c_int, u8p, u8p]
+            l.orc_key_len.argtypes = [ctypes.c_int, ctypes.c_int]
+            l.orc_key_len.restype = ctypes.c_size_t
+            for g in (l.orc_dpf_gen, l.orc_dcf_gen):
+                g.argtypes = [ctypes.c_int, u32, u32, u8p, u8p, u8p, u8p]
+                g.restype = None
+            for e in (l.orc_dpf_eval, l.orc_dcf_eval):
+                e.argtypes = [u8p, u32]
+                e.restype = u32
+            l.orc_token_len.argtypes = [ctypes.POINTER(_Pred), u32, ctypes.c_int]
+            l.orc_token_len.restype = ctypes.c_size_t
+            l.orc_keygen.argtypes = [ctypes.POINTER(_Pred), u32, ctypes.c_int, u8p, u8p, u8p, u8p, ctypes.c_size_t]
+            l.orc_filter.argtypes = [u8p, u8p, u8p, ctypes.POINTER(ctypes.c_size_t), u32, u8p,
+                                     ctypes.POINTER(_Table), u32, u32, u8p, u64, u8p]
+            l.orc_pred_z.argtypes = [u8p, u8p, u8p, ctypes.POINTER(ctypes.c_size_t), u32, u32, u8p, u8p]
+            l.orc_reshare.argtypes = [u8p, u8p, u8p, u64, u32, u32, u32]
+            l.orc_init()
+            _lib = l
+    return _lib
+
+
+def _buf(b: bytes):
+    return ctypes.create_string_buffer(bytes(b), len(b))
+
+
+def _addr(buf):
+    return ctypes.cast(buf, ctypes.c_void_p)
+
+
+# ---------------------------------------------------------------- primitives
+
+def aes128(key: bytes, block: bytes) -> bytes:
+    """AES-128 encryption of one block (FIPS-197)."""
+    out = ctypes.create_string_buffer(16)
+    lib().orc_aes128(_addr(_buf(key)), _addr(_buf(block)), _addr(out))
+    return out.raw
+
+
+def prg(which: int, seed: bytes) -> bytes:
+    """H_K(s) = AES_K(s) xor s with fixed key K_which (0 L, 1 R, 2 vL, 3 vR)."""
+    out = ctypes.create_string_buffer(16)
+    lib().orc_prg(which, _addr(_buf(seed)), _addr(out))
+    return out.raw
+
+
+def key_len(kind: int, n: int) -> int:
+    return lib().orc_key_len(kind, n)
+
+
+def _gen(fn, kind, n, alpha, beta, s0, s1):
+    L = key_len(kind, n)
+    k0, k1 = ctypes.create_string_buffer(L), ctypes.create_string_buffer(L)
+    fn(n, alpha & MASK32, beta & MASK32, _addr(_buf(s0)), _addr(_buf(s1)), _addr(k0), _addr(k1))
+    return k0.raw, k1.raw
+
+
+def dpf_gen(n: int, alpha: int, beta: int, s0: bytes, s1: bytes):
+    """DPF Gen for f^=_{alpha,beta} over Z_{2^32} (domain {0,1}^n)."""
+    return _gen(lib().orc_dpf_gen, KIND_DPF, n, alpha, beta, s0, s1)
+
+
+def dcf_gen(n: int, alpha: int, beta: int, s0: bytes, s1: bytes):
+    """DCF Gen for g^<_{alpha,beta} over Z_{2^32} (domain {0,1}^n)."""
+    return _gen(lib().orc_dcf_gen, KIND_DCF, n, alpha, beta, s0, s1)
+
+
+def dpf_eval(key: bytes, x: int) -> int:
+    return lib().orc_dpf_eval(_addr(_buf(key)), x & MASK32)
+
+
+def dcf_eval(key: bytes, x: int) -> int:
+    return lib().orc_dcf_eval(_addr(_buf(key)), x & MASK32)
+
+
+def eval_many(key: bytes, xs, kind: int) -> np.ndarray:
+    """Eval one key at many points (plain loop over the C Eval)."""
+    k = _buf(key)
+    fn = lib().orc_dpf_eval if kind == KIND_DPF else lib().orc_dcf_eval
+    return np.array([fn(_addr(k), int(x) & MASK32) for x in xs], dtype=np.uint32)
+
+
+# ---------------------------------------------------------------- token + secEval
+
+def _preds(preds):
+    arr = (_Pred * len(preds))()
+    for i, p in enumerate(preds):
+        arr[i].kind, arr[i].table, arr[i].attr = p["kind"], p["table"], p["attr"]
+        arr[i].group, arr[i].lo, arr[i].hi = p.get("group", 0), p["lo"], p.get("hi", p["lo"])
+    return arr
+
+
+def token_len(preds, n: int) -> int:
+    return lib().orc_token_len(_preds(preds), len(preds), n)
+
+
+def keygen(preds, n: int, seed: bytes):
+    """The three server tokens tok^(1..3) for a list of predicates (Sec. V-C).
+
+    Each predicate is a dict with kind (PRED_EQ / PRED_RANGE), table, attr,
+    group (AND-group index) and lo (= alpha for EQ), hi (inclusive, RANGE).
+    """
+    arr = _preds(preds)
+    L = token_len(preds, n)
+    bufs = [ctypes.create_string_buffer(L) for _ in range(3)]
+    rc = lib().orc_keygen(arr, len(preds), n, _addr(_buf(seed)), *[_addr(b) for b in bufs], L)
+    if rc != 0:
+        raise ValueError(f"oracle keygen rejected the predicates (code {rc})")
+    return tuple(b.raw for b in bufs)
+
+
+def _tables(tables):
+    """tables: list of 3-tuples of uint32 arrays shaped [n_attrs, n_elems] plus n_bits."""
+    arr = (_Table * len(tables))()
+    keep = []
+    for i, (shares, n_bits) in enumerate(tables):
+        shares = [np.ascontiguousarray(s, dtype=np.uint32) for s in shares]
+        keep.extend(shares)
+        arr[i].n_attrs, arr[i].n_elems = shares[0].shape
+        arr[i].n_bits = n_bits
+        for j in range(3):
+            arr[i].share[j] = shares[j].ctypes.data
+    return arr, keep
+
+
+def filter_group(tokens, query_id: int, prf_keys: bytes, tables, group: int, elems,
+                 threads: int = 1) -> np.ndarray:
+    """secEval + re-share + AND fold of one AND-group on the listed elements.
+
+    Returns the three RSS share sets, shape (3, len(elems)), uint32.
+    ``threads`` > 1 splits the element list across threads (the C code holds
+    no shared mutable state after initialisation).
+    """
+    elems = np.ascontiguousarray(elems, dtype=np.uint64)
+    tarr, keep = _tables(tables)
+    toks = [_buf(t) for t in tokens]
+    lens = (ctypes.c_size_t * 3)(*[len(t) for t in tokens])
+    pk = _buf(prf_keys)
+    out = np.zeros((3, len(elems)), dtype=np.uint32)
+
+    def run(lo, hi):
+        part = np.ascontiguousarray(elems[lo:hi])
+        o = np.zeros((3, hi - lo), dtype=np.uint32)
+        rc = lib().orc_filter(*[_addr(t) for t in toks], lens, query_id, _addr(pk), tarr, len(tables),
+                              group, part.ctypes.data, hi - lo, o.ctypes.data)
+        if rc != 0:
+            raise ValueError(f"oracle filter failed (code {rc})")
+        out[:, lo:hi] = o
+
+    n = len(elems)
+    if threads <= 1 or n < 2 * threads:
+        if n:
+            run(0, n)
+    else:
+        cuts = np.linspace(0, n, threads + 1).astype(int)
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(lambda i: run(cuts[i], cuts[i + 1]), range(threads)))
+    del keep
+    return out
+
+
+def pred_z(tokens, pred: int, xhat: int):
+    """z_1..z_3 and the six key-half outputs y of one predicate at masked input xhat."""
+    toks = [_buf(t) for t in tokens]
+    lens = (ctypes.c_size_t * 3)(*[len(t) for t in tokens])
+    z = (ctypes.c_uint32 * 3)()
+    y = (ctypes.c_uint32 * 6)()
+    rc = lib().orc_pred_z(*[_addr(t) for t in toks], lens, pred, xhat & MASK32,
+                          ctypes.cast(z, ctypes.c_void_p), ctypes.cast(y, ctypes.c_void_p))
+    if rc != 0:
+        raise ValueError("bad token")
+    return list(z), list(y)
+
+
+def reshare(prf_keys: bytes, z, elem: int, step: int, table: int, query: int):
+    zi = (ctypes.c_uint32 * 3)(*[int(v) & MASK32 for v in z])
+    out = (ctypes.c_uint32 * 3)()
+    lib().orc_reshare(_addr(_buf(prf_keys)), ctypes.cast(zi, ctypes.c_void_p), ctypes.cast(out, ctypes.c_void_p),
+                      elem, step, table, query)
+    return list(out)
+
+
+def reconstruct(shares) -> np.ndarray:
+    """Sum of the three share sets mod 2^32."""
+    s = np.asarray(shares, dtype=np.uint64)
+    return ((s[0] + s[1] + s[2]) & MASK32).astype(np.uint32)
+
+
+# ---------------------------------------------------------------- plaintext definitions
+
+def plain_pred(pred, values) -> np.ndarray:
+    """Def. 2 on plaintext values: equality or inclusive range membership, as 0/1."""
+    v = np.asarray(values, dtype=np.uint64)
+    if pred["kind"] == PRED_EQ:
+        return (v == pred["lo"]).astype(np.uint32)
+    return ((v >= pred["lo"]) & (v <= pred["hi"])).astype(np.uint32)
+
+
+def plain_group(preds, group: int, attrs) -> np.ndarray:
+    """AND over the group's predicates on plaintext attribute rows attrs[attr][elem]."""
+    res = None
+    for p in preds:
+        if p.get("group", 0) != group:
+            continue
+        b = plain_pred(p, attrs[p["attr"]])
+        res = b if res is None else res & b
+    return res
+
+
+def match(n_vertices: int, edges, query_vertices: int, query_edges, vertex_ok, edge_ok):
+    """Def. 2 attributed subgraph matching, brute-force backtracking (tiny graphs only).
+
+    edges: array (M, 2) of undirected graph edges, edge id = row index.
+    query_edges: list of (qa, qb) pairs over query vertices 0..query_vertices-1.
+    vertex_ok[qv]: bool array over graph vertices (None = no predicate).
+    edge_ok[qe]:   bool array over graph edge ids (None = no predicate).
+    Returns the sorted list of embeddings (tuples mapping query vertex -> graph vertex),
+    injective, each query edge mapped onto a graph edge whose predicate holds.
+    """
+    adj = [dict() for _ in range(n_vertices)]
+    for eid, (a, b) in enumerate(np.asarray(edges)):
+        a, b = int(a), int(b)
+        adj[a][b] = eid
+        adj[b][a] = eid
+    qadj = [[] for _ in range(query_vertices)]
+    for qe, (qa, qb) in enumerate(query_edges):
+        qadj[qa].append((qb, qe))
+        qadj[qb].append((qa, qe))
+    out = []
+    assign = [-1] * query_vertices
+
+    def ok_vertex(qv, v):
+        return vertex_ok[qv] is None or bool(vertex_ok[qv][v])
+
+    def extend(qv):
+        if qv == query_vertices:
+            out.append(tuple(assign))
+            return
+        # candidates: neighbours of an already-mapped query neighbour, else all vertices
+        anchor = next(((qn, qe) for qn, qe in qadj[qv] if assign[qn] >= 0), None)
+        cands = adj[assign[anchor[0]]].keys() if anchor else range(n_vertices)
+        used = set(a for a in assign if a >= 0)
+        for v in cands:
+            if v in used or not ok_vertex(qv, v):
+                continue
+            good = True
+            for qn, qe in qadj[qv]:
+                if assign[qn] < 0:
+                    continue
+                eid = adj[v].get(assign[qn])
+                if eid is None or (edge_ok[qe] is not None and not edge_ok[qe][eid]):
+                    good = False
+                    break
+            if good:
+                assign[qv] = v
+                extend(qv + 1)
+                assign[qv] = -1
+
+    extend(0)
+    return sorted(out)

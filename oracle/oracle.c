@@ -1,0 +1,701 @@
+/*
+ * oracle.c -- plain, slow CPU oracle for the masked FSS predicate-evaluation path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py load this code.  The product
+ * library (paper_2209_03526_gb300/) shares no code, table or header with it.
+ *
+ * What it computes (OblivGM, arXiv 2209.03526):
+ *   - AES-128 exactly as FIPS-197 writes it, byte by byte; the S-box is derived
+ *     at start-up from the GF(2^8) inverse and the affine map (Sec. VII-A fixes
+ *     the security parameter lambda = 128; the paper is silent on the PRG).
+ *   - the PRG  H_K(s) = AES_K(s) xor s  under four fixed public keys
+ *     K_L, K_R, K_vL, K_vR with K_j[i] = 16 j + i   (reading P1 of the design).
+ *   - DPF Gen/Eval for the point function f^=_{alpha,beta} (Sec. V-C; the
+ *     tree construction of Boyle-Gilboa-Ishai, CCS'16, which the paper cites).
+ *   - DCF Gen/Eval for the comparison function g^<_{alpha,beta} (Sec. V-C;
+ *     the construction of Boyle et al., Eurocrypt'21, which the paper cites).
+ *   - the secure query token of Sec. V-C: three independent key pairs per
+ *     predicate, handed to CS1..CS3 as (k^1_1,k^2_1), (k^2_2,k^3_1), (k^3_2,k^1_2).
+ *   - secEval (Alg. 3) on additively masked inputs (Sec. V-C, the masked-input
+ *     approach), the per-server sum of Eq. (predEval), the PRF re-share of
+ *     Sec. III-B and the RSS AND fold of Sec. V-D, all over Z_{2^32}.
+ *
+ * Every step is written in the order the construction states it; nothing is
+ * blocked, fused or reordered.  Eval computes only the child the input bit
+ * selects: the other half of G(s) is computed and then discarded by the
+ * construction, so leaving it out changes no output.
+ */
+#include <stdint.h>
+#include <stddef.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* GF(2^8) with the AES polynomial x^8 + x^4 + x^3 + x + 1 (FIPS-197 Sec. 4) */
+/* ------------------------------------------------------------------------ */
+
+static uint8_t gf_mul(uint8_t a, uint8_t b)
+{
+    uint8_t p = 0;
+    for (int i = 0; i < 8; i++) {
+        if (b & 1) p ^= a;
+        uint8_t carry = (uint8_t)(a & 0x80);
+        a = (uint8_t)(a << 1);
+        if (carry) a ^= 0x1b;
+        b >>= 1;
+    }
+    return p;
+}
+
+/* multiplicative inverse by exhaustive search; 0 maps to 0 (FIPS-197 Sec. 5.1.1) */
+static uint8_t gf_inv(uint8_t a)
+{
+    if (a == 0) return 0;
+    for (int x = 1; x < 256; x++)
+        if (gf_mul(a, (uint8_t)x) == 1) return (uint8_t)x;
+    return 0;
+}
+
+/* S-box entry: inverse followed by the affine map b'_i = b_i ^ b_{i+4} ^ b_{i+5} ^ b_{i+6} ^ b_{i+7} ^ c_i, c = 0x63 */
+static uint8_t sbox_entry(uint8_t a)
+{
+    uint8_t b = gf_inv(a), s = 0;
+    for (int i = 0; i < 8; i++) {
+        int bit = ((b >> i) ^ (b >> ((i + 4) & 7)) ^ (b >> ((i + 5) & 7)) ^
+                   (b >> ((i + 6) & 7)) ^ (b >> ((i + 7) & 7)) ^ (0x63 >> i)) & 1;
+        s |= (uint8_t)(bit << i);
+    }
+    return s;
+}
+
+static uint8_t SBOX[256];
+
+/* ------------------------------------------------------------------------ */
+/* AES-128 (FIPS-197 Sec. 5.1 cipher, Sec. 5.2 key expansion)               */
+/* ------------------------------------------------------------------------ */
+
+typedef struct { uint8_t w[44][4]; } aes_ks;   /* 44 words of 4 bytes */
+
+static void key_expansion(const uint8_t key[16], aes_ks* ks)
+{
+    uint8_t rcon = 0x01;
+    for (int i = 0; i < 4; i++)
+        for (int j = 0; j < 4; j++) ks->w[i][j] = key[4 * i + j];
+    for (int i = 4; i < 44; i++) {
+        uint8_t temp[4];
+        memcpy(temp, ks->w[i - 1], 4);
+        if (i % 4 == 0) {
+            uint8_t t0 = temp[0];                       /* RotWord */
+            temp[0] = temp[1]; temp[1] = temp[2]; temp[2] = temp[3]; temp[3] = t0;
+            for (int j = 0; j < 4; j++) temp[j] = SBOX[temp[j]];   /* SubWord */
+            temp[0] ^= rcon;                            /* Rcon[i/4] = x^(i/4 - 1) */
+            rcon = gf_mul(rcon, 0x02);
+        }
+        for (int j = 0; j < 4; j++) ks->w[i][j] = (uint8_t)(ks->w[i - 4][j] ^ temp[j]);
+    }
+}
+
+static void add_round_key(uint8_t st[4][4], const aes_ks* ks, int round)
+{
+    for (int c = 0; c < 4; c++)
+        for (int r = 0; r < 4; r++) st[r][c] ^= ks->w[4 * round + c][r];
+}
+
+static void sub_bytes(uint8_t st[4][4])
+{
+    for (int r = 0; r < 4; r++)
+        for (int c = 0; c < 4; c++) st[r][c] = SBOX[st[r][c]];
+}
+
+static void shift_rows(uint8_t st[4][4])
+{
+    for (int r = 1; r < 4; r++) {
+        uint8_t row[4];
+        for (int c = 0; c < 4; c++) row[c] = st[r][(c + r) % 4];
+        for (int c = 0; c < 4; c++) st[r][c] = row[c];
+    }
+}
+
+static void mix_columns(uint8_t st[4][4])
+{
+    for (int c = 0; c < 4; c++) {
+        uint8_t a0 = st[0][c], a1 = st[1][c], a2 = st[2][c], a3 = st[3][c];
+        st[0][c] = (uint8_t)(gf_mul(a0, 2) ^ gf_mul(a1, 3) ^ a2 ^ a3);
+        st[1][c] = (uint8_t)(a0 ^ gf_mul(a1, 2) ^ gf_mul(a2, 3) ^ a3);
+        st[2][c] = (uint8_t)(a0 ^ a1 ^ gf_mul(a2, 2) ^ gf_mul(a3, 3));
+        st[3][c] = (uint8_t)(gf_mul(a0, 3) ^ a1 ^ a2 ^ gf_mul(a3, 2));
+    }
+}
+
+static void aes_encrypt(const aes_ks* ks, const uint8_t in[16], uint8_t out[16])
+{
+    uint8_t st[4][4];
+    for (int i = 0; i < 16; i++) st[i % 4][i / 4] = in[i];
+    add_round_key(st, ks, 0);
+    for (int round = 1; round < 10; round++) {
+        sub_bytes(st);
+        shift_rows(st);
+        mix_columns(st);
+        add_round_key(st, ks, round);
+    }
+    sub_bytes(st);
+    shift_rows(st);
+    add_round_key(st, ks, 10);
+    for (int i = 0; i < 16; i++) out[i] = st[i % 4][i / 4];
+}
+
+/* ------------------------------------------------------------------------ */
+/* PRG: H_K(s) = AES_K(s) xor s with fixed public keys K_j[i] = 16 j + i     */
+/* ------------------------------------------------------------------------ */
+
+enum { KEY_L = 0, KEY_R = 1, KEY_VL = 2, KEY_VR = 3 };
+static aes_ks FIXED[4];
+static int ready = 0;
+
+void orc_init(void)
+{
+    if (ready) return;
+    for (int a = 0; a < 256; a++) SBOX[a] = sbox_entry((uint8_t)a);
+    for (int j = 0; j < 4; j++) {
+        uint8_t k[16];
+        for (int i = 0; i < 16; i++) k[i] = (uint8_t)(16 * j + i);
+        key_expansion(k, &FIXED[j]);
+    }
+    ready = 1;
+}
+
+static void prg_h(int which, const uint8_t s[16], uint8_t out[16])
+{
+    uint8_t e[16];
+    aes_encrypt(&FIXED[which], s, e);
+    for (int i = 0; i < 16; i++) out[i] = (uint8_t)(e[i] ^ s[i]);
+}
+
+/* child seed and control bit: t = bit 0 of byte 0, seed = block with that bit cleared */
+static void child(int dir, const uint8_t s[16], uint8_t cs[16], int* ct)
+{
+    prg_h(dir == 0 ? KEY_L : KEY_R, s, cs);
+    *ct = cs[0] & 1;
+    cs[0] &= 0xFE;
+}
+
+static uint32_t le32(const uint8_t* p)
+{
+    return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+
+static void put32(uint8_t* p, uint32_t v)
+{
+    p[0] = (uint8_t)v; p[1] = (uint8_t)(v >> 8); p[2] = (uint8_t)(v >> 16); p[3] = (uint8_t)(v >> 24);
+}
+
+/* Convert of a seed into Z_{2^32}: bytes 4..7, little-endian (byte 0 carries the control bit) */
+static uint32_t convert_seed(const uint8_t s[16]) { return le32(s + 4); }
+
+/* DCF value word of a child: bytes 0..3 of H_{K_vL or K_vR}(s) */
+static uint32_t value_word(int dir, const uint8_t s[16])
+{
+    uint8_t v[16];
+    prg_h(dir == 0 ? KEY_VL : KEY_VR, s, v);
+    return le32(v);
+}
+
+/* i-th input bit, i = 1..n, most significant first */
+static int bit_of(uint32_t x, int n, int i) { return (int)((x >> (n - i)) & 1u); }
+
+/* ------------------------------------------------------------------------ */
+/* Key wire format (little-endian):                                          */
+/*   header  u8 kind (1 DPF, 2 DCF), u8 n, u8 party b, u8 group (0 = Z_2^32), */
+/*           u32 0                                                            */
+/*   seed    16 bytes                                                         */
+/*   level i s_CW[16], u8 t^L_CW, u8 t^R_CW, u16 0, [DCF only: u32 V_CW]      */
+/*   final   u32 CW_{n+1}                                                     */
+/* ------------------------------------------------------------------------ */
+
+#define KIND_DPF 1
+#define KIND_DCF 2
+
+static size_t level_bytes(int kind) { return kind == KIND_DPF ? 20u : 24u; }
+
+size_t orc_key_len(int kind, int n) { return 24u + (size_t)n * level_bytes(kind) + 4u; }
+
+static void write_header(uint8_t* k, int kind, int n, int b, const uint8_t seed[16])
+{
+    memset(k, 0, 8);
+    k[0] = (uint8_t)kind; k[1] = (uint8_t)n; k[2] = (uint8_t)b; k[3] = 0;
+    memcpy(k + 8, seed, 16);
+}
+
+/* DPF Gen(1^lambda, alpha, beta): keys k0, k1 from the root seeds s0, s1 */
+void orc_dpf_gen(int n, uint32_t alpha, uint32_t beta, const uint8_t s0[16], const uint8_t s1[16],
+                 uint8_t* k0, uint8_t* k1)
+{
+    uint8_t s[2][16];
+    int t[2] = {0, 1};
+    memcpy(s[0], s0, 16);
+    memcpy(s[1], s1, 16);
+    write_header(k0, KIND_DPF, n, 0, s0);
+    write_header(k1, KIND_DPF, n, 1, s1);
+    for (int i = 1; i <= n; i++) {
+        uint8_t sc[2][2][16];   /* [party][dir] */
+        int tc[2][2];
+        for (int b = 0; b < 2; b++)
+            for (int dir = 0; dir < 2; dir++) child(dir, s[b], sc[b][dir], &tc[b][dir]);
+        int a = bit_of(alpha, n, i);
+        int keep = a, lose = 1 - a;
+        uint8_t s_cw[16];
+        for (int j = 0; j < 16; j++) s_cw[j] = (uint8_t)(sc[0][lose][j] ^ sc[1][lose][j]);
+        int tl_cw = tc[0][0] ^ tc[1][0] ^ a ^ 1;
+        int tr_cw = tc[0][1] ^ tc[1][1] ^ a;
+        size_t off = 24 + (size_t)(i - 1) * level_bytes(KIND_DPF);
+        for (int p = 0; p < 2; p++) {
+            uint8_t* k = p ? k1 : k0;
+            memcpy(k + off, s_cw, 16);
+            k[off + 16] = (uint8_t)tl_cw;
+            k[off + 17] = (uint8_t)tr_cw;
+            k[off + 18] = 0; k[off + 19] = 0;
+        }
+        int t_keep_cw = keep == 0 ? tl_cw : tr_cw;
+        for (int b = 0; b < 2; b++) {
+            for (int j = 0; j < 16; j++) s[b][j] = (uint8_t)(sc[b][keep][j] ^ (t[b] ? s_cw[j] : 0));
+            t[b] = tc[b][keep] ^ (t[b] & t_keep_cw);
+        }
+    }
+    uint32_t cw = beta - convert_seed(s[0]) + convert_seed(s[1]);
+    if (t[1]) cw = 0u - cw;
+    size_t off = 24 + (size_t)n * level_bytes(KIND_DPF);
+    put32(k0 + off, cw);
+    put32(k1 + off, cw);
+}
+
+/* DPF Eval(b, k_b, x) -> share of beta * [x == alpha] */
+uint32_t orc_dpf_eval(const uint8_t* key, uint32_t x)
+{
+    int n = key[1], b = key[2];
+    uint8_t s[16];
+    int t = b;
+    memcpy(s, key + 8, 16);
+    for (int i = 1; i <= n; i++) {
+        const uint8_t* cw = key + 24 + (size_t)(i - 1) * level_bytes(KIND_DPF);
+        int dir = bit_of(x, n, i);
+        uint8_t ns[16];
+        int nt;
+        child(dir, s, ns, &nt);
+        if (t) {
+            for (int j = 0; j < 16; j++) ns[j] ^= cw[j];
+            nt ^= dir == 0 ? cw[16] : cw[17];
+        }
+        memcpy(s, ns, 16);
+        t = nt;
+    }
+    uint32_t y = convert_seed(s) + (t ? le32(key + 24 + (size_t)n * level_bytes(KIND_DPF)) : 0u);
+    return b ? 0u - y : y;
+}
+
+/* DCF Gen(1^lambda, alpha, beta): shares of beta * [x < alpha] */
+void orc_dcf_gen(int n, uint32_t alpha, uint32_t beta, const uint8_t s0[16], const uint8_t s1[16],
+                 uint8_t* k0, uint8_t* k1)
+{
+    uint8_t s[2][16];
+    int t[2] = {0, 1};
+    uint32_t v_alpha = 0;
+    memcpy(s[0], s0, 16);
+    memcpy(s[1], s1, 16);
+    write_header(k0, KIND_DCF, n, 0, s0);
+    write_header(k1, KIND_DCF, n, 1, s1);
+    for (int i = 1; i <= n; i++) {
+        uint8_t sc[2][2][16];
+        int tc[2][2];
+        uint32_t vc[2][2];
+        for (int b = 0; b < 2; b++)
+            for (int dir = 0; dir < 2; dir++) {
+                child(dir, s[b], sc[b][dir], &tc[b][dir]);
+                vc[b][dir] = value_word(dir, s[b]);
+            }
+        int a = bit_of(alpha, n, i);
+        int keep = a, lose = 1 - a;
+        uint8_t s_cw[16];
+        for (int j = 0; j < 16; j++) s_cw[j] = (uint8_t)(sc[0][lose][j] ^ sc[1][lose][j]);
+        int neg = t[1];   /* (-1)^{t_1^{(i-1)}} */
+        uint32_t v_cw = vc[1][lose] - vc[0][lose] - v_alpha;
+        if (neg) v_cw = 0u - v_cw;
+        if (lose == 0) v_cw += neg ? 0u - beta : beta;
+        v_alpha = v_alpha - vc[1][keep] + vc[0][keep] + (neg ? 0u - v_cw : v_cw);
+        int tl_cw = tc[0][0] ^ tc[1][0] ^ a ^ 1;
+        int tr_cw = tc[0][1] ^ tc[1][1] ^ a;
+        size_t off = 24 + (size_t)(i - 1) * level_bytes(KIND_DCF);
+        for (int p = 0; p < 2; p++) {
+            uint8_t* k = p ? k1 : k0;
+            memcpy(k + off, s_cw, 16);
+            k[off + 16] = (uint8_t)tl_cw;
+            k[off + 17] = (uint8_t)tr_cw;
+            k[off + 18] = 0; k[off + 19] = 0;
+            put32(k + off + 20, v_cw);
+        }
+        int t_keep_cw = keep == 0 ? tl_cw : tr_cw;
+        for (int b = 0; b < 2; b++) {
+            for (int j = 0; j < 16; j++) s[b][j] = (uint8_t)(sc[b][keep][j] ^ (t[b] ? s_cw[j] : 0));
+            t[b] = tc[b][keep] ^ (t[b] & t_keep_cw);
+        }
+    }
+    uint32_t cw = convert_seed(s[1]) - convert_seed(s[0]) - v_alpha;
+    if (t[1]) cw = 0u - cw;
+    size_t off = 24 + (size_t)n * level_bytes(KIND_DCF);
+    put32(k0 + off, cw);
+    put32(k1 + off, cw);
+}
+
+/* DCF Eval(b, k_b, x) -> share of beta * [x < alpha] */
+uint32_t orc_dcf_eval(const uint8_t* key, uint32_t x)
+{
+    int n = key[1], b = key[2];
+    uint8_t s[16];
+    int t = b;
+    uint32_t v = 0;
+    memcpy(s, key + 8, 16);
+    for (int i = 1; i <= n; i++) {
+        const uint8_t* cw = key + 24 + (size_t)(i - 1) * level_bytes(KIND_DCF);
+        int dir = bit_of(x, n, i);
+        uint8_t ns[16];
+        int nt;
+        child(dir, s, ns, &nt);
+        uint32_t vw = value_word(dir, s);
+        uint32_t term = vw + (t ? le32(cw + 20) : 0u);
+        v += b ? 0u - term : term;
+        if (t) {
+            for (int j = 0; j < 16; j++) ns[j] ^= cw[j];
+            nt ^= dir == 0 ? cw[16] : cw[17];
+        }
+        memcpy(s, ns, 16);
+        t = nt;
+    }
+    uint32_t term = convert_seed(s) + (t ? le32(key + 24 + (size_t)n * level_bytes(KIND_DCF)) : 0u);
+    v += b ? 0u - term : term;
+    return v;
+}
+
+void orc_aes128(const uint8_t key[16], const uint8_t in[16], uint8_t out[16])
+{
+    aes_ks ks;
+    key_expansion(key, &ks);
+    aes_encrypt(&ks, in, out);
+}
+
+void orc_prg(int which, const uint8_t s[16], uint8_t out[16]) { prg_h(which, s, out); }
+
+/* ------------------------------------------------------------------------ */
+/* Secure query token (Sec. V-C) over masked inputs                          */
+/* ------------------------------------------------------------------------ */
+/*
+ * Token of server i (little-endian):
+ *   header (16 B)  u32 magic 0x544D474F, u8 version 1, u8 server i (1..3),
+ *                  u8 n, u8 group 0, u16 n_preds, u16 0, u32 total length
+ *   per predicate  record (24 B): u8 kind (1 EQ, 2 RANGE), u8 n, u16 table,
+ *                  u16 attr, u16 and-group, u32 <r>_i, u32 <r>_{i+1},
+ *                  u32 c*beta' (RANGE) or 0, u32 0
+ *                  then key half A and key half B of this server; a half is
+ *                  one DPF key (EQ) or two DCF keys, a1 first then a0 (RANGE).
+ * Halves held: CS1 (pair 1, party 0), (pair 2, party 0); CS2 (2,1), (3,0);
+ * CS3 (3,1), (1,1)  -- the assignment of Sec. V-C.
+ * beta' = 3^{-1} mod 2^32 for every pair, so the three pairs sum to f.
+ * Randomness: AES-128 under the 16-byte seed in counter mode, counter block =
+ * u64 index (LE) || 8 zero bytes; per predicate one block for the mask
+ * (bytes 0..3 r, 4..7 <r>_1, 8..11 <r>_2, each reduced mod 2^n), then for
+ * pair 1..3 and each key of the pair two blocks (root seeds s0, s1).
+ */
+
+#define TOKEN_MAGIC 0x544D474Fu
+#define PRED_EQ 1
+#define PRED_RANGE 2
+#define BETA_PRIME 0xAAAAAAABu   /* 3 * 0xAAAAAAAB = 1 mod 2^32 */
+#define MAX_HALF (2 * (24 + 32 * 24 + 4))   /* two DCF keys at n = 32 */
+
+typedef struct {
+    uint32_t kind, table, attr, group, lo, hi;
+} orc_pred;
+
+static const int HOLD_PAIR[3][2] = {{1, 2}, {2, 3}, {3, 1}};
+static const int HOLD_PARTY[3][2] = {{0, 0}, {1, 0}, {1, 1}};
+
+typedef struct { aes_ks ks; uint64_t ctr; } ctr_rng;
+
+static void rng_block(ctr_rng* g, uint8_t out[16])
+{
+    uint8_t c[16] = {0};
+    for (int i = 0; i < 8; i++) c[i] = (uint8_t)(g->ctr >> (8 * i));
+    g->ctr++;
+    aes_encrypt(&g->ks, c, out);
+}
+
+static uint32_t mask_n(int n) { return n >= 32 ? 0xFFFFFFFFu : ((1u << n) - 1u); }
+
+size_t orc_token_len(const orc_pred* preds, uint32_t n_preds, int n)
+{
+    size_t len = 16;
+    for (uint32_t p = 0; p < n_preds; p++) {
+        len += 24;
+        if (preds[p].kind == PRED_EQ) len += 2 * orc_key_len(KIND_DPF, n);
+        else len += 4 * orc_key_len(KIND_DCF, n);
+    }
+    return len;
+}
+
+/* returns 0, or -1 on an invalid predicate, -2 if a buffer is too small */
+int orc_keygen(const orc_pred* preds, uint32_t n_preds, int n, const uint8_t seed[16],
+               uint8_t* tok1, uint8_t* tok2, uint8_t* tok3, size_t cap)
+{
+    uint8_t* tok[3] = {tok1, tok2, tok3};
+    if (n < 1 || n > 32 || n_preds == 0 || n_preds > 64) return -1;
+    uint32_t m = mask_n(n);
+    for (uint32_t p = 0; p < n_preds; p++) {
+        const orc_pred* q = &preds[p];
+        if (q->kind == PRED_EQ) { if (q->lo > m) return -1; }
+        else if (q->kind == PRED_RANGE) { if (q->lo > q->hi || q->hi > m) return -1; }
+        else return -1;
+        if (q->table > 0xFFFF || q->attr > 0xFFFF || q->group > 0xFFFF) return -1;
+    }
+    size_t total = orc_token_len(preds, n_preds, n);
+    if (cap < total) return -2;
+    ctr_rng g;
+    key_expansion(seed, &g.ks);
+    g.ctr = 0;
+    size_t dpf_len = orc_key_len(KIND_DPF, n), dcf_len = orc_key_len(KIND_DCF, n);
+    for (int i = 0; i < 3; i++) {
+        uint8_t* h = tok[i];
+        memset(h, 0, 16);
+        put32(h, TOKEN_MAGIC);
+        h[4] = 1; h[5] = (uint8_t)(i + 1); h[6] = (uint8_t)n; h[7] = 0;
+        h[8] = (uint8_t)n_preds; h[9] = (uint8_t)(n_preds >> 8);
+        put32(h + 12, (uint32_t)total);
+    }
+    size_t off = 16;
+    for (uint32_t p = 0; p < n_preds; p++) {
+        const orc_pred* q = &preds[p];
+        uint8_t blk[16];
+        rng_block(&g, blk);
+        uint32_t r = le32(blk) & m;
+        uint32_t rs[3];
+        rs[0] = le32(blk + 4) & m;
+        rs[1] = le32(blk + 8) & m;
+        rs[2] = (r - rs[0] - rs[1]) & m;
+        /* the functions of the three pairs */
+        uint32_t a_eq = 0, a0 = 0, a1 = 0, cbeta = 0;
+        if (q->kind == PRED_EQ) {
+            a_eq = (q->lo + r) & m;
+        } else {
+            a0 = (q->lo + r) & m;
+            a1 = (q->hi + 1u + r) & m;
+            cbeta = a1 <= a0 ? BETA_PRIME : 0u;
+        }
+        /* keys of pair j, party b: one DPF key or two DCF keys (a1 then a0) */
+        size_t half_len = q->kind == PRED_EQ ? dpf_len : 2 * dcf_len;
+        uint8_t keys[3][2][MAX_HALF];   /* [pair][party][bytes of one key half] */
+        for (int j = 0; j < 3; j++) {
+            if (q->kind == PRED_EQ) {
+                uint8_t s0[16], s1[16];
+                rng_block(&g, s0);
+                rng_block(&g, s1);
+                orc_dpf_gen(n, a_eq, BETA_PRIME, s0, s1, keys[j][0], keys[j][1]);
+            } else {
+                uint8_t s0[16], s1[16];
+                rng_block(&g, s0);
+                rng_block(&g, s1);
+                orc_dcf_gen(n, a1, BETA_PRIME, s0, s1, keys[j][0], keys[j][1]);
+                rng_block(&g, s0);
+                rng_block(&g, s1);
+                orc_dcf_gen(n, a0, 0u - BETA_PRIME, s0, s1, keys[j][0] + dcf_len, keys[j][1] + dcf_len);
+            }
+        }
+        for (int i = 0; i < 3; i++) {
+            uint8_t* rec = tok[i] + off;
+            memset(rec, 0, 24);
+            rec[0] = (uint8_t)q->kind; rec[1] = (uint8_t)n;
+            rec[2] = (uint8_t)q->table; rec[3] = (uint8_t)(q->table >> 8);
+            rec[4] = (uint8_t)q->attr; rec[5] = (uint8_t)(q->attr >> 8);
+            rec[6] = (uint8_t)q->group; rec[7] = (uint8_t)(q->group >> 8);
+            put32(rec + 8, rs[i]);
+            put32(rec + 12, rs[(i + 1) % 3]);
+            put32(rec + 16, cbeta);
+            for (int h = 0; h < 2; h++) {
+                int j = HOLD_PAIR[i][h] - 1, b = HOLD_PARTY[i][h];
+                memcpy(rec + 24 + (size_t)h * half_len, keys[j][b], half_len);
+            }
+        }
+        off += 24 + 2 * half_len;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Server-side evaluation: secEval (Alg. 3), re-share (Sec. III-B), AND fold  */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    uint64_t n_elems;
+    uint32_t n_attrs;
+    uint32_t n_bits;
+    const uint32_t* share[3];   /* share[j][attr * n_elems + e], additive mod 2^n_bits */
+} orc_table;
+
+typedef struct {
+    const uint8_t* rec[3];      /* the predicate's record in each server's token */
+    int kind, n, table, attr, group;
+} pred_view;
+
+static int parse_tokens(const uint8_t* const tok[3], const size_t tok_len[3], pred_view* pv, int max_preds)
+{
+    int np = -1, n = -1;
+    for (int i = 0; i < 3; i++) {
+        if (tok_len[i] < 16 || le32(tok[i]) != TOKEN_MAGIC || tok[i][4] != 1 || tok[i][5] != i + 1) return -1;
+        if (le32(tok[i] + 12) != tok_len[i]) return -1;
+        int this_np = tok[i][8] | (tok[i][9] << 8);
+        if (np < 0) { np = this_np; n = tok[i][6]; }
+        else if (np != this_np || n != tok[i][6]) return -1;
+    }
+    if (np <= 0 || np > max_preds || n < 1 || n > 32) return -1;
+    size_t off = 16;
+    size_t dpf_len = orc_key_len(KIND_DPF, n), dcf_len = orc_key_len(KIND_DCF, n);
+    for (int p = 0; p < np; p++) {
+        if (off + 24 > tok_len[0]) return -1;
+        const uint8_t* r0 = tok[0] + off;
+        int kind = r0[0];
+        if (kind != PRED_EQ && kind != PRED_RANGE) return -1;
+        size_t half_len = kind == PRED_EQ ? dpf_len : 2 * dcf_len;
+        if (off + 24 + 2 * half_len > tok_len[0]) return -1;
+        pv[p].kind = kind;
+        pv[p].n = r0[1];
+        pv[p].table = r0[2] | (r0[3] << 8);
+        pv[p].attr = r0[4] | (r0[5] << 8);
+        pv[p].group = r0[6] | (r0[7] << 8);
+        for (int i = 0; i < 3; i++) {
+            pv[p].rec[i] = tok[i] + off;
+            if (memcmp(tok[i] + off, r0, 8) != 0) return -1;
+        }
+        off += 24 + 2 * half_len;
+    }
+    if (off != tok_len[0]) return -1;
+    return np;
+}
+
+/* F(k, ctr): bytes 0..3 of AES_k(ctr) with ctr = elem (u64) || step (u16) || table (u16) || query (u32) */
+static uint32_t prf(const aes_ks* k, uint64_t elem, uint32_t step, uint32_t table, uint32_t query)
+{
+    uint8_t c[16], o[16];
+    for (int i = 0; i < 8; i++) c[i] = (uint8_t)(elem >> (8 * i));
+    c[8] = (uint8_t)step; c[9] = (uint8_t)(step >> 8);
+    c[10] = (uint8_t)table; c[11] = (uint8_t)(table >> 8);
+    put32(c + 12, query);
+    aes_encrypt(k, c, o);
+    return le32(o);
+}
+
+/* re-share a 3-out-of-3 additive sharing z into RSS: r_i = z_i + F(k_i, ctr) - F(k_{i-1}, ctr) */
+static void reshare(const aes_ks prf_ks[3], const uint32_t z[3], uint32_t out[3],
+                    uint64_t elem, uint32_t step, uint32_t table, uint32_t query)
+{
+    uint32_t f[3];
+    for (int i = 0; i < 3; i++) f[i] = prf(&prf_ks[i], elem, step, table, query);
+    for (int i = 0; i < 3; i++) out[i] = z[i] + f[i] - f[(i + 2) % 3];
+}
+
+/* y for one key half held by a server: DPF (EQ) or two DCFs plus c*beta' for party 0 (RANGE) */
+static uint32_t eval_half(const pred_view* pv, int server, int h, uint32_t xhat)
+{
+    size_t dpf_len = orc_key_len(KIND_DPF, pv->n), dcf_len = orc_key_len(KIND_DCF, pv->n);
+    const uint8_t* rec = pv->rec[server];
+    if (pv->kind == PRED_EQ) {
+        const uint8_t* key = rec + 24 + (size_t)h * dpf_len;
+        return orc_dpf_eval(key, xhat);
+    }
+    const uint8_t* k_hi = rec + 24 + (size_t)h * 2 * dcf_len;
+    const uint8_t* k_lo = k_hi + dcf_len;
+    uint32_t y = orc_dcf_eval(k_hi, xhat) + orc_dcf_eval(k_lo, xhat);
+    if (k_hi[2] == 0) y += le32(rec + 16);
+    return y;
+}
+
+/*
+ * Evaluate and-group `group` of the query on the listed elements of its table.
+ * out is [3][n_sel]: the three RSS share sets of the AND of the group's predicates.
+ * Returns 0, or a negative code on malformed input.
+ */
+int orc_filter(const uint8_t* tok1, const uint8_t* tok2, const uint8_t* tok3, const size_t tok_len[3],
+               uint32_t query_id, const uint8_t prf_keys[48], const orc_table* tables, uint32_t n_tables,
+               uint32_t group, const uint64_t* elems, uint64_t n_sel, uint32_t* out)
+{
+    const uint8_t* tok[3] = {tok1, tok2, tok3};
+    pred_view pv[64];
+    int np = parse_tokens(tok, tok_len, pv, 64);
+    if (np < 0) return -1;
+    int members[64], nm = 0;
+    for (int p = 0; p < np; p++)
+        if ((uint32_t)pv[p].group == group) members[nm++] = p;
+    if (nm == 0) return -2;
+    int table = pv[members[0]].table;
+    for (int k = 0; k < nm; k++) {
+        const pred_view* q = &pv[members[k]];
+        if (q->table != table || (uint32_t)q->table >= n_tables) return -3;
+        if ((uint32_t)q->attr >= tables[table].n_attrs || (uint32_t)q->n != tables[table].n_bits) return -3;
+    }
+    const orc_table* T = &tables[table];
+    aes_ks prf_ks[3];
+    for (int i = 0; i < 3; i++) key_expansion(prf_keys + 16 * i, &prf_ks[i]);
+    for (uint64_t s = 0; s < n_sel; s++) {
+        uint64_t e = elems[s];
+        if (e >= T->n_elems) return -4;
+        uint32_t acc[3] = {0, 0, 0};
+        for (int k = 0; k < nm; k++) {
+            int p = members[k];
+            const pred_view* q = &pv[p];
+            uint32_t m = mask_n(q->n);
+            /* open x^ = x + r: every server adds its own share of x and of r */
+            uint32_t xhat = 0;
+            for (int j = 0; j < 3; j++)
+                xhat += T->share[j][(uint64_t)q->attr * T->n_elems + e] + le32(q->rec[j] + 8);
+            xhat &= m;
+            /* Eq. (predEval): CS_i sums its two key halves */
+            uint32_t z[3];
+            for (int i = 0; i < 3; i++) z[i] = eval_half(q, i, 0, xhat) + eval_half(q, i, 1, xhat);
+            uint32_t bsh[3];
+            reshare(prf_ks, z, bsh, e, (uint32_t)p, (uint32_t)table, query_id);
+            if (k == 0) {
+                memcpy(acc, bsh, sizeof acc);
+            } else {
+                uint32_t w[3];
+                for (int i = 0; i < 3; i++) {
+                    int i1 = (i + 1) % 3;
+                    w[i] = acc[i] * bsh[i] + acc[i] * bsh[i1] + acc[i1] * bsh[i];
+                }
+                reshare(prf_ks, w, acc, e, 64u + (uint32_t)p, (uint32_t)table, query_id);
+            }
+        }
+        for (int i = 0; i < 3; i++) out[(uint64_t)i * n_sel + s] = acc[i];
+    }
+    return 0;
+}
+
+/* the per-server additive shares z_1..z_3 of one predicate before the re-share (for invariant tests) */
+int orc_pred_z(const uint8_t* tok1, const uint8_t* tok2, const uint8_t* tok3, const size_t tok_len[3],
+               uint32_t pred, uint32_t xhat, uint32_t z_out[3], uint32_t y_out[6])
+{
+    const uint8_t* tok[3] = {tok1, tok2, tok3};
+    pred_view pv[64];
+    int np = parse_tokens(tok, tok_len, pv, 64);
+    if (np < 0 || pred >= (uint32_t)np) return -1;
+    for (int i = 0; i < 3; i++) {
+        uint32_t y0 = eval_half(&pv[pred], i, 0, xhat), y1 = eval_half(&pv[pred], i, 1, xhat);
+        y_out[2 * i] = y0;
+        y_out[2 * i + 1] = y1;
+        z_out[i] = y0 + y1;
+    }
+    return 0;
+}
+
+/* re-share on its own, for the zero-sharing invariant */
+void orc_reshare(const uint8_t prf_keys[48], const uint32_t z[3], uint32_t out[3],
+                 uint64_t elem, uint32_t step, uint32_t table, uint32_t query)
+{
+    aes_ks prf_ks[3];
+    for (int i = 0; i < 3; i++) key_expansion(prf_keys + 16 * i, &prf_ks[i]);
+    reshare(prf_ks, z, out, elem, step, table, query);
+}
