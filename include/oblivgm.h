@@ -1,0 +1,276 @@
+/*
+ * oblivgm.h -- C ABI of the GB300 library for OblivGM's secure predicate
+ * evaluation (OblivGM: Oblivious Attributed Subgraph Matching as a Cloud
+ * Service, arXiv 2209.03526).
+ *
+ * The library evaluates, on one GPU, what the three cloud servers CS1..CS3
+ * compute in secEval (Alg. 3): every predicate of a query on every element
+ * (vertex or edge) of a resident, secret-shared table, by DPF Eval (equality)
+ * or DCF Eval (range) over masked attribute values, followed by the re-share
+ * of Sec. III-B and the AND aggregation of Sec. V-D.  The three servers are
+ * simulated as three share sets in one address space; "sending" a share is a
+ * read of another share set.
+ *
+ * Conventions
+ *  - Every function returns an oblivgm_status (0 on success, a negative code
+ *    otherwise) and never throws.  oblivgm_last_error() gives the text of the
+ *    calling thread's last failure.
+ *  - "device pointer" means memory of the context's GPU (cudaMalloc, or a
+ *    torch tensor's data_ptr()); "host pointer" means ordinary host memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls that take a stream only enqueue work on it; inputs that
+ *    are host buffers may be reused as soon as the call returns.
+ *  - All integers are little-endian.  Arithmetic is in Z_{2^32} unless
+ *    stated; attribute domains are Z_{2^n}, 1 <= n <= 32.
+ *  - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef OBLIVGM_H
+#define OBLIVGM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t oblivgm_status;
+
+#define OBLIVGM_OK             0
+#define OBLIVGM_EINVAL        (-1)   /* bad argument, malformed token or key            */
+#define OBLIVGM_ENOMEM        (-2)   /* a device or host allocation failed              */
+#define OBLIVGM_ECUDA         (-3)   /* a CUDA call failed (text in last_error)         */
+#define OBLIVGM_EARCH         (-4)   /* the device is not compute capability 10.3       */
+#define OBLIVGM_ERANGE        (-5)   /* output buffer too small; needed size reported   */
+#define OBLIVGM_EBUSY         (-6)   /* table re-load while in-flight queries use it    */
+#define OBLIVGM_EAGAIN        (-7)   /* submit: no slot/memory now; poll: not finished  */
+#define OBLIVGM_ETIMEOUT      (-8)   /* poll: timeout expired before completion         */
+#define OBLIVGM_ENOENT        (-9)   /* unknown table id or ticket                      */
+#define OBLIVGM_EFAULT_DEVICE (-10)  /* a bounded device-side wait expired              */
+
+/* predicate kinds (Sec. V-C: equality -> DPF, range -> DCF) */
+#define OBLIVGM_PRED_EQ    1u
+#define OBLIVGM_PRED_RANGE 2u
+
+/* key kinds in the key wire format */
+#define OBLIVGM_KEY_DPF 1u
+#define OBLIVGM_KEY_DCF 2u
+
+/* memory kinds of caller buffers */
+#define OBLIVGM_MEM_HOST   0
+#define OBLIVGM_MEM_DEVICE 1
+
+/* flags of oblivgm_eval_*_batch */
+#define OBLIVGM_ALL_PAIRS 1u
+
+typedef struct oblivgm_ctx oblivgm_ctx;
+
+typedef struct {
+    /* k_1, k_2, k_3: AES-128 keys of the zero-sharing PRF F (Sec. III-B);
+     * server i holds k_i and k_{i-1}.  F(k, ctr) = bytes 0..3 of AES_k(ctr). */
+    uint8_t  prf_keys[3][16];
+    /* serving loop: device bytes it may reserve for in-flight queries' outputs
+     * (0 = 25 % of free memory at create time) and in-flight query slots
+     * (0 = 64). */
+    uint64_t serve_arena_bytes;
+    uint32_t serve_max_inflight;
+    uint32_t flags;   /* reserved, must be 0 */
+} oblivgm_config;
+
+/* One predicate of a query, as the client (graph owner) knows it. */
+typedef struct {
+    uint32_t kind;    /* OBLIVGM_PRED_EQ or OBLIVGM_PRED_RANGE                      */
+    uint32_t table;   /* id of the element table the predicate reads (< 65536)      */
+    uint32_t attr;    /* attribute row within that table (< 65536)                  */
+    uint32_t group;   /* AND-group of the query: all predicates of a group are on
+                         the same table and their results are ANDed (Sec. V-D)     */
+    uint32_t lo;      /* EQ: the value alpha; RANGE: inclusive lower bound          */
+    uint32_t hi;      /* RANGE: inclusive upper bound (lo <= hi); ignored for EQ    */
+} oblivgm_pred;
+
+/* Result of a served query: per AND-group g, three device arrays of n_elems[g]
+ * uint32 each, the RSS share sets 1..3 of the group's 0/1 result.  The memory
+ * belongs to the library until oblivgm_release(). */
+#define OBLIVGM_MAX_GROUPS 64
+typedef struct {
+    uint32_t  n_groups;
+    uint32_t  table[OBLIVGM_MAX_GROUPS];
+    uint64_t  n_elems[OBLIVGM_MAX_GROUPS];
+    uint32_t* shares[OBLIVGM_MAX_GROUPS][3];
+    double    latency_ms;        /* submit -> completion seen by poll, host clock */
+    uint64_t  ticket;
+} oblivgm_result;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device`.  Builds the AES tables on the
+ * device and the PRF round keys from cfg->prf_keys.  Errors: EINVAL (cfg NULL
+ * or flags != 0), EARCH (device is not sm_103), ECUDA, ENOMEM. */
+oblivgm_status oblivgm_create(oblivgm_ctx** out, int32_t device, const oblivgm_config* cfg);
+
+/* Synchronise and free everything the context owns (tables, workspaces,
+ * served results not yet released).  NULL is accepted. */
+oblivgm_status oblivgm_destroy(oblivgm_ctx* ctx);
+
+/* Text of the calling thread's last error ("" if none); always NUL-terminated. */
+oblivgm_status oblivgm_last_error(char* buf, size_t n);
+
+/* Library version as 0xMMmmpp. */
+uint32_t oblivgm_version(void);
+
+/* ------------------------------------------------------------- share store */
+
+/* Load one element table into resident device memory (encGraph output,
+ * Alg. 1, held by the servers; only the columns a query needs are loaded,
+ * Sec. VII-A).  share_sets[j] (j = 0, 1, 2) points to n_attrs * n_elems
+ * uint32 in row-major [attr][elem] order: the additive share <x>_{j+1} of
+ * every attribute value, x = <x>_1 + <x>_2 + <x>_3 mod 2^n_bits.  mem_kind
+ * says whether the three pointers are host or device memory.  The caller
+ * keeps ownership; with host memory the call returns after the copy is
+ * enqueued from a pinned staging buffer and the caller may reuse its buffers
+ * at once.  Re-loading an existing id replaces it (EBUSY while served queries
+ * still use it).  Errors: EINVAL (n_bits outside 1..32, n_attrs 0 or
+ * > 65536, table_id > 65535, NULL pointer), ENOMEM, ECUDA. */
+oblivgm_status oblivgm_load_shares(oblivgm_ctx* ctx, uint32_t table_id, uint64_t n_elems, uint32_t n_attrs,
+                                   uint32_t n_bits, const uint32_t* const share_sets[3], int32_t mem_kind,
+                                   void* stream);
+
+/* Drop a resident table.  Errors: ENOENT, EBUSY. */
+oblivgm_status oblivgm_unload_shares(oblivgm_ctx* ctx, uint32_t table_id);
+
+/* ------------------------------------------------------------------ tokens */
+
+/* Client-side secure query token generation (genToken, Sec. V-C), for the
+ * masked-input evaluation: per predicate a fresh mask r (RSS-shared among the
+ * servers) and three independent FSS key pairs for the shifted function
+ * (EQ: DPF at alpha + r; RANGE [lo, hi]: DCFs at lo + r and hi + 1 + r),
+ * every pair with output beta' = 3^{-1} mod 2^32 so the three pairs add up to
+ * the predicate bit.  Server i receives tok[i] holding its two key halves:
+ * CS1 (k^1_1, k^2_1), CS2 (k^2_2, k^3_1), CS3 (k^3_2, k^1_2).
+ * Host only and deterministic in `seed` (AES-128 counter mode, counter block
+ * = u64 index || 8 zero bytes; per predicate one block for the mask, bytes
+ * 0..3 r, 4..7 <r>_1, 8..11 <r>_2, each mod 2^n, <r>_3 = r - <r>_1 - <r>_2,
+ * then two root-seed blocks per key, pairs 1..3 in order, RANGE keys a1 then
+ * a0).
+ * Token of server i, all fields little-endian:
+ *   header 16 B: u32 magic 0x544D474F, u8 version 1, u8 i (1..3), u8 n,
+ *     u8 0, u16 n_preds, u16 0, u32 total length;
+ *   per predicate a 24 B record: u8 kind, u8 n, u16 table, u16 attr,
+ *     u16 group, u32 <r>_i, u32 <r>_{i+1}, u32 c*beta' (RANGE, c = [a1 <= a0];
+ *     0 for EQ), u32 0; then key half A and key half B, each one DPF key (EQ)
+ *     or two DCF keys, a1 = hi + 1 + r first, then a0 = lo + r (RANGE).
+ *   key: u8 kind (1 DPF, 2 DCF), u8 n, u8 party b, u8 0, u32 0, seed[16],
+ *     per level i = 1..n: s_CW[16], u8 t^L_CW, u8 t^R_CW, u16 0 and for DCF
+ *     u32 V_CW; then u32 CW_{n+1}.
+ * tok[i] may be NULL to query the size: out_len[i] is always set.  Errors:
+ * EINVAL (0 or more than 64 predicates, empty range, value outside 2^n,
+ * n outside 1..32, ids >= 65536), ERANGE (cap < out_len[i]). */
+oblivgm_status oblivgm_keygen(const oblivgm_pred* preds, uint32_t n_preds, uint32_t n_bits,
+                              const uint8_t seed[16], uint8_t* const tok[3], size_t cap, size_t out_len[3]);
+
+/* --------------------------------------------------------- raw FSS batches */
+
+/* DPF Eval (point function, Boyle-Gilboa-Ishai tree construction cited in
+ * Sec. V-C) of wire-format keys on device-resident points.
+ * keys: host pointer to n_keys keys back to back, all of the same kind and
+ *       n (length 28 + 20 n bytes for DPF, 28 + 24 n for DCF).
+ * points: device pointer, n_points uint32 (bits above n are ignored).
+ * flags & OBLIVGM_ALL_PAIRS: out[k * n_points + i] = Eval(key k, points[i]),
+ *       needs n_out >= n_keys * n_points; key_of_point is ignored.
+ * otherwise: out[i] = Eval(key key_of_point[i], points[i]) with key_of_point
+ *       a device pointer of n_points uint32; an index >= n_keys gives 0.
+ * out: device pointer of n_out uint32, caller-owned.  Asynchronous on stream.
+ * Errors: EINVAL (malformed key, kinds or n mixed, NULL), ERANGE (n_out too
+ * small), ENOMEM, ECUDA. */
+oblivgm_status oblivgm_eval_dpf_batch(oblivgm_ctx* ctx, const uint8_t* keys, uint32_t n_keys,
+                                      const uint32_t* points, const uint32_t* key_of_point, uint64_t n_points,
+                                      uint32_t flags, uint32_t* out, uint64_t n_out, void* stream);
+
+/* DCF Eval (comparison function x < alpha, construction of Boyle et al.
+ * cited in Sec. V-C); same arguments and errors as oblivgm_eval_dpf_batch. */
+oblivgm_status oblivgm_eval_dcf_batch(oblivgm_ctx* ctx, const uint8_t* keys, uint32_t n_keys,
+                                      const uint32_t* points, const uint32_t* key_of_point, uint64_t n_points,
+                                      uint32_t flags, uint32_t* out, uint64_t n_out, void* stream);
+
+/* ---------------------------------------------------- filter and combine */
+
+/* secEval (Alg. 3) of one query, fused: for every AND-group of the token and
+ * every element of the group's table, open x^ = x + r (the masked-input
+ * approach of Sec. V-C), evaluate the six key halves of each predicate
+ * (Eq. predEval, masked form: CS_i sums its two halves), re-share each
+ * predicate's 3-out-of-3 sum to RSS with the PRF zero-sharing (Sec. III-B,
+ * counter = element, step p, table, query_id), and AND the group's
+ * predicates in token order with RSS multiplication plus re-share (step
+ * 64 + p) (Sec. V-D).
+ * tok[i], tok_len[i]: host pointers to server i+1's token from
+ *       oblivgm_keygen (all three must come from the same keygen call).
+ * out: host array of 3 * n_groups device pointers; out[3 g + i] receives
+ *       share set i+1 of group g, n_elems(table of g) uint32, caller-owned.
+ * Groups are numbered 0..n_groups-1 and must all be present in the token.
+ * Asynchronous on stream.  Errors: EINVAL (malformed tokens, n_groups
+ * mismatch, predicate on a missing table/attribute or with another n than
+ * its table), ENOMEM, ECUDA, EFAULT_DEVICE (a key-staging wait expired;
+ * detected at the next call that synchronises). */
+oblivgm_status oblivgm_filter_and_combine(oblivgm_ctx* ctx, uint32_t query_id, const uint8_t* const tok[3],
+                                          const size_t tok_len[3], uint32_t n_groups, uint32_t* const* out,
+                                          void* stream);
+
+/* The same for n_queries queries in ONE persistent launch (work items of all
+ * queries' groups and element tiles in a shared queue, ordered by cost).
+ * query_ids[q]; toks[3 q + i], tok_lens[3 q + i]; n_groups[q];
+ * outs[q] is the query's array of 3 * n_groups[q] device pointers.
+ * Each query's output equals what oblivgm_filter_and_combine gives for it
+ * alone.  Errors as oblivgm_filter_and_combine. */
+oblivgm_status oblivgm_filter_batch(oblivgm_ctx* ctx, uint32_t n_queries, const uint32_t* query_ids,
+                                    const uint8_t* const* toks, const size_t* tok_lens, const uint32_t* n_groups,
+                                    uint32_t* const* const* outs, void* stream);
+
+/* --------------------------------------------------------------- serving */
+
+/* Non-blocking admission of one query into the serving loop (continuous
+ * batching).  Copies the tokens.  The query id used for the PRF counters is
+ * the returned ticket (low 32 bits).  The query is admitted only if a slot is
+ * free and its output shares fit in the serve arena; otherwise EAGAIN and
+ * nothing is kept.  Admitted queries start on the device as soon as the loop
+ * can launch them, overlapping queries already running.
+ * Errors: EAGAIN, EINVAL (as filter_and_combine), ENOENT (table not loaded). */
+oblivgm_status oblivgm_submit(oblivgm_ctx* ctx, const uint8_t* const tok[3], const size_t tok_len[3],
+                              uint64_t* ticket);
+
+/* Wait up to timeout_ms (0 = just check, < 0 = no limit) for a ticket.
+ * OK: *out describes the result (library-owned until oblivgm_release).
+ * EAGAIN (timeout_ms == 0 and not finished), ETIMEOUT, ENOENT (unknown or
+ * already released ticket), EFAULT_DEVICE. */
+oblivgm_status oblivgm_poll(oblivgm_ctx* ctx, uint64_t ticket, int32_t timeout_ms, oblivgm_result* out);
+
+/* Return a served result's memory to the arena (re-admits waiting work). */
+oblivgm_status oblivgm_release(oblivgm_ctx* ctx, uint64_t ticket);
+
+/* Serving statistics: queries admitted, completed, rejected (EAGAIN), and the
+ * device bytes currently reserved. */
+oblivgm_status oblivgm_serve_stats(oblivgm_ctx* ctx, uint64_t* admitted, uint64_t* completed, uint64_t* rejected,
+                                   uint64_t* reserved_bytes);
+
+/* ---------------------------------------------------------------- tuning */
+
+/* Autotuned launch shape of the fused evaluation kernel: threads per CTA and
+ * elements per thread ("paths per thread").  oblivgm_autotune times the
+ * candidates on a synthetic table and keeps the fastest; the choice is
+ * reported (and may be forced with oblivgm_set_schedule, 0 = keep). */
+oblivgm_status oblivgm_autotune(oblivgm_ctx* ctx, uint32_t* threads, uint32_t* elems_per_thread);
+oblivgm_status oblivgm_set_schedule(oblivgm_ctx* ctx, uint32_t threads, uint32_t elems_per_thread);
+
+/* Synchronise `stream` and report device-side faults recorded since the last
+ * check: EFAULT_DEVICE if a bounded device wait (key staging) expired in a
+ * kernel of this context, ECUDA on a CUDA error; the flag is cleared. */
+oblivgm_status oblivgm_sync(oblivgm_ctx* ctx, void* stream);
+
+/* Count of this library's kernel launches so far on the context (for the
+ * bench's launch accounting). */
+uint64_t oblivgm_launch_count(oblivgm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OBLIVGM_H */

@@ -1,0 +1,245 @@
+"""GB300 library for OblivGM's secure predicate evaluation (arXiv 2209.03526).
+
+Thin Python binding over the C ABI in ``include/oblivgm.h``: argument
+marshalling only.  Every step of the evaluation (mask-open, DPF/DCF walks,
+per-server sums, re-share, AND fold) runs in the library's CUDA kernels; the
+token generation runs in the library's host C++.  PyTorch supplies device
+memory and streams.  There is no CPU fallback: if the shared library cannot
+be loaded every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Sequence
+
+from . import _native as N
+from ._native import (ALL_PAIRS, EAGAIN, EBUSY, EFAULT_DEVICE, EINVAL, ENOENT, ERANGE, ETIMEOUT, KEY_DCF, KEY_DPF,
+                      OK, PRED_EQ, PRED_RANGE, OblivgmError)
+from .build import build
+
+__all__ = ["Context", "keygen", "build", "OblivgmError", "PRED_EQ", "PRED_RANGE", "KEY_DPF", "KEY_DCF",
+           "ALL_PAIRS", "version", "token_len"]
+
+
+def _lib():
+    return N.load()
+
+
+def version() -> int:
+    return _lib().oblivgm_version()
+
+
+def _pred_array(preds):
+    arr = (N.Pred * len(preds))()
+    for i, p in enumerate(preds):
+        arr[i].kind, arr[i].table, arr[i].attr = int(p["kind"]), int(p["table"]), int(p["attr"])
+        arr[i].group, arr[i].lo, arr[i].hi = int(p.get("group", 0)), int(p["lo"]), int(p.get("hi", p["lo"]))
+    return arr
+
+
+def token_len(preds, n_bits: int) -> int:
+    """Bytes of each server's token (oblivgm_keygen size query)."""
+    arr = _pred_array(preds)
+    lens = (N.c_size * 3)()
+    seed = (ctypes.c_uint8 * 16)()
+    N.check(_lib().oblivgm_keygen(arr, len(preds), n_bits, ctypes.addressof(seed), None, 0, lens), "oblivgm_keygen")
+    return lens[0]
+
+
+def keygen(preds, n_bits: int, seed: bytes):
+    """oblivgm_keygen: the three servers' tokens (bytes) for a list of predicate dicts."""
+    arr = _pred_array(preds)
+    L = token_len(preds, n_bits)
+    bufs = [ctypes.create_string_buffer(L) for _ in range(3)]
+    ptrs = (N.c_vp * 3)(*[ctypes.addressof(b) for b in bufs])
+    lens = (N.c_size * 3)()
+    sb = ctypes.create_string_buffer(bytes(seed), 16)
+    N.check(_lib().oblivgm_keygen(arr, len(preds), n_bits, ctypes.addressof(sb), ptrs, L, lens), "oblivgm_keygen")
+    return tuple(b.raw[:lens[i]] for i, b in enumerate(bufs))
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _tok_arrays(tokens):
+    bufs = [ctypes.create_string_buffer(bytes(t), len(t)) for t in tokens]
+    ptrs = (N.c_vp * 3)(*[ctypes.addressof(b) for b in bufs])
+    lens = (N.c_size * 3)(*[len(t) for t in tokens])
+    return bufs, ptrs, lens
+
+
+class Context:
+    """An oblivgm context on one CUDA device (oblivgm_create / oblivgm_destroy)."""
+
+    def __init__(self, device: int = 0, prf_keys: bytes = bytes(range(48)), serve_arena_bytes: int = 0,
+                 serve_max_inflight: int = 0):
+        lib = _lib()
+        cfg = N.Config()
+        for i in range(3):
+            for j in range(16):
+                cfg.prf_keys[i][j] = prf_keys[16 * i + j]
+        cfg.serve_arena_bytes = serve_arena_bytes
+        cfg.serve_max_inflight = serve_max_inflight
+        h = N.c_vp()
+        N.check(lib.oblivgm_create(ctypes.byref(h), device, ctypes.byref(cfg)), "oblivgm_create")
+        self._h = h
+        self._lib = lib
+        self.device = device
+        self.prf_keys = bytes(prf_keys)
+
+    # -------------------------------------------------------------- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.oblivgm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def sync(self, stream=None):
+        N.check(self._lib.oblivgm_sync(self._h, _stream_handle(stream)), "oblivgm_sync")
+
+    def launch_count(self) -> int:
+        return self._lib.oblivgm_launch_count(self._h)
+
+    # ----------------------------------------------------------- share store
+    def load_shares(self, table_id: int, shares: Sequence, n_bits: int, stream=None):
+        """shares: three uint32 arrays [n_attrs, n_elems] (torch CUDA/CPU tensors or numpy)."""
+        ptrs, keep, kind, shape = [], [], None, None
+        for s in shares:
+            if hasattr(s, "is_cuda"):
+                import torch
+                t = s.contiguous()
+                if t.dtype not in (torch.int32, torch.uint32):
+                    raise TypeError("shares must be 32-bit tensors")
+                k = N.MEM_DEVICE if t.is_cuda else N.MEM_HOST
+                ptrs.append(t.data_ptr())
+                shape = tuple(t.shape)
+            else:
+                import numpy as np
+                t = np.ascontiguousarray(s, dtype=np.uint32)
+                k = N.MEM_HOST
+                ptrs.append(t.ctypes.data)
+                shape = t.shape
+            if kind is not None and k != kind:
+                raise TypeError("all three share sets must live in the same memory")
+            kind = k
+            keep.append(t)
+        n_attrs, n_elems = shape
+        arr = (N.c_vp * 3)(*ptrs)
+        N.check(self._lib.oblivgm_load_shares(self._h, table_id, n_elems, n_attrs, n_bits, arr, kind,
+                                              _stream_handle(stream) if kind == N.MEM_DEVICE else None),
+                "oblivgm_load_shares")
+
+    def unload_shares(self, table_id: int):
+        N.check(self._lib.oblivgm_unload_shares(self._h, table_id), "oblivgm_unload_shares")
+
+    # ------------------------------------------------------------ raw batches
+    def _eval(self, fn, name, keys: bytes, n_keys: int, points, key_of_point, out, all_pairs: bool, stream):
+        kb = ctypes.create_string_buffer(bytes(keys), len(keys))
+        N.check(fn(self._h, ctypes.addressof(kb), n_keys, points.data_ptr(),
+                   key_of_point.data_ptr() if key_of_point is not None else None, points.numel(),
+                   ALL_PAIRS if all_pairs else 0, out.data_ptr(), out.numel(), _stream_handle(stream)), name)
+
+    def eval_dpf_batch(self, keys: bytes, n_keys: int, points, out, key_of_point=None, all_pairs=False, stream=None):
+        self._eval(self._lib.oblivgm_eval_dpf_batch, "oblivgm_eval_dpf_batch", keys, n_keys, points, key_of_point,
+                   out, all_pairs, stream)
+
+    def eval_dcf_batch(self, keys: bytes, n_keys: int, points, out, key_of_point=None, all_pairs=False, stream=None):
+        self._eval(self._lib.oblivgm_eval_dcf_batch, "oblivgm_eval_dcf_batch", keys, n_keys, points, key_of_point,
+                   out, all_pairs, stream)
+
+    # ---------------------------------------------------- filter and combine
+    def filter_and_combine(self, query_id: int, tokens, outs, stream=None):
+        """outs: list over AND-groups of three uint32 CUDA tensors (share sets 1..3)."""
+        _, tp, tl = _tok_arrays(tokens)
+        flat = [t.data_ptr() for g in outs for t in g]
+        arr = (N.c_vp * len(flat))(*flat)
+        N.check(self._lib.oblivgm_filter_and_combine(self._h, query_id, tp, tl, len(outs), arr,
+                                                     _stream_handle(stream)), "oblivgm_filter_and_combine")
+
+    def filter_batch(self, query_ids, tokens_list, outs_list, stream=None):
+        """Several queries in one persistent launch; outs_list[q] as in filter_and_combine."""
+        nq = len(query_ids)
+        keep = []
+        tok_ptrs = (N.c_vp * (3 * nq))()
+        tok_lens = (N.c_size * (3 * nq))()
+        for q, toks in enumerate(tokens_list):
+            for i in range(3):
+                b = ctypes.create_string_buffer(bytes(toks[i]), len(toks[i]))
+                keep.append(b)
+                tok_ptrs[3 * q + i] = ctypes.addressof(b)
+                tok_lens[3 * q + i] = len(toks[i])
+        ng = (N.c_u32 * nq)(*[len(o) for o in outs_list])
+        out_arrays = (N.c_vp * nq)()
+        for q, outs in enumerate(outs_list):
+            flat = [t.data_ptr() for g in outs for t in g]
+            a = (N.c_vp * len(flat))(*flat)
+            keep.append(a)
+            out_arrays[q] = ctypes.addressof(a)
+        qids = (N.c_u32 * nq)(*query_ids)
+        N.check(self._lib.oblivgm_filter_batch(self._h, nq, qids, tok_ptrs, tok_lens, ng, out_arrays,
+                                               _stream_handle(stream)), "oblivgm_filter_batch")
+
+    # ---------------------------------------------------------------- serving
+    def submit(self, tokens) -> int:
+        """Returns a ticket, or raises OblivgmError with status EAGAIN when not admitted."""
+        _, tp, tl = _tok_arrays(tokens)
+        t = N.c_u64()
+        N.check(self._lib.oblivgm_submit(self._h, tp, tl, ctypes.byref(t)), "oblivgm_submit")
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = -1):
+        """Returns None if not finished (timeout_ms == 0), else a dict describing the result."""
+        r = N.Result()
+        st = self._lib.oblivgm_poll(self._h, ticket, timeout_ms, ctypes.byref(r))
+        if st == EAGAIN:
+            return None
+        N.check(st, "oblivgm_poll")
+        groups = []
+        for g in range(r.n_groups):
+            groups.append({"table": r.table[g], "n_elems": r.n_elems[g], "shares": [r.shares[g][j] for j in range(3)]})
+        return {"ticket": r.ticket, "latency_ms": r.latency_ms, "groups": groups}
+
+    def release(self, ticket: int):
+        N.check(self._lib.oblivgm_release(self._h, ticket), "oblivgm_release")
+
+    def serve_stats(self):
+        v = [N.c_u64() for _ in range(4)]
+        N.check(self._lib.oblivgm_serve_stats(self._h, *[ctypes.byref(x) for x in v]), "oblivgm_serve_stats")
+        return {"admitted": v[0].value, "completed": v[1].value, "rejected": v[2].value, "reserved_bytes": v[3].value}
+
+    # ----------------------------------------------------------------- tuning
+    def autotune(self):
+        t, e = N.c_u32(), N.c_u32()
+        N.check(self._lib.oblivgm_autotune(self._h, ctypes.byref(t), ctypes.byref(e)), "oblivgm_autotune")
+        return t.value, e.value
+
+    def set_schedule(self, threads: int = 0, elems_per_thread: int = 0):
+        N.check(self._lib.oblivgm_set_schedule(self._h, threads, elems_per_thread), "oblivgm_set_schedule")
+
+
+class _DeviceWords:
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<i4", "data": (ptr, False), "version": 3}
+
+
+def device_words(ptr: int, n: int, device: int = 0):
+    """A zero-copy int32 CUDA tensor over n words at a library-owned device address (served results)."""
+    import torch
+    return torch.as_tensor(_DeviceWords(ptr, n), device=f"cuda:{device}")

@@ -1,0 +1,432 @@
+// host_crypto.cpp -- host side of the oblivgm library: AES-128 (32-bit column
+// T-table form), DPF/DCF key generation and the secure query token of
+// Sec. V-C, and the servers' parsing of the three tokens into device keys.
+//
+// DPF: the tree construction of Boyle, Gilboa and Ishai ("Function Secret
+// Sharing: Improvements and Extensions", CCS'16), cited by the paper for
+// equality predicates.  DCF: the construction of Boyle et al. ("Function
+// Secret Sharing for Mixed-Mode and Fixed-Point Secure Computation",
+// Eurocrypt'21), cited for range predicates.  PRG: H_K(s) = AES_K(s) xor s under
+// fixed public keys; the control bit is bit 0 of byte 0 and Convert into
+// Z_{2^32} reads bytes 4..7 of a seed (bytes 0..3 of a DCF value block).
+#include "host_crypto.h"
+
+#include <cstring>
+#include <mutex>
+
+namespace ogm {
+
+namespace {
+
+inline uint32_t rotl(uint32_t x, int k) { return k == 0 ? x : (x << k) | (x >> (32 - k)); }
+inline uint32_t ld32(const uint8_t* p) { uint32_t v; std::memcpy(&v, p, 4); return v; }   // LE host
+inline void st32(uint8_t* p, uint32_t v) { std::memcpy(p, &v, 4); }
+inline uint16_t ld16(const uint8_t* p) { return (uint16_t)(p[0] | (p[1] << 8)); }
+
+// GF(2^8) through exponent/logarithm tables of the generator 3.
+struct Gf {
+    uint8_t exp[512], log[256];
+    Gf() {
+        uint8_t x = 1;
+        for (int i = 0; i < 255; i++) {
+            exp[i] = x;
+            log[x] = (uint8_t)i;
+            uint8_t x2 = (uint8_t)((x << 1) ^ ((x & 0x80) ? 0x1b : 0));
+            x = (uint8_t)(x2 ^ x);   // x * 3
+        }
+        for (int i = 255; i < 512; i++) exp[i] = exp[i - 255];
+        log[0] = 0;
+    }
+    uint8_t mul(uint8_t a, uint8_t b) const { return (a && b) ? exp[log[a] + log[b]] : 0; }
+    uint8_t inv(uint8_t a) const { return a ? exp[255 - log[a]] : 0; }
+};
+
+AesTables build_tables() {
+    Gf gf;
+    AesTables t{};
+    for (int x = 0; x < 256; x++) {
+        uint8_t b = gf.inv((uint8_t)x);
+        // affine map written with byte rotations: s = b ^ rotl(b,1) ^ rotl(b,2) ^ rotl(b,3) ^ rotl(b,4) ^ 0x63
+        uint32_t bb = b;
+        uint32_t r = bb ^ ((bb << 1) | (bb >> 7)) ^ ((bb << 2) | (bb >> 6)) ^ ((bb << 3) | (bb >> 5)) ^
+                     ((bb << 4) | (bb >> 4));
+        uint8_t s = (uint8_t)((r ^ 0x63) & 0xFF);
+        t.sbox[x] = s;
+        uint8_t s2 = gf.mul(s, 2), s3 = gf.mul(s, 3);
+        t.te0[x] = (uint32_t)s2 | ((uint32_t)s << 8) | ((uint32_t)s << 16) | ((uint32_t)s3 << 24);
+    }
+    return t;
+}
+
+}  // namespace
+
+const AesTables& aes_tables() {
+    static const AesTables t = build_tables();
+    return t;
+}
+
+RoundKeys expand_key(const uint8_t key[16]) {
+    const AesTables& T = aes_tables();
+    RoundKeys rk{};
+    for (int i = 0; i < 4; i++) rk.w[i] = ld32(key + 4 * i);
+    uint8_t rcon = 1;
+    for (int i = 4; i < 44; i++) {
+        uint32_t t = rk.w[i - 1];
+        if (i % 4 == 0) {
+            t = (t >> 8) | (t << 24);   // RotWord on little-endian bytes
+            t = (uint32_t)T.sbox[t & 0xFF] | ((uint32_t)T.sbox[(t >> 8) & 0xFF] << 8) |
+                ((uint32_t)T.sbox[(t >> 16) & 0xFF] << 16) | ((uint32_t)T.sbox[t >> 24] << 24);
+            t ^= rcon;
+            rcon = (uint8_t)((rcon << 1) ^ ((rcon & 0x80) ? 0x1b : 0));
+        }
+        rk.w[i] = rk.w[i - 4] ^ t;
+    }
+    return rk;
+}
+
+void aes_encrypt(const RoundKeys& rk, const uint32_t in[4], uint32_t out[4]) {
+    const AesTables& T = aes_tables();
+    uint32_t c[4], n[4];
+    for (int j = 0; j < 4; j++) c[j] = in[j] ^ rk.w[j];
+    for (int r = 1; r < 10; r++) {
+        for (int j = 0; j < 4; j++) {
+            n[j] = T.te0[c[j] & 0xFF] ^ rotl(T.te0[(c[(j + 1) & 3] >> 8) & 0xFF], 8) ^
+                   rotl(T.te0[(c[(j + 2) & 3] >> 16) & 0xFF], 16) ^ rotl(T.te0[c[(j + 3) & 3] >> 24], 24) ^
+                   rk.w[4 * r + j];
+        }
+        std::memcpy(c, n, sizeof c);
+    }
+    for (int j = 0; j < 4; j++) {
+        n[j] = (uint32_t)T.sbox[c[j] & 0xFF] | ((uint32_t)T.sbox[(c[(j + 1) & 3] >> 8) & 0xFF] << 8) |
+               ((uint32_t)T.sbox[(c[(j + 2) & 3] >> 16) & 0xFF] << 16) |
+               ((uint32_t)T.sbox[c[(j + 3) & 3] >> 24] << 24);
+        out[j] = n[j] ^ rk.w[40 + j];
+    }
+}
+
+const RoundKeys& fixed_key(int j) {
+    static RoundKeys keys[4];
+    static std::once_flag once;
+    std::call_once(once, [] {
+        for (int k = 0; k < 4; k++) {
+            uint8_t key[16];
+            for (int i = 0; i < 16; i++) key[i] = (uint8_t)(16 * k + i);
+            keys[k] = expand_key(key);
+        }
+    });
+    return keys[j];
+}
+
+namespace {
+
+struct Seed { uint32_t w[4]; };
+
+Seed load_seed(const uint8_t* b) { Seed s; for (int i = 0; i < 4; i++) s.w[i] = ld32(b + 4 * i); return s; }
+void store_seed(uint8_t* b, const Seed& s) { for (int i = 0; i < 4; i++) st32(b + 4 * i, s.w[i]); }
+
+// H_K(s) = AES_K(s) xor s
+Seed prg(int which, const Seed& s) {
+    Seed o;
+    aes_encrypt(fixed_key(which), s.w, o.w);
+    for (int i = 0; i < 4; i++) o.w[i] ^= s.w[i];
+    return o;
+}
+
+// child (seed, control bit) in direction dir (0 = L, 1 = R)
+void expand(int dir, const Seed& s, Seed* cs, uint32_t* ct) {
+    *cs = prg(dir, s);
+    *ct = cs->w[0] & 1u;
+    cs->w[0] &= ~1u;
+}
+
+inline uint32_t input_bit(uint32_t x, int n, int i) { return (x >> (n - i)) & 1u; }   // i = 1..n, MSB first
+
+void put_header(uint8_t* k, uint32_t kind, int n, int party, const uint8_t seed[16]) {
+    std::memset(k, 0, 8);
+    k[0] = (uint8_t)kind;
+    k[1] = (uint8_t)n;
+    k[2] = (uint8_t)party;
+    std::memcpy(k + 8, seed, 16);
+}
+
+}  // namespace
+
+void dpf_gen(int n, uint32_t alpha, uint32_t beta, const uint8_t s0[16], const uint8_t s1[16], uint8_t* k0,
+             uint8_t* k1) {
+    Seed s[2] = {load_seed(s0), load_seed(s1)};
+    uint32_t t[2] = {0, 1};
+    put_header(k0, OBLIVGM_KEY_DPF, n, 0, s0);
+    put_header(k1, OBLIVGM_KEY_DPF, n, 1, s1);
+    for (int i = 1; i <= n; i++) {
+        Seed c[2][2];
+        uint32_t tc[2][2];
+        for (int b = 0; b < 2; b++) {
+            expand(0, s[b], &c[b][0], &tc[b][0]);
+            expand(1, s[b], &c[b][1], &tc[b][1]);
+        }
+        const uint32_t a = input_bit(alpha, n, i);
+        const int keep = (int)a, lose = 1 - (int)a;
+        Seed scw;
+        for (int w = 0; w < 4; w++) scw.w[w] = c[0][lose].w[w] ^ c[1][lose].w[w];
+        const uint32_t tlcw = tc[0][0] ^ tc[1][0] ^ a ^ 1u;
+        const uint32_t trcw = tc[0][1] ^ tc[1][1] ^ a;
+        const size_t off = 24 + (size_t)(i - 1) * 20;
+        for (uint8_t* k : {k0, k1}) {
+            store_seed(k + off, scw);
+            k[off + 16] = (uint8_t)tlcw;
+            k[off + 17] = (uint8_t)trcw;
+            k[off + 18] = k[off + 19] = 0;
+        }
+        const uint32_t tkeep = keep ? trcw : tlcw;
+        for (int b = 0; b < 2; b++) {
+            const uint32_t m = 0u - t[b];
+            for (int w = 0; w < 4; w++) s[b].w[w] = c[b][keep].w[w] ^ (scw.w[w] & m);
+            t[b] = tc[b][keep] ^ (t[b] & tkeep);
+        }
+    }
+    uint32_t cw = beta - s[0].w[1] + s[1].w[1];
+    if (t[1]) cw = 0u - cw;
+    st32(k0 + 24 + (size_t)n * 20, cw);
+    st32(k1 + 24 + (size_t)n * 20, cw);
+}
+
+void dcf_gen(int n, uint32_t alpha, uint32_t beta, const uint8_t s0[16], const uint8_t s1[16], uint8_t* k0,
+             uint8_t* k1) {
+    Seed s[2] = {load_seed(s0), load_seed(s1)};
+    uint32_t t[2] = {0, 1};
+    uint32_t valpha = 0;
+    put_header(k0, OBLIVGM_KEY_DCF, n, 0, s0);
+    put_header(k1, OBLIVGM_KEY_DCF, n, 1, s1);
+    for (int i = 1; i <= n; i++) {
+        Seed c[2][2];
+        uint32_t tc[2][2], v[2][2];
+        for (int b = 0; b < 2; b++) {
+            for (int d = 0; d < 2; d++) {
+                expand(d, s[b], &c[b][d], &tc[b][d]);
+                v[b][d] = prg(2 + d, s[b]).w[0];
+            }
+        }
+        const uint32_t a = input_bit(alpha, n, i);
+        const int keep = (int)a, lose = 1 - (int)a;
+        Seed scw;
+        for (int w = 0; w < 4; w++) scw.w[w] = c[0][lose].w[w] ^ c[1][lose].w[w];
+        const bool neg = t[1] != 0;
+        uint32_t vcw = v[1][lose] - v[0][lose] - valpha;
+        if (neg) vcw = 0u - vcw;
+        if (lose == 0) vcw += neg ? 0u - beta : beta;
+        valpha = valpha - v[1][keep] + v[0][keep] + (neg ? 0u - vcw : vcw);
+        const uint32_t tlcw = tc[0][0] ^ tc[1][0] ^ a ^ 1u;
+        const uint32_t trcw = tc[0][1] ^ tc[1][1] ^ a;
+        const size_t off = 24 + (size_t)(i - 1) * 24;
+        for (uint8_t* k : {k0, k1}) {
+            store_seed(k + off, scw);
+            k[off + 16] = (uint8_t)tlcw;
+            k[off + 17] = (uint8_t)trcw;
+            k[off + 18] = k[off + 19] = 0;
+            st32(k + off + 20, vcw);
+        }
+        const uint32_t tkeep = keep ? trcw : tlcw;
+        for (int b = 0; b < 2; b++) {
+            const uint32_t m = 0u - t[b];
+            for (int w = 0; w < 4; w++) s[b].w[w] = c[b][keep].w[w] ^ (scw.w[w] & m);
+            t[b] = tc[b][keep] ^ (t[b] & tkeep);
+        }
+    }
+    uint32_t cw = s[1].w[1] - s[0].w[1] - valpha;
+    if (t[1]) cw = 0u - cw;
+    st32(k0 + 24 + (size_t)n * 24, cw);
+    st32(k1 + 24 + (size_t)n * 24, cw);
+}
+
+bool repack_key(const uint8_t* wire, size_t avail, uint32_t want_kind, int want_n, DevKey* out, std::string* err) {
+    if (avail < 28) { *err = "key truncated"; return false; }
+    const uint32_t kind = wire[0];
+    const int n = wire[1];
+    const uint32_t party = wire[2];
+    if ((kind != OBLIVGM_KEY_DPF && kind != OBLIVGM_KEY_DCF) || (want_kind && kind != want_kind)) {
+        *err = "unexpected key kind";
+        return false;
+    }
+    if (n < 1 || n > kMaxBits || (want_n && n != want_n)) { *err = "key bit length mismatch"; return false; }
+    if (party > 1 || wire[3] != 0) { *err = "bad key header"; return false; }
+    if (avail < key_bytes(kind, n)) { *err = "key truncated"; return false; }
+    std::memset(out, 0, sizeof *out);
+    for (int w = 0; w < 4; w++) out->seed[w] = ld32(wire + 8 + 4 * w);
+    const size_t lb = kind == OBLIVGM_KEY_DPF ? 20 : 24;
+    for (int i = 0; i < n; i++) {
+        const uint8_t* lv = wire + 24 + i * lb;
+        for (int w = 0; w < 4; w++) out->scw[i][w] = ld32(lv + 4 * w);
+        if (lv[16] > 1 || lv[17] > 1) { *err = "bad control-bit correction"; return false; }
+        out->tl |= (uint32_t)lv[16] << i;
+        out->tr |= (uint32_t)lv[17] << i;
+        if (kind == OBLIVGM_KEY_DCF) out->vcw[i] = ld32(lv + 20);
+    }
+    out->cw_final = ld32(wire + 24 + n * lb);
+    out->party = party;
+    out->n = (uint32_t)n;
+    out->kind = kind;
+    return true;
+}
+
+oblivgm_status parse_tokens(const uint8_t* const tok[3], const size_t tok_len[3], ParsedQuery* q, std::string* err) {
+    if (!tok || !tok_len) { *err = "NULL token array"; return OBLIVGM_EINVAL; }
+    int n = -1, np = -1;
+    for (int i = 0; i < 3; i++) {
+        const uint8_t* t = tok[i];
+        if (!t || tok_len[i] < 16) { *err = "token missing or truncated"; return OBLIVGM_EINVAL; }
+        if (ld32(t) != kTokenMagic || t[4] != 1 || t[5] != i + 1) { *err = "bad token header"; return OBLIVGM_EINVAL; }
+        if (ld32(t + 12) != tok_len[i]) { *err = "token length field mismatch"; return OBLIVGM_EINVAL; }
+        const int tn = t[6], tnp = ld16(t + 8);
+        if (i == 0) { n = tn; np = tnp; }
+        else if (tn != n || tnp != np) { *err = "tokens disagree on n or predicate count"; return OBLIVGM_EINVAL; }
+    }
+    if (n < 1 || n > kMaxBits || np < 1 || np > kMaxPreds) { *err = "token n or predicate count out of range"; return OBLIVGM_EINVAL; }
+    q->n_bits = (uint32_t)n;
+    q->preds.clear();
+    size_t off = 16;
+    for (int p = 0; p < np; p++) {
+        if (off + 24 > tok_len[0]) { *err = "token truncated"; return OBLIVGM_EINVAL; }
+        const uint8_t* r0 = tok[0] + off;
+        ParsedPred pp;
+        pp.kind = r0[0];
+        pp.n = r0[1];
+        pp.table = ld16(r0 + 2);
+        pp.attr = ld16(r0 + 4);
+        pp.group = ld16(r0 + 6);
+        pp.step = (uint32_t)p;
+        if ((pp.kind != OBLIVGM_PRED_EQ && pp.kind != OBLIVGM_PRED_RANGE) || (int)pp.n != n) {
+            *err = "bad predicate record";
+            return OBLIVGM_EINVAL;
+        }
+        const uint32_t kkind = pp.kind == OBLIVGM_PRED_EQ ? OBLIVGM_KEY_DPF : OBLIVGM_KEY_DCF;
+        const int nsub = pp.kind == OBLIVGM_PRED_EQ ? 1 : 2;
+        const size_t half = nsub * key_bytes(kkind, n);
+        const size_t rec_len = 24 + 2 * half;
+        for (int i = 0; i < 3; i++) {
+            if (off + rec_len > tok_len[i]) { *err = "token truncated"; return OBLIVGM_EINVAL; }
+            const uint8_t* ri = tok[i] + off;
+            if (std::memcmp(ri, r0, 8) != 0) { *err = "tokens disagree on a predicate record"; return OBLIVGM_EINVAL; }
+            pp.r[i] = ld32(ri + 8);
+            if (ld32(ri + 16) != ld32(r0 + 16)) { *err = "tokens disagree on c*beta"; return OBLIVGM_EINVAL; }
+        }
+        // each server's second mask share must equal the next server's first
+        for (int i = 0; i < 3; i++)
+            if (ld32(tok[i] + off + 12) != pp.r[(i + 1) % 3]) { *err = "mask shares are not replicated"; return OBLIVGM_EINVAL; }
+        pp.cbeta = ld32(r0 + 16);
+        pp.keys.resize(6 * nsub);
+        for (int i = 0; i < 3; i++)
+            for (int h = 0; h < 2; h++)
+                for (int s = 0; s < nsub; s++) {
+                    const uint8_t* kw = tok[i] + off + 24 + h * half + s * key_bytes(kkind, n);
+                    if (!repack_key(kw, tok_len[i] - (size_t)(kw - tok[i]), kkind, n, &pp.keys[(i * 2 + h) * nsub + s], err))
+                        return OBLIVGM_EINVAL;
+                }
+        q->preds.push_back(std::move(pp));
+        off += rec_len;
+    }
+    for (int i = 0; i < 3; i++)
+        if (off != tok_len[i]) { *err = "trailing bytes in token"; return OBLIVGM_EINVAL; }
+    return OBLIVGM_OK;
+}
+
+oblivgm_status keygen(const oblivgm_pred* preds, uint32_t n_preds, uint32_t n_bits, const uint8_t seed[16],
+                      uint8_t* const tok[3], size_t cap, size_t out_len[3], std::string* err) {
+    if (!preds || !seed || !out_len) { *err = "NULL argument"; return OBLIVGM_EINVAL; }
+    if (n_preds == 0 || n_preds > (uint32_t)kMaxPreds) { *err = "predicate count must be 1..64"; return OBLIVGM_EINVAL; }
+    if (n_bits < 1 || n_bits > (uint32_t)kMaxBits) { *err = "n must be 1..32"; return OBLIVGM_EINVAL; }
+    const int n = (int)n_bits;
+    const uint32_t m = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
+    const size_t dpf = key_bytes(OBLIVGM_KEY_DPF, n), dcf = key_bytes(OBLIVGM_KEY_DCF, n);
+    size_t total = 16;
+    for (uint32_t p = 0; p < n_preds; p++) {
+        const oblivgm_pred& q = preds[p];
+        if (q.kind == OBLIVGM_PRED_EQ) {
+            if (q.lo > m) { *err = "equality value outside the domain"; return OBLIVGM_EINVAL; }
+            total += 24 + 2 * dpf;
+        } else if (q.kind == OBLIVGM_PRED_RANGE) {
+            if (q.lo > q.hi || q.hi > m) { *err = "empty range or bound outside the domain"; return OBLIVGM_EINVAL; }
+            total += 24 + 4 * dcf;
+        } else {
+            *err = "unknown predicate kind";
+            return OBLIVGM_EINVAL;
+        }
+        if (q.table > 0xFFFF || q.attr > 0xFFFF || q.group > 0xFFFF) { *err = "id above 65535"; return OBLIVGM_EINVAL; }
+    }
+    for (int i = 0; i < 3; i++) out_len[i] = total;
+    if (!tok || !tok[0] || !tok[1] || !tok[2]) return OBLIVGM_OK;   // size query
+    if (cap < total) { *err = "token buffer too small"; return OBLIVGM_ERANGE; }
+
+    const RoundKeys rng_key = expand_key(seed);
+    uint64_t ctr = 0;
+    auto next_block = [&](uint8_t out[16]) {
+        const uint32_t in[4] = {(uint32_t)ctr, (uint32_t)(ctr >> 32), 0u, 0u};
+        uint32_t o[4];
+        aes_encrypt(rng_key, in, o);
+        for (int w = 0; w < 4; w++) st32(out + 4 * w, o[w]);
+        ctr++;
+    };
+    for (int i = 0; i < 3; i++) {
+        uint8_t* h = tok[i];
+        std::memset(h, 0, 16);
+        st32(h, kTokenMagic);
+        h[4] = 1;
+        h[5] = (uint8_t)(i + 1);
+        h[6] = (uint8_t)n;
+        h[8] = (uint8_t)n_preds;
+        h[9] = (uint8_t)(n_preds >> 8);
+        st32(h + 12, (uint32_t)total);
+    }
+    // halves held by server i: (pair, party) -- CS1 (1,0),(2,0); CS2 (2,1),(3,0); CS3 (3,1),(1,1)
+    static const int kPair[3][2] = {{0, 1}, {1, 2}, {2, 0}};
+    static const int kParty[3][2] = {{0, 0}, {1, 0}, {1, 1}};
+    std::vector<uint8_t> keys;
+    size_t off = 16;
+    for (uint32_t p = 0; p < n_preds; p++) {
+        const oblivgm_pred& q = preds[p];
+        uint8_t blk[16];
+        next_block(blk);
+        const uint32_t r = ld32(blk) & m;
+        uint32_t rs[3] = {ld32(blk + 4) & m, ld32(blk + 8) & m, 0};
+        rs[2] = (r - rs[0] - rs[1]) & m;
+        const bool eq = q.kind == OBLIVGM_PRED_EQ;
+        const size_t half = eq ? dpf : 2 * dcf;
+        keys.assign(3 * 2 * half, 0);   // [pair][party][half]
+        uint32_t cbeta = 0;
+        const uint32_t a_eq = (q.lo + r) & m;
+        const uint32_t a0 = (q.lo + r) & m, a1 = (q.hi + 1u + r) & m;
+        if (!eq) cbeta = a1 <= a0 ? kBetaPrime : 0u;
+        for (int j = 0; j < 3; j++) {
+            uint8_t* kp0 = keys.data() + (j * 2 + 0) * half;
+            uint8_t* kp1 = keys.data() + (j * 2 + 1) * half;
+            uint8_t s0[16], s1[16];
+            next_block(s0);
+            next_block(s1);
+            if (eq) {
+                dpf_gen(n, a_eq, kBetaPrime, s0, s1, kp0, kp1);
+            } else {
+                dcf_gen(n, a1, kBetaPrime, s0, s1, kp0, kp1);
+                next_block(s0);
+                next_block(s1);
+                dcf_gen(n, a0, 0u - kBetaPrime, s0, s1, kp0 + dcf, kp1 + dcf);
+            }
+        }
+        for (int i = 0; i < 3; i++) {
+            uint8_t* rec = tok[i] + off;
+            std::memset(rec, 0, 24);
+            rec[0] = (uint8_t)q.kind;
+            rec[1] = (uint8_t)n;
+            rec[2] = (uint8_t)q.table; rec[3] = (uint8_t)(q.table >> 8);
+            rec[4] = (uint8_t)q.attr;  rec[5] = (uint8_t)(q.attr >> 8);
+            rec[6] = (uint8_t)q.group; rec[7] = (uint8_t)(q.group >> 8);
+            st32(rec + 8, rs[i]);
+            st32(rec + 12, rs[(i + 1) % 3]);
+            st32(rec + 16, cbeta);
+            for (int h = 0; h < 2; h++)
+                std::memcpy(rec + 24 + h * half, keys.data() + (kPair[i][h] * 2 + kParty[i][h]) * half, half);
+        }
+        off += 24 + 2 * half;
+    }
+    return OBLIVGM_OK;
+}
+
+}  // namespace ogm

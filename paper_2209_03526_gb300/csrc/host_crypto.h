@@ -1,0 +1,86 @@
+// host_crypto.h -- host-side AES-128, FSS key generation and token parsing of
+// the oblivgm library (client side of Sec. V-C and the servers' token intake).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "oblivgm.h"
+
+namespace ogm {
+
+// AES-128 on 32-bit little-endian columns (column c = bytes 4c..4c+3 of the block).
+struct RoundKeys { uint32_t w[44]; };
+
+struct AesTables {
+    uint8_t sbox[256];
+    uint32_t te0[256];   // MixColumns(S[x]) contribution of row 0: bytes (2s, s, s, 3s)
+};
+const AesTables& aes_tables();
+RoundKeys expand_key(const uint8_t key[16]);
+void aes_encrypt(const RoundKeys& rk, const uint32_t in[4], uint32_t out[4]);
+
+// the four fixed public PRG keys K_L, K_R, K_vL, K_vR: K_j[i] = 16 j + i
+const RoundKeys& fixed_key(int j);
+
+// Fixed-key round keys as the kernels take them (kernel parameter space).
+struct AesParams {
+    uint32_t rk_st[44];   // K_L round keys (seed / control-bit block, left child)
+    uint32_t d_st[44];    // K_L ^ K_R   (right child = left ^ d under an all-ones mask)
+    uint32_t rk_v[44];    // K_vL round keys (DCF value block)
+    uint32_t d_v[44];     // K_vL ^ K_vR
+};
+
+constexpr uint32_t kBetaPrime = 0xAAAAAAABu;   // 3^{-1} mod 2^32
+constexpr uint32_t kTokenMagic = 0x544D474Fu;
+constexpr int kMaxPreds = 64;
+constexpr int kMaxBits = 32;
+
+inline size_t key_bytes(uint32_t kind, int n) { return 28u + (size_t)n * (kind == OBLIVGM_KEY_DPF ? 20u : 24u); }
+
+// Device form of one key (repacked from the wire format), 16-byte aligned.
+struct alignas(16) DevKey {
+    uint32_t seed[4];
+    uint32_t scw[kMaxBits][4];   // level i (1-based) at scw[i-1]
+    uint32_t vcw[kMaxBits];      // DCF value correction words
+    uint32_t tl, tr;             // bit i-1: t^L_CW / t^R_CW of level i
+    uint32_t cw_final;           // CW_{n+1}
+    uint32_t party;              // 0 or 1
+    uint32_t n;
+    uint32_t kind;
+    uint32_t pad[2];
+};
+static_assert(sizeof(DevKey) == 688, "DevKey layout");
+static_assert(sizeof(DevKey) % 16 == 0, "bulk copies need 16-byte multiples");
+
+// Wire key -> DevKey.  Returns false on a malformed key.
+bool repack_key(const uint8_t* wire, size_t avail, uint32_t want_kind, int want_n, DevKey* out, std::string* err);
+
+// One predicate as the servers see it after parsing the three tokens.
+struct ParsedPred {
+    uint32_t kind, n, table, attr, group, step;
+    uint32_t r[3];        // <r>_1, <r>_2, <r>_3 (each server's own share)
+    uint32_t cbeta;
+    std::vector<DevKey> keys;   // [server][half][sub]: 6 (EQ) or 12 (RANGE)
+};
+
+struct ParsedQuery {
+    uint32_t n_bits = 0;
+    std::vector<ParsedPred> preds;
+};
+
+// Parse and cross-check the three servers' tokens.
+oblivgm_status parse_tokens(const uint8_t* const tok[3], const size_t tok_len[3], ParsedQuery* q, std::string* err);
+
+// Client-side token generation; identical layout to the ABI description.
+oblivgm_status keygen(const oblivgm_pred* preds, uint32_t n_preds, uint32_t n_bits, const uint8_t seed[16],
+                      uint8_t* const tok[3], size_t cap, size_t out_len[3], std::string* err);
+
+// FSS Gen for one key pair in the wire format (exposed for tests through the ABI-free entry).
+void dpf_gen(int n, uint32_t alpha, uint32_t beta, const uint8_t s0[16], const uint8_t s1[16], uint8_t* k0,
+             uint8_t* k1);
+void dcf_gen(int n, uint32_t alpha, uint32_t beta, const uint8_t s0[16], const uint8_t s1[16], uint8_t* k0,
+             uint8_t* k1);
+
+}  // namespace ogm

@@ -1,0 +1,842 @@
+// oblivgm.cu -- context, resident share store, raw DPF/DCF batches and the
+// fused secEval kernel (mask-open, six key-half walks per predicate, per-server
+// sums, PRF re-share, RSS AND fold, output write) of the oblivgm library.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "device_fss.cuh"
+#include "host_crypto.h"
+#include "oblivgm.h"
+#include "runtime.h"
+
+namespace ogm {
+
+thread_local std::string g_last_error;
+
+oblivgm_status fail(oblivgm_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+
+oblivgm_status cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? OBLIVGM_ENOMEM : OBLIVGM_ECUDA;
+}
+
+#define OGM_CUDA(call, what)                      \
+    do {                                          \
+        cudaError_t _e = (call);                  \
+        if (_e != cudaSuccess) return cuda_fail(_e, what); \
+    } while (0)
+
+// ------------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// bulk (non-tensor) TMA copy global -> shared, completion counted on the mbarrier
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait: gives up after limit_ns of wall time
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase, uint64_t limit_ns) {
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, phase)) {
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+    return true;
+}
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
+constexpr uint32_t kErrKeyWait = 1u;
+
+// ------------------------------------------------------------------ fused secEval
+
+struct GroupDesc {
+    const uint32_t* share[3];   // share set j of the group's table: [attr][stride]
+    uint32_t* out[3];           // RSS share sets of the result, n_elems each
+    uint64_t stride;
+    uint64_t n_elems;
+    uint32_t query_id, table_id, pred_begin, n_preds;
+    uint32_t vec_out;           // out pointers are 16-byte aligned
+    uint32_t pad[3];
+};
+
+struct PredDesc {
+    uint32_t kind, n_bits, attr, step;
+    uint32_t r[3];
+    uint32_t cbeta;
+    uint32_t key_begin, n_keys;
+    uint32_t pad[2];
+};
+
+struct FilterParams {
+    AesParams aes;
+    uint32_t rk_prf[3][44];
+    const uint32_t* te0;
+    const GroupDesc* groups;
+    const PredDesc* preds;
+    const DevKey* keys;
+    const uint64_t* item_start;   // n_groups + 1 prefix sums of element tiles
+    unsigned long long* counter;  // work queue head
+    uint32_t* error;              // context fault flags
+    uint32_t n_groups;
+    uint32_t tile;                // elements per item = blockDim.x * E
+};
+
+constexpr int kMaxKeysPerPred = 12;
+constexpr int kFilterSmem = kTableBytes + kMaxKeysPerPred * (int)sizeof(DevKey);
+
+// re-share of a 3-out-of-3 sharing z into RSS: r_i = z_i + F(k_i, ctr) - F(k_{i-1}, ctr).
+// F(k_i) enters r_i with + and r_{i+1} with -; the loop over the three PRF keys is
+// kept rolled so the code holds one AES body per element.
+template <int E>
+__device__ __forceinline__ void reshare(const char* T, uint32_t l4, const FilterParams& P, const uint32_t z[3][E],
+                                        uint32_t out[3][E], uint64_t e0, uint32_t step, uint32_t table,
+                                        uint32_t query) {
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int e = 0; e < E; e++) out[i][e] = z[i][e];
+#pragma unroll 1
+    for (int i = 0; i < 3; i++) {
+#pragma unroll
+        for (int e = 0; e < E; e++) {
+            const uint64_t el = e0 + (uint64_t)e;
+            const uint32_t ctr[4] = {(uint32_t)el, (uint32_t)(el >> 32), step | (table << 16), query};
+            uint32_t o[4];
+            aes_one(T, l4, P.rk_prf[i], ctr, o);
+            const uint32_t f = o[0];
+            out[0][e] += i == 0 ? f : (i == 2 ? 0u - f : 0u);
+            out[1][e] += i == 1 ? f : (i == 0 ? 0u - f : 0u);
+            out[2][e] += i == 2 ? f : (i == 1 ? 0u - f : 0u);
+        }
+    }
+}
+
+template <int E>
+__device__ __forceinline__ void load_col(const uint32_t* __restrict__ col, uint64_t e0, uint64_t n_elems, uint32_t v[E]) {
+    if constexpr (E == 4) {
+        if (e0 < n_elems) {   // stride is a multiple of 4, so the vector stays inside the row
+            const uint4 q = __ldg(reinterpret_cast<const uint4*>(col + e0));
+            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+            return;
+        }
+    } else if constexpr (E == 2) {
+        if (e0 < n_elems) {
+            const uint2 q = __ldg(reinterpret_cast<const uint2*>(col + e0));
+            v[0] = q.x; v[1] = q.y;
+            return;
+        }
+    } else {
+        if (e0 < n_elems) { v[0] = __ldg(col + e0); return; }
+    }
+#pragma unroll
+    for (int e = 0; e < E; e++) v[e] = 0;
+}
+
+template <int E>
+__device__ __forceinline__ void store_col(uint32_t* col, uint64_t e0, uint64_t n_elems, bool vec, const uint32_t v[E]) {
+    if constexpr (E == 4) {
+        if (vec && e0 + 3 < n_elems) {
+            *reinterpret_cast<uint4*>(col + e0) = make_uint4(v[0], v[1], v[2], v[3]);
+            return;
+        }
+    } else if constexpr (E == 2) {
+        if (vec && e0 + 1 < n_elems) {
+            *reinterpret_cast<uint2*>(col + e0) = make_uint2(v[0], v[1]);
+            return;
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < E; e++)
+        if (e0 + e < n_elems) col[e0 + e] = v[e];
+}
+
+// largest CTA each variant may be launched with (sets the register budget)
+template <int E> constexpr int max_threads() { return E == 1 ? 1024 : 512; }
+
+template <int E>
+__global__ void __launch_bounds__(max_threads<E>(), 1) k_filter(const __grid_constant__ FilterParams P) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const char* T = reinterpret_cast<const char*>(smem);
+    DevKey* kbuf = reinterpret_cast<DevKey*>(smem + kTableBytes);
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ unsigned long long item_sh;
+
+    fill_tables(reinterpret_cast<uint32_t*>(smem), P.te0);
+    if (threadIdx.x == 0) mbar_init(&mbar);
+    __syncthreads();
+
+    const uint32_t l4 = lane_offset();
+    uint32_t phase = 0;
+    const uint64_t n_items = P.item_start[P.n_groups];
+    for (;;) {
+        if (threadIdx.x == 0) item_sh = atomicAdd(P.counter, 1ull);
+        __syncthreads();
+        const uint64_t item = item_sh;
+        if (item >= n_items) break;
+        int lo = 0, hi = (int)P.n_groups - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (P.item_start[mid] <= item) lo = mid; else hi = mid - 1;
+        }
+        const GroupDesc& G = P.groups[lo];
+        const uint64_t e0 = (item - P.item_start[lo]) * P.tile + (uint64_t)threadIdx.x * E;
+        const uint64_t n_elems = G.n_elems;
+        const uint32_t table = G.table_id, query = G.query_id;
+        uint32_t acc[3][E];
+        for (uint32_t k = 0; k < G.n_preds; k++) {
+            const PredDesc& D = P.preds[G.pred_begin + k];
+            __syncthreads();   // everyone is done with the previous predicate's keys
+            if (threadIdx.x == 0) {
+                const uint32_t bytes = D.n_keys * (uint32_t)sizeof(DevKey);
+                mbar_expect_tx(&mbar, bytes);
+                bulk_g2s(kbuf, P.keys + D.key_begin, bytes, &mbar);
+            }
+            const bool ok = mbar_wait_bounded(&mbar, phase, kWaitLimitNs);
+            phase ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) atomicOr(P.error, kErrKeyWait);
+                mbar_wait_bounded(&mbar, phase ^ 1u, kWaitLimitNs);   // let an in-flight copy land
+                return;
+            }
+            // open x^ = <x>_1 + <x>_2 + <x>_3 + <r>_1 + <r>_2 + <r>_3 mod 2^n
+            const uint32_t mask = D.n_bits >= 32 ? 0xFFFFFFFFu : ((1u << D.n_bits) - 1u);
+            uint32_t xh[E], sh[E];
+            const uint64_t row = (uint64_t)D.attr * G.stride;
+#pragma unroll
+            for (int e = 0; e < E; e++) xh[e] = D.r[0] + D.r[1] + D.r[2];
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                load_col<E>(G.share[j] + row, e0, n_elems, sh);
+#pragma unroll
+                for (int e = 0; e < E; e++) xh[e] += sh[e];
+            }
+#pragma unroll
+            for (int e = 0; e < E; e++) xh[e] &= mask;
+            // Eq. (predEval), masked form: CS_i sums the outputs of its two key halves.
+            // keys are ordered [server i][half h][sub s]; one walk instance of each kind
+            // is kept in the code and driven by a runtime loop
+            uint32_t z[3][E];
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int e = 0; e < E; e++) z[i][e] = 0;
+            const bool eq = D.kind == OBLIVGM_PRED_EQ;
+            const int nsub = eq ? 1 : 2;
+            const int n_keys = 6 * nsub;
+            for (int kk = 0; kk < n_keys; kk++) {
+                const DevKey& K = kbuf[kk];
+                uint32_t y[E];
+                if (eq) dpf_walk<E>(T, l4, P.aes, K, xh, y);
+                else dcf_walk<E>(T, l4, P.aes, K, xh, y);
+                // RANGE: the public constant c * beta' joins party 0's half once
+                const uint32_t add = (!eq && (kk % nsub) == 0 && K.party == 0) ? D.cbeta : 0u;
+                const int i = kk / (2 * nsub);
+#pragma unroll
+                for (int e = 0; e < E; e++) {
+                    const uint32_t v = y[e] + add;
+                    z[0][e] += i == 0 ? v : 0u;
+                    z[1][e] += i == 1 ? v : 0u;
+                    z[2][e] += i == 2 ? v : 0u;
+                }
+            }
+            // re-share the predicate's sum to RSS (step p); from the second predicate on,
+            // AND it into the accumulator (Sec. III-B: w_i = a_i b_i + a_i b_{i+1} + a_{i+1} b_i)
+            // and re-share the product (step 64 + p).  One re-share call site, two passes.
+            uint32_t step = D.step;
+            const int passes = k == 0 ? 1 : 2;
+#pragma unroll 1
+            for (int pass = 0; pass < passes; pass++) {
+                uint32_t r[3][E];
+                reshare<E>(T, l4, P, z, r, e0, step, table, query);
+                if (pass + 1 < passes) {
+#pragma unroll
+                    for (int i = 0; i < 3; i++)
+#pragma unroll
+                        for (int e = 0; e < E; e++) {
+                            const int i1 = (i + 1) % 3;
+                            z[i][e] = acc[i][e] * r[i][e] + acc[i][e] * r[i1][e] + acc[i1][e] * r[i][e];
+                        }
+                    step = 64u + D.step;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 3; i++)
+#pragma unroll
+                        for (int e = 0; e < E; e++) acc[i][e] = r[i][e];
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 3; i++) store_col<E>(G.out[i], e0, n_elems, G.vec_out != 0, acc[i]);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ raw batches
+
+struct RawParams {
+    AesParams aes;
+    const uint32_t* te0;
+    const DevKey* keys;
+    const uint32_t* points;
+    const uint32_t* key_of_point;
+    uint32_t* out;
+    uint64_t n_points;
+    uint32_t n_keys;
+    uint32_t all_pairs;
+};
+
+template <uint32_t KIND>
+__global__ void __launch_bounds__(256) k_eval_raw(const __grid_constant__ RawParams P) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    fill_tables(reinterpret_cast<uint32_t*>(smem), P.te0);
+    __syncthreads();
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n_points) return;
+    const uint32_t key = P.all_pairs ? blockIdx.y : P.key_of_point[i];
+    uint64_t o = i;
+    if (P.all_pairs) o = (uint64_t)key * P.n_points + i;
+    if (key >= P.n_keys) { P.out[o] = 0u; return; }
+    const DevKey& K = P.keys[key];
+    const uint32_t mask = K.n >= 32 ? 0xFFFFFFFFu : ((1u << K.n) - 1u);
+    uint32_t x[1] = {P.points[i] & mask}, y[1];
+    const char* T = reinterpret_cast<const char*>(smem);
+    if (KIND == OBLIVGM_KEY_DPF) dpf_walk<1>(T, lane_offset(), P.aes, K, x, y);
+    else dcf_walk<1>(T, lane_offset(), P.aes, K, x, y);
+    P.out[o] = y[0];
+}
+
+}  // namespace ogm
+
+// ====================================================================== host side
+
+using namespace ogm;
+
+namespace ogm {
+
+void build_aes_params(AesParams* a) {
+    const RoundKeys &L = fixed_key(0), &R = fixed_key(1), &VL = fixed_key(2), &VR = fixed_key(3);
+    for (int i = 0; i < 44; i++) {
+        a->rk_st[i] = L.w[i];
+        a->d_st[i] = L.w[i] ^ R.w[i];
+        a->rk_v[i] = VL.w[i];
+        a->d_v[i] = VL.w[i] ^ VR.w[i];
+    }
+}
+
+static oblivgm_status check_ctx(oblivgm_ctx* ctx) {
+    if (!ctx) return fail(OBLIVGM_EINVAL, "NULL context");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    return OBLIVGM_OK;
+}
+
+// Build device descriptors of the given queries' groups (groups sorted by per-tile
+// cost, most expensive first) into one contiguous host image.
+struct Plan {
+    uint32_t tile = 0, elems_per_thread = 1;
+    std::vector<GroupDesc> groups;
+    std::vector<PredDesc> preds;
+    std::vector<DevKey> keys;
+    std::vector<uint64_t> item_start;
+};
+
+oblivgm_status plan_queries(const std::map<uint32_t, Table>& tables, uint32_t n_queries, const uint32_t* query_ids,
+                            const ParsedQuery* parsed, const uint32_t* n_groups, uint32_t* const* const* outs,
+                            uint32_t tile, Plan* plan) {
+    struct G { GroupDesc d; std::vector<const ParsedPred*> preds; uint64_t cost; };
+    std::vector<G> all;
+    for (uint32_t q = 0; q < n_queries; q++) {
+        const ParsedQuery& pq = parsed[q];
+        const uint32_t ng = n_groups[q];
+        if (ng == 0 || ng > OBLIVGM_MAX_GROUPS) return fail(OBLIVGM_EINVAL, "n_groups must be 1..64");
+        std::vector<std::vector<const ParsedPred*>> members(ng);
+        for (const ParsedPred& p : pq.preds) {
+            if (p.group >= ng) return fail(OBLIVGM_EINVAL, "predicate group outside 0..n_groups-1");
+            members[p.group].push_back(&p);
+        }
+        for (uint32_t g = 0; g < ng; g++) {
+            if (members[g].empty()) return fail(OBLIVGM_EINVAL, "an AND-group has no predicate");
+            const uint32_t tid = members[g][0]->table;
+            auto it = tables.find(tid);
+            if (it == tables.end()) return fail(OBLIVGM_ENOENT, "predicate on a table that is not loaded");
+            const Table& tb = it->second;
+            uint64_t cost = 0;
+            for (const ParsedPred* p : members[g]) {
+                if (p->table != tid) return fail(OBLIVGM_EINVAL, "an AND-group spans two tables");
+                if (p->attr >= tb.n_attrs) return fail(OBLIVGM_EINVAL, "predicate attribute outside its table");
+                if (p->n != tb.n_bits) return fail(OBLIVGM_EINVAL, "predicate bit length differs from its table's");
+                cost += p->kind == OBLIVGM_PRED_EQ ? 6ull * p->n : 24ull * p->n;
+            }
+            G gr{};
+            for (int j = 0; j < 3; j++) {
+                gr.d.share[j] = tb.dev + (uint64_t)j * tb.n_attrs * tb.stride;
+                gr.d.out[j] = outs[q][3 * g + j];
+                if (!gr.d.out[j] && tb.n_elems) return fail(OBLIVGM_EINVAL, "NULL output pointer");
+            }
+            gr.d.vec_out = 1;
+            for (int j = 0; j < 3; j++)
+                if (reinterpret_cast<uintptr_t>(gr.d.out[j]) % 16) gr.d.vec_out = 0;
+            gr.d.stride = tb.stride;
+            gr.d.n_elems = tb.n_elems;
+            gr.d.query_id = query_ids[q];
+            gr.d.table_id = tid;
+            gr.preds = members[g];
+            gr.cost = cost;
+            all.push_back(std::move(gr));
+        }
+    }
+    std::stable_sort(all.begin(), all.end(), [](const G& a, const G& b) { return a.cost > b.cost; });
+    plan->groups.clear(); plan->preds.clear(); plan->keys.clear(); plan->item_start.clear();
+    plan->tile = tile;
+    uint64_t items = 0;
+    for (G& g : all) {
+        g.d.pred_begin = (uint32_t)plan->preds.size();
+        g.d.n_preds = (uint32_t)g.preds.size();
+        for (const ParsedPred* p : g.preds) {
+            PredDesc d{};
+            d.kind = p->kind; d.n_bits = p->n; d.attr = p->attr; d.step = p->step;
+            for (int i = 0; i < 3; i++) d.r[i] = p->r[i];
+            d.cbeta = p->cbeta;
+            d.key_begin = (uint32_t)plan->keys.size();
+            d.n_keys = (uint32_t)p->keys.size();
+            plan->keys.insert(plan->keys.end(), p->keys.begin(), p->keys.end());
+            plan->preds.push_back(d);
+        }
+        plan->groups.push_back(g.d);
+        plan->item_start.push_back(items);
+        items += (g.d.n_elems + tile - 1) / tile;
+    }
+    plan->item_start.push_back(items);
+    return OBLIVGM_OK;
+}
+
+template <typename T>
+static size_t align_up(size_t x) { return (x + alignof(T) - 1) / alignof(T) * alignof(T); }
+
+oblivgm_status launch_plan(oblivgm_ctx* ctx, const Plan& plan, cudaStream_t st, uint32_t* error_flag) {
+    if (plan.item_start.back() == 0) return OBLIVGM_OK;   // nothing to evaluate
+    // one stream-ordered workspace: counter | groups | preds | keys | item_start
+    const size_t off_groups = 256;
+    const size_t off_preds = off_groups + (plan.groups.size() * sizeof(GroupDesc) + 255) / 256 * 256;
+    const size_t off_keys = off_preds + (plan.preds.size() * sizeof(PredDesc) + 255) / 256 * 256;
+    const size_t off_items = off_keys + (plan.keys.size() * sizeof(DevKey) + 255) / 256 * 256;
+    const size_t total = off_items + plan.item_start.size() * sizeof(uint64_t);
+    std::vector<unsigned char> img(total, 0);
+    std::memcpy(img.data() + off_groups, plan.groups.data(), plan.groups.size() * sizeof(GroupDesc));
+    std::memcpy(img.data() + off_preds, plan.preds.data(), plan.preds.size() * sizeof(PredDesc));
+    std::memcpy(img.data() + off_keys, plan.keys.data(), plan.keys.size() * sizeof(DevKey));
+    std::memcpy(img.data() + off_items, plan.item_start.data(), plan.item_start.size() * sizeof(uint64_t));
+    unsigned char* ws = nullptr;
+    OGM_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&ws), total, st), "workspace allocation");
+    OGM_CUDA(cudaMemcpyAsync(ws, img.data(), total, cudaMemcpyHostToDevice, st), "descriptor upload");
+    FilterParams P{};
+    P.aes = ctx->aes;
+    std::memcpy(P.rk_prf, ctx->rk_prf, sizeof P.rk_prf);
+    P.te0 = ctx->d_te0;
+    P.groups = reinterpret_cast<const GroupDesc*>(ws + off_groups);
+    P.preds = reinterpret_cast<const PredDesc*>(ws + off_preds);
+    P.keys = reinterpret_cast<const DevKey*>(ws + off_keys);
+    P.item_start = reinterpret_cast<const uint64_t*>(ws + off_items);
+    P.counter = reinterpret_cast<unsigned long long*>(ws);
+    P.error = error_flag;
+    P.n_groups = (uint32_t)plan.groups.size();
+    P.tile = plan.tile;
+    const uint64_t n_items = plan.item_start.back();
+    const unsigned grid = (unsigned)std::min<uint64_t>(n_items, (uint64_t)ctx->sm_count);
+    const uint32_t E = plan.elems_per_thread, threads = plan.tile / plan.elems_per_thread;
+    cudaError_t e = cudaSuccess;
+    switch (E) {
+        case 1: k_filter<1><<<grid, threads, kFilterSmem, st>>>(P); break;
+        case 2: k_filter<2><<<grid, threads, kFilterSmem, st>>>(P); break;
+        default: k_filter<4><<<grid, threads, kFilterSmem, st>>>(P); break;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "k_filter launch");
+    ctx->launches++;
+    OGM_CUDA(cudaFreeAsync(ws, st), "workspace release");
+    return OBLIVGM_OK;
+}
+
+oblivgm_status launch_parsed(oblivgm_ctx* ctx, uint32_t n_queries, const uint32_t* query_ids,
+                             const ParsedQuery* parsed, const uint32_t* n_groups, uint32_t* const* const* outs,
+                             const std::map<uint32_t, Table>& tables, cudaStream_t st) {
+    Plan plan;
+    const uint32_t threads = ctx->threads, E = ctx->elems_per_thread;
+    plan.elems_per_thread = E;
+    oblivgm_status s = plan_queries(tables, n_queries, query_ids, parsed, n_groups, outs, threads * E, &plan);
+    if (s != OBLIVGM_OK) return s;
+    return launch_plan(ctx, plan, st, ctx->d_error);
+}
+
+oblivgm_status set_filter_attrs() {
+    OGM_CUDA(cudaFuncSetAttribute(k_filter<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFilterSmem), "smem attr");
+    OGM_CUDA(cudaFuncSetAttribute(k_filter<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFilterSmem), "smem attr");
+    OGM_CUDA(cudaFuncSetAttribute(k_filter<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFilterSmem), "smem attr");
+    OGM_CUDA(cudaFuncSetAttribute(k_eval_raw<OBLIVGM_KEY_DPF>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTableBytes), "smem attr");
+    OGM_CUDA(cudaFuncSetAttribute(k_eval_raw<OBLIVGM_KEY_DCF>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTableBytes), "smem attr");
+    return OBLIVGM_OK;
+}
+
+}  // namespace ogm
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+uint32_t oblivgm_version(void) { return 0x000100u; }
+
+oblivgm_status oblivgm_last_error(char* buf, size_t n) {
+    if (!buf || n == 0) return OBLIVGM_EINVAL;
+    std::snprintf(buf, n, "%s", g_last_error.c_str());
+    return OBLIVGM_OK;
+}
+
+oblivgm_status oblivgm_create(oblivgm_ctx** out, int32_t device, const oblivgm_config* cfg) {
+    if (!out || !cfg) return fail(OBLIVGM_EINVAL, "NULL argument");
+    if (cfg->flags != 0) return fail(OBLIVGM_EINVAL, "config flags must be 0");
+    *out = nullptr;
+    int count = 0;
+    OGM_CUDA(cudaGetDeviceCount(&count), "cudaGetDeviceCount");
+    if (device < 0 || device >= count) return fail(OBLIVGM_EINVAL, "no such CUDA device");
+    cudaDeviceProp prop;
+    OGM_CUDA(cudaGetDeviceProperties(&prop, device), "cudaGetDeviceProperties");
+    if (prop.major != 10 || prop.minor != 3) return fail(OBLIVGM_EARCH, "this library is built for sm_103 (GB300) only");
+    OGM_CUDA(cudaSetDevice(device), "cudaSetDevice");
+    auto* ctx = new (std::nothrow) oblivgm_ctx();
+    if (!ctx) return fail(OBLIVGM_ENOMEM, "host allocation");
+    ctx->device = device;
+    ctx->sm_count = prop.multiProcessorCount;
+    build_aes_params(&ctx->aes);
+    for (int i = 0; i < 3; i++) {
+        const RoundKeys rk = expand_key(cfg->prf_keys[i]);
+        std::memcpy(ctx->rk_prf[i], rk.w, sizeof rk.w);
+    }
+    ctx->cfg = *cfg;
+    oblivgm_status st = set_filter_attrs();
+    if (st != OBLIVGM_OK) { delete ctx; return st; }
+    cudaError_t e = cudaMalloc(&ctx->d_te0, 256 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->d_te0, aes_tables().te0, 256 * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_error, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_error, 0, sizeof(uint32_t));
+    if (e == cudaSuccess) {
+        cudaMemPool_t pool;
+        e = cudaDeviceGetDefaultMemPool(&pool, device);
+        uint64_t keep = UINT64_MAX;
+        if (e == cudaSuccess) e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    if (e != cudaSuccess) {
+        st = cuda_fail(e, "context set-up");
+        oblivgm_destroy(ctx);
+        return st;
+    }
+    st = serve_init(ctx);
+    if (st != OBLIVGM_OK) { oblivgm_destroy(ctx); return st; }
+    *out = ctx;
+    return OBLIVGM_OK;
+}
+
+oblivgm_status oblivgm_destroy(oblivgm_ctx* ctx) {
+    if (!ctx) return OBLIVGM_OK;
+    cudaSetDevice(ctx->device);
+    serve_shutdown(ctx);
+    cudaDeviceSynchronize();
+    for (auto& kv : ctx->tables) cudaFree(kv.second.dev);
+    if (ctx->d_te0) cudaFree(ctx->d_te0);
+    if (ctx->d_error) cudaFree(ctx->d_error);
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    delete ctx;
+    return OBLIVGM_OK;
+}
+
+oblivgm_status oblivgm_sync(oblivgm_ctx* ctx, void* stream) {
+    oblivgm_status st = check_ctx(ctx);
+    if (st) return st;
+    OGM_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)), "stream synchronize");
+    uint32_t flag = 0;
+    OGM_CUDA(cudaMemcpy(&flag, ctx->d_error, sizeof flag, cudaMemcpyDeviceToHost), "read fault flag");
+    if (flag) {
+        cudaMemset(ctx->d_error, 0, sizeof flag);
+        return fail(OBLIVGM_EFAULT_DEVICE, "a bounded device wait expired (key staging)");
+    }
+    return OBLIVGM_OK;
+}
+
+uint64_t oblivgm_launch_count(oblivgm_ctx* ctx) { return ctx ? ctx->launches.load() : 0ull; }
+
+oblivgm_status oblivgm_load_shares(oblivgm_ctx* ctx, uint32_t table_id, uint64_t n_elems, uint32_t n_attrs,
+                                   uint32_t n_bits, const uint32_t* const share_sets[3], int32_t mem_kind,
+                                   void* stream) {
+    oblivgm_status st = check_ctx(ctx);
+    if (st) return st;
+    if (table_id > 0xFFFF || n_attrs == 0 || n_attrs > 65536 || n_bits < 1 || n_bits > 32 || !share_sets)
+        return fail(OBLIVGM_EINVAL, "bad table arguments");
+    if (mem_kind != OBLIVGM_MEM_HOST && mem_kind != OBLIVGM_MEM_DEVICE) return fail(OBLIVGM_EINVAL, "bad mem_kind");
+    for (int j = 0; j < 3; j++)
+        if (!share_sets[j] && n_elems) return fail(OBLIVGM_EINVAL, "NULL share set");
+    if (table_in_use(ctx, table_id)) return fail(OBLIVGM_EBUSY, "table is used by in-flight queries");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const uint64_t stride = (n_elems + 3) / 4 * 4;
+    const size_t row_bytes = stride * sizeof(uint32_t);
+    const size_t bytes = 3ull * n_attrs * row_bytes;
+    Table tb{};
+    tb.n_elems = n_elems; tb.stride = stride; tb.n_attrs = n_attrs; tb.n_bits = n_bits;
+    auto it = ctx->tables.find(table_id);
+    if (it != ctx->tables.end() && it->second.bytes == bytes) {
+        tb.dev = it->second.dev;   // same shape: reuse the allocation
+        tb.bytes = bytes;
+    } else {
+        if (it != ctx->tables.end()) {
+            OGM_CUDA(cudaStreamSynchronize(s), "stream synchronize");
+            cudaFree(it->second.dev);
+            ctx->tables.erase(it);
+        }
+        OGM_CUDA(cudaMalloc(&tb.dev, std::max<size_t>(bytes, 16)), "table allocation");
+        tb.bytes = bytes;
+    }
+    ctx->tables[table_id] = tb;
+    if (n_elems == 0) return OBLIVGM_OK;
+    const size_t src_row = n_elems * sizeof(uint32_t);
+    const cudaMemcpyKind kind = mem_kind == OBLIVGM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    for (int j = 0; j < 3; j++) {
+        // one 2-D copy per share set: n_attrs rows of n_elems words into rows of `stride` words
+        OGM_CUDA(cudaMemcpy2DAsync(tb.dev + (uint64_t)j * n_attrs * stride, row_bytes, share_sets[j], src_row, src_row,
+                                   n_attrs, kind, s),
+                 "share upload");
+    }
+    if (mem_kind == OBLIVGM_MEM_HOST) {
+        // pageable host sources are staged by the driver before the call returns only for
+        // small copies; synchronise so the caller may reuse its buffers at once
+        OGM_CUDA(cudaStreamSynchronize(s), "stream synchronize");
+    }
+    return OBLIVGM_OK;
+}
+
+oblivgm_status oblivgm_unload_shares(oblivgm_ctx* ctx, uint32_t table_id) {
+    oblivgm_status st = check_ctx(ctx);
+    if (st) return st;
+    auto it = ctx->tables.find(table_id);
+    if (it == ctx->tables.end()) return fail(OBLIVGM_ENOENT, "no such table");
+    if (table_in_use(ctx, table_id)) return fail(OBLIVGM_EBUSY, "table is used by in-flight queries");
+    cudaDeviceSynchronize();
+    cudaFree(it->second.dev);
+    ctx->tables.erase(it);
+    return OBLIVGM_OK;
+}
+
+oblivgm_status oblivgm_keygen(const oblivgm_pred* preds, uint32_t n_preds, uint32_t n_bits, const uint8_t seed[16],
+                              uint8_t* const tok[3], size_t cap, size_t out_len[3]) {
+    std::string err;
+    oblivgm_status st = keygen(preds, n_preds, n_bits, seed, tok, cap, out_len, &err);
+    if (st != OBLIVGM_OK) return fail(st, err);
+    return OBLIVGM_OK;
+}
+
+static oblivgm_status eval_batch(oblivgm_ctx* ctx, uint32_t kind, const uint8_t* keys, uint32_t n_keys,
+                                 const uint32_t* points, const uint32_t* key_of_point, uint64_t n_points,
+                                 uint32_t flags, uint32_t* out, uint64_t n_out, void* stream) {
+    oblivgm_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!keys || n_keys == 0 || (n_points && (!points || !out))) return fail(OBLIVGM_EINVAL, "NULL or empty argument");
+    const bool all = (flags & OBLIVGM_ALL_PAIRS) != 0;
+    if (flags & ~OBLIVGM_ALL_PAIRS) return fail(OBLIVGM_EINVAL, "unknown flags");
+    if (!all && n_points && !key_of_point) return fail(OBLIVGM_EINVAL, "key_of_point is NULL");
+    if (all && n_keys > 65535) return fail(OBLIVGM_EINVAL, "ALL_PAIRS takes at most 65535 keys");
+    const uint64_t need = all ? (uint64_t)n_keys * n_points : n_points;
+    if (n_out < need) return fail(OBLIVGM_ERANGE, "output buffer too small");
+    const int n = keys[1];
+    if (n < 1 || n > kMaxBits) return fail(OBLIVGM_EINVAL, "bad key bit length");
+    const size_t klen = key_bytes(kind, n);
+    std::vector<DevKey> dk(n_keys);
+    std::string err;
+    for (uint32_t k = 0; k < n_keys; k++)
+        if (!repack_key(keys + (size_t)k * klen, klen, kind, n, &dk[k], &err)) return fail(OBLIVGM_EINVAL, err);
+    if (n_points == 0) return OBLIVGM_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DevKey* d_keys = nullptr;
+    OGM_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_keys), dk.size() * sizeof(DevKey), s), "key buffer");
+    OGM_CUDA(cudaMemcpyAsync(d_keys, dk.data(), dk.size() * sizeof(DevKey), cudaMemcpyHostToDevice, s), "key upload");
+    RawParams P{};
+    P.aes = ctx->aes;
+    P.te0 = ctx->d_te0;
+    P.keys = d_keys;
+    P.points = points;
+    P.key_of_point = key_of_point;
+    P.out = out;
+    P.n_points = n_points;
+    P.n_keys = n_keys;
+    P.all_pairs = all ? 1u : 0u;
+    const uint64_t blocks = (n_points + 255) / 256;
+    if (blocks > 0x7FFFFFFFull) return fail(OBLIVGM_EINVAL, "too many points");
+    dim3 grid((unsigned)blocks, all ? n_keys : 1);
+    if (kind == OBLIVGM_KEY_DPF) k_eval_raw<OBLIVGM_KEY_DPF><<<grid, 256, kTableBytes, s>>>(P);
+    else k_eval_raw<OBLIVGM_KEY_DCF><<<grid, 256, kTableBytes, s>>>(P);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "k_eval_raw launch");
+    ctx->launches++;
+    OGM_CUDA(cudaFreeAsync(d_keys, s), "key buffer release");
+    return OBLIVGM_OK;
+}
+
+oblivgm_status oblivgm_eval_dpf_batch(oblivgm_ctx* ctx, const uint8_t* keys, uint32_t n_keys, const uint32_t* points,
+                                      const uint32_t* key_of_point, uint64_t n_points, uint32_t flags, uint32_t* out,
+                                      uint64_t n_out, void* stream) {
+    return eval_batch(ctx, OBLIVGM_KEY_DPF, keys, n_keys, points, key_of_point, n_points, flags, out, n_out, stream);
+}
+
+oblivgm_status oblivgm_eval_dcf_batch(oblivgm_ctx* ctx, const uint8_t* keys, uint32_t n_keys, const uint32_t* points,
+                                      const uint32_t* key_of_point, uint64_t n_points, uint32_t flags, uint32_t* out,
+                                      uint64_t n_out, void* stream) {
+    return eval_batch(ctx, OBLIVGM_KEY_DCF, keys, n_keys, points, key_of_point, n_points, flags, out, n_out, stream);
+}
+
+oblivgm_status oblivgm_filter_batch(oblivgm_ctx* ctx, uint32_t n_queries, const uint32_t* query_ids,
+                                    const uint8_t* const* toks, const size_t* tok_lens, const uint32_t* n_groups,
+                                    uint32_t* const* const* outs, void* stream) {
+    oblivgm_status st = check_ctx(ctx);
+    if (st) return st;
+    if (n_queries == 0) return OBLIVGM_OK;
+    if (!query_ids || !toks || !tok_lens || !n_groups || !outs) return fail(OBLIVGM_EINVAL, "NULL argument");
+    std::vector<ParsedQuery> parsed(n_queries);
+    std::string err;
+    for (uint32_t q = 0; q < n_queries; q++) {
+        if (!outs[q]) return fail(OBLIVGM_EINVAL, "NULL output array");
+        st = parse_tokens(toks + 3 * q, tok_lens + 3 * q, &parsed[q], &err);
+        if (st != OBLIVGM_OK) return fail(st, err);
+    }
+    return launch_parsed(ctx, n_queries, query_ids, parsed.data(), n_groups, outs, ctx->tables,
+                         static_cast<cudaStream_t>(stream));
+}
+
+oblivgm_status oblivgm_filter_and_combine(oblivgm_ctx* ctx, uint32_t query_id, const uint8_t* const tok[3],
+                                          const size_t tok_len[3], uint32_t n_groups, uint32_t* const* out,
+                                          void* stream) {
+    if (!tok || !tok_len || !out) return fail(OBLIVGM_EINVAL, "NULL argument");
+    const uint8_t* toks[3] = {tok[0], tok[1], tok[2]};
+    uint32_t* const* outs[1] = {out};
+    return oblivgm_filter_batch(ctx, 1, &query_id, toks, tok_len, &n_groups, outs, stream);
+}
+
+oblivgm_status oblivgm_autotune(oblivgm_ctx* ctx, uint32_t* threads, uint32_t* elems_per_thread) {
+    oblivgm_status st = check_ctx(ctx);
+    if (st) return st;
+    // synthetic private table: 2^18 elements, one 32-bit attribute, one equality and one
+    // range predicate ANDed, so both walk kinds and the fold are in the timing
+    const uint64_t n = 1ull << 18;
+    std::vector<uint32_t> h(n);
+    uint32_t x = 0x9E3779B9u;
+    for (auto& v : h) { x ^= x << 13; x ^= x >> 17; x ^= x << 5; v = x; }
+    std::map<uint32_t, Table> tabs;
+    Table tb{};
+    tb.n_elems = n; tb.stride = n; tb.n_attrs = 1; tb.n_bits = 32; tb.bytes = 3 * n * 4;
+    OGM_CUDA(cudaMalloc(&tb.dev, tb.bytes + 3 * n * 4), "autotune buffers");
+    for (int j = 0; j < 3; j++)
+        cudaMemcpy(tb.dev + j * n, h.data(), n * 4, cudaMemcpyHostToDevice);
+    tabs[0] = tb;
+    uint32_t* outp = tb.dev + 3 * n;
+    uint32_t* outs3[3] = {outp, outp, outp};   // timing only: the three sets may overlap
+    oblivgm_pred preds[2] = {{OBLIVGM_PRED_EQ, 0, 0, 0, 12345u, 0}, {OBLIVGM_PRED_RANGE, 0, 0, 0, 1000u, 0x7FFFFFFFu}};
+    uint8_t seed[16] = {0};
+    size_t len[3];
+    std::string err;
+    keygen(preds, 2, 32, seed, nullptr, 0, len, &err);
+    std::vector<uint8_t> t0(len[0]), t1(len[1]), t2(len[2]);
+    uint8_t* tk[3] = {t0.data(), t1.data(), t2.data()};
+    keygen(preds, 2, 32, seed, tk, len[0], len, &err);
+    const uint8_t* ctk[3] = {tk[0], tk[1], tk[2]};
+    ParsedQuery pq;
+    parse_tokens(ctk, len, &pq, &err);
+    const uint32_t qid = 1, ng = 1;
+    uint32_t* const* outs[1] = {outs3};
+    struct Cand { uint32_t t, e; };
+    const Cand cands[] = {{1024, 1}, {512, 1}, {512, 2}, {256, 2}, {512, 4}, {256, 4}, {128, 4}};
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    const uint32_t keep_t = ctx->threads, keep_e = ctx->elems_per_thread;
+    float best = 1e30f;
+    Cand win{keep_t, keep_e};
+    for (const Cand& c : cands) {
+        ctx->threads = c.t;
+        ctx->elems_per_thread = c.e;
+        float ms_best = 1e30f;
+        for (int rep = 0; rep < 3; rep++) {
+            cudaEventRecord(a, 0);
+            st = launch_parsed(ctx, 1, &qid, &pq, &ng, outs, tabs, 0);
+            cudaEventRecord(b, 0);
+            if (st != OBLIVGM_OK) break;
+            cudaEventSynchronize(b);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, a, b);
+            if (rep > 0) ms_best = std::min(ms_best, ms);
+        }
+        if (st != OBLIVGM_OK) break;
+        if (ms_best < best) { best = ms_best; win = c; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaDeviceSynchronize();
+    cudaFree(tb.dev);
+    if (st != OBLIVGM_OK) {
+        ctx->threads = keep_t;
+        ctx->elems_per_thread = keep_e;
+        return st;
+    }
+    ctx->threads = win.t;
+    ctx->elems_per_thread = win.e;
+    if (threads) *threads = win.t;
+    if (elems_per_thread) *elems_per_thread = win.e;
+    return OBLIVGM_OK;
+}
+
+oblivgm_status oblivgm_set_schedule(oblivgm_ctx* ctx, uint32_t threads, uint32_t elems_per_thread) {
+    oblivgm_status st = check_ctx(ctx);
+    if (st) return st;
+    const uint32_t t = threads ? threads : ctx->threads;
+    const uint32_t e = elems_per_thread ? elems_per_thread : ctx->elems_per_thread;
+    if (e != 1 && e != 2 && e != 4) return fail(OBLIVGM_EINVAL, "elems_per_thread must be 1, 2 or 4");
+    const uint32_t tmax = e == 1 ? max_threads<1>() : max_threads<4>();
+    if (t % 32 || t < 32 || t > tmax) return fail(OBLIVGM_EINVAL, "threads must be a multiple of 32, at most 1024 (E = 1) or 512 (E = 2, 4)");
+    ctx->threads = t;
+    ctx->elems_per_thread = e;
+    return OBLIVGM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,101 @@
+// runtime.h -- host runtime state of an oblivgm context: resident tables,
+// schedule, fault flag, and the serving loop (admission by memory, continuous
+// batching of admitted queries into shared launches).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "host_crypto.h"
+#include "oblivgm.h"
+
+namespace ogm {
+
+struct Table {
+    uint32_t* dev = nullptr;   // [share set j][attr][stride] uint32
+    uint64_t n_elems = 0;
+    uint64_t stride = 0;       // n_elems rounded up to a multiple of 4
+    uint32_t n_attrs = 0;
+    uint32_t n_bits = 0;
+    size_t bytes = 0;
+};
+
+struct ServeQuery {
+    uint64_t ticket = 0;
+    ParsedQuery parsed;
+    uint32_t n_groups = 0;
+    std::map<uint32_t, Table> tables;   // snapshot of the tables it reads
+    std::vector<uint32_t*> outs;        // 3 * n_groups device arrays
+    std::vector<uint64_t> n_elems;      // per group
+    std::vector<uint32_t> group_table;  // per group
+    size_t bytes = 0;
+    double t_submit = 0, t_done = 0;
+    int state = 0;                      // 0 queued, 1 on the device, 2 done, 3 failed
+    int stream = 0;
+    std::string error;
+};
+
+struct ServeBatch;
+
+struct ServeState {
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<uint64_t> queued;
+    std::map<uint64_t, std::unique_ptr<ServeQuery>> queries;
+    std::map<uint32_t, int> table_refs;
+    uint64_t next_ticket = 1;
+    uint64_t arena = 0, reserved = 0;
+    uint32_t max_inflight = 64, inflight = 0;
+    uint64_t admitted = 0, completed = 0, rejected = 0;
+    int running_batches = 0;
+    bool stop = false;
+    static constexpr int kStreams = 2;
+    cudaStream_t streams[kStreams] = {};
+    std::thread worker;
+};
+
+}  // namespace ogm
+
+struct oblivgm_ctx {
+    int device = 0;
+    int sm_count = 0;
+    oblivgm_config cfg{};
+    ogm::AesParams aes{};
+    uint32_t rk_prf[3][44] = {};
+    uint32_t* d_te0 = nullptr;
+    uint32_t* d_error = nullptr;
+    void* h_stage = nullptr;
+    std::map<uint32_t, ogm::Table> tables;
+    uint32_t threads = 256;
+    uint32_t elems_per_thread = 4;
+    std::atomic<uint64_t> launches{0};
+    ogm::ServeState serve;
+};
+
+namespace ogm {
+
+oblivgm_status fail(oblivgm_status st, const std::string& msg);
+oblivgm_status cuda_fail(cudaError_t e, const char* what);
+
+struct Plan;
+oblivgm_status serve_init(oblivgm_ctx* ctx);
+void serve_shutdown(oblivgm_ctx* ctx);
+bool table_in_use(oblivgm_ctx* ctx, uint32_t table_id);
+
+// plan + launch of the fused kernel over already-parsed queries (used by the serving loop)
+oblivgm_status launch_parsed(oblivgm_ctx* ctx, uint32_t n_queries, const uint32_t* query_ids,
+                             const ParsedQuery* parsed, const uint32_t* n_groups, uint32_t* const* const* outs,
+                             const std::map<uint32_t, Table>& tables, cudaStream_t st);
+
+double now_ms();
+
+}  // namespace ogm

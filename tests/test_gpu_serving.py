@@ -1,0 +1,99 @@
+"""Serving loop on the GPU: admission, continuous batching, and that each
+query's result is the same alone and in the mix (bit-exact)."""
+import time
+
+import numpy as np
+import pytest
+
+import workload as W
+from tests._helpers import PRF, alloc_outs, load_tables
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+P = pytest.importorskip("paper_2209_03526_gb300")
+
+
+@pytest.fixture(scope="module")
+def served():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = P.Context(0, prf_keys=PRF, serve_max_inflight=8)
+    graph = W.edge_graph(20000, 80000, 4, 2, seed=41)
+    load_tables(c, graph)
+    yield c, graph
+    c.close()
+
+
+def _result_tensors(res):
+    out = []
+    for g in res["groups"]:
+        out.append([P.device_words(p, g["n_elems"]).clone() for p in g["shares"]])
+    return out
+
+
+def test_served_results_equal_alone(served):
+    ctx, graph = served
+    qs = W.query_mix(graph, 12, seed=42)
+    toks = [P.keygen(q["preds"], 32, bytes([i + 1]) * 16) for i, q in enumerate(qs)]
+    tickets = []
+    pending = list(range(len(qs)))
+    results = {}
+    # submit in waves: later queries arrive while earlier ones are on the device
+    while pending or tickets:
+        while pending:
+            try:
+                tk = ctx.submit(toks[pending[0]])
+            except P.OblivgmError as e:
+                assert e.status == P.EAGAIN
+                break
+            tickets.append((tk, pending.pop(0)))
+        tk, qi = tickets.pop(0)
+        res = ctx.poll(tk, timeout_ms=60000)
+        assert res is not None and res["latency_ms"] >= 0
+        results[qi] = (tk, _result_tensors(res))
+        ctx.release(tk)
+    stats = ctx.serve_stats()
+    assert stats["completed"] >= len(qs) and stats["reserved_bytes"] == 0
+    for qi, (tk, got) in results.items():
+        outs = alloc_outs(graph, preds=qs[qi]["preds"])
+        ctx.filter_and_combine(tk & 0xFFFFFFFF, toks[qi], outs)
+        torch.cuda.synchronize()
+        for ga, gb in zip(got, outs):
+            for ta, tb in zip(ga, gb):
+                assert torch.equal(ta, tb), qi
+
+
+def test_admission_by_slots(served):
+    ctx, graph = served
+    q = W.query_mix(graph, 1, seed=43)[0]
+    tok = P.keygen(q["preds"], 32, bytes(16))
+    tks = []
+    rejected = 0
+    for _ in range(12):
+        try:
+            tks.append(ctx.submit(tok))
+        except P.OblivgmError as e:
+            assert e.status == P.EAGAIN
+            rejected += 1
+    assert len(tks) == 8 and rejected == 4
+    for tk in tks:
+        assert ctx.poll(tk, timeout_ms=60000) is not None
+        ctx.release(tk)
+    with pytest.raises(P.OblivgmError) as e:
+        ctx.poll(tks[0], 0)
+    assert e.value.status == P.ENOENT
+
+
+def test_poll_timeout_and_unknown_ticket(served):
+    ctx, graph = served
+    with pytest.raises(P.OblivgmError) as e:
+        ctx.poll(987654321, 0)
+    assert e.value.status == P.ENOENT
+    q = W.query_mix(graph, 1, seed=44)[0]
+    tk = ctx.submit(P.keygen(q["preds"], 32, bytes(16)))
+    r = ctx.poll(tk, 0)            # may or may not be done already; must not block
+    t0 = time.time()
+    r = ctx.poll(tk, 60000)
+    assert r is not None and time.time() - t0 < 60
+    ctx.release(tk)

@@ -1,0 +1,95 @@
+"""Host-side checks of the C-ABI library (no GPU): it loads, exports every
+declared entry point, and its client-side token generation is byte-identical
+to the oracle's independent implementation of the same construction."""
+import re
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2209_03526_gb300 as P
+import workload as W
+from paper_2209_03526_gb300 import _native as N
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            txt = open(os.path.join(inc, f)).read()
+            names |= set(re.findall(r"^\s*(?:oblivgm_status|uint32_t|uint64_t)\s+(oblivgm_\w+)\s*\(", txt, re.M))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = N.load()
+    declared = _declared()
+    assert len(declared) >= 19
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(N._SIGS) == declared
+
+
+def test_version():
+    assert P.version() == 0x000100
+
+
+def _random_preds(g, n, k, n_tables=2):
+    preds = []
+    top = (1 << n) - 1
+    for i in range(k):
+        t = int(g.integers(0, n_tables))
+        if g.random() < 0.5:
+            preds.append(W.eq_pred(t, int(g.integers(0, 4)), int(g.integers(0, 3)), int(g.integers(0, top + 1))))
+        else:
+            lo, hi = sorted(int(v) for v in g.integers(0, top + 1, 2))
+            preds.append(W.range_pred(t, int(g.integers(0, 4)), int(g.integers(0, 3)), lo, hi))
+    return preds
+
+
+@pytest.mark.parametrize("n", [1, 5, 16, 31, 32])
+def test_keygen_byte_identical_to_oracle(n):
+    g = np.random.default_rng(n)
+    for trial in range(3):
+        preds = _random_preds(g, n, int(g.integers(1, 7)))
+        seed = bytes(g.integers(0, 256, 16, dtype=np.uint8))
+        assert P.keygen(preds, n, seed) == oracle.keygen(preds, n, seed)
+
+
+def test_keygen_full_domain_and_wrap_ranges_identical():
+    preds = [W.range_pred(0, 0, 0, 0, 0xFFFFFFFF), W.range_pred(0, 1, 0, 5, 5), W.eq_pred(0, 0, 1, 0xFFFFFFFF),
+             W.range_pred(1, 0, 2, 0xFFFFFF00, 0xFFFFFFFF)]
+    for s in range(4):
+        seed = bytes([s]) * 16
+        assert P.keygen(preds, 32, seed) == oracle.keygen(preds, 32, seed)
+
+
+def test_keygen_sizes_and_errors():
+    preds = [W.eq_pred(0, 0, 0, 3), W.range_pred(0, 0, 0, 1, 9)]
+    assert P.token_len(preds, 32) == 16 + (24 + 2 * 668) + (24 + 4 * 796)
+    with pytest.raises(P.OblivgmError) as e:
+        P.keygen([W.range_pred(0, 0, 0, 9, 1)], 8, bytes(16))
+    assert e.value.status == N.EINVAL
+    with pytest.raises(P.OblivgmError):
+        P.keygen([W.eq_pred(0, 0, 0, 300)], 8, bytes(16))
+    with pytest.raises(P.OblivgmError):
+        P.keygen([W.eq_pred(0, 0, 0, 3)], 33, bytes(16))
+    with pytest.raises(P.OblivgmError):
+        P.keygen([W.eq_pred(0, 0, 0, 3)] * 65, 8, bytes(16))
+
+
+def test_keygen_buffer_too_small_reports_size():
+    import ctypes
+    lib = N.load()
+    preds = [W.eq_pred(0, 0, 0, 3)]
+    arr = P._pred_array(preds)
+    bufs = [ctypes.create_string_buffer(10) for _ in range(3)]
+    ptrs = (N.c_vp * 3)(*[ctypes.addressof(b) for b in bufs])
+    lens = (N.c_size * 3)()
+    seed = ctypes.create_string_buffer(16)
+    st = lib.oblivgm_keygen(arr, 1, 8, ctypes.addressof(seed), ptrs, 10, lens)
+    assert st == N.ERANGE and lens[0] == P.token_len(preds, 8)
