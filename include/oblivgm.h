@@ -225,6 +225,33 @@ oblivgm_status oblivgm_filter_batch(oblivgm_ctx* ctx, uint32_t n_queries, const 
                                     const uint8_t* const* toks, const size_t* tok_lens, const uint32_t* n_groups,
                                     uint32_t* const* const* outs, void* stream);
 
+/* Same inputs, outputs and results as oblivgm_filter_and_combine, for
+ * callers that cannot allocate device memory while they run: code inside a
+ * region where every allocation was made up front (a fixed memory budget, a
+ * latency-critical serving thread), or a caller that has no business
+ * touching the allocator at all.  The ordinary entry point takes its
+ * per-call workspace (work-queue counter, descriptors and device keys) from
+ * cudaMallocAsync; this one takes it from one fixed device array of
+ * OBLIVGM_NOALLOC_SCRATCH_BYTES (256 KiB) compiled into the library, which
+ * every GPU that loads the library holds until the process exits.  The
+ * paper has no counterpart: it is an engineering variant only.
+ * Limits and rules:
+ *  - a query needing more workspace than the array (about 31 range or 62
+ *    equality predicates) is rejected with ERANGE before anything runs;
+ *  - the call makes no cudaMalloc/cudaFree or other device allocation (host
+ *    memory is still used to parse the tokens);
+ *  - all calls share the one array: the call overwrites it (and zeroes the
+ *    work counter) in stream order, so calls that can overlap on the GPU --
+ *    on different streams, or from several threads or contexts on the same
+ *    device -- race and give wrong results; issue them on one stream;
+ *  - the first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Errors as oblivgm_filter_and_combine, plus ERANGE. */
+#define OBLIVGM_NOALLOC_SCRATCH_BYTES (256u * 1024u)
+oblivgm_status oblivgm_filter_and_combine_noalloc(oblivgm_ctx* ctx, uint32_t query_id, const uint8_t* const tok[3],
+                                                  const size_t tok_len[3], uint32_t n_groups, uint32_t* const* out,
+                                                  void* stream);
+
 /* --------------------------------------------------------------- serving */
 
 /* Non-blocking admission of one query into the serving loop (continuous

@@ -173,6 +173,16 @@ class Context:
         N.check(self._lib.oblivgm_filter_and_combine(self._h, query_id, tp, tl, len(outs), arr,
                                                      _stream_handle(stream)), "oblivgm_filter_and_combine")
 
+    def filter_and_combine_noalloc(self, query_id: int, tokens, outs, stream=None):
+        """As filter_and_combine, with the workspace in the library's fixed device array
+        (no device allocation during the call; calls must not overlap on the GPU)."""
+        _, tp, tl = _tok_arrays(tokens)
+        flat = [t.data_ptr() for g in outs for t in g]
+        arr = (N.c_vp * len(flat))(*flat)
+        N.check(self._lib.oblivgm_filter_and_combine_noalloc(self._h, query_id, tp, tl, len(outs), arr,
+                                                             _stream_handle(stream)),
+                "oblivgm_filter_and_combine_noalloc")
+
     def filter_batch(self, query_ids, tokens_list, outs_list, stream=None):
         """Several queries in one persistent launch; outs_list[q] as in filter_and_combine."""
         nq = len(query_ids)

@@ -28,6 +28,7 @@ KEY_DPF, KEY_DCF = 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 ALL_PAIRS = 1
 MAX_GROUPS = 64
+NOALLOC_SCRATCH_BYTES = 256 * 1024
 
 STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EARCH: "EARCH", ERANGE: "ERANGE",
                 EBUSY: "EBUSY", EAGAIN: "EAGAIN", ETIMEOUT: "ETIMEOUT", ENOENT: "ENOENT",
@@ -63,6 +64,8 @@ _SIGS = {
     "oblivgm_eval_dcf_batch": ([c_vp, c_u8p, c_u32, c_vp, c_vp, c_u64, c_u32, c_vp, c_u64, c_vp], c_i32),
     "oblivgm_filter_and_combine": ([c_vp, c_u32, ctypes.POINTER(c_vp), ctypes.POINTER(c_size), c_u32,
                                     ctypes.POINTER(c_vp), c_vp], c_i32),
+    "oblivgm_filter_and_combine_noalloc": ([c_vp, c_u32, ctypes.POINTER(c_vp), ctypes.POINTER(c_size), c_u32,
+                                            ctypes.POINTER(c_vp), c_vp], c_i32),
     "oblivgm_filter_batch": ([c_vp, c_u32, ctypes.POINTER(c_u32), ctypes.POINTER(c_vp), ctypes.POINTER(c_size),
                               ctypes.POINTER(c_u32), ctypes.POINTER(c_vp), c_vp], c_i32),
     "oblivgm_submit": ([c_vp, ctypes.POINTER(c_vp), ctypes.POINTER(c_size), ctypes.POINTER(c_u64)], c_i32),

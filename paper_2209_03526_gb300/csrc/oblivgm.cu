@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -840,3 +841,103 @@ oblivgm_status oblivgm_set_schedule(oblivgm_ctx* ctx, uint32_t threads, uint32_t
 }
 
 }  // extern "C"
+
+// ====================================================================== no-allocation variant
+//
+// oblivgm_filter_and_combine_noalloc runs the same fused kernel as
+// oblivgm_filter_and_combine, but its per-call workspace (work-queue counter,
+// group and predicate descriptors, device keys, tile offsets) lives in the
+// fixed device array below instead of memory obtained with cudaMallocAsync.
+// It is for callers that must not allocate device memory at call time.  The
+// array is part of the loaded module: every GPU that loads this library holds
+// OBLIVGM_NOALLOC_SCRATCH_BYTES of it until the process exits.
+
+namespace ogm {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[OBLIVGM_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_addr[kMaxDevices] = {};   // device address of g_noalloc_scratch, per device
+
+// Once per device, with that device current: the host-side name of a __device__
+// array is only a stand-in, so ask the runtime for the array's device address.
+oblivgm_status scratch_address(int device, unsigned char** out) {
+    if (device < 0 || device >= kMaxDevices) return fail(OBLIVGM_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_addr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
+        g_scratch_addr[device] = p;
+    }
+    *out = static_cast<unsigned char*>(g_scratch_addr[device]);
+    return OBLIVGM_OK;
+}
+
+}  // namespace
+}  // namespace ogm
+
+extern "C" oblivgm_status oblivgm_filter_and_combine_noalloc(oblivgm_ctx* ctx, uint32_t query_id,
+                                                             const uint8_t* const tok[3], const size_t tok_len[3],
+                                                             uint32_t n_groups, uint32_t* const* out, void* stream) {
+    oblivgm_status st = check_ctx(ctx);   // also makes the context's device current
+    if (st) return st;
+    if (!tok || !tok_len || !out) return fail(OBLIVGM_EINVAL, "NULL argument");
+    ParsedQuery parsed;
+    std::string err;
+    st = parse_tokens(tok, tok_len, &parsed, &err);
+    if (st != OBLIVGM_OK) return fail(st, err);
+    uint32_t* const* outs[1] = {out};
+    Plan plan;
+    plan.elems_per_thread = ctx->elems_per_thread;
+    st = plan_queries(ctx->tables, 1, &query_id, &parsed, &n_groups, outs, ctx->threads * ctx->elems_per_thread,
+                      &plan);
+    if (st != OBLIVGM_OK) return st;
+    if (plan.item_start.back() == 0) return OBLIVGM_OK;
+    // workspace image: counter (zeroed every call) | groups | preds | keys | tile offsets
+    const size_t off_groups = 256;
+    const size_t off_preds = off_groups + (plan.groups.size() * sizeof(GroupDesc) + 255) / 256 * 256;
+    const size_t off_keys = off_preds + (plan.preds.size() * sizeof(PredDesc) + 255) / 256 * 256;
+    const size_t off_items = off_keys + (plan.keys.size() * sizeof(DevKey) + 255) / 256 * 256;
+    const size_t total = off_items + plan.item_start.size() * sizeof(uint64_t);
+    if (total > OBLIVGM_NOALLOC_SCRATCH_BYTES)
+        return fail(OBLIVGM_ERANGE, "query needs " + std::to_string(total) + " workspace bytes; the no-alloc entry point holds " +
+                                        std::to_string(OBLIVGM_NOALLOC_SCRATCH_BYTES));
+    unsigned char* ws = nullptr;
+    st = scratch_address(ctx->device, &ws);
+    if (st != OBLIVGM_OK) return st;
+    std::vector<unsigned char> img(total, 0);
+    std::memcpy(img.data() + off_groups, plan.groups.data(), plan.groups.size() * sizeof(GroupDesc));
+    std::memcpy(img.data() + off_preds, plan.preds.data(), plan.preds.size() * sizeof(PredDesc));
+    std::memcpy(img.data() + off_keys, plan.keys.data(), plan.keys.size() * sizeof(DevKey));
+    std::memcpy(img.data() + off_items, plan.item_start.data(), plan.item_start.size() * sizeof(uint64_t));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    OGM_CUDA(cudaMemcpyAsync(ws, img.data(), total, cudaMemcpyHostToDevice, s), "no-alloc workspace upload");
+    FilterParams P{};
+    P.aes = ctx->aes;
+    std::memcpy(P.rk_prf, ctx->rk_prf, sizeof P.rk_prf);
+    P.te0 = ctx->d_te0;
+    P.groups = reinterpret_cast<const GroupDesc*>(ws + off_groups);
+    P.preds = reinterpret_cast<const PredDesc*>(ws + off_preds);
+    P.keys = reinterpret_cast<const DevKey*>(ws + off_keys);
+    P.item_start = reinterpret_cast<const uint64_t*>(ws + off_items);
+    P.counter = reinterpret_cast<unsigned long long*>(ws);
+    P.error = ctx->d_error;
+    P.n_groups = (uint32_t)plan.groups.size();
+    P.tile = plan.tile;
+    const uint64_t n_items = plan.item_start.back();
+    const unsigned grid = (unsigned)std::min<uint64_t>(n_items, (uint64_t)ctx->sm_count);
+    const uint32_t E = plan.elems_per_thread, threads = plan.tile / plan.elems_per_thread;
+    switch (E) {
+        case 1: k_filter<1><<<grid, threads, kFilterSmem, s>>>(P); break;
+        case 2: k_filter<2><<<grid, threads, kFilterSmem, s>>>(P); break;
+        default: k_filter<4><<<grid, threads, kFilterSmem, s>>>(P); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "k_filter launch (no-alloc)");
+    ctx->launches++;
+    return OBLIVGM_OK;
+}
