@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -218,8 +219,11 @@ __global__ void __launch_bounds__(max_threads<E>(), 1) k_filter(const __grid_con
             if (P.item_start[mid] <= item) lo = mid; else hi = mid - 1;
         }
         const GroupDesc& G = P.groups[lo];
+        // threads past the tile width (a multiple of 32 E, so whole warps) stay idle
+        const bool in_tile = threadIdx.x * E < P.tile;
         const uint64_t e0 = (item - P.item_start[lo]) * P.tile + (uint64_t)threadIdx.x * E;
         const uint64_t n_elems = G.n_elems;
+        const bool warp_busy = __any_sync(0xFFFFFFFFu, in_tile && e0 < n_elems);
         const uint32_t table = G.table_id, query = G.query_id;
         uint32_t acc[3][E];
         for (uint32_t k = 0; k < G.n_preds; k++) {
@@ -237,6 +241,7 @@ __global__ void __launch_bounds__(max_threads<E>(), 1) k_filter(const __grid_con
                 mbar_wait_bounded(&mbar, phase ^ 1u, kWaitLimitNs);   // let an in-flight copy land
                 return;
             }
+            if (!warp_busy) continue;
             // open x^ = <x>_1 + <x>_2 + <x>_3 + <r>_1 + <r>_2 + <r>_3 mod 2^n
             const uint32_t mask = D.n_bits >= 32 ? 0xFFFFFFFFu : ((1u << D.n_bits) - 1u);
             uint32_t xh[E], sh[E];
@@ -304,8 +309,10 @@ __global__ void __launch_bounds__(max_threads<E>(), 1) k_filter(const __grid_con
                 }
             }
         }
+        if (in_tile) {
 #pragma unroll
-        for (int i = 0; i < 3; i++) store_col<E>(G.out[i], e0, n_elems, G.vec_out != 0, acc[i]);
+            for (int i = 0; i < 3; i++) store_col<E>(G.out[i], e0, n_elems, G.vec_out != 0, acc[i]);
+        }
         __syncthreads();
     }
 }
@@ -372,16 +379,51 @@ static oblivgm_status check_ctx(oblivgm_ctx* ctx) {
 // Build device descriptors of the given queries' groups (groups sorted by per-tile
 // cost, most expensive first) into one contiguous host image.
 struct Plan {
-    uint32_t tile = 0, elems_per_thread = 1;
+    uint32_t tile = 0, elems_per_thread = 1, threads = 0;
     std::vector<GroupDesc> groups;
     std::vector<PredDesc> preds;
     std::vector<DevKey> keys;
     std::vector<uint64_t> item_start;
 };
 
+// Element tile per work item.  The items (group, tile) are taken by one persistent CTA
+// per SM in cost order; a tile width that leaves the last wave half empty wastes the
+// idle SMs' time, so widths from step_elems up to max_tile (in steps of a warp's worth
+// of elements, down to half the CTA's width) are tried by simulating that greedy schedule, and the width with the
+// shortest makespan wins (the widest on ties).  Large item counts skip the search: their
+// tail is already a small fraction.
+template <typename NF, typename CF>
+uint32_t choose_tile(size_t n_groups, NF n_elems_of, CF cost_of, uint32_t max_tile, uint32_t step_elems, int sm_count) {
+    uint64_t items_at_max = 0;
+    for (size_t g = 0; g < n_groups; g++) items_at_max += (n_elems_of(g) + max_tile - 1) / max_tile;
+    if (items_at_max == 0 || items_at_max > 64ull * (uint64_t)sm_count || step_elems == 0) return max_tile;
+    uint32_t best_tile = max_tile;
+    double best = -1.0;
+    std::vector<double> finish;
+    const uint32_t min_tile = std::max(step_elems, max_tile / 2 / step_elems * step_elems);
+    for (uint32_t t = max_tile; t >= min_tile; t -= step_elems) {
+        finish.assign((size_t)sm_count, 0.0);
+        std::make_heap(finish.begin(), finish.end(), std::greater<double>());
+        for (size_t g = 0; g < n_groups; g++) {
+            const uint64_t n = n_elems_of(g);
+            for (uint64_t e = 0; e < n; e += t) {
+                const uint64_t width = std::min<uint64_t>(t, n - e);
+                const uint64_t warps_elems = (width + 31) / 32 * 32;
+                std::pop_heap(finish.begin(), finish.end(), std::greater<double>());
+                finish.back() += (double)cost_of(g) * (double)warps_elems;
+                std::push_heap(finish.begin(), finish.end(), std::greater<double>());
+            }
+        }
+        const double makespan = *std::max_element(finish.begin(), finish.end());
+        if (best < 0 || makespan < best * (1.0 - 1e-9)) { best = makespan; best_tile = t; }
+        if (t == min_tile) break;
+    }
+    return best_tile;
+}
+
 oblivgm_status plan_queries(const std::map<uint32_t, Table>& tables, uint32_t n_queries, const uint32_t* query_ids,
                             const ParsedQuery* parsed, const uint32_t* n_groups, uint32_t* const* const* outs,
-                            uint32_t tile, Plan* plan) {
+                            uint32_t tile, uint32_t step_elems, int sm_count, Plan* plan) {
     struct G { GroupDesc d; std::vector<const ParsedPred*> preds; uint64_t cost; };
     std::vector<G> all;
     for (uint32_t q = 0; q < n_queries; q++) {
@@ -425,6 +467,8 @@ oblivgm_status plan_queries(const std::map<uint32_t, Table>& tables, uint32_t n_
         }
     }
     std::stable_sort(all.begin(), all.end(), [](const G& a, const G& b) { return a.cost > b.cost; });
+    tile = choose_tile(all.size(), [&](size_t i) { return all[i].d.n_elems; }, [&](size_t i) { return all[i].cost; },
+                       tile, step_elems, sm_count);
     plan->groups.clear(); plan->preds.clear(); plan->keys.clear(); plan->item_start.clear();
     plan->tile = tile;
     uint64_t items = 0;
@@ -482,7 +526,7 @@ oblivgm_status launch_plan(oblivgm_ctx* ctx, const Plan& plan, cudaStream_t st, 
     P.tile = plan.tile;
     const uint64_t n_items = plan.item_start.back();
     const unsigned grid = (unsigned)std::min<uint64_t>(n_items, (uint64_t)ctx->sm_count);
-    const uint32_t E = plan.elems_per_thread, threads = plan.tile / plan.elems_per_thread;
+    const uint32_t E = plan.elems_per_thread, threads = plan.threads;
     cudaError_t e = cudaSuccess;
     switch (E) {
         case 1: k_filter<1><<<grid, threads, kFilterSmem, st>>>(P); break;
@@ -502,7 +546,9 @@ oblivgm_status launch_parsed(oblivgm_ctx* ctx, uint32_t n_queries, const uint32_
     Plan plan;
     const uint32_t threads = ctx->threads, E = ctx->elems_per_thread;
     plan.elems_per_thread = E;
-    oblivgm_status s = plan_queries(tables, n_queries, query_ids, parsed, n_groups, outs, threads * E, &plan);
+    plan.threads = threads;
+    oblivgm_status s = plan_queries(tables, n_queries, query_ids, parsed, n_groups, outs, threads * E, 32 * E,
+                                    ctx->sm_count, &plan);
     if (s != OBLIVGM_OK) return s;
     return launch_plan(ctx, plan, st, ctx->d_error);
 }
@@ -758,9 +804,10 @@ oblivgm_status oblivgm_filter_and_combine(oblivgm_ctx* ctx, uint32_t query_id, c
 oblivgm_status oblivgm_autotune(oblivgm_ctx* ctx, uint32_t* threads, uint32_t* elems_per_thread) {
     oblivgm_status st = check_ctx(ctx);
     if (st) return st;
-    // synthetic private table: 2^18 elements, one 32-bit attribute, one equality and one
-    // range predicate ANDed, so both walk kinds and the fold are in the timing
-    const uint64_t n = 1ull << 18;
+    // synthetic private table: 2^20 elements (every candidate shape gets at least one tile
+    // per SM), one 32-bit attribute, one equality and one range predicate ANDed, so both
+    // walk kinds and the fold are in the timing
+    const uint64_t n = 1ull << 20;
     std::vector<uint32_t> h(n);
     uint32_t x = 0x9E3779B9u;
     for (auto& v : h) { x ^= x << 13; x ^= x >> 17; x ^= x << 5; v = x; }
@@ -893,8 +940,9 @@ extern "C" oblivgm_status oblivgm_filter_and_combine_noalloc(oblivgm_ctx* ctx, u
     uint32_t* const* outs[1] = {out};
     Plan plan;
     plan.elems_per_thread = ctx->elems_per_thread;
+    plan.threads = ctx->threads;
     st = plan_queries(ctx->tables, 1, &query_id, &parsed, &n_groups, outs, ctx->threads * ctx->elems_per_thread,
-                      &plan);
+                      32 * ctx->elems_per_thread, ctx->sm_count, &plan);
     if (st != OBLIVGM_OK) return st;
     if (plan.item_start.back() == 0) return OBLIVGM_OK;
     // workspace image: counter (zeroed every call) | groups | preds | keys | tile offsets
@@ -930,7 +978,7 @@ extern "C" oblivgm_status oblivgm_filter_and_combine_noalloc(oblivgm_ctx* ctx, u
     P.tile = plan.tile;
     const uint64_t n_items = plan.item_start.back();
     const unsigned grid = (unsigned)std::min<uint64_t>(n_items, (uint64_t)ctx->sm_count);
-    const uint32_t E = plan.elems_per_thread, threads = plan.tile / plan.elems_per_thread;
+    const uint32_t E = plan.elems_per_thread, threads = plan.threads;
     switch (E) {
         case 1: k_filter<1><<<grid, threads, kFilterSmem, s>>>(P); break;
         case 2: k_filter<2><<<grid, threads, kFilterSmem, s>>>(P); break;
