@@ -296,6 +296,44 @@ def run_ours(args):
                     "steps": e2e_steps},
             "gpu_launches": launches,
             "clocks": clocks}
+    # ---- the plain per-query GPU path on the same step (same shares, parity-tested)
+    if not args.no_compare:
+        l0 = ctx.launch_count()
+        ctx.filter_plain(1, toks, outs, stream)          # warm-up
+        stream.synchronize()
+        plain_launches = ctx.launch_count() - l0
+        plain_s = time_plain(ctx, [toks], [outs], stream, reps=2)
+        line["plain_path"] = {"value": units / plain_s, "unit": UNIT, "ms_per_step": plain_s * 1e3,
+                              "gpu_launches_per_step": plain_launches,
+                              "what": "per predicate: open + one launch per key half (6 DPF / 12 DCF walks, "
+                                      "global-memory AES tables) + sum/re-share + AND launches",
+                              "fused_speedup": value / (units / plain_s)}
+        # ---- query latency under Poisson arrivals at half the fused path's measured capacity:
+        # 32 queries of 1-8 predicates (one AND-group) on the resident table, served by the
+        # serving loop (continuous batching) and by the plain path (FIFO)
+        g = W.rng(77)
+        tabs = wl["tables"]
+        qlist = []
+        for _ in range(32):
+            q = W.random_query(g, tabs, 32, int(g.integers(1, 9)), 1, vertex_table=0, edge_table=0)
+            qlist.append(q["preds"])
+        toks_q = [P.keygen(q, 32, bytes([i % 256]) * 16) for i, q in enumerate(qlist)]
+        table_n = {0: N_VERTICES}
+        svc = [query_aes(q, table_n) / (achieved_aes * 1e9) for q in qlist]
+        rate = 0.5 / float(np.mean(svc))
+        arrivals = np.cumsum(g.exponential(1.0 / rate, len(qlist)))
+        arrivals -= arrivals[0]
+        lat, tot, rej = serve_latency(ctx, toks_q, arrivals, P)
+        plain_outs = [query_outs(torch, dev, q, table_n) for q in qlist]
+        plat, ptot = plain_latency(ctx, toks_q, plain_outs, arrivals, stream)
+        del plain_outs
+        line["latency"] = {"queries": len(qlist), "arrival": "Poisson", "rate_qps": rate,
+                           "offered_load": "50% of fused capacity",
+                           "predicates_per_query": "1-8 (uniform), one AND-group on the resident table",
+                           "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "completed_qps": len(qlist) / tot,
+                           "rejected": rej,
+                           "plain_p50_ms": pct(plat, 50), "plain_p99_ms": pct(plat, 99),
+                           "plain_completed_qps": len(qlist) / ptot}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
@@ -343,6 +381,229 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def query_aes(preds, table_n, n_bits=32):
+    """Algorithmic AES blocks of one query: per AND-group, its per-element cost times its table's size."""
+    groups = {}
+    for p in preds:
+        groups.setdefault(p["group"], []).append(p)
+    return sum(aes_per_element(g, n_bits) * table_n[g[0]["table"]] for g in groups.values())
+
+
+def query_units(preds, table_n):
+    return sum(table_n[p["table"]] for p in preds)
+
+
+def query_outs(torch, dev, preds, table_n):
+    ng = max(p["group"] for p in preds) + 1
+    tab = {p["group"]: p["table"] for p in preds}
+    return [[torch.empty(table_n[tab[g]], dtype=torch.int32, device=dev) for _ in range(3)] for g in range(ng)]
+
+
+def serve_latency(ctx, toks_list, arrivals, P):
+    """Real-time arrivals through submit/poll/release.  Latency runs from a query's scheduled
+    arrival to the moment its completion is seen; a query the loop cannot admit yet waits in a
+    client-side backlog (counted as rejected once) and is resubmitted as results are released."""
+    from collections import deque
+    n = len(toks_list)
+    t0 = time.perf_counter()
+    nxt, done = 0, 0
+    backlog, inflight = deque(), {}
+    lat = [0.0] * n
+    rejected = set()
+    while done < n:
+        now = time.perf_counter() - t0
+        while nxt < n and arrivals[nxt] <= now:
+            backlog.append(nxt)
+            nxt += 1
+        while backlog:
+            i = backlog[0]
+            try:
+                tk = ctx.submit(toks_list[i])
+            except P.OblivgmError as e:
+                if e.status != P.EAGAIN:
+                    raise
+                rejected.add(i)
+                break
+            backlog.popleft()
+            inflight[tk] = i
+        progressed = False
+        for tk in list(inflight):
+            if ctx.poll(tk, 0) is not None:
+                i = inflight.pop(tk)
+                lat[i] = time.perf_counter() - t0 - arrivals[i]
+                ctx.release(tk)
+                done += 1
+                progressed = True
+        if not progressed:
+            if not inflight and not backlog and nxt < n:
+                time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
+            else:
+                time.sleep(0.0002)
+    return lat, time.perf_counter() - t0, len(rejected)
+
+
+def plain_latency(ctx, toks_list, outs_list, arrivals, stream):
+    """The plain per-query path as a FIFO server: one query at a time, in arrival order."""
+    t0 = time.perf_counter()
+    lat = []
+    for i, toks in enumerate(toks_list):
+        wait = arrivals[i] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        ctx.filter_plain(5000 + i, toks, outs_list[i], stream)
+        stream.synchronize()
+        lat.append(time.perf_counter() - t0 - arrivals[i])
+    return lat, time.perf_counter() - t0
+
+
+def pct(xs, q):
+    return float(np.percentile(np.asarray(xs) * 1e3, q))
+
+
+def time_plain(ctx, toks_list, outs_list, stream, reps=1):
+    """Seconds the plain path takes for the listed queries, run one after another."""
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        for i, toks in enumerate(toks_list):
+            ctx.filter_plain(7000 + i, toks, outs_list[i], stream)
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / 1e3 / reps
+
+
+def _load_graph(ctx, torch, dev, graph):
+    for tid, t in enumerate(graph["tables"]):
+        ctx.load_shares(tid, [torch.from_numpy(x.view(np.int32)).to(dev) for x in t["shares"]], t["bits"])
+    return {tid: t["values"].shape[1] for tid, t in enumerate(graph["tables"])}
+
+
+def _timed_graph(torch, ctx, plan, stream, warmup, steps):
+    """Capture one plan launch in a CUDA graph, replay it warmup + steps times, time the steps."""
+    for _ in range(max(1, warmup)):
+        ctx.plan_launch(plan, stream)
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ctx.plan_launch(plan, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.replay()
+        b.record()
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    return ms
+
+
+def run_workload(args):
+    """The other configurations, one JSON line each (not the headline line):
+    tiny   -- 1,000-vertex / 4,000-edge path query, n = 16 (parity-sized);
+    edges  -- 1,000,000 vertices / 10,000,000 edges, triangle + pendant, 6 predicates;
+    batch  -- 256 queries (2-8 vertices, 1-6 predicates) on that graph in one persistent
+              launch replayed from a CUDA graph, against the plain path on the first 8;
+    serve  -- 4,000,000 vertices / 40,000,000 edges resident, Poisson arrivals at 50, 200 and
+              1000 queries/s plus one rate at half the measured capacity."""
+    import torch
+    import paper_2209_03526_gb300 as P
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = P.Context(0, prf_keys=PRF)
+    sched = tuple(int(v) for v in args.schedule.split(",")) if args.schedule else ctx.autotune()
+    if args.schedule:
+        ctx.set_schedule(*sched)
+    peaks = measured_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_aes = sm_count * LDS_LANES_PER_CLK * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / LOOKUPS_PER_AES / 1e9
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "u32",
+            "data": "synthetic", "workload_mode": args.workload, "schedule": list(sched)}
+
+    if args.workload in ("tiny", "edges", "batch"):
+        if args.workload == "tiny":
+            wl = W.tiny_path(seed=1)
+            graph = {"tables": wl["tables"], "n_bits": 16}
+            queries = [{"preds": wl["preds"]}]
+            name = wl["name"]
+        elif args.workload == "edges":
+            graph = W.edge_graph(1_000_000, 10_000_000, 2, 2, seed=3)
+            queries = [W.triangle_pendant(graph, seed=3)]
+            name = "triangle_pendant_1Mv_10Me_6pred_n32"
+        else:
+            graph = W.edge_graph(1_000_000, 10_000_000, 4, 2, seed=4)
+            queries = W.query_mix(graph, 256, seed=4)
+            name = "query_mix_256q_1Mv_10Me_n32"
+        table_n = _load_graph(ctx, torch, dev, graph)
+        n_bits = graph["n_bits"]
+        toks = [P.keygen(q["preds"], n_bits, bytes([i % 256, i // 256]) + bytes(14)) for i, q in enumerate(queries)]
+        outs = [query_outs(torch, dev, q["preds"], table_n) for q in queries]
+        qids = list(range(1, len(queries) + 1))
+        units = sum(query_units(q["preds"], table_n) for q in queries)
+        aes = sum(query_aes(q["preds"], table_n, n_bits) for q in queries)
+        plan = ctx.plan_create(qids, toks, outs)
+        ms = _timed_graph(torch, ctx, plan, stream, args.warmup, args.steps)
+        ctx.plan_destroy(plan)
+        step_s = float(np.mean(ms)) / 1e3
+        t0 = time.perf_counter()
+        ctx.filter_batch(qids, toks, outs, stream)        # end to end: tokens from the host
+        stream.synchronize()
+        e2e_s = time.perf_counter() - t0
+        line.update({"value": units / step_s, "ms_per_step": step_s * 1e3, "steps": args.steps,
+                     "warmup": args.warmup,
+                     "config": {"workload": name, "queries": len(queries), "element_predicates_per_step": units,
+                                "aes_blocks_per_step": aes, "tables": {str(k): v for k, v in table_n.items()},
+                                "launch": "one persistent k_filter launch replayed from a CUDA graph"},
+                     "roofline": {"bound": "alu", "achieved": aes / step_s / 1e9, "peak": peak_aes,
+                                  "unit": "GAES/s", "frac": aes / step_s / 1e9 / peak_aes},
+                     "e2e": {"value": units / e2e_s, "unit": UNIT, "what": "filter_batch from host tokens, "
+                             "outputs left on the device"}})
+        if not args.no_compare:
+            k = min(8, len(queries))
+            sub = list(range(k))
+            plan = ctx.plan_create([qids[i] for i in sub], [toks[i] for i in sub], [outs[i] for i in sub])
+            fms = _timed_graph(torch, ctx, plan, stream, 1, 2)
+            ctx.plan_destroy(plan)
+            ps = time_plain(ctx, [toks[i] for i in sub], [outs[i] for i in sub], stream)
+            u = sum(query_units(queries[i]["preds"], table_n) for i in sub)
+            line["plain_path"] = {"queries": k, "value": u / ps, "fused_value": u / (np.mean(fms) / 1e3),
+                                  "fused_speedup": ps / (np.mean(fms) / 1e3)}
+    else:
+        graph = W.edge_graph(4_000_000, 40_000_000, 4, 2, seed=5)
+        table_n = _load_graph(ctx, torch, dev, graph)
+        n_arr = args.serve_queries
+        queries = W.query_mix(graph, n_arr, seed=5)
+        toks = [P.keygen(q["preds"], 32, bytes([i % 256, i // 256]) + bytes(14)) for i, q in enumerate(queries)]
+        svc = [query_aes(q["preds"], table_n) / (peak_aes * 0.95e9) for q in queries]
+        capacity = 1.0 / float(np.mean(svc))
+        rates = [50.0, 200.0, 1000.0, 0.5 * capacity]
+        runs = []
+        g = W.rng(55)
+        for rate in rates:
+            arrivals = np.cumsum(g.exponential(1.0 / rate, n_arr))
+            arrivals -= arrivals[0]
+            lat, tot, rej = serve_latency(ctx, toks, arrivals, P)
+            units = sum(query_units(q["preds"], table_n) for q in queries)
+            run = {"rate_qps": rate, "queries": n_arr, "completed_qps": n_arr / tot, "p50_ms": pct(lat, 50),
+                   "p99_ms": pct(lat, 99), "rejected": rej, "element_predicates_per_s": units / tot}
+            if not args.no_compare:
+                k = min(args.plain_queries, n_arr)
+                pouts = [query_outs(torch, dev, queries[i]["preds"], table_n) for i in range(k)]
+                plat, ptot = plain_latency(ctx, toks[:k], pouts, arrivals[:k], stream)
+                del pouts
+                run.update({"plain_queries": k, "plain_p50_ms": pct(plat, 50), "plain_p99_ms": pct(plat, 99),
+                            "fused_p99_ms_same_queries": pct(lat[:k], 99)})
+            runs.append(run)
+        line.update({"value": runs[-1]["element_predicates_per_s"], "config": {
+            "workload": "serve_4Mv_40Me_mixed_queries_n32", "tables": {str(k): v for k, v in table_n.items()},
+            "queries": "2-8 vertices, 1-6 predicates", "estimated_capacity_qps": capacity},
+            "serving": runs})
+    ctx.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -351,6 +612,11 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain-path and latency comparisons")
+    ap.add_argument("--serve-queries", type=int, default=48, help="arrivals per rate in --workload serve")
+    ap.add_argument("--plain-queries", type=int, default=6, help="plain-path queries per rate in --workload serve")
+    ap.add_argument("--workload", choices=["bulk", "tiny", "edges", "batch", "serve"], default="bulk",
+                    help="bulk (default, the headline line); the others print their own line")
     ap.add_argument("--schedule", default="", help="threads,elems_per_thread (skips the autotuner)")
     ap.add_argument("--profile-case", action="store_true",
                     help="one small fused launch for ncu: 4,194,304 elements, 1 attribute, 1 equality + 1 range "
@@ -360,6 +626,8 @@ def main():
         return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "bulk":
+        return run_workload(args)
     return run_ours(args)
 
 

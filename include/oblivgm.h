@@ -225,6 +225,34 @@ oblivgm_status oblivgm_filter_batch(oblivgm_ctx* ctx, uint32_t n_queries, const 
                                     const uint8_t* const* toks, const size_t* tok_lens, const uint32_t* n_groups,
                                     uint32_t* const* const* outs, void* stream);
 
+/* Prepared batches for CUDA-graph capture.  oblivgm_plan_create parses the
+ * queries (arguments as oblivgm_filter_batch), fixes the launch shape and
+ * uploads descriptors and device keys into a plan-owned device buffer
+ * (synchronous; allocates).  oblivgm_plan_launch then only resets the plan's
+ * work counter and launches the fused kernel on `stream`: no host-side work,
+ * no allocation and no pageable copies, so it may be captured into a CUDA
+ * graph and replayed; every launch recomputes the same shares into the
+ * outputs given at creation (which must stay valid).  Launches of one plan
+ * must not overlap on the GPU.  oblivgm_plan_destroy synchronises the device
+ * and frees the plan.  Errors as oblivgm_filter_batch. */
+typedef struct oblivgm_plan oblivgm_plan;
+oblivgm_status oblivgm_plan_create(oblivgm_ctx* ctx, uint32_t n_queries, const uint32_t* query_ids,
+                                   const uint8_t* const* toks, const size_t* tok_lens, const uint32_t* n_groups,
+                                   uint32_t* const* const* outs, oblivgm_plan** plan);
+oblivgm_status oblivgm_plan_launch(oblivgm_plan* plan, void* stream);
+oblivgm_status oblivgm_plan_destroy(oblivgm_plan* plan);
+
+/* The plain per-query GPU path: the same computation and results as
+ * oblivgm_filter_and_combine (Alg. 3 + Eq. predEval + re-share + AND), but
+ * launched the straightforward way -- per predicate one mask-open launch, one
+ * launch per key half (6 DPF or 12 DCF walks, AES T-tables read from global
+ * memory, one element per thread), one sum-and-re-share launch and one AND
+ * launch -- with its scratch from cudaMallocAsync.  It is the comparison point
+ * of the fused kernel and is parity-tested like it.  Errors as
+ * oblivgm_filter_and_combine. */
+oblivgm_status oblivgm_filter_plain(oblivgm_ctx* ctx, uint32_t query_id, const uint8_t* const tok[3],
+                                    const size_t tok_len[3], uint32_t n_groups, uint32_t* const* out, void* stream);
+
 /* Same inputs, outputs and results as oblivgm_filter_and_combine, for
  * callers that cannot allocate device memory while they run: code inside a
  * region where every allocation was made up front (a fixed memory budget, a

@@ -173,6 +173,14 @@ class Context:
         N.check(self._lib.oblivgm_filter_and_combine(self._h, query_id, tp, tl, len(outs), arr,
                                                      _stream_handle(stream)), "oblivgm_filter_and_combine")
 
+    def filter_plain(self, query_id: int, tokens, outs, stream=None):
+        """The plain per-query path (one launch per key half, global-memory AES tables)."""
+        _, tp, tl = _tok_arrays(tokens)
+        flat = [t.data_ptr() for g in outs for t in g]
+        arr = (N.c_vp * len(flat))(*flat)
+        N.check(self._lib.oblivgm_filter_plain(self._h, query_id, tp, tl, len(outs), arr, _stream_handle(stream)),
+                "oblivgm_filter_plain")
+
     def filter_and_combine_noalloc(self, query_id: int, tokens, outs, stream=None):
         """As filter_and_combine, with the workspace in the library's fixed device array
         (no device allocation during the call; calls must not overlap on the GPU)."""
@@ -182,6 +190,41 @@ class Context:
         N.check(self._lib.oblivgm_filter_and_combine_noalloc(self._h, query_id, tp, tl, len(outs), arr,
                                                              _stream_handle(stream)),
                 "oblivgm_filter_and_combine_noalloc")
+
+    def _batch_args(self, query_ids, tokens_list, outs_list):
+        nq = len(query_ids)
+        keep = []
+        tok_ptrs = (N.c_vp * (3 * nq))()
+        tok_lens = (N.c_size * (3 * nq))()
+        for q, toks in enumerate(tokens_list):
+            for i in range(3):
+                b = ctypes.create_string_buffer(bytes(toks[i]), len(toks[i]))
+                keep.append(b)
+                tok_ptrs[3 * q + i] = ctypes.addressof(b)
+                tok_lens[3 * q + i] = len(toks[i])
+        ng = (N.c_u32 * nq)(*[len(o) for o in outs_list])
+        out_arrays = (N.c_vp * nq)()
+        for q, outs in enumerate(outs_list):
+            flat = [t.data_ptr() for g in outs for t in g]
+            a = (N.c_vp * len(flat))(*flat)
+            keep.append(a)
+            out_arrays[q] = ctypes.addressof(a)
+        qids = (N.c_u32 * nq)(*query_ids)
+        return keep, qids, tok_ptrs, tok_lens, ng, out_arrays
+
+    def plan_create(self, query_ids, tokens_list, outs_list):
+        """A prepared batch (oblivgm_plan_create); launch it with plan_launch, free with plan_destroy."""
+        keep, qids, tp, tl, ng, oa = self._batch_args(query_ids, tokens_list, outs_list)
+        h = N.c_vp()
+        N.check(self._lib.oblivgm_plan_create(self._h, len(query_ids), qids, tp, tl, ng, oa, ctypes.byref(h)),
+                "oblivgm_plan_create")
+        return h
+
+    def plan_launch(self, plan, stream=None):
+        N.check(self._lib.oblivgm_plan_launch(plan, _stream_handle(stream)), "oblivgm_plan_launch")
+
+    def plan_destroy(self, plan):
+        N.check(self._lib.oblivgm_plan_destroy(plan), "oblivgm_plan_destroy")
 
     def filter_batch(self, query_ids, tokens_list, outs_list, stream=None):
         """Several queries in one persistent launch; outs_list[q] as in filter_and_combine."""

@@ -64,6 +64,12 @@ _SIGS = {
     "oblivgm_eval_dcf_batch": ([c_vp, c_u8p, c_u32, c_vp, c_vp, c_u64, c_u32, c_vp, c_u64, c_vp], c_i32),
     "oblivgm_filter_and_combine": ([c_vp, c_u32, ctypes.POINTER(c_vp), ctypes.POINTER(c_size), c_u32,
                                     ctypes.POINTER(c_vp), c_vp], c_i32),
+    "oblivgm_plan_create": ([c_vp, c_u32, ctypes.POINTER(c_u32), ctypes.POINTER(c_vp), ctypes.POINTER(c_size),
+                             ctypes.POINTER(c_u32), ctypes.POINTER(c_vp), ctypes.POINTER(c_vp)], c_i32),
+    "oblivgm_plan_launch": ([c_vp, c_vp], c_i32),
+    "oblivgm_plan_destroy": ([c_vp], c_i32),
+    "oblivgm_filter_plain": ([c_vp, c_u32, ctypes.POINTER(c_vp), ctypes.POINTER(c_size), c_u32,
+                              ctypes.POINTER(c_vp), c_vp], c_i32),
     "oblivgm_filter_and_combine_noalloc": ([c_vp, c_u32, ctypes.POINTER(c_vp), ctypes.POINTER(c_size), c_u32,
                                             ctypes.POINTER(c_vp), c_vp], c_i32),
     "oblivgm_filter_batch": ([c_vp, c_u32, ctypes.POINTER(c_u32), ctypes.POINTER(c_vp), ctypes.POINTER(c_size),

@@ -27,62 +27,81 @@ __device__ __forceinline__ void fill_tables(uint32_t* tab, const uint32_t* __res
     }
 }
 
-// lookup of table TABLE at byte BYTE of column col
-template <int BYTE, int TABLE>
-__device__ __forceinline__ uint32_t tlu(const char* tab, uint32_t col, uint32_t lane4) {
-    const uint32_t off = __byte_perm(col, lane4, 0x5504u | (BYTE << 4));   // lane4 | byte << 8
-    return *reinterpret_cast<const uint32_t*>(tab + off + ((TABLE >> 1) * 65536 + (TABLE & 1) * 128));
-}
+// Table access policies.  SmemTab: the bank-replicated shared-memory tables above
+// (lookup of table TABLE at byte BYTE of column col).  GlobalTab: the four 1 KiB
+// tables read straight from global memory through L1 (the plain path's layout).
+struct SmemTab {
+    const char* T;
+    uint32_t lane4;
+    template <int BYTE, int TABLE>
+    __device__ __forceinline__ uint32_t lu(uint32_t col) const {
+        const uint32_t off = __byte_perm(col, lane4, 0x5504u | (BYTE << 4));   // lane4 | byte << 8
+        return *reinterpret_cast<const uint32_t*>(T + off + ((TABLE >> 1) * 65536 + (TABLE & 1) * 128));
+    }
+};
+
+struct GlobalTab {
+    const uint32_t* __restrict__ te;   // te[k * 256 + x] = rotl(Te0[x], 8 k)
+    template <int BYTE, int TABLE>
+    __device__ __forceinline__ uint32_t lu(uint32_t col) const {
+        return __ldg(te + TABLE * 256 + ((col >> (8 * BYTE)) & 0xFFu));
+    }
+};
 
 // One full AES round on four columns (SubBytes, ShiftRows, MixColumns, AddRoundKey).
-__device__ __forceinline__ void aes_round(const char* T, uint32_t l4, uint32_t c[4], uint32_t k0, uint32_t k1,
-                                          uint32_t k2, uint32_t k3) {
-    const uint32_t n0 = tlu<0, 0>(T, c[0], l4) ^ tlu<1, 1>(T, c[1], l4) ^ tlu<2, 2>(T, c[2], l4) ^ tlu<3, 3>(T, c[3], l4) ^ k0;
-    const uint32_t n1 = tlu<0, 0>(T, c[1], l4) ^ tlu<1, 1>(T, c[2], l4) ^ tlu<2, 2>(T, c[3], l4) ^ tlu<3, 3>(T, c[0], l4) ^ k1;
-    const uint32_t n2 = tlu<0, 0>(T, c[2], l4) ^ tlu<1, 1>(T, c[3], l4) ^ tlu<2, 2>(T, c[0], l4) ^ tlu<3, 3>(T, c[1], l4) ^ k2;
-    const uint32_t n3 = tlu<0, 0>(T, c[3], l4) ^ tlu<1, 1>(T, c[0], l4) ^ tlu<2, 2>(T, c[1], l4) ^ tlu<3, 3>(T, c[2], l4) ^ k3;
+template <class Tab>
+__device__ __forceinline__ void aes_round(const Tab& T, uint32_t c[4], uint32_t k0, uint32_t k1, uint32_t k2,
+                                          uint32_t k3) {
+    const uint32_t n0 = T.template lu<0, 0>(c[0]) ^ T.template lu<1, 1>(c[1]) ^ T.template lu<2, 2>(c[2]) ^ T.template lu<3, 3>(c[3]) ^ k0;
+    const uint32_t n1 = T.template lu<0, 0>(c[1]) ^ T.template lu<1, 1>(c[2]) ^ T.template lu<2, 2>(c[3]) ^ T.template lu<3, 3>(c[0]) ^ k1;
+    const uint32_t n2 = T.template lu<0, 0>(c[2]) ^ T.template lu<1, 1>(c[3]) ^ T.template lu<2, 2>(c[0]) ^ T.template lu<3, 3>(c[1]) ^ k2;
+    const uint32_t n3 = T.template lu<0, 0>(c[3]) ^ T.template lu<1, 1>(c[0]) ^ T.template lu<2, 2>(c[1]) ^ T.template lu<3, 3>(c[2]) ^ k3;
     c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
 }
 
 // S-box byte r of the final round comes from table (r + 3) % 4, whose byte r holds S[x].
-__device__ __forceinline__ uint32_t last_col(const char* T, uint32_t l4, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
-    const uint32_t x0 = tlu<0, 3>(T, a, l4), x1 = tlu<1, 0>(T, b, l4), x2 = tlu<2, 1>(T, c, l4), x3 = tlu<3, 2>(T, d, l4);
+template <class Tab>
+__device__ __forceinline__ uint32_t last_col(const Tab& T, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    const uint32_t x0 = T.template lu<0, 3>(a), x1 = T.template lu<1, 0>(b), x2 = T.template lu<2, 1>(c),
+                   x3 = T.template lu<3, 2>(d);
     return __byte_perm(__byte_perm(x0, x1, 0x3250u), __byte_perm(x2, x3, 0x7210u), 0x7610u);
 }
 
-__device__ __forceinline__ void aes_last(const char* T, uint32_t l4, uint32_t c[4], uint32_t k0, uint32_t k1,
-                                         uint32_t k2, uint32_t k3) {
-    const uint32_t n0 = last_col(T, l4, c[0], c[1], c[2], c[3]) ^ k0;
-    const uint32_t n1 = last_col(T, l4, c[1], c[2], c[3], c[0]) ^ k1;
-    const uint32_t n2 = last_col(T, l4, c[2], c[3], c[0], c[1]) ^ k2;
-    const uint32_t n3 = last_col(T, l4, c[3], c[0], c[1], c[2]) ^ k3;
+template <class Tab>
+__device__ __forceinline__ void aes_last(const Tab& T, uint32_t c[4], uint32_t k0, uint32_t k1, uint32_t k2,
+                                         uint32_t k3) {
+    const uint32_t n0 = last_col(T, c[0], c[1], c[2], c[3]) ^ k0;
+    const uint32_t n1 = last_col(T, c[1], c[2], c[3], c[0]) ^ k1;
+    const uint32_t n2 = last_col(T, c[2], c[3], c[0], c[1]) ^ k2;
+    const uint32_t n3 = last_col(T, c[3], c[0], c[1], c[2]) ^ k3;
     c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
 }
 
 // AES-128 under round keys rk ^ (m & d): m = 0 selects key A, m = ~0 key B.
-__device__ __forceinline__ void aes_sel(const char* T, uint32_t l4, const uint32_t* rk, const uint32_t* d, uint32_t m,
+template <class Tab>
+__device__ __forceinline__ void aes_sel(const Tab& T, const uint32_t* rk, const uint32_t* d, uint32_t m,
                                         const uint32_t in[4], uint32_t out[4]) {
     uint32_t c[4];
 #pragma unroll
     for (int j = 0; j < 4; j++) c[j] = in[j] ^ rk[j] ^ (m & d[j]);
 #pragma unroll
     for (int r = 1; r < 10; r++)
-        aes_round(T, l4, c, rk[4 * r] ^ (m & d[4 * r]), rk[4 * r + 1] ^ (m & d[4 * r + 1]),
+        aes_round(T, c, rk[4 * r] ^ (m & d[4 * r]), rk[4 * r + 1] ^ (m & d[4 * r + 1]),
                   rk[4 * r + 2] ^ (m & d[4 * r + 2]), rk[4 * r + 3] ^ (m & d[4 * r + 3]));
-    aes_last(T, l4, c, rk[40] ^ (m & d[40]), rk[41] ^ (m & d[41]), rk[42] ^ (m & d[42]), rk[43] ^ (m & d[43]));
+    aes_last(T, c, rk[40] ^ (m & d[40]), rk[41] ^ (m & d[41]), rk[42] ^ (m & d[42]), rk[43] ^ (m & d[43]));
 #pragma unroll
     for (int j = 0; j < 4; j++) out[j] = c[j];
 }
 
 // AES-128 under one key.
-__device__ __forceinline__ void aes_one(const char* T, uint32_t l4, const uint32_t* rk, const uint32_t in[4],
-                                        uint32_t out[4]) {
+template <class Tab>
+__device__ __forceinline__ void aes_one(const Tab& T, const uint32_t* rk, const uint32_t in[4], uint32_t out[4]) {
     uint32_t c[4];
 #pragma unroll
     for (int j = 0; j < 4; j++) c[j] = in[j] ^ rk[j];
 #pragma unroll
-    for (int r = 1; r < 10; r++) aes_round(T, l4, c, rk[4 * r], rk[4 * r + 1], rk[4 * r + 2], rk[4 * r + 3]);
-    aes_last(T, l4, c, rk[40], rk[41], rk[42], rk[43]);
+    for (int r = 1; r < 10; r++) aes_round(T, c, rk[4 * r], rk[4 * r + 1], rk[4 * r + 2], rk[4 * r + 3]);
+    aes_last(T, c, rk[40], rk[41], rk[42], rk[43]);
 #pragma unroll
     for (int j = 0; j < 4; j++) out[j] = c[j];
 }
@@ -90,9 +109,9 @@ __device__ __forceinline__ void aes_one(const char* T, uint32_t l4, const uint32
 // DPF Eval (BGI16) of one key at E inputs: per level one PRG call for the child
 // the input bit selects, the conditional correction, and at the end
 // (-1)^b (Convert(s) + t * CW_{n+1}).
-template <int E>
-__device__ __forceinline__ void dpf_walk(const char* T, uint32_t l4, const AesParams& A, const DevKey& K,
-                                         const uint32_t xh[E], uint32_t y[E]) {
+template <int E, class Tab>
+__device__ __forceinline__ void dpf_walk(const Tab& T, const AesParams& A, const DevKey& K, const uint32_t xh[E],
+                                         uint32_t y[E]) {
     uint32_t s[E][4], t[E];
     const uint32_t party = K.party;
 #pragma unroll
@@ -110,7 +129,7 @@ __device__ __forceinline__ void dpf_walk(const char* T, uint32_t l4, const AesPa
         for (int e = 0; e < E; e++) {
             const uint32_t dir = (xh[e] >> sh) & 1u;
             uint32_t o[4];
-            aes_sel(T, l4, A.rk_st, A.d_st, 0u - dir, s[e], o);
+            aes_sel(T, A.rk_st, A.d_st, 0u - dir, s[e], o);
 #pragma unroll
             for (int w = 0; w < 4; w++) o[w] ^= s[e][w];
             uint32_t tn = o[0] & 1u;
@@ -135,9 +154,9 @@ __device__ __forceinline__ void dpf_walk(const char* T, uint32_t l4, const AesPa
 // DCF Eval (BCG+21) of one key at E inputs: per level the seed/control block and
 // the value block of the selected child (two PRG calls on the same seed),
 // V += (-1)^b (Convert(v) + t * V_CW), then the final term.
-template <int E>
-__device__ __forceinline__ void dcf_walk(const char* T, uint32_t l4, const AesParams& A, const DevKey& K,
-                                         const uint32_t xh[E], uint32_t y[E]) {
+template <int E, class Tab>
+__device__ __forceinline__ void dcf_walk(const Tab& T, const AesParams& A, const DevKey& K, const uint32_t xh[E],
+                                         uint32_t y[E]) {
     uint32_t s[E][4], t[E], V[E];
     const uint32_t party = K.party;
 #pragma unroll
@@ -158,8 +177,8 @@ __device__ __forceinline__ void dcf_walk(const char* T, uint32_t l4, const AesPa
             const uint32_t dir = (xh[e] >> sh) & 1u;
             const uint32_t m = 0u - dir;
             uint32_t o[4], v[4];
-            aes_sel(T, l4, A.rk_st, A.d_st, m, s[e], o);
-            aes_sel(T, l4, A.rk_v, A.d_v, m, s[e], v);
+            aes_sel(T, A.rk_st, A.d_st, m, s[e], o);
+            aes_sel(T, A.rk_v, A.d_v, m, s[e], v);
             const uint32_t term = (v[0] ^ s[e][0]) + (t[e] ? vcw : 0u);
             V[e] += party ? 0u - term : term;
 #pragma unroll

@@ -127,8 +127,8 @@ constexpr int kFilterSmem = kTableBytes + kMaxKeysPerPred * (int)sizeof(DevKey);
 // re-share of a 3-out-of-3 sharing z into RSS: r_i = z_i + F(k_i, ctr) - F(k_{i-1}, ctr).
 // F(k_i) enters r_i with + and r_{i+1} with -; the loop over the three PRF keys is
 // kept rolled so the code holds one AES body per element.
-template <int E>
-__device__ __forceinline__ void reshare(const char* T, uint32_t l4, const FilterParams& P, const uint32_t z[3][E],
+template <int E, class Tab>
+__device__ __forceinline__ void reshare(const Tab& T, const uint32_t (&rk_prf)[3][44], const uint32_t z[3][E],
                                         uint32_t out[3][E], uint64_t e0, uint32_t step, uint32_t table,
                                         uint32_t query) {
 #pragma unroll
@@ -142,7 +142,7 @@ __device__ __forceinline__ void reshare(const char* T, uint32_t l4, const Filter
             const uint64_t el = e0 + (uint64_t)e;
             const uint32_t ctr[4] = {(uint32_t)el, (uint32_t)(el >> 32), step | (table << 16), query};
             uint32_t o[4];
-            aes_one(T, l4, P.rk_prf[i], ctr, o);
+            aes_one(T, rk_prf[i], ctr, o);
             const uint32_t f = o[0];
             out[0][e] += i == 0 ? f : (i == 2 ? 0u - f : 0u);
             out[1][e] += i == 1 ? f : (i == 0 ? 0u - f : 0u);
@@ -196,7 +196,7 @@ template <int E> constexpr int max_threads() { return E == 1 ? 1024 : 512; }
 template <int E>
 __global__ void __launch_bounds__(max_threads<E>(), 1) k_filter(const __grid_constant__ FilterParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
-    const char* T = reinterpret_cast<const char*>(smem);
+    const SmemTab T{reinterpret_cast<const char*>(smem), lane_offset()};
     DevKey* kbuf = reinterpret_cast<DevKey*>(smem + kTableBytes);
     __shared__ __align__(8) uint64_t mbar;
     __shared__ unsigned long long item_sh;
@@ -205,7 +205,6 @@ __global__ void __launch_bounds__(max_threads<E>(), 1) k_filter(const __grid_con
     if (threadIdx.x == 0) mbar_init(&mbar);
     __syncthreads();
 
-    const uint32_t l4 = lane_offset();
     uint32_t phase = 0;
     const uint64_t n_items = P.item_start[P.n_groups];
     for (;;) {
@@ -270,8 +269,8 @@ __global__ void __launch_bounds__(max_threads<E>(), 1) k_filter(const __grid_con
             for (int kk = 0; kk < n_keys; kk++) {
                 const DevKey& K = kbuf[kk];
                 uint32_t y[E];
-                if (eq) dpf_walk<E>(T, l4, P.aes, K, xh, y);
-                else dcf_walk<E>(T, l4, P.aes, K, xh, y);
+                if (eq) dpf_walk<E>(T, P.aes, K, xh, y);
+                else dcf_walk<E>(T, P.aes, K, xh, y);
                 // RANGE: the public constant c * beta' joins party 0's half once
                 const uint32_t add = (!eq && (kk % nsub) == 0 && K.party == 0) ? D.cbeta : 0u;
                 const int i = kk / (2 * nsub);
@@ -291,7 +290,7 @@ __global__ void __launch_bounds__(max_threads<E>(), 1) k_filter(const __grid_con
 #pragma unroll 1
             for (int pass = 0; pass < passes; pass++) {
                 uint32_t r[3][E];
-                reshare<E>(T, l4, P, z, r, e0, step, table, query);
+                reshare<E>(T, P.rk_prf, z, r, e0, step, table, query);
                 if (pass + 1 < passes) {
 #pragma unroll
                     for (int i = 0; i < 3; i++)
@@ -345,9 +344,9 @@ __global__ void __launch_bounds__(256) k_eval_raw(const __grid_constant__ RawPar
     const DevKey& K = P.keys[key];
     const uint32_t mask = K.n >= 32 ? 0xFFFFFFFFu : ((1u << K.n) - 1u);
     uint32_t x[1] = {P.points[i] & mask}, y[1];
-    const char* T = reinterpret_cast<const char*>(smem);
-    if (KIND == OBLIVGM_KEY_DPF) dpf_walk<1>(T, lane_offset(), P.aes, K, x, y);
-    else dcf_walk<1>(T, lane_offset(), P.aes, K, x, y);
+    const SmemTab T{reinterpret_cast<const char*>(smem), lane_offset()};
+    if (KIND == OBLIVGM_KEY_DPF) dpf_walk<1>(T, P.aes, K, x, y);
+    else dcf_walk<1>(T, P.aes, K, x, y);
     P.out[o] = y[0];
 }
 
@@ -601,6 +600,16 @@ oblivgm_status oblivgm_create(oblivgm_ctx** out, int32_t device, const oblivgm_c
     if (st != OBLIVGM_OK) { delete ctx; return st; }
     cudaError_t e = cudaMalloc(&ctx->d_te0, 256 * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemcpy(ctx->d_te0, aes_tables().te0, 256 * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_te4, 4 * 256 * sizeof(uint32_t));
+    if (e == cudaSuccess) {
+        uint32_t te4[4 * 256];
+        for (int k = 0; k < 4; k++)
+            for (int x = 0; x < 256; x++) {
+                const uint32_t v = aes_tables().te0[x];
+                te4[k * 256 + x] = k ? (v << (8 * k)) | (v >> (32 - 8 * k)) : v;
+            }
+        e = cudaMemcpy(ctx->d_te4, te4, sizeof te4, cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_error, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_error, 0, sizeof(uint32_t));
     if (e == cudaSuccess) {
@@ -627,6 +636,7 @@ oblivgm_status oblivgm_destroy(oblivgm_ctx* ctx) {
     cudaDeviceSynchronize();
     for (auto& kv : ctx->tables) cudaFree(kv.second.dev);
     if (ctx->d_te0) cudaFree(ctx->d_te0);
+    if (ctx->d_te4) cudaFree(ctx->d_te4);
     if (ctx->d_error) cudaFree(ctx->d_error);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     delete ctx;
@@ -987,5 +997,108 @@ extern "C" oblivgm_status oblivgm_filter_and_combine_noalloc(oblivgm_ctx* ctx, u
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "k_filter launch (no-alloc)");
     ctx->launches++;
+    return OBLIVGM_OK;
+}
+
+// ====================================================================== prepared plans (CUDA-graph capture)
+//
+// A plan holds a batch's descriptors and device keys in its own device buffer, so
+// launching it is only a counter reset and one kernel launch: no host work, no
+// allocation and no pageable copies, which is what stream capture into a CUDA graph
+// needs.  Replaying the plan recomputes the same shares into the same outputs.
+
+struct oblivgm_plan {
+    oblivgm_ctx* ctx = nullptr;
+    unsigned char* ws = nullptr;
+    FilterParams params{};
+    unsigned grid = 0;
+    uint32_t threads = 0, E = 1;
+    uint64_t n_items = 0;
+};
+
+extern "C" oblivgm_status oblivgm_plan_create(oblivgm_ctx* ctx, uint32_t n_queries, const uint32_t* query_ids,
+                                              const uint8_t* const* toks, const size_t* tok_lens,
+                                              const uint32_t* n_groups, uint32_t* const* const* outs,
+                                              oblivgm_plan** out_plan) {
+    oblivgm_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!out_plan || !query_ids || !toks || !tok_lens || !n_groups || !outs || n_queries == 0)
+        return fail(OBLIVGM_EINVAL, "NULL or empty argument");
+    *out_plan = nullptr;
+    std::vector<ParsedQuery> parsed(n_queries);
+    std::string err;
+    for (uint32_t q = 0; q < n_queries; q++) {
+        if (!outs[q]) return fail(OBLIVGM_EINVAL, "NULL output array");
+        st = parse_tokens(toks + 3 * q, tok_lens + 3 * q, &parsed[q], &err);
+        if (st != OBLIVGM_OK) return fail(st, err);
+    }
+    Plan plan;
+    plan.elems_per_thread = ctx->elems_per_thread;
+    plan.threads = ctx->threads;
+    st = plan_queries(ctx->tables, n_queries, query_ids, parsed.data(), n_groups, outs,
+                      ctx->threads * ctx->elems_per_thread, 32 * ctx->elems_per_thread, ctx->sm_count, &plan);
+    if (st != OBLIVGM_OK) return st;
+    const size_t off_groups = 256;
+    const size_t off_preds = off_groups + (plan.groups.size() * sizeof(GroupDesc) + 255) / 256 * 256;
+    const size_t off_keys = off_preds + (plan.preds.size() * sizeof(PredDesc) + 255) / 256 * 256;
+    const size_t off_items = off_keys + (plan.keys.size() * sizeof(DevKey) + 255) / 256 * 256;
+    const size_t total = off_items + plan.item_start.size() * sizeof(uint64_t);
+    std::vector<unsigned char> img(total, 0);
+    std::memcpy(img.data() + off_groups, plan.groups.data(), plan.groups.size() * sizeof(GroupDesc));
+    std::memcpy(img.data() + off_preds, plan.preds.data(), plan.preds.size() * sizeof(PredDesc));
+    std::memcpy(img.data() + off_keys, plan.keys.data(), plan.keys.size() * sizeof(DevKey));
+    std::memcpy(img.data() + off_items, plan.item_start.data(), plan.item_start.size() * sizeof(uint64_t));
+    auto* p = new (std::nothrow) oblivgm_plan();
+    if (!p) return fail(OBLIVGM_ENOMEM, "host allocation");
+    cudaError_t e = cudaMalloc(&p->ws, total);
+    if (e == cudaSuccess) e = cudaMemcpy(p->ws, img.data(), total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (p->ws) cudaFree(p->ws);
+        delete p;
+        return cuda_fail(e, "plan buffer");
+    }
+    p->ctx = ctx;
+    FilterParams& P = p->params;
+    P.aes = ctx->aes;
+    std::memcpy(P.rk_prf, ctx->rk_prf, sizeof P.rk_prf);
+    P.te0 = ctx->d_te0;
+    P.groups = reinterpret_cast<const GroupDesc*>(p->ws + off_groups);
+    P.preds = reinterpret_cast<const PredDesc*>(p->ws + off_preds);
+    P.keys = reinterpret_cast<const DevKey*>(p->ws + off_keys);
+    P.item_start = reinterpret_cast<const uint64_t*>(p->ws + off_items);
+    P.counter = reinterpret_cast<unsigned long long*>(p->ws);
+    P.error = ctx->d_error;
+    P.n_groups = (uint32_t)plan.groups.size();
+    P.tile = plan.tile;
+    p->n_items = plan.item_start.back();
+    p->grid = (unsigned)std::min<uint64_t>(p->n_items, (uint64_t)ctx->sm_count);
+    p->threads = plan.threads;
+    p->E = plan.elems_per_thread;
+    *out_plan = p;
+    return OBLIVGM_OK;
+}
+
+extern "C" oblivgm_status oblivgm_plan_launch(oblivgm_plan* p, void* stream) {
+    if (!p) return fail(OBLIVGM_EINVAL, "NULL plan");
+    if (p->n_items == 0) return OBLIVGM_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    OGM_CUDA(cudaMemsetAsync(p->ws, 0, sizeof(unsigned long long), s), "plan counter reset");
+    switch (p->E) {
+        case 1: k_filter<1><<<p->grid, p->threads, kFilterSmem, s>>>(p->params); break;
+        case 2: k_filter<2><<<p->grid, p->threads, kFilterSmem, s>>>(p->params); break;
+        default: k_filter<4><<<p->grid, p->threads, kFilterSmem, s>>>(p->params); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "k_filter launch (plan)");
+    p->ctx->launches++;
+    return OBLIVGM_OK;
+}
+
+extern "C" oblivgm_status oblivgm_plan_destroy(oblivgm_plan* p) {
+    if (!p) return OBLIVGM_OK;
+    cudaSetDevice(p->ctx->device);
+    cudaDeviceSynchronize();
+    cudaFree(p->ws);
+    delete p;
     return OBLIVGM_OK;
 }

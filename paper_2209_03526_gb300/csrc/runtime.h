@@ -38,6 +38,7 @@ struct ServeQuery {
     std::vector<uint64_t> n_elems;      // per group
     std::vector<uint32_t> group_table;  // per group
     size_t bytes = 0;
+    double est_aes = 0;                 // algorithmic AES blocks, for batch sizing
     double t_submit = 0, t_done = 0;
     int state = 0;                      // 0 queued, 1 on the device, 2 done, 3 failed
     int stream = 0;
@@ -57,6 +58,7 @@ struct ServeState {
     uint32_t max_inflight = 64, inflight = 0;
     uint64_t admitted = 0, completed = 0, rejected = 0;
     int running_batches = 0;
+    double batch_aes_target = 3e9;     // a batch closes once it holds this much work
     bool stop = false;
     static constexpr int kStreams = 2;
     cudaStream_t streams[kStreams] = {};
@@ -72,6 +74,7 @@ struct oblivgm_ctx {
     ogm::AesParams aes{};
     uint32_t rk_prf[3][44] = {};
     uint32_t* d_te0 = nullptr;
+    uint32_t* d_te4 = nullptr;   // the four T-tables, 4 x 256 words, for the plain path
     uint32_t* d_error = nullptr;
     void* h_stage = nullptr;
     std::map<uint32_t, ogm::Table> tables;

@@ -1,11 +1,12 @@
 // serve.cpp -- the serving loop of an oblivgm context.
 //
 // Queries are admitted by memory (their output share sets must fit in the
-// serve arena) and by slot count.  A worker thread takes every admitted query
-// that is not yet on the device and launches them together as one batch of the
-// fused kernel on one of two streams, so a batch formed while another runs is
-// launched at once and fills the SMs the running one releases (continuous
-// batching).  A host callback on the batch's stream marks its queries done.
+// serve arena) and by slot count.  A worker thread takes admitted queries in
+// arrival order into a batch until the batch holds enough work to fill the GPU
+// (about 3e9 AES blocks) and launches it as one fused kernel on one of two
+// streams; the next batch goes to the other stream at once and takes over the
+// SMs the running one releases (continuous batching).  A host callback on the
+// batch's stream marks its queries done.
 // Each query's shares depend only on its tokens, ticket and tables (the PRF
 // counters carry element, step, table and query id), never on the batch it ran
 // in.
@@ -58,11 +59,18 @@ void worker_main(oblivgm_ctx* ctx) {
     for (;;) {
         S.cv_work.wait(lk, [&] { return S.stop || (!S.queued.empty() && S.running_batches < ServeState::kStreams); });
         if (S.stop) break;
+        // take queued queries in arrival order until the batch holds enough work to fill the
+        // GPU: small queries share a launch, a large one runs on its own, and a query that
+        // arrives meanwhile starts in the next batch on the other stream
         std::vector<ServeQuery*> batch;
-        while (!S.queued.empty()) {
+        double work = 0;
+        while (!S.queued.empty() && work < S.batch_aes_target) {
             auto it = S.queries.find(S.queued.front());
             S.queued.pop_front();
-            if (it != S.queries.end() && it->second->state == 0) batch.push_back(it->second.get());
+            if (it != S.queries.end() && it->second->state == 0) {
+                batch.push_back(it->second.get());
+                work += it->second->est_aes;
+            }
         }
         if (batch.empty()) continue;
         const int si = next_stream;
@@ -184,6 +192,11 @@ oblivgm_status oblivgm_submit(oblivgm_ctx* ctx, const uint8_t* const tok[3], con
     for (uint32_t g = 0; g < ng; g++)
         if (q->group_table[g] == 0xFFFFFFFFu) return fail(OBLIVGM_EINVAL, "an AND-group has no predicate");
     q->outs.assign(3 * ng, nullptr);
+    for (const ParsedPred& p : q->parsed.preds) {
+        // FSS walks of the predicate plus its re-shares (and the AND's), per element
+        const double walks = p.kind == OBLIVGM_PRED_EQ ? 6.0 * p.n : 24.0 * p.n;
+        q->est_aes += (walks + 6.0) * (double)q->n_elems[p.group];
+    }
     q->bytes = 0;
     for (uint32_t g = 0; g < ng; g++) q->bytes += 3 * std::max<uint64_t>(q->n_elems[g], 4) * sizeof(uint32_t);
     ServeState& S = ctx->serve;

@@ -250,3 +250,70 @@ def test_full_size_bulk_filter_sampled(ctx):
                                        W.rng(7).integers(0, n, 250)]))
     want = oracle_group(oracle, wl, toks, 1, 0, sample, threads=16)
     assert np.array_equal(got[:, sample], want)
+
+
+def test_plain_path_equals_fused_and_oracle(ctx):
+    """The plain per-query path (one launch per key half, global-memory AES tables) gives the
+    same shares as the fused kernel and the oracle."""
+    wl = W.tiny_path(seed=1)
+    load_tables(ctx, wl)
+    toks = P.keygen(wl["preds"], 16, bytes(range(16)))
+    fused = alloc_outs(wl)
+    plain = alloc_outs(wl)
+    ctx.filter_and_combine(21, toks, fused)
+    ctx.filter_plain(21, toks, plain)
+    torch.cuda.synchronize()
+    for ga, gb in zip(fused, plain):
+        for ta, tb in zip(ga, gb):
+            assert torch.equal(ta, tb)
+    bulk = W.bulk_vertex_filter(n_vertices=2053, seed=6)
+    load_tables(ctx, bulk)
+    toks = P.keygen(bulk["preds"], 32, bytes(range(5, 21)))
+    plain = alloc_outs(bulk)
+    ctx.filter_plain(22, toks, plain)
+    torch.cuda.synchronize()
+    got = np.stack([from_dev(t) for t in plain[0]])
+    assert np.array_equal(got, oracle_group(oracle, bulk, toks, 22, 0, np.arange(2053), threads=16))
+
+
+def test_prepared_plan_and_cuda_graph_replay(ctx):
+    """A prepared batch launched directly, then captured into a CUDA graph and replayed twice,
+    gives the shares of filter_batch for the same queries."""
+    graph = W.edge_graph(6000, 20000, 4, 2, seed=61)
+    load_tables(ctx, graph)
+    qs = W.query_mix(graph, 5, seed=62)
+    qids = list(range(200, 205))
+    toks = [P.keygen(q["preds"], 32, bytes([i + 7]) * 16) for i, q in enumerate(qs)]
+    want = [alloc_outs(graph, preds=q["preds"]) for q in qs]
+    ctx.filter_batch(qids, toks, want)
+    torch.cuda.synchronize()
+    got = [alloc_outs(graph, preds=q["preds"]) for q in qs]
+
+    def same():
+        torch.cuda.synchronize()
+        return all(torch.equal(a, b) for qa, qb in zip(got, want) for ga, gb in zip(qa, qb) for a, b in zip(ga, gb))
+
+    def clear():
+        for q in got:
+            for grp in q:
+                for t in grp:
+                    t.fill_(-1)
+
+    plan = ctx.plan_create(qids, toks, got)
+    try:
+        s = torch.cuda.Stream()
+        ctx.plan_launch(plan, s)
+        s.synchronize()
+        assert same()
+        clear()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            ctx.plan_launch(plan, torch.cuda.current_stream())
+        for _ in range(2):
+            clear()
+            g.replay()
+            assert same()
+        ctx.sync()
+    finally:
+        ctx.plan_destroy(plan)
