@@ -320,6 +320,15 @@ oblivgm_status oblivgm_set_schedule(oblivgm_ctx* ctx, uint32_t threads, uint32_t
  * kernel of this context, ECUDA on a CUDA error; the flag is cleared. */
 oblivgm_status oblivgm_sync(oblivgm_ctx* ctx, void* stream);
 
+/* Failure-path test hook.  The next fused launch of this context (filter,
+ * batch or served batch) asks its first key-staging barrier for 16 bytes
+ * more than the copy delivers, so every CTA's bounded wait runs out after
+ * limit_us microseconds (1..2,000,000) instead of the normal 2 s.  Each CTA
+ * then records the fault and returns without touching its outputs, and
+ * oblivgm_sync reports EFAULT_DEVICE; the context stays usable.  Nothing
+ * faults, traps or spins without a bound.  For tests only. */
+oblivgm_status oblivgm_test_expire_next_wait(oblivgm_ctx* ctx, uint32_t limit_us);
+
 /* Count of this library's kernel launches so far on the context (for the
  * bench's launch accounting). */
 uint64_t oblivgm_launch_count(oblivgm_ctx* ctx);

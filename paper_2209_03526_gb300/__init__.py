@@ -283,6 +283,10 @@ class Context:
         N.check(self._lib.oblivgm_autotune(self._h, ctypes.byref(t), ctypes.byref(e)), "oblivgm_autotune")
         return t.value, e.value
 
+    def test_expire_next_wait(self, limit_us: int):
+        """Failure-path test hook: the next fused launch's key-staging waits run out after limit_us."""
+        N.check(self._lib.oblivgm_test_expire_next_wait(self._h, limit_us), "oblivgm_test_expire_next_wait")
+
     def set_schedule(self, threads: int = 0, elems_per_thread: int = 0):
         N.check(self._lib.oblivgm_set_schedule(self._h, threads, elems_per_thread), "oblivgm_set_schedule")
 

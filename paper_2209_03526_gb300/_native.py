@@ -80,6 +80,7 @@ _SIGS = {
     "oblivgm_serve_stats": ([c_vp] + [ctypes.POINTER(c_u64)] * 4, c_i32),
     "oblivgm_autotune": ([c_vp, ctypes.POINTER(c_u32), ctypes.POINTER(c_u32)], c_i32),
     "oblivgm_set_schedule": ([c_vp, c_u32, c_u32], c_i32),
+    "oblivgm_test_expire_next_wait": ([c_vp, c_u32], c_i32),
 }
 
 

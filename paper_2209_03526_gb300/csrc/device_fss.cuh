@@ -93,6 +93,32 @@ __device__ __forceinline__ void aes_sel(const Tab& T, const uint32_t* rk, const 
     for (int j = 0; j < 4; j++) out[j] = c[j];
 }
 
+// Word 0 (bytes 0..3) of AES-128 under rk ^ (m & d): the final round computes only the
+// output column it needs (4 lookups instead of 16).
+template <class Tab>
+__device__ __forceinline__ uint32_t aes_sel_w0(const Tab& T, const uint32_t* rk, const uint32_t* d, uint32_t m,
+                                               const uint32_t in[4]) {
+    uint32_t c[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) c[j] = in[j] ^ rk[j] ^ (m & d[j]);
+#pragma unroll
+    for (int r = 1; r < 10; r++)
+        aes_round(T, c, rk[4 * r] ^ (m & d[4 * r]), rk[4 * r + 1] ^ (m & d[4 * r + 1]),
+                  rk[4 * r + 2] ^ (m & d[4 * r + 2]), rk[4 * r + 3] ^ (m & d[4 * r + 3]));
+    return last_col(T, c[0], c[1], c[2], c[3]) ^ rk[40] ^ (m & d[40]);
+}
+
+// Word 0 of AES-128 under one key.
+template <class Tab>
+__device__ __forceinline__ uint32_t aes_one_w0(const Tab& T, const uint32_t* rk, const uint32_t in[4]) {
+    uint32_t c[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) c[j] = in[j] ^ rk[j];
+#pragma unroll
+    for (int r = 1; r < 10; r++) aes_round(T, c, rk[4 * r], rk[4 * r + 1], rk[4 * r + 2], rk[4 * r + 3]);
+    return last_col(T, c[0], c[1], c[2], c[3]) ^ rk[40];
+}
+
 // AES-128 under one key.
 template <class Tab>
 __device__ __forceinline__ void aes_one(const Tab& T, const uint32_t* rk, const uint32_t in[4], uint32_t out[4]) {
@@ -176,10 +202,10 @@ __device__ __forceinline__ void dcf_walk(const Tab& T, const AesParams& A, const
         for (int e = 0; e < E; e++) {
             const uint32_t dir = (xh[e] >> sh) & 1u;
             const uint32_t m = 0u - dir;
-            uint32_t o[4], v[4];
+            uint32_t o[4];
             aes_sel(T, A.rk_st, A.d_st, m, s[e], o);
-            aes_sel(T, A.rk_v, A.d_v, m, s[e], v);
-            const uint32_t term = (v[0] ^ s[e][0]) + (t[e] ? vcw : 0u);
+            const uint32_t v0 = aes_sel_w0(T, A.rk_v, A.d_v, m, s[e]);   // Convert(v) needs bytes 0..3 only
+            const uint32_t term = (v0 ^ s[e][0]) + (t[e] ? vcw : 0u);
             V[e] += party ? 0u - term : term;
 #pragma unroll
             for (int w = 0; w < 4; w++) o[w] ^= s[e][w];

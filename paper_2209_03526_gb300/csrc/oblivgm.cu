@@ -118,7 +118,9 @@ struct FilterParams {
     unsigned long long* counter;  // work queue head
     uint32_t* error;              // context fault flags
     uint32_t n_groups;
-    uint32_t tile;                // elements per item = blockDim.x * E
+    uint32_t tile;                // elements per item (a multiple of 32 E, at most blockDim.x * E)
+    uint64_t wait_limit_ns;       // bound of every key-staging wait
+    uint32_t expect_extra;        // failure-path test only: bytes expected beyond the copy (0 normally)
 };
 
 constexpr int kMaxKeysPerPred = 12;
@@ -141,9 +143,7 @@ __device__ __forceinline__ void reshare(const Tab& T, const uint32_t (&rk_prf)[3
         for (int e = 0; e < E; e++) {
             const uint64_t el = e0 + (uint64_t)e;
             const uint32_t ctr[4] = {(uint32_t)el, (uint32_t)(el >> 32), step | (table << 16), query};
-            uint32_t o[4];
-            aes_one(T, rk_prf[i], ctr, o);
-            const uint32_t f = o[0];
+            const uint32_t f = aes_one_w0(T, rk_prf[i], ctr);   // F keeps bytes 0..3
             out[0][e] += i == 0 ? f : (i == 2 ? 0u - f : 0u);
             out[1][e] += i == 1 ? f : (i == 0 ? 0u - f : 0u);
             out[2][e] += i == 2 ? f : (i == 1 ? 0u - f : 0u);
@@ -230,14 +230,14 @@ __global__ void __launch_bounds__(max_threads<E>(), 1) k_filter(const __grid_con
             __syncthreads();   // everyone is done with the previous predicate's keys
             if (threadIdx.x == 0) {
                 const uint32_t bytes = D.n_keys * (uint32_t)sizeof(DevKey);
-                mbar_expect_tx(&mbar, bytes);
+                mbar_expect_tx(&mbar, bytes + P.expect_extra);
                 bulk_g2s(kbuf, P.keys + D.key_begin, bytes, &mbar);
             }
-            const bool ok = mbar_wait_bounded(&mbar, phase, kWaitLimitNs);
+            const bool ok = mbar_wait_bounded(&mbar, phase, P.wait_limit_ns);
             phase ^= 1u;
             if (__syncthreads_or(!ok)) {
                 if (threadIdx.x == 0) atomicOr(P.error, kErrKeyWait);
-                mbar_wait_bounded(&mbar, phase ^ 1u, kWaitLimitNs);   // let an in-flight copy land
+                mbar_wait_bounded(&mbar, phase ^ 1u, P.wait_limit_ns);   // let an in-flight copy land
                 return;
             }
             if (!warp_busy) continue;
@@ -523,6 +523,12 @@ oblivgm_status launch_plan(oblivgm_ctx* ctx, const Plan& plan, cudaStream_t st, 
     P.error = error_flag;
     P.n_groups = (uint32_t)plan.groups.size();
     P.tile = plan.tile;
+    P.wait_limit_ns = kWaitLimitNs;
+    if (ctx->test_expire_next) {   // one-shot failure-path test (oblivgm_test_expire_next_wait)
+        P.expect_extra = 16;
+        P.wait_limit_ns = ctx->test_wait_limit_ns;
+        ctx->test_expire_next = false;
+    }
     const uint64_t n_items = plan.item_start.back();
     const unsigned grid = (unsigned)std::min<uint64_t>(n_items, (uint64_t)ctx->sm_count);
     const uint32_t E = plan.elems_per_thread, threads = plan.threads;
@@ -884,6 +890,15 @@ oblivgm_status oblivgm_autotune(oblivgm_ctx* ctx, uint32_t* threads, uint32_t* e
     return OBLIVGM_OK;
 }
 
+oblivgm_status oblivgm_test_expire_next_wait(oblivgm_ctx* ctx, uint32_t limit_us) {
+    oblivgm_status st = check_ctx(ctx);
+    if (st) return st;
+    if (limit_us == 0 || limit_us > 2000000) return fail(OBLIVGM_EINVAL, "limit must be 1..2000000 us");
+    ctx->test_wait_limit_ns = (uint64_t)limit_us * 1000ull;
+    ctx->test_expire_next = true;
+    return OBLIVGM_OK;
+}
+
 oblivgm_status oblivgm_set_schedule(oblivgm_ctx* ctx, uint32_t threads, uint32_t elems_per_thread) {
     oblivgm_status st = check_ctx(ctx);
     if (st) return st;
@@ -986,6 +1001,7 @@ extern "C" oblivgm_status oblivgm_filter_and_combine_noalloc(oblivgm_ctx* ctx, u
     P.error = ctx->d_error;
     P.n_groups = (uint32_t)plan.groups.size();
     P.tile = plan.tile;
+    P.wait_limit_ns = kWaitLimitNs;
     const uint64_t n_items = plan.item_start.back();
     const unsigned grid = (unsigned)std::min<uint64_t>(n_items, (uint64_t)ctx->sm_count);
     const uint32_t E = plan.elems_per_thread, threads = plan.threads;
@@ -1070,6 +1086,7 @@ extern "C" oblivgm_status oblivgm_plan_create(oblivgm_ctx* ctx, uint32_t n_queri
     P.error = ctx->d_error;
     P.n_groups = (uint32_t)plan.groups.size();
     P.tile = plan.tile;
+    P.wait_limit_ns = kWaitLimitNs;
     p->n_items = plan.item_start.back();
     p->grid = (unsigned)std::min<uint64_t>(p->n_items, (uint64_t)ctx->sm_count);
     p->threads = plan.threads;

@@ -42,9 +42,7 @@ __global__ void k_plain_walk(const __grid_constant__ AesParams A, const uint32_t
 __device__ __forceinline__ uint32_t prf(const GlobalTab& T, const uint32_t* rk, uint64_t el, uint32_t step,
                                         uint32_t table, uint32_t query) {
     const uint32_t ctr[4] = {(uint32_t)el, (uint32_t)(el >> 32), step | (table << 16), query};
-    uint32_t o[4];
-    aes_one(T, rk, ctr, o);
-    return o[0];
+    return aes_one_w0(T, rk, ctr);
 }
 
 // z_i = sum of server i's key-half outputs, then r_i = z_i + F(k_i) - F(k_{i-1})

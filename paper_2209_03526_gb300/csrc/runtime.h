@@ -81,6 +81,8 @@ struct oblivgm_ctx {
     uint32_t threads = 256;
     uint32_t elems_per_thread = 4;
     std::atomic<uint64_t> launches{0};
+    bool test_expire_next = false;      // failure-path test hook, one-shot
+    uint64_t test_wait_limit_ns = 0;
     ogm::ServeState serve;
 };
 

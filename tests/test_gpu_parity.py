@@ -317,3 +317,26 @@ def test_prepared_plan_and_cuda_graph_replay(ctx):
         ctx.sync()
     finally:
         ctx.plan_destroy(plan)
+
+
+def test_expired_device_wait_is_reported_and_context_survives(ctx):
+    """A bounded device wait that runs out (the test hook asks the key-staging barrier for
+    bytes that never come) is reported as EFAULT_DEVICE by sync, and the next call is correct."""
+    wl = W.bulk_vertex_filter(n_vertices=5000, seed=8)
+    load_tables(ctx, wl)
+    toks = P.keygen(wl["preds"][:2], 32, bytes(16))
+    outs = alloc_outs(wl, preds=wl["preds"][:2])
+    ctx.test_expire_next_wait(20000)            # 20 ms
+    ctx.filter_and_combine(3, toks, outs)
+    torch.cuda.synchronize()
+    with pytest.raises(P.OblivgmError) as e:
+        ctx.sync()
+    assert e.value.status == P.EFAULT_DEVICE
+    ctx.sync()                                   # the flag was cleared
+    ctx.filter_and_combine(3, toks, outs)
+    ctx.sync()
+    got = np.stack([from_dev(t) for t in outs[0]])
+    wl2 = dict(wl)
+    wl2["preds"] = wl["preds"][:2]
+    sample = np.array([0, 1, 4999, wl["target"]])
+    assert np.array_equal(got[:, sample], oracle_group(oracle, wl2, toks, 3, 0, sample))
