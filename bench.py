@@ -123,6 +123,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def make_reduce_max(dist_mod, device):
+    """max over ranks of a host float (all_reduce MAX on a one-element tensor)."""
+    def reduce_max(x: float) -> float:
+        import torch
+        t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+        dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+        return float(t.item())
+    return reduce_max
+
+
+def aggregate_ranks(local_seconds: float, units_per_step: int, steps: int, world: int, reduce_max=None):
+    """Whole-job throughput of weak-scaled replicas: every rank's units over the slowest rank's time."""
+    t = reduce_max(local_seconds) if reduce_max else local_seconds
+    return units_per_step * steps * world / t, t
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -242,12 +258,8 @@ def run_ours(args):
     ctx.sync(stream)
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_s = sum(step_ms) / 1e3
-    if pg:
-        t = torch.tensor([total_s], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = units * args.steps * world / total_s
+    reduce_max = make_reduce_max(pg, dev) if pg else None
+    value, total_s = aggregate_ranks(sum(step_ms) / 1e3, units, args.steps, world, reduce_max)
     ms_per_step = total_s / args.steps * 1e3
 
     # ---- end to end through the public API with host buffers (pinned), every step:
@@ -266,12 +278,7 @@ def run_ours(args):
             h.copy_(d, non_blocking=True)
         stream.synchronize()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if pg:
-        t = torch.tensor([e2e_s], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = units * e2e_steps * world / e2e_s
+    e2e_value, e2e_s = aggregate_ranks(time.perf_counter() - t0, units, e2e_steps, world, reduce_max)
 
     peaks = measured_peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count

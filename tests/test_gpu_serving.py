@@ -97,3 +97,28 @@ def test_poll_timeout_and_unknown_ticket(served):
     r = ctx.poll(tk, 60000)
     assert r is not None and time.time() - t0 < 60
     ctx.release(tk)
+
+
+def test_admission_by_memory():
+    """A query whose output share sets do not fit in the serve arena is not admitted; one that
+    fits is, and releasing it returns its bytes."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    g = W.rng(45)
+    tab = W.table(W.uniform_attrs(g, 1, 10000, 32), 32, g)
+    small = W.table(W.uniform_attrs(g, 1, 1000, 32), 32, g)
+    # 1,000-element group needs 12,000 B of outputs; 10,000 elements need 120,000 B
+    with P.Context(0, prf_keys=PRF, serve_arena_bytes=50000) as c:
+        from tests._helpers import to_dev
+        c.load_shares(0, [to_dev(s) for s in tab["shares"]], 32)
+        c.load_shares(1, [to_dev(s) for s in small["shares"]], 32)
+        big_tok = P.keygen([W.eq_pred(0, 0, 0, 5)], 32, bytes(16))
+        with pytest.raises(P.OblivgmError) as e:
+            c.submit(big_tok)
+        assert e.value.status == P.EAGAIN
+        tk = c.submit(P.keygen([W.eq_pred(1, 0, 0, 5)], 32, bytes(16)))
+        assert c.serve_stats()["reserved_bytes"] == 12000
+        assert c.poll(tk, 60000) is not None
+        c.release(tk)
+        st = c.serve_stats()
+        assert st["reserved_bytes"] == 0 and st["rejected"] == 1 and st["completed"] == 1
