@@ -79,6 +79,12 @@ def lib():
             l.orc_filter.argtypes = [u8p, u8p, u8p, ctypes.POINTER(ctypes.c_size_t), u32, u8p,
                                      ctypes.POINTER(_Table), u32, u32, u8p, u64, u8p]
             l.orc_pred_z.argtypes = [u8p, u8p, u8p, ctypes.POINTER(ctypes.c_size_t), u32, u32, u8p, u8p]
+            for g in (l.orc_dpf_gen_g, l.orc_dcf_gen_g):
+                g.argtypes = [ctypes.c_int, u32, u32, u8p, u8p, u8p, u8p, ctypes.c_int]
+                g.restype = None
+            l.orc_keygen_onehot.argtypes = l.orc_keygen.argtypes
+            l.orc_filter_onehot.argtypes = [u8p, u8p, u8p, ctypes.POINTER(ctypes.c_size_t), u32, u8p,
+                                            ctypes.POINTER(_Table), u32, u32, u8p, u64, u8p]
             l.orc_reshare.argtypes = [u8p, u8p, u8p, u64, u32, u32, u32]
             l.orc_init()
             _lib = l
@@ -130,6 +136,22 @@ def dcf_gen(n: int, alpha: int, beta: int, s0: bytes, s1: bytes):
     return _gen(lib().orc_dcf_gen, KIND_DCF, n, alpha, beta, s0, s1)
 
 
+def dpf_gen_z2(n: int, alpha: int, s0: bytes, s1: bytes):
+    """DPF Gen for f^=_{alpha,1} over Z_2 (the one-hot mode's output group)."""
+    L = key_len(KIND_DPF, n)
+    k0, k1 = ctypes.create_string_buffer(L), ctypes.create_string_buffer(L)
+    lib().orc_dpf_gen_g(n, alpha & MASK32, 1, _addr(_buf(s0)), _addr(_buf(s1)), _addr(k0), _addr(k1), 1)
+    return k0.raw, k1.raw
+
+
+def dcf_gen_z2(n: int, alpha: int, s0: bytes, s1: bytes):
+    """DCF Gen for g^<_{alpha,1} over Z_2."""
+    L = key_len(KIND_DCF, n)
+    k0, k1 = ctypes.create_string_buffer(L), ctypes.create_string_buffer(L)
+    lib().orc_dcf_gen_g(n, alpha & MASK32, 1, _addr(_buf(s0)), _addr(_buf(s1)), _addr(k0), _addr(k1), 1)
+    return k0.raw, k1.raw
+
+
 def dpf_eval(key: bytes, x: int) -> int:
     return lib().orc_dpf_eval(_addr(_buf(key)), x & MASK32)
 
@@ -172,6 +194,51 @@ def keygen(preds, n: int, seed: bytes):
     if rc != 0:
         raise ValueError(f"oracle keygen rejected the predicates (code {rc})")
     return tuple(b.raw for b in bufs)
+
+
+def keygen_onehot(preds, n: int, seed: bytes):
+    """Tokens of the one-hot mode (Sec. V-C as written): no mask, Z_2 keys with beta = 1."""
+    arr = _preds(preds)
+    L = token_len(preds, n)
+    bufs = [ctypes.create_string_buffer(L) for _ in range(3)]
+    rc = lib().orc_keygen_onehot(arr, len(preds), n, _addr(_buf(seed)), *[_addr(b) for b in bufs], L)
+    if rc != 0:
+        raise ValueError(f"oracle one-hot keygen rejected the predicates (code {rc})")
+    return tuple(b.raw for b in bufs)
+
+
+def filter_onehot(tokens, query_id: int, prf_keys: bytes, tables, group: int, elems) -> np.ndarray:
+    """One-hot secEval (Eq. predEval) + binary re-share + binary AND of one AND-group.
+
+    tables: list of (three uint32 arrays [n_attrs, n_elems, W], n_bits) of one-hot shares.
+    Returns the three binary RSS share sets as 0/1 values, shape (3, len(elems)).
+    """
+    elems = np.ascontiguousarray(elems, dtype=np.uint64)
+    arr = (_Table * len(tables))()
+    keep = []
+    for i, (shares, n_bits) in enumerate(tables):
+        shares = [np.ascontiguousarray(x, dtype=np.uint32) for x in shares]
+        keep.extend(shares)
+        arr[i].n_attrs, arr[i].n_elems = shares[0].shape[0], shares[0].shape[1]
+        arr[i].n_bits = n_bits
+        for j in range(3):
+            arr[i].share[j] = shares[j].ctypes.data
+    toks = [_buf(t) for t in tokens]
+    lens = (ctypes.c_size_t * 3)(*[len(t) for t in tokens])
+    out = np.zeros((3, len(elems)), dtype=np.uint32)
+    if len(elems):
+        rc = lib().orc_filter_onehot(*[_addr(t) for t in toks], lens, query_id, _addr(_buf(prf_keys)), arr,
+                                     len(tables), group, elems.ctypes.data, len(elems), out.ctypes.data)
+        if rc != 0:
+            raise ValueError(f"oracle one-hot filter failed (code {rc})")
+    del keep
+    return out
+
+
+def reconstruct_bits(shares) -> np.ndarray:
+    """XOR of the three binary share sets."""
+    s = np.asarray(shares, dtype=np.uint32)
+    return (s[0] ^ s[1] ^ s[2]) & 1
 
 
 def _tables(tables):

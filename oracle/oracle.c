@@ -189,15 +189,25 @@ static void put32(uint8_t* p, uint32_t v)
     p[0] = (uint8_t)v; p[1] = (uint8_t)(v >> 8); p[2] = (uint8_t)(v >> 16); p[3] = (uint8_t)(v >> 24);
 }
 
-/* Convert of a seed into Z_{2^32}: bytes 4..7, little-endian (byte 0 carries the control bit) */
-static uint32_t convert_seed(const uint8_t s[16]) { return le32(s + 4); }
+/* Output groups: 0 = Z_{2^32}, 1 = Z_2 (the one-hot mode of Sec. V-B/V-C, beta = 1 in Z_2).
+ * Convert of a seed: Z_{2^32} bytes 4..7 little-endian; Z_2 bit 1 of byte 0 (bit 0 of
+ * byte 0 is the control bit).  Z_2 arithmetic is Z_{2^32} arithmetic reduced mod 2, so
+ * the constructions below run unchanged and only stored words and outputs are masked. */
+#define GROUP_Z2_32 0
+#define GROUP_Z2 1
+static uint32_t group_mask(int group) { return group == GROUP_Z2 ? 1u : 0xFFFFFFFFu; }
 
-/* DCF value word of a child: bytes 0..3 of H_{K_vL or K_vR}(s) */
-static uint32_t value_word(int dir, const uint8_t s[16])
+static uint32_t convert_seed_g(const uint8_t s[16], int group)
+{
+    return group == GROUP_Z2 ? (uint32_t)((s[0] >> 1) & 1) : le32(s + 4);
+}
+
+/* DCF value of a child: Convert of H_{K_vL or K_vR}(s) -- bytes 0..3 (Z_{2^32}) or bit 0 of byte 0 (Z_2) */
+static uint32_t value_word_g(int dir, const uint8_t s[16], int group)
 {
     uint8_t v[16];
     prg_h(dir == 0 ? KEY_VL : KEY_VR, s, v);
-    return le32(v);
+    return group == GROUP_Z2 ? (uint32_t)(v[0] & 1) : le32(v);
 }
 
 /* i-th input bit, i = 1..n, most significant first */
@@ -219,23 +229,23 @@ static size_t level_bytes(int kind) { return kind == KIND_DPF ? 20u : 24u; }
 
 size_t orc_key_len(int kind, int n) { return 24u + (size_t)n * level_bytes(kind) + 4u; }
 
-static void write_header(uint8_t* k, int kind, int n, int b, const uint8_t seed[16])
+static void write_header(uint8_t* k, int kind, int n, int b, const uint8_t seed[16], int group)
 {
     memset(k, 0, 8);
-    k[0] = (uint8_t)kind; k[1] = (uint8_t)n; k[2] = (uint8_t)b; k[3] = 0;
+    k[0] = (uint8_t)kind; k[1] = (uint8_t)n; k[2] = (uint8_t)b; k[3] = (uint8_t)group;
     memcpy(k + 8, seed, 16);
 }
 
-/* DPF Gen(1^lambda, alpha, beta): keys k0, k1 from the root seeds s0, s1 */
-void orc_dpf_gen(int n, uint32_t alpha, uint32_t beta, const uint8_t s0[16], const uint8_t s1[16],
-                 uint8_t* k0, uint8_t* k1)
+/* DPF Gen(1^lambda, alpha, beta): keys k0, k1 from the root seeds s0, s1, output group `group` */
+void orc_dpf_gen_g(int n, uint32_t alpha, uint32_t beta, const uint8_t s0[16], const uint8_t s1[16],
+                   uint8_t* k0, uint8_t* k1, int group)
 {
     uint8_t s[2][16];
     int t[2] = {0, 1};
     memcpy(s[0], s0, 16);
     memcpy(s[1], s1, 16);
-    write_header(k0, KIND_DPF, n, 0, s0);
-    write_header(k1, KIND_DPF, n, 1, s1);
+    write_header(k0, KIND_DPF, n, 0, s0, group);
+    write_header(k1, KIND_DPF, n, 1, s1, group);
     for (int i = 1; i <= n; i++) {
         uint8_t sc[2][2][16];   /* [party][dir] */
         int tc[2][2];
@@ -261,17 +271,24 @@ void orc_dpf_gen(int n, uint32_t alpha, uint32_t beta, const uint8_t s0[16], con
             t[b] = tc[b][keep] ^ (t[b] & t_keep_cw);
         }
     }
-    uint32_t cw = beta - convert_seed(s[0]) + convert_seed(s[1]);
+    uint32_t cw = beta - convert_seed_g(s[0], group) + convert_seed_g(s[1], group);
     if (t[1]) cw = 0u - cw;
+    cw &= group_mask(group);
     size_t off = 24 + (size_t)n * level_bytes(KIND_DPF);
     put32(k0 + off, cw);
     put32(k1 + off, cw);
 }
 
+void orc_dpf_gen(int n, uint32_t alpha, uint32_t beta, const uint8_t s0[16], const uint8_t s1[16],
+                 uint8_t* k0, uint8_t* k1)
+{
+    orc_dpf_gen_g(n, alpha, beta, s0, s1, k0, k1, GROUP_Z2_32);
+}
+
 /* DPF Eval(b, k_b, x) -> share of beta * [x == alpha] */
 uint32_t orc_dpf_eval(const uint8_t* key, uint32_t x)
 {
-    int n = key[1], b = key[2];
+    int n = key[1], b = key[2], group = key[3];
     uint8_t s[16];
     int t = b;
     memcpy(s, key + 8, 16);
@@ -288,21 +305,21 @@ uint32_t orc_dpf_eval(const uint8_t* key, uint32_t x)
         memcpy(s, ns, 16);
         t = nt;
     }
-    uint32_t y = convert_seed(s) + (t ? le32(key + 24 + (size_t)n * level_bytes(KIND_DPF)) : 0u);
-    return b ? 0u - y : y;
+    uint32_t y = convert_seed_g(s, group) + (t ? le32(key + 24 + (size_t)n * level_bytes(KIND_DPF)) : 0u);
+    return (b ? 0u - y : y) & group_mask(group);
 }
 
-/* DCF Gen(1^lambda, alpha, beta): shares of beta * [x < alpha] */
-void orc_dcf_gen(int n, uint32_t alpha, uint32_t beta, const uint8_t s0[16], const uint8_t s1[16],
-                 uint8_t* k0, uint8_t* k1)
+/* DCF Gen(1^lambda, alpha, beta): shares of beta * [x < alpha], output group `group` */
+void orc_dcf_gen_g(int n, uint32_t alpha, uint32_t beta, const uint8_t s0[16], const uint8_t s1[16],
+                   uint8_t* k0, uint8_t* k1, int group)
 {
     uint8_t s[2][16];
     int t[2] = {0, 1};
     uint32_t v_alpha = 0;
     memcpy(s[0], s0, 16);
     memcpy(s[1], s1, 16);
-    write_header(k0, KIND_DCF, n, 0, s0);
-    write_header(k1, KIND_DCF, n, 1, s1);
+    write_header(k0, KIND_DCF, n, 0, s0, group);
+    write_header(k1, KIND_DCF, n, 1, s1, group);
     for (int i = 1; i <= n; i++) {
         uint8_t sc[2][2][16];
         int tc[2][2];
@@ -310,7 +327,7 @@ void orc_dcf_gen(int n, uint32_t alpha, uint32_t beta, const uint8_t s0[16], con
         for (int b = 0; b < 2; b++)
             for (int dir = 0; dir < 2; dir++) {
                 child(dir, s[b], sc[b][dir], &tc[b][dir]);
-                vc[b][dir] = value_word(dir, s[b]);
+                vc[b][dir] = value_word_g(dir, s[b], group);
             }
         int a = bit_of(alpha, n, i);
         int keep = a, lose = 1 - a;
@@ -330,7 +347,7 @@ void orc_dcf_gen(int n, uint32_t alpha, uint32_t beta, const uint8_t s0[16], con
             k[off + 16] = (uint8_t)tl_cw;
             k[off + 17] = (uint8_t)tr_cw;
             k[off + 18] = 0; k[off + 19] = 0;
-            put32(k + off + 20, v_cw);
+            put32(k + off + 20, v_cw & group_mask(group));
         }
         int t_keep_cw = keep == 0 ? tl_cw : tr_cw;
         for (int b = 0; b < 2; b++) {
@@ -338,17 +355,24 @@ void orc_dcf_gen(int n, uint32_t alpha, uint32_t beta, const uint8_t s0[16], con
             t[b] = tc[b][keep] ^ (t[b] & t_keep_cw);
         }
     }
-    uint32_t cw = convert_seed(s[1]) - convert_seed(s[0]) - v_alpha;
+    uint32_t cw = convert_seed_g(s[1], group) - convert_seed_g(s[0], group) - v_alpha;
     if (t[1]) cw = 0u - cw;
+    cw &= group_mask(group);
     size_t off = 24 + (size_t)n * level_bytes(KIND_DCF);
     put32(k0 + off, cw);
     put32(k1 + off, cw);
 }
 
+void orc_dcf_gen(int n, uint32_t alpha, uint32_t beta, const uint8_t s0[16], const uint8_t s1[16],
+                 uint8_t* k0, uint8_t* k1)
+{
+    orc_dcf_gen_g(n, alpha, beta, s0, s1, k0, k1, GROUP_Z2_32);
+}
+
 /* DCF Eval(b, k_b, x) -> share of beta * [x < alpha] */
 uint32_t orc_dcf_eval(const uint8_t* key, uint32_t x)
 {
-    int n = key[1], b = key[2];
+    int n = key[1], b = key[2], group = key[3];
     uint8_t s[16];
     int t = b;
     uint32_t v = 0;
@@ -359,7 +383,7 @@ uint32_t orc_dcf_eval(const uint8_t* key, uint32_t x)
         uint8_t ns[16];
         int nt;
         child(dir, s, ns, &nt);
-        uint32_t vw = value_word(dir, s);
+        uint32_t vw = value_word_g(dir, s, group);
         uint32_t term = vw + (t ? le32(cw + 20) : 0u);
         v += b ? 0u - term : term;
         if (t) {
@@ -369,9 +393,9 @@ uint32_t orc_dcf_eval(const uint8_t* key, uint32_t x)
         memcpy(s, ns, 16);
         t = nt;
     }
-    uint32_t term = convert_seed(s) + (t ? le32(key + 24 + (size_t)n * level_bytes(KIND_DCF)) : 0u);
+    uint32_t term = convert_seed_g(s, group) + (t ? le32(key + 24 + (size_t)n * level_bytes(KIND_DCF)) : 0u);
     v += b ? 0u - term : term;
-    return v;
+    return v & group_mask(group);
 }
 
 void orc_aes128(const uint8_t key[16], const uint8_t in[16], uint8_t out[16])
@@ -440,12 +464,21 @@ size_t orc_token_len(const orc_pred* preds, uint32_t n_preds, int n)
     return len;
 }
 
-/* returns 0, or -1 on an invalid predicate, -2 if a buffer is too small */
-int orc_keygen(const orc_pred* preds, uint32_t n_preds, int n, const uint8_t seed[16],
-               uint8_t* tok1, uint8_t* tok2, uint8_t* tok3, size_t cap)
+/*
+ * Token generation for both modes.  Masked mode (onehot = 0): a fresh mask r per
+ * predicate, keys for the shifted functions over Z_{2^32} with beta' = 3^{-1}.
+ * One-hot mode (onehot = 1, Sec. V-C as written): no mask, keys for the predicate
+ * itself over Z_2 with beta = 1, to be evaluated at every position of the one-hot
+ * encoding; the token header's group byte is 1 and every <r> field is 0.  The random
+ * stream then skips the mask block.  Returns 0, or -1 on an invalid predicate, -2 if a
+ * buffer is too small.
+ */
+static int keygen_impl(const orc_pred* preds, uint32_t n_preds, int n, const uint8_t seed[16],
+                       uint8_t* tok1, uint8_t* tok2, uint8_t* tok3, size_t cap, int onehot)
 {
     uint8_t* tok[3] = {tok1, tok2, tok3};
-    if (n < 1 || n > 32 || n_preds == 0 || n_preds > 64) return -1;
+    const int group = onehot ? GROUP_Z2 : GROUP_Z2_32;
+    if (n < 1 || n > (onehot ? 16 : 32) || n_preds == 0 || n_preds > 64) return -1;
     uint32_t m = mask_n(n);
     for (uint32_t p = 0; p < n_preds; p++) {
         const orc_pred* q = &preds[p];
@@ -464,20 +497,23 @@ int orc_keygen(const orc_pred* preds, uint32_t n_preds, int n, const uint8_t see
         uint8_t* h = tok[i];
         memset(h, 0, 16);
         put32(h, TOKEN_MAGIC);
-        h[4] = 1; h[5] = (uint8_t)(i + 1); h[6] = (uint8_t)n; h[7] = 0;
+        h[4] = 1; h[5] = (uint8_t)(i + 1); h[6] = (uint8_t)n; h[7] = (uint8_t)group;
         h[8] = (uint8_t)n_preds; h[9] = (uint8_t)(n_preds >> 8);
         put32(h + 12, (uint32_t)total);
     }
     size_t off = 16;
     for (uint32_t p = 0; p < n_preds; p++) {
         const orc_pred* q = &preds[p];
-        uint8_t blk[16];
-        rng_block(&g, blk);
-        uint32_t r = le32(blk) & m;
-        uint32_t rs[3];
-        rs[0] = le32(blk + 4) & m;
-        rs[1] = le32(blk + 8) & m;
-        rs[2] = (r - rs[0] - rs[1]) & m;
+        uint32_t r = 0, rs[3] = {0, 0, 0};
+        if (!onehot) {
+            uint8_t blk[16];
+            rng_block(&g, blk);
+            r = le32(blk) & m;
+            rs[0] = le32(blk + 4) & m;
+            rs[1] = le32(blk + 8) & m;
+            rs[2] = (r - rs[0] - rs[1]) & m;
+        }
+        const uint32_t beta = onehot ? 1u : BETA_PRIME;
         /* the functions of the three pairs */
         uint32_t a_eq = 0, a0 = 0, a1 = 0, cbeta = 0;
         if (q->kind == PRED_EQ) {
@@ -485,7 +521,7 @@ int orc_keygen(const orc_pred* preds, uint32_t n_preds, int n, const uint8_t see
         } else {
             a0 = (q->lo + r) & m;
             a1 = (q->hi + 1u + r) & m;
-            cbeta = a1 <= a0 ? BETA_PRIME : 0u;
+            cbeta = a1 <= a0 ? beta : 0u;
         }
         /* keys of pair j, party b: one DPF key or two DCF keys (a1 then a0) */
         size_t half_len = q->kind == PRED_EQ ? dpf_len : 2 * dcf_len;
@@ -495,15 +531,15 @@ int orc_keygen(const orc_pred* preds, uint32_t n_preds, int n, const uint8_t see
                 uint8_t s0[16], s1[16];
                 rng_block(&g, s0);
                 rng_block(&g, s1);
-                orc_dpf_gen(n, a_eq, BETA_PRIME, s0, s1, keys[j][0], keys[j][1]);
+                orc_dpf_gen_g(n, a_eq, beta, s0, s1, keys[j][0], keys[j][1], group);
             } else {
                 uint8_t s0[16], s1[16];
                 rng_block(&g, s0);
                 rng_block(&g, s1);
-                orc_dcf_gen(n, a1, BETA_PRIME, s0, s1, keys[j][0], keys[j][1]);
+                orc_dcf_gen_g(n, a1, beta, s0, s1, keys[j][0], keys[j][1], group);
                 rng_block(&g, s0);
                 rng_block(&g, s1);
-                orc_dcf_gen(n, a0, 0u - BETA_PRIME, s0, s1, keys[j][0] + dcf_len, keys[j][1] + dcf_len);
+                orc_dcf_gen_g(n, a0, 0u - beta, s0, s1, keys[j][0] + dcf_len, keys[j][1] + dcf_len, group);
             }
         }
         for (int i = 0; i < 3; i++) {
@@ -526,6 +562,18 @@ int orc_keygen(const orc_pred* preds, uint32_t n_preds, int n, const uint8_t see
     return 0;
 }
 
+int orc_keygen(const orc_pred* preds, uint32_t n_preds, int n, const uint8_t seed[16],
+               uint8_t* tok1, uint8_t* tok2, uint8_t* tok3, size_t cap)
+{
+    return keygen_impl(preds, n_preds, n, seed, tok1, tok2, tok3, cap, 0);
+}
+
+int orc_keygen_onehot(const orc_pred* preds, uint32_t n_preds, int n, const uint8_t seed[16],
+                      uint8_t* tok1, uint8_t* tok2, uint8_t* tok3, size_t cap)
+{
+    return keygen_impl(preds, n_preds, n, seed, tok1, tok2, tok3, cap, 1);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Server-side evaluation: secEval (Alg. 3), re-share (Sec. III-B), AND fold  */
 /* ------------------------------------------------------------------------ */
@@ -540,6 +588,7 @@ typedef struct {
 typedef struct {
     const uint8_t* rec[3];      /* the predicate's record in each server's token */
     int kind, n, table, attr, group;
+    int out_group;              /* 0 = Z_{2^32} (masked mode), 1 = Z_2 (one-hot mode) */
 } pred_view;
 
 static int parse_tokens(const uint8_t* const tok[3], const size_t tok_len[3], pred_view* pv, int max_preds)
@@ -547,6 +596,7 @@ static int parse_tokens(const uint8_t* const tok[3], const size_t tok_len[3], pr
     int np = -1, n = -1;
     for (int i = 0; i < 3; i++) {
         if (tok_len[i] < 16 || le32(tok[i]) != TOKEN_MAGIC || tok[i][4] != 1 || tok[i][5] != i + 1) return -1;
+        if (tok[i][7] != tok[0][7] || tok[i][7] > GROUP_Z2) return -1;
         if (le32(tok[i] + 12) != tok_len[i]) return -1;
         int this_np = tok[i][8] | (tok[i][9] << 8);
         if (np < 0) { np = this_np; n = tok[i][6]; }
@@ -567,6 +617,7 @@ static int parse_tokens(const uint8_t* const tok[3], const size_t tok_len[3], pr
         pv[p].table = r0[2] | (r0[3] << 8);
         pv[p].attr = r0[4] | (r0[5] << 8);
         pv[p].group = r0[6] | (r0[7] << 8);
+        pv[p].out_group = tok[0][7];
         for (int i = 0; i < 3; i++) {
             pv[p].rec[i] = tok[i] + off;
             if (memcmp(tok[i] + off, r0, 8) != 0) return -1;
@@ -626,7 +677,7 @@ int orc_filter(const uint8_t* tok1, const uint8_t* tok2, const uint8_t* tok3, co
     const uint8_t* tok[3] = {tok1, tok2, tok3};
     pred_view pv[64];
     int np = parse_tokens(tok, tok_len, pv, 64);
-    if (np < 0) return -1;
+    if (np < 0 || pv[0].out_group != GROUP_Z2_32) return -1;
     int members[64], nm = 0;
     for (int p = 0; p < np; p++)
         if ((uint32_t)pv[p].group == group) members[nm++] = p;
@@ -698,4 +749,121 @@ void orc_reshare(const uint8_t prf_keys[48], const uint32_t z[3], uint32_t out[3
     aes_ks prf_ks[3];
     for (int i = 0; i < 3; i++) key_expansion(prf_keys + 16 * i, &prf_ks[i]);
     reshare(prf_ks, z, out, elem, step, table, query);
+}
+
+/* ------------------------------------------------------------------------ */
+/* One-hot mode: secEval exactly as Eq. (predEval) writes it (Sec. V-D)      */
+/* ------------------------------------------------------------------------ */
+/*
+ * A value v of an n-bit attribute is the one-hot vector e_v in {0,1}^(2^n), shared
+ * in binary RSS: e_v = <e>_1 xor <e>_2 xor <e>_3 (Sec. V-B).  Storage: bit l of
+ * the vector is bit (l mod 32) of 32-bit word l / 32; share[j] holds, per attribute
+ * and element, W = max(1, 2^n / 32) words: share[j][(attr * n_elems + e) * W + w].
+ * Server CS_i evaluates its key halves at every public position l and computes
+ *   x = XOR_l Eval(k, l) AND <e>_j[l]
+ * with j = i for its first half and j = i + 1 for its second (pair j meets share j),
+ * XORs its two results, re-shares in binary RSS (F = bit 0 of AES_k(ctr)) and the
+ * group's predicates are ANDed with binary RSS multiplication.
+ */
+typedef struct {
+    uint64_t n_elems;
+    uint32_t n_attrs;
+    uint32_t n_bits;
+    const uint32_t* share[3];
+} orc_onehot_table;
+
+static uint32_t prf_bit(const aes_ks* k, uint64_t elem, uint32_t step, uint32_t table, uint32_t query)
+{
+    return prf(k, elem, step, table, query) & 1u;
+}
+
+static void reshare_bin(const aes_ks prf_ks[3], const uint32_t z[3], uint32_t out[3],
+                        uint64_t elem, uint32_t step, uint32_t table, uint32_t query)
+{
+    uint32_t f[3];
+    for (int i = 0; i < 3; i++) f[i] = prf_bit(&prf_ks[i], elem, step, table, query);
+    for (int i = 0; i < 3; i++) out[i] = z[i] ^ f[i] ^ f[(i + 2) % 3];
+}
+
+/* value of server i's key half h at public position l (0/1) */
+static uint32_t half_at(const pred_view* pv, int server, int h, uint32_t l)
+{
+    size_t dpf_len = orc_key_len(KIND_DPF, pv->n), dcf_len = orc_key_len(KIND_DCF, pv->n);
+    const uint8_t* rec = pv->rec[server];
+    if (pv->kind == PRED_EQ) return orc_dpf_eval(rec + 24 + (size_t)h * dpf_len, l);
+    const uint8_t* k_hi = rec + 24 + (size_t)h * 2 * dcf_len;
+    const uint8_t* k_lo = k_hi + dcf_len;
+    uint32_t y = orc_dcf_eval(k_hi, l) ^ orc_dcf_eval(k_lo, l);
+    if (k_hi[2] == 0) y ^= le32(rec + 16) & 1u;
+    return y;
+}
+
+#include <stdlib.h>
+
+int orc_filter_onehot(const uint8_t* tok1, const uint8_t* tok2, const uint8_t* tok3, const size_t tok_len[3],
+                      uint32_t query_id, const uint8_t prf_keys[48], const orc_onehot_table* tables,
+                      uint32_t n_tables, uint32_t group, const uint64_t* elems, uint64_t n_sel, uint32_t* out)
+{
+    const uint8_t* tok[3] = {tok1, tok2, tok3};
+    pred_view pv[64];
+    int np = parse_tokens(tok, tok_len, pv, 64);
+    if (np < 0 || pv[0].out_group != GROUP_Z2) return -1;
+    int members[64], nm = 0;
+    for (int p = 0; p < np; p++)
+        if ((uint32_t)pv[p].group == group) members[nm++] = p;
+    if (nm == 0) return -2;
+    int table = pv[members[0]].table;
+    for (int k = 0; k < nm; k++) {
+        const pred_view* q = &pv[members[k]];
+        if (q->table != table || (uint32_t)q->table >= n_tables) return -3;
+        if ((uint32_t)q->attr >= tables[table].n_attrs || (uint32_t)q->n != tables[table].n_bits) return -3;
+    }
+    const orc_onehot_table* T = &tables[table];
+    const uint32_t D = 1u << T->n_bits;
+    const uint32_t W = D >= 32 ? D / 32 : 1;
+    /* Eval of every key half at every public position, once per predicate */
+    uint8_t* ev = (uint8_t*)malloc((size_t)nm * 6 * D);
+    if (!ev) return -5;
+    for (int k = 0; k < nm; k++)
+        for (int i = 0; i < 3; i++)
+            for (int h = 0; h < 2; h++)
+                for (uint32_t l = 0; l < D; l++)
+                    ev[(((size_t)k * 3 + i) * 2 + h) * D + l] = (uint8_t)half_at(&pv[members[k]], i, h, l);
+    aes_ks prf_ks[3];
+    for (int i = 0; i < 3; i++) key_expansion(prf_keys + 16 * i, &prf_ks[i]);
+    for (uint64_t s = 0; s < n_sel; s++) {
+        uint64_t e = elems[s];
+        if (e >= T->n_elems) { free(ev); return -4; }
+        uint32_t acc[3] = {0, 0, 0};
+        for (int k = 0; k < nm; k++) {
+            int p = members[k];
+            const pred_view* q = &pv[p];
+            uint32_t z[3];
+            for (int i = 0; i < 3; i++) {
+                z[i] = 0;
+                for (int h = 0; h < 2; h++) {
+                    const uint32_t* d = T->share[(i + h) % 3] + ((uint64_t)q->attr * T->n_elems + e) * W;
+                    const uint8_t* v = ev + (((size_t)k * 3 + i) * 2 + h) * D;
+                    uint32_t x = 0;
+                    for (uint32_t l = 0; l < D; l++) x ^= v[l] & ((d[l / 32] >> (l % 32)) & 1u);
+                    z[i] ^= x;
+                }
+            }
+            uint32_t bsh[3];
+            reshare_bin(prf_ks, z, bsh, e, (uint32_t)p, (uint32_t)table, query_id);
+            if (k == 0) {
+                memcpy(acc, bsh, sizeof acc);
+            } else {
+                uint32_t w[3];
+                for (int i = 0; i < 3; i++) {
+                    int i1 = (i + 1) % 3;
+                    w[i] = (acc[i] & bsh[i]) ^ (acc[i] & bsh[i1]) ^ (acc[i1] & bsh[i]);
+                }
+                reshare_bin(prf_ks, w, acc, e, 64u + (uint32_t)p, (uint32_t)table, query_id);
+            }
+        }
+        for (int i = 0; i < 3; i++) out[(uint64_t)i * n_sel + s] = acc[i];
+    }
+    free(ev);
+    return 0;
 }

@@ -107,6 +107,33 @@ def range_around(g: np.random.Generator, value: int, bits: int, width_frac: floa
     return lo, hi
 
 
+def onehot_words(bits: int) -> int:
+    """32-bit words of one packed one-hot vector of length 2^bits (at least one word)."""
+    return max(1, (1 << bits) // 32)
+
+
+def onehot_shares(g: np.random.Generator, values: np.ndarray, bits: int):
+    """Binary RSS of one-hot encodings (the data owner's encryption of Sec. V-B): value v
+    becomes e_v in {0,1}^(2^bits), bit l in bit l % 32 of word l // 32, and
+    e_v = <e>_1 xor <e>_2 xor <e>_3 with <e>_1, <e>_2 uniform on the 2^bits valid bits.
+    values: [n_attrs, n_elems]; returns three uint32 arrays [n_attrs, n_elems, W]."""
+    wds = onehot_words(bits)
+    valid = np.uint32(0xFFFFFFFF) if bits >= 5 else np.uint32((1 << (1 << bits)) - 1)
+    na, ne = values.shape
+    e = np.zeros((na, ne, wds), dtype=np.uint32)
+    v = values.astype(np.int64)
+    ai, ei = np.meshgrid(np.arange(na), np.arange(ne), indexing="ij")
+    e[ai, ei, v // 32] = (np.uint32(1) << (v % 32).astype(np.uint32))
+    s1 = g.integers(0, 1 << 32, size=e.shape, dtype=np.uint64).astype(np.uint32) & valid
+    s2 = g.integers(0, 1 << 32, size=e.shape, dtype=np.uint64).astype(np.uint32) & valid
+    return s1, s2, e ^ s1 ^ s2
+
+
+def onehot_table(values: np.ndarray, bits: int, g: np.random.Generator):
+    """A one-hot element table: plaintext rows and the three binary one-hot share sets."""
+    return {"values": values, "bits": bits, "shares": onehot_shares(g, values, bits), "onehot": True}
+
+
 def table(values: np.ndarray, bits: int, g: np.random.Generator):
     """A resident element table: its plaintext rows and their three share sets."""
     return {"values": values, "bits": bits, "shares": share3(g, values, bits)}
