@@ -280,6 +280,46 @@ oblivgm_status oblivgm_filter_and_combine_noalloc(oblivgm_ctx* ctx, uint32_t que
                                                   const size_t tok_len[3], uint32_t n_groups, uint32_t* const* out,
                                                   void* stream);
 
+/* ------------------------------------------------------------- one-hot mode */
+
+/* The paper's secEval as written (Sec. V-B, V-C, Eq. predEval, Alg. 3), for
+ * attribute domains of at most 2^16 values.  An n-bit attribute value v is
+ * the one-hot vector e_v in {0,1}^(2^n), shared in binary RSS
+ * (e_v = <e>_1 xor <e>_2 xor <e>_3).  The FSS keys are evaluated at every
+ * public position of that vector, with no mask, so the masked mode's leak of
+ * value differences does not arise; outputs are bits (Z_2) throughout.
+ *
+ * oblivgm_keygen_onehot: genToken of Sec. V-C -- three key pairs per
+ * predicate for the predicate itself, output group Z_2, beta = 1 (EQ: DPF at
+ * alpha; RANGE [lo, hi]: DCFs at hi + 1 and lo, plus the constant 1 for
+ * party 0 when hi is the domain's last value).  Same token layout as
+ * oblivgm_keygen with header byte 7 = 1 and all <r> fields 0; the random
+ * stream has no mask block.  n_bits 1..16.  Errors as oblivgm_keygen. */
+oblivgm_status oblivgm_keygen_onehot(const oblivgm_pred* preds, uint32_t n_preds, uint32_t n_bits,
+                                     const uint8_t seed[16], uint8_t* const tok[3], size_t cap, size_t out_len[3]);
+
+/* Load a one-hot table: share_sets[j] holds n_attrs * n_elems * W uint32
+ * (W = max(1, 2^n_bits / 32)) in [attr][elem][word] order; bit l of an
+ * element's vector is bit l % 32 of word l / 32 (bits past 2^n_bits zero).
+ * Replaces an existing one-hot table with that id.  Errors as
+ * oblivgm_load_shares (n_bits 1..16). */
+oblivgm_status oblivgm_load_onehot(oblivgm_ctx* ctx, uint32_t table_id, uint64_t n_elems, uint32_t n_attrs,
+                                   uint32_t n_bits, const uint32_t* const share_sets[3], int32_t mem_kind,
+                                   void* stream);
+
+/* One-hot secEval of one query: per predicate each server evaluates its two
+ * key halves at all 2^n positions (EvalAll) and takes the parity of their AND
+ * with the binary share its key pair is tied to (CS_i: shares i and i+1);
+ * it XORs its two bits, re-shares in binary RSS (F = bit 0 of AES_k(ctr),
+ * same counters as the masked mode) and the group's predicates are ANDed in
+ * binary RSS.  out[3 g + i] receives share set i+1 of group g packed 32
+ * elements per word (element e in bit e % 32 of word e / 32; ceil(n_elems / 32)
+ * words; bits past n_elems are 0).  Asynchronous on stream.  Errors as
+ * oblivgm_filter_and_combine; EINVAL for a masked-mode token. */
+oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query_id, const uint8_t* const tok[3],
+                                     const size_t tok_len[3], uint32_t n_groups, uint32_t* const* out,
+                                     void* stream);
+
 /* --------------------------------------------------------------- serving */
 
 /* Non-blocking admission of one query into the serving loop (continuous

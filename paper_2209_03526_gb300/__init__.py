@@ -17,7 +17,7 @@ from ._native import (ALL_PAIRS, EAGAIN, EBUSY, EFAULT_DEVICE, EINVAL, ENOENT, E
                       OK, PRED_EQ, PRED_RANGE, OblivgmError)
 from .build import build
 
-__all__ = ["Context", "keygen", "build", "OblivgmError", "PRED_EQ", "PRED_RANGE", "KEY_DPF", "KEY_DCF",
+__all__ = ["Context", "keygen", "keygen_onehot", "build", "OblivgmError", "PRED_EQ", "PRED_RANGE", "KEY_DPF", "KEY_DCF",
            "ALL_PAIRS", "version", "token_len"]
 
 
@@ -55,6 +55,21 @@ def keygen(preds, n_bits: int, seed: bytes):
     lens = (N.c_size * 3)()
     sb = ctypes.create_string_buffer(bytes(seed), 16)
     N.check(_lib().oblivgm_keygen(arr, len(preds), n_bits, ctypes.addressof(sb), ptrs, L, lens), "oblivgm_keygen")
+    return tuple(b.raw[:lens[i]] for i, b in enumerate(bufs))
+
+
+def keygen_onehot(preds, n_bits: int, seed: bytes):
+    """oblivgm_keygen_onehot: tokens of the one-hot mode (no mask, Z_2 keys, beta = 1)."""
+    arr = _pred_array(preds)
+    lens = (N.c_size * 3)()
+    sb = ctypes.create_string_buffer(bytes(seed), 16)
+    N.check(_lib().oblivgm_keygen_onehot(arr, len(preds), n_bits, ctypes.addressof(sb), None, 0, lens),
+            "oblivgm_keygen_onehot")
+    L = lens[0]
+    bufs = [ctypes.create_string_buffer(L) for _ in range(3)]
+    ptrs = (N.c_vp * 3)(*[ctypes.addressof(b) for b in bufs])
+    N.check(_lib().oblivgm_keygen_onehot(arr, len(preds), n_bits, ctypes.addressof(sb), ptrs, L, lens),
+            "oblivgm_keygen_onehot")
     return tuple(b.raw[:lens[i]] for i, b in enumerate(bufs))
 
 
@@ -145,6 +160,24 @@ class Context:
         N.check(self._lib.oblivgm_load_shares(self._h, table_id, n_elems, n_attrs, n_bits, arr, kind,
                                               _stream_handle(stream) if kind == N.MEM_DEVICE else None),
                 "oblivgm_load_shares")
+
+    def load_onehot(self, table_id: int, shares: Sequence, n_bits: int, stream=None):
+        """shares: three uint32 CUDA tensors [n_attrs, n_elems, W] of binary one-hot shares."""
+        ts = [s.contiguous() for s in shares]
+        n_attrs, n_elems = ts[0].shape[0], ts[0].shape[1]
+        arr = (N.c_vp * 3)(*[t.data_ptr() for t in ts])
+        kind = N.MEM_DEVICE if ts[0].is_cuda else N.MEM_HOST
+        N.check(self._lib.oblivgm_load_onehot(self._h, table_id, n_elems, n_attrs, n_bits, arr, kind,
+                                              _stream_handle(stream) if kind == N.MEM_DEVICE else None),
+                "oblivgm_load_onehot")
+
+    def filter_onehot(self, query_id: int, tokens, outs, stream=None):
+        """outs: per AND-group three int32 CUDA tensors of ceil(n_elems / 32) packed words."""
+        _, tp, tl = _tok_arrays(tokens)
+        flat = [t.data_ptr() for g in outs for t in g]
+        arr = (N.c_vp * len(flat))(*flat)
+        N.check(self._lib.oblivgm_filter_onehot(self._h, query_id, tp, tl, len(outs), arr, _stream_handle(stream)),
+                "oblivgm_filter_onehot")
 
     def unload_shares(self, table_id: int):
         N.check(self._lib.oblivgm_unload_shares(self._h, table_id), "oblivgm_unload_shares")

@@ -135,7 +135,8 @@ __device__ __forceinline__ void aes_one(const Tab& T, const uint32_t* rk, const 
 // DPF Eval (BGI16) of one key at E inputs: per level one PRG call for the child
 // the input bit selects, the conditional correction, and at the end
 // (-1)^b (Convert(s) + t * CW_{n+1}).
-template <int E, class Tab>
+// Z2 = true: output group Z_2 (one-hot mode): Convert(seed) = bit 1 of byte 0, the result mod 2.
+template <int E, class Tab, bool Z2 = false>
 __device__ __forceinline__ void dpf_walk(const Tab& T, const AesParams& A, const DevKey& K, const uint32_t xh[E],
                                          uint32_t y[E]) {
     uint32_t s[E][4], t[E];
@@ -172,15 +173,16 @@ __device__ __forceinline__ void dpf_walk(const Tab& T, const AesParams& A, const
     const uint32_t cwf = K.cw_final;
 #pragma unroll
     for (int e = 0; e < E; e++) {
-        const uint32_t v = s[e][1] + (t[e] ? cwf : 0u);
-        y[e] = party ? 0u - v : v;
+        const uint32_t conv = Z2 ? ((s[e][0] >> 1) & 1u) : s[e][1];
+        const uint32_t v = conv + (t[e] ? cwf : 0u);
+        y[e] = (party ? 0u - v : v) & (Z2 ? 1u : 0xFFFFFFFFu);
     }
 }
 
 // DCF Eval (BCG+21) of one key at E inputs: per level the seed/control block and
 // the value block of the selected child (two PRG calls on the same seed),
 // V += (-1)^b (Convert(v) + t * V_CW), then the final term.
-template <int E, class Tab>
+template <int E, class Tab, bool Z2 = false>
 __device__ __forceinline__ void dcf_walk(const Tab& T, const AesParams& A, const DevKey& K, const uint32_t xh[E],
                                          uint32_t y[E]) {
     uint32_t s[E][4], t[E], V[E];
@@ -205,7 +207,8 @@ __device__ __forceinline__ void dcf_walk(const Tab& T, const AesParams& A, const
             uint32_t o[4];
             aes_sel(T, A.rk_st, A.d_st, m, s[e], o);
             const uint32_t v0 = aes_sel_w0(T, A.rk_v, A.d_v, m, s[e]);   // Convert(v) needs bytes 0..3 only
-            const uint32_t term = (v0 ^ s[e][0]) + (t[e] ? vcw : 0u);
+            const uint32_t vconv = Z2 ? ((v0 ^ s[e][0]) & 1u) : (v0 ^ s[e][0]);
+            const uint32_t term = vconv + (t[e] ? vcw : 0u);
             V[e] += party ? 0u - term : term;
 #pragma unroll
             for (int w = 0; w < 4; w++) o[w] ^= s[e][w];
@@ -223,8 +226,9 @@ __device__ __forceinline__ void dcf_walk(const Tab& T, const AesParams& A, const
     const uint32_t cwf = K.cw_final;
 #pragma unroll
     for (int e = 0; e < E; e++) {
-        const uint32_t term = s[e][1] + (t[e] ? cwf : 0u);
-        y[e] = V[e] + (party ? 0u - term : term);
+        const uint32_t conv = Z2 ? ((s[e][0] >> 1) & 1u) : s[e][1];
+        const uint32_t term = conv + (t[e] ? cwf : 0u);
+        y[e] = (V[e] + (party ? 0u - term : term)) & (Z2 ? 1u : 0xFFFFFFFFu);
     }
 }
 

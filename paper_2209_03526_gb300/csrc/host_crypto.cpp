@@ -141,22 +141,30 @@ void expand(int dir, const Seed& s, Seed* cs, uint32_t* ct) {
 
 inline uint32_t input_bit(uint32_t x, int n, int i) { return (x >> (n - i)) & 1u; }   // i = 1..n, MSB first
 
-void put_header(uint8_t* k, uint32_t kind, int n, int party, const uint8_t seed[16]) {
+void put_header(uint8_t* k, uint32_t kind, int n, int party, const uint8_t seed[16], int group) {
     std::memset(k, 0, 8);
     k[0] = (uint8_t)kind;
     k[1] = (uint8_t)n;
     k[2] = (uint8_t)party;
+    k[3] = (uint8_t)group;
     std::memcpy(k + 8, seed, 16);
 }
+
+// Convert into the output group: Z_{2^32} reads bytes 4..7 of a seed (bytes 0..3 of a
+// value block); Z_2 reads bit 1 of byte 0 of a seed (bit 0 of byte 0 of a value block).
+// Z_2 arithmetic is the Z_{2^32} arithmetic reduced mod 2, so only stored words are masked.
+inline uint32_t conv_seed(const Seed& s, int group) { return group ? (s.w[0] >> 1) & 1u : s.w[1]; }
+inline uint32_t conv_value(uint32_t w0, int group) { return group ? (w0 & 1u) : w0; }
+inline uint32_t gmask(int group) { return group ? 1u : 0xFFFFFFFFu; }
 
 }  // namespace
 
 void dpf_gen(int n, uint32_t alpha, uint32_t beta, const uint8_t s0[16], const uint8_t s1[16], uint8_t* k0,
-             uint8_t* k1) {
+             uint8_t* k1, int group) {
     Seed s[2] = {load_seed(s0), load_seed(s1)};
     uint32_t t[2] = {0, 1};
-    put_header(k0, OBLIVGM_KEY_DPF, n, 0, s0);
-    put_header(k1, OBLIVGM_KEY_DPF, n, 1, s1);
+    put_header(k0, OBLIVGM_KEY_DPF, n, 0, s0, group);
+    put_header(k1, OBLIVGM_KEY_DPF, n, 1, s1, group);
     for (int i = 1; i <= n; i++) {
         Seed c[2][2];
         uint32_t tc[2][2];
@@ -184,26 +192,27 @@ void dpf_gen(int n, uint32_t alpha, uint32_t beta, const uint8_t s0[16], const u
             t[b] = tc[b][keep] ^ (t[b] & tkeep);
         }
     }
-    uint32_t cw = beta - s[0].w[1] + s[1].w[1];
+    uint32_t cw = beta - conv_seed(s[0], group) + conv_seed(s[1], group);
     if (t[1]) cw = 0u - cw;
+    cw &= gmask(group);
     st32(k0 + 24 + (size_t)n * 20, cw);
     st32(k1 + 24 + (size_t)n * 20, cw);
 }
 
 void dcf_gen(int n, uint32_t alpha, uint32_t beta, const uint8_t s0[16], const uint8_t s1[16], uint8_t* k0,
-             uint8_t* k1) {
+             uint8_t* k1, int group) {
     Seed s[2] = {load_seed(s0), load_seed(s1)};
     uint32_t t[2] = {0, 1};
     uint32_t valpha = 0;
-    put_header(k0, OBLIVGM_KEY_DCF, n, 0, s0);
-    put_header(k1, OBLIVGM_KEY_DCF, n, 1, s1);
+    put_header(k0, OBLIVGM_KEY_DCF, n, 0, s0, group);
+    put_header(k1, OBLIVGM_KEY_DCF, n, 1, s1, group);
     for (int i = 1; i <= n; i++) {
         Seed c[2][2];
         uint32_t tc[2][2], v[2][2];
         for (int b = 0; b < 2; b++) {
             for (int d = 0; d < 2; d++) {
                 expand(d, s[b], &c[b][d], &tc[b][d]);
-                v[b][d] = prg(2 + d, s[b]).w[0];
+                v[b][d] = conv_value(prg(2 + d, s[b]).w[0], group);
             }
         }
         const uint32_t a = input_bit(alpha, n, i);
@@ -223,7 +232,7 @@ void dcf_gen(int n, uint32_t alpha, uint32_t beta, const uint8_t s0[16], const u
             k[off + 16] = (uint8_t)tlcw;
             k[off + 17] = (uint8_t)trcw;
             k[off + 18] = k[off + 19] = 0;
-            st32(k + off + 20, vcw);
+            st32(k + off + 20, vcw & gmask(group));
         }
         const uint32_t tkeep = keep ? trcw : tlcw;
         for (int b = 0; b < 2; b++) {
@@ -232,8 +241,9 @@ void dcf_gen(int n, uint32_t alpha, uint32_t beta, const uint8_t s0[16], const u
             t[b] = tc[b][keep] ^ (t[b] & tkeep);
         }
     }
-    uint32_t cw = s[1].w[1] - s[0].w[1] - valpha;
+    uint32_t cw = conv_seed(s[1], group) - conv_seed(s[0], group) - valpha;
     if (t[1]) cw = 0u - cw;
+    cw &= gmask(group);
     st32(k0 + 24 + (size_t)n * 24, cw);
     st32(k1 + 24 + (size_t)n * 24, cw);
 }
@@ -248,7 +258,7 @@ bool repack_key(const uint8_t* wire, size_t avail, uint32_t want_kind, int want_
         return false;
     }
     if (n < 1 || n > kMaxBits || (want_n && n != want_n)) { *err = "key bit length mismatch"; return false; }
-    if (party > 1 || wire[3] != 0) { *err = "bad key header"; return false; }
+    if (party > 1 || wire[3] > 1) { *err = "bad key header"; return false; }
     if (avail < key_bytes(kind, n)) { *err = "key truncated"; return false; }
     std::memset(out, 0, sizeof *out);
     for (int w = 0; w < 4; w++) out->seed[w] = ld32(wire + 8 + 4 * w);
@@ -265,6 +275,7 @@ bool repack_key(const uint8_t* wire, size_t avail, uint32_t want_kind, int want_
     out->party = party;
     out->n = (uint32_t)n;
     out->kind = kind;
+    out->group = wire[3];
     return true;
 }
 
@@ -277,11 +288,13 @@ oblivgm_status parse_tokens(const uint8_t* const tok[3], const size_t tok_len[3]
         if (ld32(t) != kTokenMagic || t[4] != 1 || t[5] != i + 1) { *err = "bad token header"; return OBLIVGM_EINVAL; }
         if (ld32(t + 12) != tok_len[i]) { *err = "token length field mismatch"; return OBLIVGM_EINVAL; }
         const int tn = t[6], tnp = ld16(t + 8);
+        if (t[7] > 1 || t[7] != tok[0][7]) { *err = "bad or mismatched output group"; return OBLIVGM_EINVAL; }
         if (i == 0) { n = tn; np = tnp; }
         else if (tn != n || tnp != np) { *err = "tokens disagree on n or predicate count"; return OBLIVGM_EINVAL; }
     }
     if (n < 1 || n > kMaxBits || np < 1 || np > kMaxPreds) { *err = "token n or predicate count out of range"; return OBLIVGM_EINVAL; }
     q->n_bits = (uint32_t)n;
+    q->out_group = tok[0][7];
     q->preds.clear();
     size_t off = 16;
     for (int p = 0; p < np; p++) {
@@ -318,8 +331,10 @@ oblivgm_status parse_tokens(const uint8_t* const tok[3], const size_t tok_len[3]
             for (int h = 0; h < 2; h++)
                 for (int s = 0; s < nsub; s++) {
                     const uint8_t* kw = tok[i] + off + 24 + h * half + s * key_bytes(kkind, n);
-                    if (!repack_key(kw, tok_len[i] - (size_t)(kw - tok[i]), kkind, n, &pp.keys[(i * 2 + h) * nsub + s], err))
+                    DevKey& dk = pp.keys[(i * 2 + h) * nsub + s];
+                    if (!repack_key(kw, tok_len[i] - (size_t)(kw - tok[i]), kkind, n, &dk, err))
                         return OBLIVGM_EINVAL;
+                    if (dk.group != q->out_group) { *err = "key output group differs from the token's"; return OBLIVGM_EINVAL; }
                 }
         q->preds.push_back(std::move(pp));
         off += rec_len;
@@ -330,10 +345,14 @@ oblivgm_status parse_tokens(const uint8_t* const tok[3], const size_t tok_len[3]
 }
 
 oblivgm_status keygen(const oblivgm_pred* preds, uint32_t n_preds, uint32_t n_bits, const uint8_t seed[16],
-                      uint8_t* const tok[3], size_t cap, size_t out_len[3], std::string* err) {
+                      uint8_t* const tok[3], size_t cap, size_t out_len[3], std::string* err, bool onehot) {
     if (!preds || !seed || !out_len) { *err = "NULL argument"; return OBLIVGM_EINVAL; }
     if (n_preds == 0 || n_preds > (uint32_t)kMaxPreds) { *err = "predicate count must be 1..64"; return OBLIVGM_EINVAL; }
-    if (n_bits < 1 || n_bits > (uint32_t)kMaxBits) { *err = "n must be 1..32"; return OBLIVGM_EINVAL; }
+    if (n_bits < 1 || n_bits > (uint32_t)(onehot ? kMaxOnehotBits : kMaxBits)) {
+        *err = onehot ? "one-hot n must be 1..16" : "n must be 1..32";
+        return OBLIVGM_EINVAL;
+    }
+    const int group = onehot ? 1 : 0;
     const int n = (int)n_bits;
     const uint32_t m = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
     const size_t dpf = key_bytes(OBLIVGM_KEY_DPF, n), dcf = key_bytes(OBLIVGM_KEY_DCF, n);
@@ -372,6 +391,7 @@ oblivgm_status keygen(const oblivgm_pred* preds, uint32_t n_preds, uint32_t n_bi
         h[4] = 1;
         h[5] = (uint8_t)(i + 1);
         h[6] = (uint8_t)n;
+        h[7] = (uint8_t)group;
         h[8] = (uint8_t)n_preds;
         h[9] = (uint8_t)(n_preds >> 8);
         st32(h + 12, (uint32_t)total);
@@ -383,18 +403,24 @@ oblivgm_status keygen(const oblivgm_pred* preds, uint32_t n_preds, uint32_t n_bi
     size_t off = 16;
     for (uint32_t p = 0; p < n_preds; p++) {
         const oblivgm_pred& q = preds[p];
-        uint8_t blk[16];
-        next_block(blk);
-        const uint32_t r = ld32(blk) & m;
-        uint32_t rs[3] = {ld32(blk + 4) & m, ld32(blk + 8) & m, 0};
-        rs[2] = (r - rs[0] - rs[1]) & m;
+        // masked mode: a fresh mask r, replicated-shared; one-hot mode: no mask
+        uint32_t r = 0, rs[3] = {0, 0, 0};
+        if (!onehot) {
+            uint8_t blk[16];
+            next_block(blk);
+            r = ld32(blk) & m;
+            rs[0] = ld32(blk + 4) & m;
+            rs[1] = ld32(blk + 8) & m;
+            rs[2] = (r - rs[0] - rs[1]) & m;
+        }
+        const uint32_t beta = onehot ? 1u : kBetaPrime;
         const bool eq = q.kind == OBLIVGM_PRED_EQ;
         const size_t half = eq ? dpf : 2 * dcf;
         keys.assign(3 * 2 * half, 0);   // [pair][party][half]
         uint32_t cbeta = 0;
         const uint32_t a_eq = (q.lo + r) & m;
         const uint32_t a0 = (q.lo + r) & m, a1 = (q.hi + 1u + r) & m;
-        if (!eq) cbeta = a1 <= a0 ? kBetaPrime : 0u;
+        if (!eq) cbeta = a1 <= a0 ? beta : 0u;
         for (int j = 0; j < 3; j++) {
             uint8_t* kp0 = keys.data() + (j * 2 + 0) * half;
             uint8_t* kp1 = keys.data() + (j * 2 + 1) * half;
@@ -402,12 +428,12 @@ oblivgm_status keygen(const oblivgm_pred* preds, uint32_t n_preds, uint32_t n_bi
             next_block(s0);
             next_block(s1);
             if (eq) {
-                dpf_gen(n, a_eq, kBetaPrime, s0, s1, kp0, kp1);
+                dpf_gen(n, a_eq, beta, s0, s1, kp0, kp1, group);
             } else {
-                dcf_gen(n, a1, kBetaPrime, s0, s1, kp0, kp1);
+                dcf_gen(n, a1, beta, s0, s1, kp0, kp1, group);
                 next_block(s0);
                 next_block(s1);
-                dcf_gen(n, a0, 0u - kBetaPrime, s0, s1, kp0 + dcf, kp1 + dcf);
+                dcf_gen(n, a0, 0u - beta, s0, s1, kp0 + dcf, kp1 + dcf, group);
             }
         }
         for (int i = 0; i < 3; i++) {

@@ -36,6 +36,7 @@ constexpr uint32_t kBetaPrime = 0xAAAAAAABu;   // 3^{-1} mod 2^32
 constexpr uint32_t kTokenMagic = 0x544D474Fu;
 constexpr int kMaxPreds = 64;
 constexpr int kMaxBits = 32;
+constexpr int kMaxOnehotBits = 16;   // one-hot vectors of 2^n bits per element
 
 inline size_t key_bytes(uint32_t kind, int n) { return 28u + (size_t)n * (kind == OBLIVGM_KEY_DPF ? 20u : 24u); }
 
@@ -49,7 +50,8 @@ struct alignas(16) DevKey {
     uint32_t party;              // 0 or 1
     uint32_t n;
     uint32_t kind;
-    uint32_t pad[2];
+    uint32_t group;              // output group: 0 = Z_{2^32}, 1 = Z_2 (one-hot mode)
+    uint32_t pad;
 };
 static_assert(sizeof(DevKey) == 688, "DevKey layout");
 static_assert(sizeof(DevKey) % 16 == 0, "bulk copies need 16-byte multiples");
@@ -67,6 +69,7 @@ struct ParsedPred {
 
 struct ParsedQuery {
     uint32_t n_bits = 0;
+    uint32_t out_group = 0;   // 0: masked mode over Z_{2^32}; 1: one-hot mode over Z_2
     std::vector<ParsedPred> preds;
 };
 
@@ -74,13 +77,15 @@ struct ParsedQuery {
 oblivgm_status parse_tokens(const uint8_t* const tok[3], const size_t tok_len[3], ParsedQuery* q, std::string* err);
 
 // Client-side token generation; identical layout to the ABI description.
+// onehot = false: masked mode; true: the one-hot mode of Sec. V-C (no mask, Z_2 keys, beta = 1).
 oblivgm_status keygen(const oblivgm_pred* preds, uint32_t n_preds, uint32_t n_bits, const uint8_t seed[16],
-                      uint8_t* const tok[3], size_t cap, size_t out_len[3], std::string* err);
+                      uint8_t* const tok[3], size_t cap, size_t out_len[3], std::string* err, bool onehot = false);
 
 // FSS Gen for one key pair in the wire format (exposed for tests through the ABI-free entry).
+// group 0: outputs in Z_{2^32}; group 1: outputs in Z_2 (Convert = one bit, words stored mod 2)
 void dpf_gen(int n, uint32_t alpha, uint32_t beta, const uint8_t s0[16], const uint8_t s1[16], uint8_t* k0,
-             uint8_t* k1);
+             uint8_t* k1, int group = 0);
 void dcf_gen(int n, uint32_t alpha, uint32_t beta, const uint8_t s0[16], const uint8_t s1[16], uint8_t* k0,
-             uint8_t* k1);
+             uint8_t* k1, int group = 0);
 
 }  // namespace ogm

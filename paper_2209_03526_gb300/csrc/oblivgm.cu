@@ -428,6 +428,7 @@ oblivgm_status plan_queries(const std::map<uint32_t, Table>& tables, uint32_t n_
     for (uint32_t q = 0; q < n_queries; q++) {
         const ParsedQuery& pq = parsed[q];
         const uint32_t ng = n_groups[q];
+        if (pq.out_group != 0) return fail(OBLIVGM_EINVAL, "a one-hot token was given to the masked-mode evaluation");
         if (ng == 0 || ng > OBLIVGM_MAX_GROUPS) return fail(OBLIVGM_EINVAL, "n_groups must be 1..64");
         std::vector<std::vector<const ParsedPred*>> members(ng);
         for (const ParsedPred& p : pq.preds) {
@@ -603,6 +604,7 @@ oblivgm_status oblivgm_create(oblivgm_ctx** out, int32_t device, const oblivgm_c
     }
     ctx->cfg = *cfg;
     oblivgm_status st = set_filter_attrs();
+    if (st == OBLIVGM_OK) st = set_onehot_attrs();
     if (st != OBLIVGM_OK) { delete ctx; return st; }
     cudaError_t e = cudaMalloc(&ctx->d_te0, 256 * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemcpy(ctx->d_te0, aes_tables().te0, 256 * sizeof(uint32_t), cudaMemcpyHostToDevice);
@@ -641,6 +643,7 @@ oblivgm_status oblivgm_destroy(oblivgm_ctx* ctx) {
     serve_shutdown(ctx);
     cudaDeviceSynchronize();
     for (auto& kv : ctx->tables) cudaFree(kv.second.dev);
+    for (auto& kv : ctx->onehot_tables) cudaFree(kv.second.dev);
     if (ctx->d_te0) cudaFree(ctx->d_te0);
     if (ctx->d_te4) cudaFree(ctx->d_te4);
     if (ctx->d_error) cudaFree(ctx->d_error);

@@ -95,6 +95,7 @@ extern "C" oblivgm_status oblivgm_filter_plain(oblivgm_ctx* ctx, uint32_t query_
     std::string err;
     oblivgm_status st = parse_tokens(tok, tok_len, &q, &err);
     if (st != OBLIVGM_OK) return fail(st, err);
+    if (q.out_group != 0) return fail(OBLIVGM_EINVAL, "a one-hot token was given to the masked-mode evaluation");
     if (n_groups == 0 || n_groups > OBLIVGM_MAX_GROUPS) return fail(OBLIVGM_EINVAL, "n_groups must be 1..64");
     std::vector<std::vector<const ParsedPred*>> members(n_groups);
     for (const ParsedPred& p : q.preds) {

@@ -29,6 +29,16 @@ struct Table {
     size_t bytes = 0;
 };
 
+// one-hot table: binary-RSS shares of one-hot vectors, [share set j][attr][elem][words]
+struct OnehotTable {
+    uint32_t* dev = nullptr;
+    uint64_t n_elems = 0;
+    uint32_t n_attrs = 0;
+    uint32_t n_bits = 0;       // one-hot length 2^n_bits
+    uint32_t words = 0;        // max(1, 2^n_bits / 32)
+    size_t bytes = 0;
+};
+
 struct ServeQuery {
     uint64_t ticket = 0;
     ParsedQuery parsed;
@@ -78,6 +88,7 @@ struct oblivgm_ctx {
     uint32_t* d_error = nullptr;
     void* h_stage = nullptr;
     std::map<uint32_t, ogm::Table> tables;
+    std::map<uint32_t, ogm::OnehotTable> onehot_tables;
     uint32_t threads = 256;
     uint32_t elems_per_thread = 4;
     std::atomic<uint64_t> launches{0};
@@ -102,5 +113,6 @@ oblivgm_status launch_parsed(oblivgm_ctx* ctx, uint32_t n_queries, const uint32_
                              const std::map<uint32_t, Table>& tables, cudaStream_t st);
 
 double now_ms();
+oblivgm_status set_onehot_attrs();
 
 }  // namespace ogm

@@ -175,6 +175,7 @@ oblivgm_status oblivgm_submit(oblivgm_ctx* ctx, const uint8_t* const tok[3], con
     std::string err;
     oblivgm_status st = parse_tokens(tok, tok_len, &q->parsed, &err);
     if (st != OBLIVGM_OK) return fail(st, err);
+    if (q->parsed.out_group != 0) return fail(OBLIVGM_EINVAL, "the serving loop evaluates masked-mode tokens only");
     uint32_t ng = 0;
     for (const ParsedPred& p : q->parsed.preds) ng = std::max(ng, p.group + 1);
     if (ng > OBLIVGM_MAX_GROUPS) return fail(OBLIVGM_EINVAL, "more than 64 AND-groups");

@@ -93,3 +93,14 @@ def test_keygen_buffer_too_small_reports_size():
     seed = ctypes.create_string_buffer(16)
     st = lib.oblivgm_keygen(arr, 1, 8, ctypes.addressof(seed), ptrs, 10, lens)
     assert st == N.ERANGE and lens[0] == P.token_len(preds, 8)
+
+
+@pytest.mark.parametrize("n", [1, 3, 8, 12, 16])
+def test_onehot_keygen_byte_identical_to_oracle(n):
+    g = np.random.default_rng(50 + n)
+    for trial in range(2):
+        preds = _random_preds(g, n, int(g.integers(1, 6)))
+        seed = bytes(g.integers(0, 256, 16, dtype=np.uint8))
+        assert P.keygen_onehot(preds, n, seed) == oracle.keygen_onehot(preds, n, seed)
+    with pytest.raises(P.OblivgmError):
+        P.keygen_onehot([W.eq_pred(0, 0, 0, 1)], 17, bytes(16))
