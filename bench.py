@@ -548,6 +548,51 @@ def run_workload(args):
     line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "u32",
             "data": "synthetic", "workload_mode": args.workload, "schedule": list(sched)}
 
+    if args.workload == "onehot":
+        # the paper's secEval as written: one-hot vectors of 2^16 positions in binary RSS,
+        # 107,614 vertices (the size of the paper's graph), one 16-bit attribute
+        n_v, n = 107_614, 16
+        g = W.rng(6)
+        vals = W.uniform_attrs(g, 1, n_v, n)
+        tab = W.onehot_table(vals, n, g)
+        ctx.load_onehot(0, [torch.from_numpy(x.view(np.int32)).to(dev) for x in tab["shares"]], n)
+        del tab
+        v0, v1 = int(vals[0, 11]), int(vals[0, 22])
+        preds = [W.eq_pred(0, 0, 0, v0), W.range_pred(0, 0, 1, v1 // 2, min((1 << n) - 1, v1 + 9000)),
+                 W.eq_pred(0, 0, 2, v1), W.range_pred(0, 0, 2, v1 // 3, (1 << n) - 1)]
+        toks = P.keygen_onehot(preds, n, KEY_SEED)
+        words_out = (n_v + 31) // 32
+        outs = [[torch.empty(words_out, dtype=torch.int32, device=dev) for _ in range(3)] for _ in range(3)]
+        for _ in range(max(1, args.warmup)):
+            ctx.filter_onehot(1, toks, outs, stream)
+        ctx.sync(stream)
+        ms = []
+        for k in range(args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.filter_onehot(2 + k, toks, outs, stream)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        ctx.sync(stream)
+        step_s = float(np.mean(ms)) / 1e3
+        units = len(preds) * n_v
+        row_bytes = 3 * ((1 << n) // 32) * 4                   # the three share rows of one element
+        algo_bytes = units * row_bytes + 3 * 3 * words_out * 4   # + packed outputs of 3 groups
+        peak_bw = float(peaks.get("hbm_gbs", 6800.0))
+        line.update({"value": units / step_s, "ms_per_step": step_s * 1e3, "steps": args.steps,
+                     "warmup": args.warmup,
+                     "config": {"workload": "onehot_107614v_n16_4pred", "elements": n_v, "one_hot_bits": 1 << n,
+                                "groups": "EQ | RANGE | EQ AND RANGE", "element_predicates_per_step": units,
+                                "bytes_per_element_predicate": row_bytes},
+                     "roofline": {"bound": "hbm", "achieved": algo_bytes / step_s / 1e9, "peak": peak_bw,
+                                  "unit": "GB/s", "frac": algo_bytes / step_s / 1e9 / peak_bw,
+                                  "what": "whole step (EvalAll + dot-product launches) against the share rows "
+                                          "and packed outputs it must move"}})
+        ctx.close()
+        print(json.dumps(line), flush=True)
+        return 0
+
     if args.workload in ("tiny", "edges", "batch"):
         if args.workload == "tiny":
             wl = W.tiny_path(seed=1)
@@ -644,7 +689,7 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-path and latency comparisons")
     ap.add_argument("--serve-queries", type=int, default=48, help="arrivals per rate in --workload serve")
     ap.add_argument("--plain-queries", type=int, default=6, help="plain-path queries per rate in --workload serve")
-    ap.add_argument("--workload", choices=["bulk", "tiny", "edges", "batch", "serve"], default="bulk",
+    ap.add_argument("--workload", choices=["bulk", "tiny", "edges", "batch", "serve", "onehot"], default="bulk",
                     help="bulk (default, the headline line); the others print their own line")
     ap.add_argument("--schedule", default="", help="threads,elems_per_thread (skips the autotuner)")
     ap.add_argument("--profile-case", action="store_true",

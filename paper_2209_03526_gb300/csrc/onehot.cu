@@ -43,31 +43,97 @@ struct EvalAllParams {
     const uint32_t* te0;
     const DevKey* keys;
     const HalfDesc* halves;
-    uint32_t* hv;          // [half][words]
+    uint32_t* hv;          // [half][words], zeroed before the launch
     uint32_t domain;       // D = 2^n
     uint32_t words;        // max(1, D / 32)
+    uint32_t n_halves;
+    int log_block;         // m = min(3, n): positions per work item = 2^m
 };
 
-__global__ void __launch_bounds__(256) k_onehot_evalall(const __grid_constant__ EvalAllParams P) {
+// One tree level of DPF / DCF Eval (Z_2 outputs) in direction dir, as in the walks of the
+// masked mode: the selected child's seed and control bit (and, for the DCF, the value
+// term V += Convert(v) + t * V_CW, taken mod 2).
+__device__ __forceinline__ void level_step(const SmemTab& T, const AesParams& A, const DevKey& K, int i, uint32_t dir,
+                                           bool dcf, uint32_t s[4], uint32_t& t, uint32_t& V) {
+    const uint32_t m = 0u - dir;
+    uint32_t o[4];
+    aes_sel(T, A.rk_st, A.d_st, m, s, o);
+    if (dcf) {
+        const uint32_t v0 = aes_sel_w0(T, A.rk_v, A.d_v, m, s);
+        V ^= ((v0 ^ s[0]) & 1u) ^ (t & K.vcw[i] & 1u);
+    }
+#pragma unroll
+    for (int w = 0; w < 4; w++) o[w] ^= s[w];
+    uint32_t tn = o[0] & 1u;
+    o[0] &= ~1u;
+    const uint32_t tm = 0u - t;
+#pragma unroll
+    for (int w = 0; w < 4; w++) s[w] = o[w] ^ (K.scw[i][w] & tm);
+    tn ^= t & (((dir ? K.tr : K.tl) >> i) & 1u);
+    t = tn;
+}
+
+// Eval of one key at the 2^m consecutive positions prefix * 2^m + j, j < 2^m (m <= 3):
+// walk the n - m shared levels once, then expand the last m levels depth first
+// (2^(m+1) - 2 more levels instead of m per position).  Bit j of the result is
+// position prefix * 2^m + j.
+__device__ __forceinline__ uint32_t eval_block(const SmemTab& T, const AesParams& A, const DevKey& K, uint32_t prefix,
+                                               int m) {
+    const int n = (int)K.n;
+    const bool dcf = K.kind == OBLIVGM_KEY_DCF;
+    uint32_t s[4] = {K.seed[0], K.seed[1], K.seed[2], K.seed[3]};
+    uint32_t t = K.party, V = 0;
+    for (int i = 0; i < n - m; i++) level_step(T, A, K, i, (prefix >> (n - m - 1 - i)) & 1u, dcf, s, t, V);
+    uint32_t bits = 0;
+    const uint32_t cwf = K.cw_final & 1u;
+    if (m == 0) {
+        return V ^ ((s[0] >> 1) & 1u) ^ (t & cwf);
+    }
+    // depth-first over the last m levels (m = 1, 2 or 3), keeping one node per level
+    uint32_t s1[4], t1, V1, s2[4], t2, V2;
+    const int L1 = n - m;            // level index of the first expanded level
+    for (uint32_t b1 = 0; b1 < 2; b1++) {
+#pragma unroll
+        for (int w = 0; w < 4; w++) s1[w] = s[w];
+        t1 = t; V1 = V;
+        level_step(T, A, K, L1, b1, dcf, s1, t1, V1);
+        if (m == 1) { bits |= (V1 ^ ((s1[0] >> 1) & 1u) ^ (t1 & cwf)) << b1; continue; }
+        for (uint32_t b2 = 0; b2 < 2; b2++) {
+#pragma unroll
+            for (int w = 0; w < 4; w++) s2[w] = s1[w];
+            t2 = t1; V2 = V1;
+            level_step(T, A, K, L1 + 1, b2, dcf, s2, t2, V2);
+            if (m == 2) { bits |= (V2 ^ ((s2[0] >> 1) & 1u) ^ (t2 & cwf)) << (b1 * 2 + b2); continue; }
+            for (uint32_t b3 = 0; b3 < 2; b3++) {
+                uint32_t s3[4] = {s2[0], s2[1], s2[2], s2[3]}, t3 = t2, V3 = V2;
+                level_step(T, A, K, L1 + 2, b3, dcf, s3, t3, V3);
+                bits |= (V3 ^ ((s3[0] >> 1) & 1u) ^ (t3 & cwf)) << (b1 * 4 + b2 * 2 + b3);
+            }
+        }
+    }
+    return bits;
+}
+
+// Every key half at every position.  Work item = (half, block of 2^m positions); the
+// items are spread over one persistent CTA per SM.  hv must be zeroed: each item ORs
+// its 2^m bits into place.
+__global__ void __launch_bounds__(1024, 1) k_onehot_evalall(const __grid_constant__ EvalAllParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
     fill_tables(reinterpret_cast<uint32_t*>(smem), P.te0);
     __syncthreads();
     const SmemTab T{reinterpret_cast<const char*>(smem), lane_offset()};
-    const HalfDesc H = P.halves[blockIdx.y];
-    const DevKey& K0 = P.keys[H.key0];
-    const uint32_t span = P.domain < 32 ? 32u : P.domain;
-    for (uint32_t base = blockIdx.x * blockDim.x; base < span; base += gridDim.x * blockDim.x) {
-        const uint32_t l = base + threadIdx.x;
-        uint32_t x[1] = {l < P.domain ? l : 0u}, y[1], y2[1] = {0u};
-        if (H.kind == OBLIVGM_KEY_DPF) {
-            dpf_walk<1, SmemTab, true>(T, P.aes, K0, x, y);
-        } else {
-            dcf_walk<1, SmemTab, true>(T, P.aes, K0, x, y);
-            dcf_walk<1, SmemTab, true>(T, P.aes, P.keys[H.key1], x, y2);
-        }
-        const uint32_t bit = l < P.domain ? ((y[0] ^ y2[0] ^ H.cbit) & 1u) : 0u;
-        const uint32_t word = __ballot_sync(0xFFFFFFFFu, bit);
-        if ((threadIdx.x & 31) == 0 && l / 32 < P.words) P.hv[(uint64_t)blockIdx.y * P.words + l / 32] = word;
+    const int m = P.log_block;
+    const uint32_t per_half = P.domain >> m;
+    const uint64_t items = (uint64_t)P.n_halves * per_half;
+    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < items;
+         idx += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t half = (uint32_t)(idx / per_half), prefix = (uint32_t)(idx % per_half);
+        const HalfDesc H = P.halves[half];
+        uint32_t bits = eval_block(T, P.aes, P.keys[H.key0], prefix, m);
+        if (H.key1 != kNoKey) bits ^= eval_block(T, P.aes, P.keys[H.key1], prefix, m);
+        if (H.cbit) bits ^= (m == 5 ? 0xFFFFFFFFu : ((1u << (1u << m)) - 1u));
+        const uint32_t pos = prefix << m;
+        atomicOr(P.hv + (uint64_t)half * P.words + pos / 32, bits << (pos % 32));
     }
 }
 
@@ -323,9 +389,15 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
     E.hv = reinterpret_cast<uint32_t*>(ws + off_v);
     E.domain = domain;
     E.words = words;
-    const uint32_t span = std::max<uint32_t>(domain, 32);
-    const unsigned gx = std::min<unsigned>((span + 255) / 256, 8u);
-    k_onehot_evalall<<<dim3(gx, (unsigned)halves.size()), 256, kTableBytes, s>>>(E);
+    E.n_halves = (uint32_t)halves.size();
+    E.log_block = (int)std::min<uint32_t>(3, n);
+    ce = cudaMemsetAsync(E.hv, 0, halves.size() * words * sizeof(uint32_t), s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "half-vector clear");
+    {
+        const uint64_t items = (uint64_t)halves.size() * (domain >> E.log_block);
+        const unsigned grid = (unsigned)std::min<uint64_t>((items + 1023) / 1024, (uint64_t)ctx->sm_count);
+        k_onehot_evalall<<<grid, 1024, kTableBytes, s>>>(E);
+    }
     ctx->launches++;
     const size_t smem = 6 * (size_t)words * sizeof(uint32_t);
     for (uint32_t g = 0; g < n_groups; g++) {
