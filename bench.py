@@ -578,17 +578,20 @@ def run_workload(args):
         step_s = float(np.mean(ms)) / 1e3
         units = len(preds) * n_v
         row_bytes = 3 * ((1 << n) // 32) * 4                   # the three share rows of one element
-        algo_bytes = units * row_bytes + 3 * 3 * words_out * 4   # + packed outputs of 3 groups
+        columns = len({(p["table"], p["attr"]) for p in preds})
+        # every share row of each column the query reads, once, plus the packed outputs
+        algo_bytes = columns * n_v * row_bytes + 3 * 3 * words_out * 4
         peak_bw = float(peaks.get("hbm_gbs", 6800.0))
         line.update({"value": units / step_s, "ms_per_step": step_s * 1e3, "steps": args.steps,
                      "warmup": args.warmup,
                      "config": {"workload": "onehot_107614v_n16_4pred", "elements": n_v, "one_hot_bits": 1 << n,
                                 "groups": "EQ | RANGE | EQ AND RANGE", "element_predicates_per_step": units,
-                                "bytes_per_element_predicate": row_bytes},
+                                "share_row_bytes_per_element": row_bytes, "columns_read": columns},
                      "roofline": {"bound": "hbm", "achieved": algo_bytes / step_s / 1e9, "peak": peak_bw,
                                   "unit": "GB/s", "frac": algo_bytes / step_s / 1e9 / peak_bw,
-                                  "what": "whole step (EvalAll + dot-product launches) against the share rows "
-                                          "and packed outputs it must move"}})
+                                  "what": "whole step (EvalAll + dot-product + fold launches) against the share "
+                                          "rows of each column read (once for all predicates on it) and the packed "
+                                          "outputs"}})
         ctx.close()
         print(json.dumps(line), flush=True)
         return 0

@@ -7,18 +7,22 @@
 // for the share j its key pair is tied to; it XORs its two results, re-shares them
 // in binary RSS and the query element's predicates are ANDed in binary RSS.
 //
-// Two kernels per query:
-//  * k_onehot_evalall: every key half at every position, one tree walk per
-//    position (the walk code of the masked mode with Z_2 outputs), 32 positions
-//    packed into one word by a warp ballot;
-//  * k_onehot_group: per AND-group, a warp per 32 elements streams each element's
-//    three share rows from HBM, ANDs them with the six half vectors staged in
-//    shared memory, reduces parities by ballots, then each lane re-shares and
-//    folds its own element and the warp writes packed result words.
+// Three kernels per query:
+//  * k_onehot_evalall: every key half at every position (the walk code of the masked
+//    mode with Z_2 outputs): the shared top levels are walked once per block of 8
+//    positions and the last 3 levels expanded depth first;
+//  * k_onehot_dots: per attribute column, one pass over the elements' three share
+//    rows serves up to 4 predicates on that column: a CTA per 32 elements, its warps
+//    splitting the rows, each lane holding its slice of the half vectors in
+//    registers; parities are reduced by ballots and each server's bit written packed;
+//  * k_onehot_fold: per AND-group, each element's bits are re-shared in binary RSS
+//    and ANDed in token order; results are packed 32 elements per word.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <utility>
 #include <vector>
 
 #include "device_fss.cuh"
@@ -137,17 +141,144 @@ __global__ void __launch_bounds__(1024, 1) k_onehot_evalall(const __grid_constan
     }
 }
 
-struct GroupParams {
-    uint32_t rk_prf[3][44];
-    const uint32_t* te4;          // global-memory T-tables for the re-share PRF
-    const uint32_t* share[3];     // share set j of the table: [attr][elem][words]
-    uint32_t* out[3];             // packed result share sets, ceil(n_elems / 32) words
+constexpr int kDotPreds = 4;   // predicates one streaming pass over a column serves
+
+// Pass over one attribute column for up to kDotPreds predicates on it: every element's
+// three share rows are read once and ANDed with the six half vectors of each predicate.
+// Output: per predicate and server, the bit z_i = x(first half) xor x(second half),
+// packed 32 elements per word into zbits[pred][server][word].
+struct DotParams {
+    const uint32_t* share[3];     // share set j at the column's first element: [elem][words]
     const uint32_t* hv;           // [half][words]
-    const uint32_t* pred_attr;    // per predicate of the group
-    const uint32_t* pred_step;
-    const uint32_t* pred_half;    // index of the predicate's first half (6 in order [server][half])
+    uint32_t half_base[kDotPreds];
+    uint32_t* zbits[kDotPreds];   // [3][ceil(n_elems / 32)] each
     uint64_t n_elems;
     uint32_t words;
+    uint32_t n_preds;
+};
+
+
+
+// One CTA per 32 elements (one packed output word).  The CTA's warps split each share
+// row: with W >= 128 words warp q covers words [128 q, 128 q + 128) of every row in steps
+// of W' = 128 * warps (one uint4 per lane when W' = W); with W < 128 one warp reads the
+// row word by word.  A lane keeps its slice of the predicates' half vectors in registers
+// for all 32 elements and streams 8 elements' rows at a time; its parity bits of the 32
+// elements are XORed over the warp by shuffles and over the warps through shared memory.
+constexpr int kDotBatch = 8;
+
+__device__ __forceinline__ void slice4(const uint32_t* row, uint32_t W, bool vec, uint32_t w0, uint32_t lane,
+                                       uint32_t out[4]) {
+    if (vec) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(row + w0));
+        out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+    } else {
+#pragma unroll
+        for (int r = 0; r < 4; r++) out[r] = lane + 32u * r < W ? __ldg(row + lane + 32u * r) : 0u;
+    }
+}
+
+__global__ void __launch_bounds__(512) k_onehot_dots(const __grid_constant__ DotParams P) {
+    __shared__ uint32_t zs[16][kDotPreds][3][2];      // per warp: element masks per (pred, share, half)
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+    const uint32_t W = P.words, np = P.n_preds;
+    const bool vec = W >= 128;
+    const uint64_t nwords = (P.n_elems + 31) / 32;
+    const uint64_t wd = blockIdx.x;
+    const uint64_t base = wd * 32;
+    uint32_t mask[kDotPreds][3][2];
+#pragma unroll
+    for (int k = 0; k < kDotPreds; k++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) mask[k][j][0] = mask[k][j][1] = 0;
+    // a lane's words: w0 .. w0 + 3 (vector path) or lane + 32 r (scalar path); the vector
+    // path loops over the row in steps of 128 * warps words
+    for (uint32_t w0 = vec ? warp * 128 + lane * 4 : 0; w0 < (vec ? W : 1u); w0 += vec ? warps * 128 : 1u) {
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            uint32_t h[kDotPreds][2][4];
+#pragma unroll
+            for (int k = 0; k < kDotPreds; k++) {
+                if ((uint32_t)k < np) {
+                    slice4(P.hv + (uint64_t)(P.half_base[k] + j * 2) * W, W, vec, w0, lane, h[k][0]);
+                    slice4(P.hv + (uint64_t)(P.half_base[k] + ((j + 2) % 3) * 2 + 1) * W, W, vec, w0, lane, h[k][1]);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 4; r++) h[k][0][r] = h[k][1][r] = 0;
+                }
+            }
+            // lane-local parity bits, bit c = element base + c; XOR-reduced over the warp below
+            uint32_t pl[kDotPreds][2];
+#pragma unroll
+            for (int k = 0; k < kDotPreds; k++) pl[k][0] = pl[k][1] = 0;
+            for (uint32_t c0 = 0; c0 < 32; c0 += kDotBatch) {
+                uint32_t v[kDotBatch][4];
+#pragma unroll
+                for (int b = 0; b < kDotBatch; b++) {
+                    const uint64_t e = base + c0 + b;
+                    if (e < P.n_elems) slice4(P.share[j] + e * W, W, vec, w0, lane, v[b]);
+                    else v[b][0] = v[b][1] = v[b][2] = v[b][3] = 0;
+                }
+#pragma unroll
+                for (int b = 0; b < kDotBatch; b++)
+#pragma unroll
+                    for (int k = 0; k < kDotPreds; k++) {
+                        if ((uint32_t)k >= np) break;
+#pragma unroll
+                        for (int hh = 0; hh < 2; hh++) {
+                            const uint32_t a = (v[b][0] & h[k][hh][0]) ^ (v[b][1] & h[k][hh][1]) ^
+                                               (v[b][2] & h[k][hh][2]) ^ (v[b][3] & h[k][hh][3]);
+                            pl[k][hh] ^= (__popc(a) & 1u) << (c0 + b);
+                        }
+                    }
+            }
+#pragma unroll
+            for (int k = 0; k < kDotPreds; k++) {
+                if ((uint32_t)k >= np) break;
+#pragma unroll
+                for (int hh = 0; hh < 2; hh++) {
+                    uint32_t m = pl[k][hh];
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) m ^= __shfl_xor_sync(0xFFFFFFFFu, m, off);
+                    mask[k][j][hh] ^= m;
+                }
+            }
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < kDotPreds; k++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                zs[warp][k][j][0] = mask[k][j][0];
+                zs[warp][k][j][1] = mask[k][j][1];
+            }
+    }
+    __syncthreads();
+    // server i: first half with share i, second half with share i + 1
+    if (threadIdx.x < np * 3) {
+        const uint32_t k = threadIdx.x / 3, i = threadIdx.x % 3;
+        uint32_t z = 0;
+        for (uint32_t q = 0; q < warps; q++) z ^= zs[q][k][i][0] ^ zs[q][k][(i + 1) % 3][1];
+        P.zbits[k][(uint64_t)i * nwords + wd] = z;
+    }
+}
+
+void launch_dots(const DotParams& D, uint64_t nwords, int /*sm_count*/, cudaStream_t s) {
+    const uint32_t warps = D.words >= 128 ? std::min<uint32_t>(16, D.words / 128) : 1u;
+    k_onehot_dots<<<(unsigned)nwords, warps * 32, 0, s>>>(D);
+}
+
+// Per AND-group: each element's predicate bits are re-shared in binary RSS and ANDed in
+// token order; one thread per element, results packed by warp ballots.
+struct FoldParams {
+    uint32_t rk_prf[3][44];
+    const uint32_t* te4;               // global-memory T-tables for the PRF
+    const uint32_t* zbase;             // the query's packed predicate bits
+    const uint64_t* zoff;              // per predicate of the group: word offset of its [3][nwords] block
+    const uint32_t* steps;             // per predicate: its index in the token
+    uint32_t* out[3];
+    uint64_t n_elems;
     uint32_t n_preds;
     uint32_t table_id, query_id;
 };
@@ -159,7 +290,7 @@ __device__ __forceinline__ uint32_t prf_bit(const GlobalTab& T, const uint32_t* 
 }
 
 // binary re-share: r_i = z_i xor F(k_i) xor F(k_{i-1})
-__device__ __forceinline__ void reshare_bits(const GlobalTab& T, const GroupParams& P, const uint32_t z[3],
+__device__ __forceinline__ void reshare_bits(const GlobalTab& T, const FoldParams& P, const uint32_t z[3],
                                              uint32_t out[3], uint64_t el, uint32_t step) {
     uint32_t f[3];
 #pragma unroll 1
@@ -169,65 +300,20 @@ __device__ __forceinline__ void reshare_bits(const GlobalTab& T, const GroupPara
     out[2] = z[2] ^ f[2] ^ f[1];
 }
 
-__device__ __forceinline__ uint32_t warp_parity(uint32_t acc) {
-    return __popc(__ballot_sync(0xFFFFFFFFu, __popc(acc) & 1u)) & 1u;
-}
-
-__global__ void __launch_bounds__(256) k_onehot_group(const __grid_constant__ GroupParams P) {
-    extern __shared__ __align__(16) uint32_t hvs[];   // the current predicate's six half vectors
+__global__ void __launch_bounds__(256) k_onehot_fold(const __grid_constant__ FoldParams P) {
     const GlobalTab T{P.te4};
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t W = P.words;
-    const uint64_t tile_elems = (uint64_t)blockDim.x;   // 32 elements per warp
-    for (uint64_t tile = blockIdx.x; tile * tile_elems < P.n_elems; tile += gridDim.x) {
-        const uint64_t base = tile * tile_elems + (uint64_t)warp * 32;
-        const uint64_t my_e = base + lane;               // the element this lane folds
+    const uint64_t nwords = (P.n_elems + 31) / 32;
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint64_t e0 = (uint64_t)blockIdx.x * blockDim.x; e0 < nwords * 32; e0 += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t e = e0 + threadIdx.x;
+        const uint64_t wd = e / 32;
+        const bool valid = e < P.n_elems;
         uint32_t acc[3] = {0, 0, 0};
         for (uint32_t k = 0; k < P.n_preds; k++) {
-            __syncthreads();
-            const uint32_t* src = P.hv + (uint64_t)P.pred_half[k] * W;
-            for (uint32_t i = threadIdx.x; i < 6 * W; i += blockDim.x) hvs[i] = src[i];
-            __syncthreads();
-            const uint64_t row = (uint64_t)P.pred_attr[k] * P.n_elems;
-            uint32_t z[3] = {0, 0, 0};
-            for (uint32_t c = 0; c < 32; c++) {
-                const uint64_t e = base + c;
-                if (e >= P.n_elems) break;                 // uniform across the warp
-                // share j meets server j's first half and server j-1's second half
-                uint32_t x[3][2];
+            uint32_t z[3], b[3];
 #pragma unroll
-                for (int j = 0; j < 3; j++) {
-                    const uint32_t* d = P.share[j] + (row + e) * W;
-                    const uint32_t* h0 = hvs + (j * 2 + 0) * W;
-                    const uint32_t* h1 = hvs + (((j + 2) % 3) * 2 + 1) * W;
-                    uint32_t a0 = 0, a1 = 0;
-                    if ((W & 127u) == 0) {
-                        for (uint32_t w = lane * 4; w < W; w += 128) {
-                            const uint4 v = __ldg(reinterpret_cast<const uint4*>(d + w));
-                            const uint4 p = *reinterpret_cast<const uint4*>(h0 + w);
-                            const uint4 q = *reinterpret_cast<const uint4*>(h1 + w);
-                            a0 ^= (v.x & p.x) ^ (v.y & p.y) ^ (v.z & p.z) ^ (v.w & p.w);
-                            a1 ^= (v.x & q.x) ^ (v.y & q.y) ^ (v.z & q.z) ^ (v.w & q.w);
-                        }
-                    } else {
-                        for (uint32_t w = lane; w < W; w += 32) {
-                            const uint32_t v = __ldg(d + w);
-                            a0 ^= v & h0[w];
-                            a1 ^= v & h1[w];
-                        }
-                    }
-                    x[j][0] = warp_parity(a0);
-                    x[j][1] = warp_parity(a1);
-                }
-                // CS_i: its first half met share i, its second share i+1
-                if (lane == c) {
-                    z[0] = x[0][0] ^ x[1][1];
-                    z[1] = x[1][0] ^ x[2][1];
-                    z[2] = x[2][0] ^ x[0][1];
-                }
-            }
-            uint32_t b[3];
-            reshare_bits(T, P, z, b, my_e, P.pred_step[k]);
+            for (int i = 0; i < 3; i++) z[i] = valid ? (P.zbase[P.zoff[k] + (uint64_t)i * nwords + wd] >> lane) & 1u : 0u;
+            reshare_bits(T, P, z, b, e, P.steps[k]);
             if (k == 0) {
                 acc[0] = b[0]; acc[1] = b[1]; acc[2] = b[2];
             } else {
@@ -237,14 +323,13 @@ __global__ void __launch_bounds__(256) k_onehot_group(const __grid_constant__ Gr
                     const int i1 = (i + 1) % 3;
                     w[i] = (acc[i] & b[i]) ^ (acc[i] & b[i1]) ^ (acc[i1] & b[i]);
                 }
-                reshare_bits(T, P, w, acc, my_e, 64u + P.pred_step[k]);
+                reshare_bits(T, P, w, acc, e, 64u + P.steps[k]);
             }
         }
-        const bool valid = my_e < P.n_elems;
 #pragma unroll
         for (int i = 0; i < 3; i++) {
             const uint32_t word = __ballot_sync(0xFFFFFFFFu, valid && (acc[i] & 1u));
-            if (lane == 0 && base < P.n_elems) P.out[i][base / 32] = word;
+            if (lane == 0 && wd < nwords) P.out[i][wd] = word;
         }
     }
 }
@@ -352,35 +437,46 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
             halves.push_back(h);
         }
     }
-    std::vector<uint32_t> pattr, pstep, phalf;
+    // packed predicate bits: per predicate [3][ceil(n_elems / 32)] words of its table
+    std::vector<uint64_t> zoff(q.preds.size());
+    uint64_t zwords = 0;
+    for (uint32_t p = 0; p < q.preds.size(); p++) {
+        const OnehotTable& tb = ctx->onehot_tables.at(q.preds[p].table);
+        zoff[p] = zwords;
+        zwords += 3 * ((tb.n_elems + 31) / 32);
+    }
+    // per group, the word offsets and token steps of its predicates (token order)
+    std::vector<uint64_t> gzoff;
+    std::vector<uint32_t> gstep;
     std::vector<size_t> gbegin;
     for (uint32_t g = 0; g < n_groups; g++) {
-        gbegin.push_back(pattr.size());
+        gbegin.push_back(gzoff.size());
         for (uint32_t p : members[g]) {
-            pattr.push_back(q.preds[p].attr);
-            pstep.push_back(q.preds[p].step);
-            phalf.push_back(6 * p);
+            gzoff.push_back(zoff[p]);
+            gstep.push_back(q.preds[p].step);
         }
     }
-    const size_t np = pattr.size();
-    // scratch: keys | halves | pred arrays (3 x np) | half vectors
+    const size_t np = gzoff.size();
+    // scratch: keys | halves | group offsets | group steps | half vectors | predicate bits
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t off_h = up(keys.size() * sizeof(DevKey));
-    const size_t off_p = off_h + up(halves.size() * sizeof(HalfDesc));
-    const size_t off_v = off_p + up(3 * np * sizeof(uint32_t));
-    const size_t total = off_v + halves.size() * words * sizeof(uint32_t);
+    const size_t off_o = off_h + up(halves.size() * sizeof(HalfDesc));
+    const size_t off_s = off_o + up(np * sizeof(uint64_t));
+    const size_t off_v = off_s + up(np * sizeof(uint32_t));
+    const size_t off_z = off_v + up(halves.size() * words * sizeof(uint32_t));
+    const size_t total = off_z + zwords * sizeof(uint32_t);
     std::vector<unsigned char> img(off_v, 0);
     std::memcpy(img.data(), keys.data(), keys.size() * sizeof(DevKey));
     std::memcpy(img.data() + off_h, halves.data(), halves.size() * sizeof(HalfDesc));
-    std::memcpy(img.data() + off_p, pattr.data(), np * 4);
-    std::memcpy(img.data() + off_p + np * 4, pstep.data(), np * 4);
-    std::memcpy(img.data() + off_p + 2 * np * 4, phalf.data(), np * 4);
+    std::memcpy(img.data() + off_o, gzoff.data(), np * sizeof(uint64_t));
+    std::memcpy(img.data() + off_s, gstep.data(), np * sizeof(uint32_t));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned char* ws = nullptr;
     ce = cudaMallocAsync(reinterpret_cast<void**>(&ws), total, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "one-hot scratch");
     ce = cudaMemcpyAsync(ws, img.data(), off_v, cudaMemcpyHostToDevice, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "one-hot descriptor upload");
+    uint32_t* zbase = reinterpret_cast<uint32_t*>(ws + off_z);
     EvalAllParams E{};
     E.aes = ctx->aes;
     E.te0 = ctx->d_te0;
@@ -399,32 +495,51 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
         k_onehot_evalall<<<grid, 1024, kTableBytes, s>>>(E);
     }
     ctx->launches++;
-    const size_t smem = 6 * (size_t)words * sizeof(uint32_t);
+    // one streaming pass per (table, attribute) for up to kDotPreds predicates on it
+    std::map<std::pair<uint32_t, uint32_t>, std::vector<uint32_t>> by_column;
+    for (uint32_t p = 0; p < q.preds.size(); p++) by_column[{q.preds[p].table, q.preds[p].attr}].push_back(p);
+    for (auto& col : by_column) {
+        const OnehotTable& tb = ctx->onehot_tables.at(col.first.first);
+        if (tb.n_elems == 0) continue;
+        const size_t set_words = (size_t)tb.n_attrs * tb.n_elems * tb.words;
+        const uint64_t nwords = (tb.n_elems + 31) / 32;
+        const std::vector<uint32_t>& ps = col.second;
+        for (size_t c0 = 0; c0 < ps.size(); c0 += kDotPreds) {
+            DotParams D{};
+            for (int j = 0; j < 3; j++) D.share[j] = tb.dev + j * set_words + (size_t)col.first.second * tb.n_elems * tb.words;
+            D.hv = E.hv;
+            D.n_preds = (uint32_t)std::min<size_t>(kDotPreds, ps.size() - c0);
+            for (uint32_t k = 0; k < D.n_preds; k++) {
+                D.half_base[k] = 6 * ps[c0 + k];
+                D.zbits[k] = zbase + zoff[ps[c0 + k]];
+            }
+            D.n_elems = tb.n_elems;
+            D.words = words;
+            launch_dots(D, nwords, ctx->sm_count, s);
+            ctx->launches++;
+        }
+    }
+    // per AND-group: binary re-share and AND fold, packed outputs
     for (uint32_t g = 0; g < n_groups; g++) {
         const OnehotTable& tb = ctx->onehot_tables.at(q.preds[members[g][0]].table);
         if (tb.n_elems == 0) continue;
-        GroupParams G{};
-        std::memcpy(G.rk_prf, ctx->rk_prf, sizeof G.rk_prf);
-        G.te4 = ctx->d_te4;
-        const size_t set_words = (size_t)tb.n_attrs * tb.n_elems * tb.words;
+        FoldParams F{};
+        std::memcpy(F.rk_prf, ctx->rk_prf, sizeof F.rk_prf);
+        F.te4 = ctx->d_te4;
+        F.zbase = zbase;
+        F.zoff = reinterpret_cast<const uint64_t*>(ws + off_o) + gbegin[g];
+        F.steps = reinterpret_cast<const uint32_t*>(ws + off_s) + gbegin[g];
         for (int j = 0; j < 3; j++) {
-            G.share[j] = tb.dev + j * set_words;
-            G.out[j] = out[3 * g + j];
-            if (!G.out[j]) return fail(OBLIVGM_EINVAL, "NULL output pointer");
+            F.out[j] = out[3 * g + j];
+            if (!F.out[j]) return fail(OBLIVGM_EINVAL, "NULL output pointer");
         }
-        G.hv = E.hv;
-        const uint32_t* pa = reinterpret_cast<const uint32_t*>(ws + off_p);
-        G.pred_attr = pa + gbegin[g];
-        G.pred_step = pa + np + gbegin[g];
-        G.pred_half = pa + 2 * np + gbegin[g];
-        G.n_elems = tb.n_elems;
-        G.words = words;
-        G.n_preds = (uint32_t)members[g].size();
-        G.table_id = q.preds[members[g][0]].table;
-        G.query_id = query_id;
-        const uint64_t tiles = (tb.n_elems + 255) / 256;
-        const unsigned grid = (unsigned)std::min<uint64_t>(tiles, (uint64_t)ctx->sm_count * 4);
-        k_onehot_group<<<grid, 256, smem, s>>>(G);
+        F.n_elems = tb.n_elems;
+        F.n_preds = (uint32_t)members[g].size();
+        F.table_id = q.preds[members[g][0]].table;
+        F.query_id = query_id;
+        const uint64_t nwords = (tb.n_elems + 31) / 32;
+        const unsigned grid = (unsigned)std::min<uint64_t>((nwords * 32 + 255) / 256, (uint64_t)ctx->sm_count * 8);
+        k_onehot_fold<<<grid, 256, 0, s>>>(F);
         ctx->launches++;
     }
     ce = cudaGetLastError();
@@ -438,9 +553,6 @@ namespace ogm {
 
 oblivgm_status set_onehot_attrs() {
     cudaError_t e = cudaFuncSetAttribute(k_onehot_evalall, cudaFuncAttributeMaxDynamicSharedMemorySize, kTableBytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_onehot_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 6 * (1 << kMaxOnehotBits) / 32 * (int)sizeof(uint32_t));
     return e == cudaSuccess ? OBLIVGM_OK : cuda_fail(e, "one-hot kernel attributes");
 }
 

@@ -93,3 +93,25 @@ def test_modes_reject_each_others_tokens(ctx):
     with pytest.raises(P.OblivgmError) as e:
         ctx.filter_and_combine(1, t_onehot, outs_words)
     assert e.value.status == P.EINVAL
+
+
+def test_onehot_many_predicates_on_one_column(ctx):
+    """Seven predicates on one attribute column (two streaming passes of up to four),
+    in three AND-groups, on a ragged table."""
+    n, n_elems = 8, 203
+    g = W.rng(31)
+    vals = W.uniform_attrs(g, 1, n_elems, n)
+    tab = W.onehot_table(vals, n, g)
+    _load(ctx, 0, tab)
+    v = [int(vals[0, i]) for i in (1, 2, 3)]
+    preds = [W.range_pred(0, 0, 0, 10, 250), W.eq_pred(0, 0, 1, v[0]), W.range_pred(0, 0, 0, 0, 200),
+             W.range_pred(0, 0, 2, 30, 255), W.eq_pred(0, 0, 0, v[1]), W.range_pred(0, 0, 2, 0, 254),
+             W.range_pred(0, 0, 1, 5, 255)]
+    preds.sort(key=lambda p: p["group"])
+    toks = P.keygen_onehot(preds, n, bytes(range(3, 19)))
+    got, _ = _run(ctx, toks, 3, [n_elems] * 3, 29)
+    tabs = [(tab["shares"], n)]
+    for grp in range(3):
+        want = oracle.filter_onehot(toks, 29, PRF, tabs, grp, np.arange(n_elems))
+        assert np.array_equal(got[grp], want), grp
+        assert np.array_equal(oracle.reconstruct_bits(got[grp]), oracle.plain_group(preds, grp, vals))
