@@ -390,3 +390,37 @@ def match(n_vertices: int, edges, query_vertices: int, query_edges, vertex_ok, e
 
     extend(0)
     return sorted(out)
+
+
+# ---------------------------------------------------------------- secFetch, case I
+
+FETCH_STEP = 256
+
+
+def fetch_unique(x_shares, tables, table: int, attrs, query_id: int, group: int, prf_keys: bytes):
+    """secFetch case I (Alg. 4, Sec. V-D) over Z_{2^32}: with x_c the RSS result of a filter
+    (one matching candidate), the matched element's index and attribute values.
+
+    index:  sum_c c * [[x_c]]                      -- linear in the shares, RSS as it stands;
+    attr a: sum_c [[v_c]] (x) [[x_c]], per server w_i = sum_c v_i x_i + v_i x_{i+1} + v_{i+1} x_i,
+            then one re-share with counter (element = a, step = 256 + group, table, query).
+    Returns a (3, 1 + len(attrs)) uint32 array: share set i of [index, attr values...].
+    """
+    x = [np.asarray(s, dtype=np.uint64) for s in x_shares]
+    n = len(x[0])
+    shares, _bits = tables[table]
+    c = np.arange(n, dtype=np.uint64)
+    out = np.zeros((3, 1 + len(attrs)), dtype=np.uint64)
+    for i in range(3):
+        out[i, 0] = int(np.sum((c * x[i]) & MASK32)) & MASK32
+    for col, a in enumerate(attrs):
+        v = [np.asarray(shares[j][a], dtype=np.uint64) for j in range(3)]
+        w = []
+        for i in range(3):
+            i1 = (i + 1) % 3
+            prod = (v[i] * x[i] + v[i] * x[i1] + v[i1] * x[i]) & MASK32
+            w.append(int(np.sum(prod)) & MASK32)
+        r = reshare(prf_keys, w, a, FETCH_STEP + group, table, query_id)
+        for i in range(3):
+            out[i, 1 + col] = r[i]
+    return out.astype(np.uint32)

@@ -98,3 +98,26 @@ def test_shares_depend_on_query_id_but_not_result():
     b = oracle.filter_group(toks, 2, PRF, [(t["shares"], 8)], 0, np.arange(64))
     assert not np.array_equal(a, b)
     assert np.array_equal(oracle.reconstruct(a), oracle.reconstruct(b))
+
+
+def test_fetch_unique_reconstructs_the_match():
+    # secFetch case I: with exactly one matching element, the fetched shares reconstruct to its
+    # index and attribute values; with none, to zero
+    g = W.rng(12)
+    bits = 16
+    vals = W.uniform_attrs(g, 3, 500, bits)
+    vals[0] = np.arange(500, dtype=np.uint32) * 7 + 3           # attribute 0 unique per element
+    t = W.table(vals, bits, g)
+    target = 321
+    preds = [W.eq_pred(0, 0, 0, int(vals[0, target]))]
+    toks = oracle.keygen(preds, bits, bytes(range(16)))
+    x = oracle.filter_group(toks, 6, PRF, [(t["shares"], bits)], 0, np.arange(500))
+    got = oracle.fetch_unique(x, [(t["shares"], bits)], 0, [0, 1, 2], 6, 0, PRF)
+    rec = oracle.reconstruct(got)
+    assert rec[0] == target
+    for col, a in enumerate([0, 1, 2]):
+        assert rec[1 + col] % (1 << bits) == vals[a, target]
+    assert len(set(got[:, 1])) == 3                              # re-shared, not the plain value
+    none = oracle.keygen([W.eq_pred(0, 0, 0, 2)], bits, bytes(16))   # 2 is no element's value
+    x0 = oracle.filter_group(none, 6, PRF, [(t["shares"], bits)], 0, np.arange(500))
+    assert not oracle.reconstruct(oracle.fetch_unique(x0, [(t["shares"], bits)], 0, [1], 6, 0, PRF)).any()
