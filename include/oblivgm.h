@@ -280,6 +280,24 @@ oblivgm_status oblivgm_filter_and_combine_noalloc(oblivgm_ctx* ctx, uint32_t que
                                                   const size_t tok_len[3], uint32_t n_groups, uint32_t* const* out,
                                                   void* stream);
 
+/* ---------------------------------------------------------- secFetch case I */
+
+/* secFetch, case I (Alg. 4, Sec. V-D): obliviously fetch the one element of a
+ * table that an AND-group matched.  x[0..2] are device pointers to the
+ * group's RSS result (the three share sets written by
+ * oblivgm_filter_and_combine for that group, n_elems of table_id each); the
+ * result assumes exactly one x_c = 1 (with none it is 0, with several the
+ * sum).  out (device, 3 * (1 + n_attrs) uint32, [share set][column]) gets
+ * the RSS shares of the matched element's index (sum_c c * [[x_c]], column
+ * 0, no re-share needed) and of each listed attribute
+ * (sum_c [[v_c]] (x) [[x_c]] with one re-share; counter element = attribute
+ * index, step = 256 + group, table, query), the attribute values reducing
+ * mod 2^n of the table.  n_attrs <= 64.  Asynchronous on stream.  Errors:
+ * EINVAL, ENOENT (table), ENOMEM, ECUDA. */
+oblivgm_status oblivgm_fetch_unique(oblivgm_ctx* ctx, uint32_t query_id, uint32_t group, uint32_t table_id,
+                                    const uint32_t* const x[3], uint32_t n_attrs, const uint32_t* attrs,
+                                    uint32_t* out, void* stream);
+
 /* ------------------------------------------------------------- one-hot mode */
 
 /* The paper's secEval as written (Sec. V-B, V-C, Eq. predEval, Alg. 3), for

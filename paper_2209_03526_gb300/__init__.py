@@ -161,6 +161,14 @@ class Context:
                                               _stream_handle(stream) if kind == N.MEM_DEVICE else None),
                 "oblivgm_load_shares")
 
+    def fetch_unique(self, query_id: int, group: int, table_id: int, x, attrs, out, stream=None):
+        """secFetch case I: x = the group's three result share tensors; out = int32 CUDA tensor of
+        3 * (1 + len(attrs)) words ([share set][index, attributes...])."""
+        xs = (N.c_vp * 3)(*[t.data_ptr() for t in x])
+        at = (N.c_u32 * max(1, len(attrs)))(*attrs)
+        N.check(self._lib.oblivgm_fetch_unique(self._h, query_id, group, table_id, xs, len(attrs), at,
+                                               out.data_ptr(), _stream_handle(stream)), "oblivgm_fetch_unique")
+
     def load_onehot(self, table_id: int, shares: Sequence, n_bits: int, stream=None):
         """shares: three uint32 CUDA tensors [n_attrs, n_elems, W] of binary one-hot shares."""
         ts = [s.contiguous() for s in shares]

@@ -68,6 +68,8 @@ _SIGS = {
                              ctypes.POINTER(c_u32), ctypes.POINTER(c_vp), ctypes.POINTER(c_vp)], c_i32),
     "oblivgm_plan_launch": ([c_vp, c_vp], c_i32),
     "oblivgm_plan_destroy": ([c_vp], c_i32),
+    "oblivgm_fetch_unique": ([c_vp, c_u32, c_u32, c_u32, ctypes.POINTER(c_vp), c_u32, ctypes.POINTER(c_u32), c_vp,
+                              c_vp], c_i32),
     "oblivgm_keygen_onehot": ([ctypes.POINTER(Pred), c_u32, c_u32, c_u8p, ctypes.POINTER(c_vp), c_size,
                                ctypes.POINTER(c_size)], c_i32),
     "oblivgm_load_onehot": ([c_vp, c_u32, c_u64, c_u32, c_u32, ctypes.POINTER(c_vp), c_i32, c_vp], c_i32),

@@ -340,3 +340,27 @@ def test_expired_device_wait_is_reported_and_context_survives(ctx):
     wl2["preds"] = wl["preds"][:2]
     sample = np.array([0, 1, 4999, wl["target"]])
     assert np.array_equal(got[:, sample], oracle_group(oracle, wl2, toks, 3, 0, sample))
+
+
+def test_fetch_unique_matches_oracle(ctx):
+    """secFetch case I after a filter: the matched element's index and attributes, share for
+    share equal to the oracle's (which runs on its own filter output)."""
+    g = W.rng(71)
+    n_el, bits = 70001, 32
+    vals = W.uniform_attrs(g, 4, n_el, bits)
+    wl = {"tables": [W.table(vals, bits, g)]}
+    load_tables(ctx, wl)
+    target = 54321
+    preds = [W.eq_pred(0, 2, 0, int(vals[2, target])), W.range_pred(0, 1, 0, 0, 0xFFFFFFFF)]
+    toks = P.keygen(preds, bits, bytes(range(7, 23)))
+    outs = alloc_outs(wl, preds=preds)
+    ctx.filter_and_combine(31, toks, outs)
+    res = torch.empty(3 * 4, dtype=torch.int32, device="cuda")
+    ctx.fetch_unique(31, 0, 0, outs[0], [0, 1, 3], res)
+    ctx.sync()
+    got = from_dev(res).reshape(3, 4)
+    x_or = oracle_group(oracle, wl, toks, 31, 0, np.arange(n_el), threads=16)
+    want = oracle.fetch_unique(x_or, [(wl["tables"][0]["shares"], bits)], 0, [0, 1, 3], 31, 0, PRF)
+    assert np.array_equal(got, want)
+    rec = oracle.reconstruct(got)
+    assert rec[0] == target and list(rec[1:]) == [vals[a, target] for a in (0, 1, 3)]
