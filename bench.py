@@ -548,6 +548,103 @@ def run_workload(args):
     line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "u32",
             "data": "synthetic", "workload_mode": args.workload, "schedule": list(sched)}
 
+    if args.workload == "fetch":
+        # secFetch case I after a filter: 1,048,576 vertices, 4 uint32 attributes, the filter
+        # matching one vertex; the fetch of its index and 4 attributes is timed alone
+        n_v = N_VERTICES
+        g = W.rng(8)
+        vals = W.uniform_attrs(g, 4, n_v, 32)
+        tab = W.table(vals, 32, g)
+        ctx.load_shares(0, [torch.from_numpy(x.view(np.int32)).to(dev) for x in tab["shares"]], 32)
+        target = int(g.integers(0, n_v))
+        preds = [W.eq_pred(0, 0, 0, int(vals[0, target]))]
+        toks = P.keygen(preds, 32, KEY_SEED)
+        outs = [[torch.empty(n_v, dtype=torch.int32, device=dev) for _ in range(3)]]
+        ctx.filter_and_combine(1, toks, outs, stream)
+        res = torch.empty(3 * 5, dtype=torch.int32, device=dev)
+        for _ in range(max(1, args.warmup)):
+            ctx.fetch_unique(1, 0, 0, outs[0], [0, 1, 2, 3], res, stream)
+        ctx.sync(stream)
+        ms = []
+        for k in range(args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.fetch_unique(1, 0, 0, outs[0], [0, 1, 2, 3], res, stream)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        rec = (res.cpu().numpy().view(np.uint32).reshape(3, 5).astype(np.uint64).sum(axis=0)) & 0xFFFFFFFF
+        ok = int(rec[0]) == target and [int(v) for v in rec[1:]] == [int(vals[a, target]) for a in range(4)]
+        step_s = float(np.mean(ms)) / 1e3
+        algo_bytes = 12 * n_v * (1 + 4)       # the three result share sets + 4 attributes' share sets
+        peak_bw = float(peaks.get("hbm_gbs", 6800.0))
+        line.update({"value": n_v / step_s, "unit": "candidates/s", "metric": "secFetch case I candidates/s",
+                     "ms_per_step": step_s * 1e3, "steps": args.steps, "warmup": args.warmup,
+                     "config": {"workload": "fetch_unique_1048576v_4attr", "attributes_fetched": 4,
+                                "reconstructs_to_the_match": ok},
+                     "roofline": {"bound": "hbm", "achieved": algo_bytes / step_s / 1e9, "peak": peak_bw,
+                                  "unit": "GB/s", "frac": algo_bytes / step_s / 1e9 / peak_bw}})
+        ctx.close()
+        print(json.dumps(line), flush=True)
+        return 0
+
+    if args.workload == "keygen":
+        # batched Gen on the device: 1,048,576 DPF pairs and 1,048,576 DCF pairs with n = 32
+        # (one fresh pair per element of a 2^20-vertex column, the masked approach's per-value
+        # keys), each timed alone; plus the host genToken time and size of Table 1's queries
+        m, n = N_VERTICES, 32
+        g = W.rng(12)
+        alpha = torch.from_numpy(g.integers(0, 1 << 32, m, dtype=np.uint64).astype(np.uint32).view(np.int32)).to(dev)
+        beta = torch.from_numpy(g.integers(0, 1 << 32, m, dtype=np.uint64).astype(np.uint32).view(np.int32)).to(dev)
+        kinds = {}
+        total_s = total_lu = total_pairs = 0.0
+        for name, kind in (("dpf", P.KEY_DPF), ("dcf", P.KEY_DCF)):
+            L = 28 + n * (20 if kind == P.KEY_DPF else 24)
+            out = torch.empty(2 * m * L, dtype=torch.uint8, device=dev)
+            for _ in range(max(1, args.warmup)):
+                ctx.keygen_device(kind, n, alpha, beta, KEY_SEED, out, stream)
+            ms = []
+            for k in range(args.steps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ctx.keygen_device(kind, n, alpha, beta, KEY_SEED, out, stream)
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+            ctx.sync(stream)
+            s_ = float(np.mean(ms)) / 1e3
+            # two root seeds, then per level 2 parties x 2 children (+ 2 x 2 value words for DCF)
+            lu = m * (2 * LOOKUPS_PER_AES + n * 4 * LOOKUPS_PER_AES
+                      + (n * 4 * LOOKUPS_PER_AES_W0 if kind == P.KEY_DCF else 0))
+            kinds[name] = {"pairs_per_s": m / s_, "ms": s_ * 1e3, "key_bytes": L,
+                           "key_GB_per_s": 2 * m * L / s_ / 1e9, "glookup_per_s": lu / s_ / 1e9}
+            total_s += s_
+            total_lu += lu
+            total_pairs += m
+            del out
+        table1 = {}
+        for sym, mk in (("=", lambda v, i: W.eq_pred(0, 0, i, v)),
+                        ("<<", lambda v, i: W.range_pred(0, 0, i, v, v + 1000))):
+            for q in (2, 4, 8):
+                preds = [mk(1000 * (i + 1), i) for i in range(q)]
+                reps, t0 = 20, time.perf_counter()
+                for _ in range(reps):
+                    tk = P.keygen(preds, 32, KEY_SEED)
+                dt = (time.perf_counter() - t0) / reps
+                table1[f"{sym} |q|={q}"] = {"host_ms": dt * 1e3, "token_MB": sum(len(t) for t in tk) / 1e6}
+        line.update({"metric": "FSS key pairs generated/s (n = 32)", "unit": "key-pairs/s",
+                     "value": total_pairs / total_s, "ms_per_step": total_s * 1e3, "steps": args.steps,
+                     "warmup": args.warmup,
+                     "config": {"workload": "keygen_1048576_dpf_1048576_dcf_n32", "pairs_per_kind": m,
+                                "launch": "one k_keygen launch per kind"},
+                     "kinds": kinds,
+                     "roofline": {"bound": "alu", "achieved": total_lu / total_s / 1e9, "peak": peak_lu,
+                                  "unit": "Glookup/s", "frac": total_lu / total_s / 1e9 / peak_lu},
+                     "table1_host_gentoken": table1})
+        ctx.close()
+        print(json.dumps(line), flush=True)
+        return 0
+
     if args.workload == "onehot":
         # the paper's secEval as written: one-hot vectors of 2^16 positions in binary RSS,
         # 107,614 vertices (the size of the paper's graph), one 16-bit attribute
@@ -692,7 +789,8 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-path and latency comparisons")
     ap.add_argument("--serve-queries", type=int, default=48, help="arrivals per rate in --workload serve")
     ap.add_argument("--plain-queries", type=int, default=6, help="plain-path queries per rate in --workload serve")
-    ap.add_argument("--workload", choices=["bulk", "tiny", "edges", "batch", "serve", "onehot"], default="bulk",
+    ap.add_argument("--workload", choices=["bulk", "tiny", "edges", "batch", "serve", "onehot", "fetch", "keygen"],
+                    default="bulk",
                     help="bulk (default, the headline line); the others print their own line")
     ap.add_argument("--schedule", default="", help="threads,elems_per_thread (skips the autotuner)")
     ap.add_argument("--profile-case", action="store_true",

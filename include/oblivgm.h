@@ -62,6 +62,7 @@ typedef int32_t oblivgm_status;
 
 /* flags of oblivgm_eval_*_batch */
 #define OBLIVGM_ALL_PAIRS 1u
+#define OBLIVGM_KEYS_DEVICE 2u   /* keys are device memory; put the key bit length n in flags bits 8..15 */
 
 typedef struct oblivgm_ctx oblivgm_ctx;
 
@@ -186,6 +187,12 @@ oblivgm_status oblivgm_eval_dpf_batch(oblivgm_ctx* ctx, const uint8_t* keys, uin
                                       const uint32_t* points, const uint32_t* key_of_point, uint64_t n_points,
                                       uint32_t flags, uint32_t* out, uint64_t n_out, void* stream);
 
+/* With flags & OBLIVGM_KEYS_DEVICE (and n in flags bits 8..15) `keys` is a
+ * 4-byte-aligned device pointer, e.g. the output of oblivgm_keygen_device;
+ * the keys are repacked on the device, and a key whose header does not match
+ * (kind, n) evaluates as a zero key and raises EFAULT_DEVICE at the next
+ * oblivgm_sync. */
+
 /* DCF Eval (comparison function x < alpha, construction of Boyle et al.
  * cited in Sec. V-C); same arguments and errors as oblivgm_eval_dpf_batch. */
 oblivgm_status oblivgm_eval_dcf_batch(oblivgm_ctx* ctx, const uint8_t* keys, uint32_t n_keys,
@@ -279,6 +286,24 @@ oblivgm_status oblivgm_filter_plain(oblivgm_ctx* ctx, uint32_t query_id, const u
 oblivgm_status oblivgm_filter_and_combine_noalloc(oblivgm_ctx* ctx, uint32_t query_id, const uint8_t* const tok[3],
                                                   const size_t tok_len[3], uint32_t n_groups, uint32_t* const* out,
                                                   void* stream);
+
+/* -------------------------------------------------- keys generated on GPU */
+
+/* Batched FSS key generation on the GPU, the client's genToken (Sec. V-C)
+ * for many functions at once -- e.g. one key pair per element, which makes
+ * the masked-input approach's per-value keys (Sec. V-C) practical and
+ * removes the one-mask-per-column leak.  Pair i (0 <= i < n_pairs) is
+ * Gen(alpha[i], beta[i]) of `kind` (DPF: beta * [x == alpha]; DCF:
+ * beta * [x < alpha]) over Z_{2^32} with n_bits input bits, from the root
+ * seeds AES_seed(2 i) and AES_seed(2 i + 1) (counter block: u64 index, 8 zero
+ * bytes); same construction, PRG and wire format as oblivgm_keygen's keys.
+ * alpha, beta: device pointers of n_pairs uint32.  keys_out: device pointer,
+ * 4-byte aligned, at least 2 * n_pairs * L bytes (L = 28 + 20 n for DPF,
+ * 28 + 24 n for DCF); key b of pair i at byte (2 i + b) L.  Asynchronous on
+ * stream.  Errors: EINVAL, ERANGE (out_bytes too small), ECUDA. */
+oblivgm_status oblivgm_keygen_device(oblivgm_ctx* ctx, uint32_t kind, uint32_t n_bits, uint64_t n_pairs,
+                                     const uint32_t* alpha, const uint32_t* beta, const uint8_t seed[16],
+                                     uint8_t* keys_out, uint64_t out_bytes, void* stream);
 
 /* ---------------------------------------------------------- secFetch case I */
 

@@ -197,6 +197,22 @@ class Context:
                    key_of_point.data_ptr() if key_of_point is not None else None, points.numel(),
                    ALL_PAIRS if all_pairs else 0, out.data_ptr(), out.numel(), _stream_handle(stream)), name)
 
+    def keygen_device(self, kind: int, n_bits: int, alpha, beta, seed: bytes, out, stream=None):
+        """oblivgm_keygen_device: len(alpha) key pairs into the uint8 CUDA tensor out."""
+        sb = ctypes.create_string_buffer(bytes(seed), 16)
+        N.check(self._lib.oblivgm_keygen_device(self._h, kind, n_bits, alpha.numel(), alpha.data_ptr(),
+                                                beta.data_ptr(), ctypes.addressof(sb), out.data_ptr(), out.numel(),
+                                                _stream_handle(stream)), "oblivgm_keygen_device")
+
+    def eval_device_keys(self, kind: int, n_bits: int, keys, n_keys: int, points, out, key_of_point=None,
+                         all_pairs=False, stream=None):
+        """Raw Eval with device-resident wire keys (OBLIVGM_KEYS_DEVICE)."""
+        fn = self._lib.oblivgm_eval_dpf_batch if kind == KEY_DPF else self._lib.oblivgm_eval_dcf_batch
+        flags = N.KEYS_DEVICE | (n_bits << 8) | (ALL_PAIRS if all_pairs else 0)
+        N.check(fn(self._h, keys.data_ptr(), n_keys, points.data_ptr(),
+                   key_of_point.data_ptr() if key_of_point is not None else None, points.numel(), flags,
+                   out.data_ptr(), out.numel(), _stream_handle(stream)), "oblivgm_eval_batch")
+
     def eval_dpf_batch(self, keys: bytes, n_keys: int, points, out, key_of_point=None, all_pairs=False, stream=None):
         self._eval(self._lib.oblivgm_eval_dpf_batch, "oblivgm_eval_dpf_batch", keys, n_keys, points, key_of_point,
                    out, all_pairs, stream)

@@ -27,6 +27,7 @@ PRED_EQ, PRED_RANGE = 1, 2
 KEY_DPF, KEY_DCF = 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 ALL_PAIRS = 1
+KEYS_DEVICE = 2
 MAX_GROUPS = 64
 NOALLOC_SCRATCH_BYTES = 256 * 1024
 
@@ -68,6 +69,7 @@ _SIGS = {
                              ctypes.POINTER(c_u32), ctypes.POINTER(c_vp), ctypes.POINTER(c_vp)], c_i32),
     "oblivgm_plan_launch": ([c_vp, c_vp], c_i32),
     "oblivgm_plan_destroy": ([c_vp], c_i32),
+    "oblivgm_keygen_device": ([c_vp, c_u32, c_u32, c_u64, c_vp, c_vp, c_u8p, c_vp, c_u64, c_vp], c_i32),
     "oblivgm_fetch_unique": ([c_vp, c_u32, c_u32, c_u32, ctypes.POINTER(c_vp), c_u32, ctypes.POINTER(c_u32), c_vp,
                               c_vp], c_i32),
     "oblivgm_keygen_onehot": ([ctypes.POINTER(Pred), c_u32, c_u32, c_u8p, ctypes.POINTER(c_vp), c_size,

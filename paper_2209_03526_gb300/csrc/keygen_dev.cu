@@ -1,0 +1,222 @@
+// keygen_dev.cu -- batched FSS key generation on the GPU (client side of Sec. V-C):
+// many DPF or DCF key pairs at once, for per-element keys.  Pair i is generated from
+// root seeds s0 = AES_seed(2i), s1 = AES_seed(2i + 1) (counter blocks: u64 index || 0),
+// with the same Gen as the host (BGI16 DPF / Boyle et al. DCF, H_K(s) = AES_K(s) xor s
+// under the fixed keys, control bit = bit 0 of byte 0, Convert = bytes 4..7), and written
+// in the key wire format: key 0 of pair i at byte 2 i L, key 1 at (2 i + 1) L.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "device_fss.cuh"
+#include "host_crypto.h"
+#include "oblivgm.h"
+#include "runtime.h"
+
+namespace ogm {
+
+namespace {
+
+#ifndef OGM_KEYGEN_THREADS
+#define OGM_KEYGEN_THREADS 768
+#endif
+constexpr int kKeygenThreads = OGM_KEYGEN_THREADS;   // one CTA per SM (the tables take 128 KiB)
+
+struct KeygenParams {
+    AesParams aes;
+    uint32_t rk_seed[44];          // round keys of the client's seed (root-seed stream)
+    const uint32_t* te0;
+    const uint32_t* alpha;         // per pair (device)
+    const uint32_t* beta;          // per pair (device)
+    uint8_t* out;                  // 2 * n_pairs keys of key_len bytes
+    uint64_t n_pairs;
+    uint32_t n, kind, key_len;
+};
+
+__device__ __forceinline__ void st32(uint8_t* p, uint32_t v) { *reinterpret_cast<uint32_t*>(p) = v; }
+
+// child of a seed in direction dir: seed with bit 0 of byte 0 cleared, control bit apart
+__device__ __forceinline__ void expand_child(const SmemTab& T, const AesParams& A, uint32_t dir, const uint32_t s[4],
+                                             uint32_t cs[4], uint32_t& ct) {
+    uint32_t o[4];
+    aes_sel(T, A.rk_st, A.d_st, 0u - dir, s, o);
+#pragma unroll
+    for (int w = 0; w < 4; w++) cs[w] = o[w] ^ s[w];
+    ct = cs[0] & 1u;
+    cs[0] &= ~1u;
+}
+
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads) k_keygen(const __grid_constant__ KeygenParams P) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    fill_tables(reinterpret_cast<uint32_t*>(smem), P.te0);
+    __syncthreads();
+    const SmemTab T{reinterpret_cast<const char*>(smem), lane_offset()};
+    const bool dcf = P.kind == OBLIVGM_KEY_DCF;
+    const uint32_t L = P.key_len, lvl = dcf ? 24u : 20u;
+    const int n = (int)P.n;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.n_pairs;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t s0[4], s1[4];
+        {
+            const uint32_t c0[4] = {(uint32_t)(2 * i), (uint32_t)((2 * i) >> 32), 0u, 0u};
+            const uint32_t c1[4] = {(uint32_t)(2 * i + 1), (uint32_t)((2 * i + 1) >> 32), 0u, 0u};
+            aes_one(T, P.rk_seed, c0, s0);
+            aes_one(T, P.rk_seed, c1, s1);
+        }
+        uint8_t* const k0 = P.out + (2 * i) * L;
+        uint8_t* const k1 = k0 + L;
+        st32(k0, (uint32_t)P.kind | ((uint32_t)n << 8));
+        st32(k1, (uint32_t)P.kind | ((uint32_t)n << 8) | (1u << 16));
+        st32(k0 + 4, 0u);
+        st32(k1 + 4, 0u);
+#pragma unroll
+        for (int w = 0; w < 4; w++) {
+            st32(k0 + 8 + 4 * w, s0[w]);
+            st32(k1 + 8 + 4 * w, s1[w]);
+        }
+        const uint32_t alpha = P.alpha[i], beta = P.beta[i];
+        uint32_t t0 = 0u, t1 = 1u, valpha = 0u;
+        for (int lv = 1; lv <= n; lv++) {
+            // children of both parties' seeds in both directions (no runtime-indexed arrays)
+            uint32_t c0l[4], c0r[4], c1l[4], c1r[4], t0l, t0r, t1l, t1r;
+            expand_child(T, P.aes, 0u, s0, c0l, t0l);
+            expand_child(T, P.aes, 1u, s0, c0r, t0r);
+            expand_child(T, P.aes, 0u, s1, c1l, t1l);
+            expand_child(T, P.aes, 1u, s1, c1r, t1r);
+            const uint32_t a = (alpha >> (n - lv)) & 1u;
+            const uint32_t tl = t0l ^ t1l ^ a ^ 1u, tr = t0r ^ t1r ^ a;
+            uint32_t scw[4];
+#pragma unroll
+            for (int w = 0; w < 4; w++) scw[w] = a ? (c0l[w] ^ c1l[w]) : (c0r[w] ^ c1r[w]);   // CW on the lose side
+            const uint32_t off = 24u + (uint32_t)(lv - 1) * lvl;
+#pragma unroll
+            for (int w = 0; w < 4; w++) {
+                st32(k0 + off + 4 * w, scw[w]);
+                st32(k1 + off + 4 * w, scw[w]);
+            }
+            st32(k0 + off + 16, tl | (tr << 8));
+            st32(k1 + off + 16, tl | (tr << 8));
+            if (dcf) {
+                const uint32_t v0l = aes_sel_w0(T, P.aes.rk_v, P.aes.d_v, 0u, s0) ^ s0[0];
+                const uint32_t v0r = aes_sel_w0(T, P.aes.rk_v, P.aes.d_v, ~0u, s0) ^ s0[0];
+                const uint32_t v1l = aes_sel_w0(T, P.aes.rk_v, P.aes.d_v, 0u, s1) ^ s1[0];
+                const uint32_t v1r = aes_sel_w0(T, P.aes.rk_v, P.aes.d_v, ~0u, s1) ^ s1[0];
+                const uint32_t v0_lose = a ? v0l : v0r, v1_lose = a ? v1l : v1r;
+                const uint32_t v0_keep = a ? v0r : v0l, v1_keep = a ? v1r : v1l;
+                const bool neg = t1 != 0;
+                uint32_t vcw = v1_lose - v0_lose - valpha;
+                if (neg) vcw = 0u - vcw;
+                if (a) vcw += neg ? 0u - beta : beta;          // lose side is L: inputs below alpha
+                valpha = valpha - v1_keep + v0_keep + (neg ? 0u - vcw : vcw);
+                st32(k0 + off + 20, vcw);
+                st32(k1 + off + 20, vcw);
+            }
+            const uint32_t tkeep = a ? tr : tl;
+            const uint32_t m0 = 0u - t0, m1 = 0u - t1;
+#pragma unroll
+            for (int w = 0; w < 4; w++) {
+                s0[w] = (a ? c0r[w] : c0l[w]) ^ (scw[w] & m0);
+                s1[w] = (a ? c1r[w] : c1l[w]) ^ (scw[w] & m1);
+            }
+            t0 = (a ? t0r : t0l) ^ (t0 & tkeep);
+            t1 = (a ? t1r : t1l) ^ (t1 & tkeep);
+        }
+        uint32_t cw = dcf ? s1[1] - s0[1] - valpha : beta - s0[1] + s1[1];
+        if (t1) cw = 0u - cw;
+        const uint32_t off = 24u + (uint32_t)n * lvl;
+        st32(k0 + off, cw);
+        st32(k1 + off, cw);
+    }
+}
+
+}  // namespace
+
+}  // namespace ogm
+
+using namespace ogm;
+
+extern "C" oblivgm_status oblivgm_keygen_device(oblivgm_ctx* ctx, uint32_t kind, uint32_t n_bits, uint64_t n_pairs,
+                                                const uint32_t* alpha, const uint32_t* beta, const uint8_t seed[16],
+                                                uint8_t* keys_out, uint64_t out_bytes, void* stream) {
+    if (!ctx || !seed || (n_pairs && (!alpha || !beta || !keys_out))) return fail(OBLIVGM_EINVAL, "NULL argument");
+    if (kind != OBLIVGM_KEY_DPF && kind != OBLIVGM_KEY_DCF) return fail(OBLIVGM_EINVAL, "unknown key kind");
+    if (n_bits < 1 || n_bits > (uint32_t)kMaxBits) return fail(OBLIVGM_EINVAL, "n must be 1..32");
+    const uint32_t L = (uint32_t)key_bytes(kind, (int)n_bits);
+    if (out_bytes < 2ull * L * n_pairs) return fail(OBLIVGM_ERANGE, "key buffer too small");
+    if (reinterpret_cast<uintptr_t>(keys_out) % 4) return fail(OBLIVGM_EINVAL, "key buffer must be 4-byte aligned");
+    cudaError_t ce = cudaSetDevice(ctx->device);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaSetDevice");
+    if (n_pairs == 0) return OBLIVGM_OK;
+    KeygenParams P{};
+    P.aes = ctx->aes;
+    const RoundKeys rk = expand_key(seed);
+    std::memcpy(P.rk_seed, rk.w, sizeof P.rk_seed);
+    P.te0 = ctx->d_te0;
+    P.alpha = alpha;
+    P.beta = beta;
+    P.out = keys_out;
+    P.n_pairs = n_pairs;
+    P.n = n_bits;
+    P.kind = kind;
+    P.key_len = L;
+    const unsigned grid =
+        (unsigned)std::min<uint64_t>((n_pairs + kKeygenThreads - 1) / kKeygenThreads, (uint64_t)ctx->sm_count);
+    k_keygen<kKeygenThreads><<<grid, kKeygenThreads, kTableBytes, static_cast<cudaStream_t>(stream)>>>(P);
+    ctx->launches++;
+    ce = cudaGetLastError();
+    if (ce != cudaSuccess) return cuda_fail(ce, "k_keygen launch");
+    return OBLIVGM_OK;
+}
+
+namespace ogm {
+oblivgm_status set_keygen_attrs() {
+    cudaError_t e = cudaFuncSetAttribute(k_keygen<kKeygenThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTableBytes);
+    return e == cudaSuccess ? OBLIVGM_OK : cuda_fail(e, "keygen kernel attributes");
+}
+}  // namespace ogm
+
+// Wire-format keys already on the device -> DevKey, one thread per key.  A key whose
+// header disagrees with (kind, n) or is malformed becomes a zero key of the expected
+// shape and raises the context's fault flag (bit 2): the walks never see an n above 32.
+namespace ogm {
+namespace {
+__global__ void k_repack(const uint8_t* __restrict__ wire, uint32_t kind, uint32_t n, uint32_t n_keys,
+                         DevKey* __restrict__ out, uint32_t* error) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_keys) return;
+    const uint32_t L = 28u + n * (kind == OBLIVGM_KEY_DPF ? 20u : 24u), lb = kind == OBLIVGM_KEY_DPF ? 20u : 24u;
+    const uint8_t* k = wire + (uint64_t)i * L;
+    DevKey d;
+    memset(&d, 0, sizeof d);
+    const bool ok = k[0] == kind && k[1] == n && k[2] <= 1 && k[3] == 0;
+    d.n = n;
+    d.kind = kind;
+    if (ok) {
+        for (int w = 0; w < 4; w++) d.seed[w] = *reinterpret_cast<const uint32_t*>(k + 8 + 4 * w);
+        for (uint32_t lv = 0; lv < n; lv++) {
+            const uint8_t* p = k + 24 + lv * lb;
+            for (int w = 0; w < 4; w++) d.scw[lv][w] = *reinterpret_cast<const uint32_t*>(p + 4 * w);
+            d.tl |= (uint32_t)(p[16] & 1u) << lv;
+            d.tr |= (uint32_t)(p[17] & 1u) << lv;
+            if (kind == OBLIVGM_KEY_DCF) d.vcw[lv] = *reinterpret_cast<const uint32_t*>(p + 20);
+        }
+        d.cw_final = *reinterpret_cast<const uint32_t*>(k + 24 + n * lb);
+        d.party = k[2];
+    } else {
+        atomicOr(error, 4u);
+    }
+    out[i] = d;
+}
+}  // namespace
+
+oblivgm_status repack_keys_device(oblivgm_ctx* ctx, const uint8_t* wire, uint32_t kind, uint32_t n, uint32_t n_keys,
+                                  DevKey* out, cudaStream_t s) {
+    if (reinterpret_cast<uintptr_t>(wire) % 4) return fail(OBLIVGM_EINVAL, "device keys must be 4-byte aligned");
+    k_repack<<<(n_keys + 127) / 128, 128, 0, s>>>(wire, kind, n, n_keys, out, ctx->d_error);
+    ctx->launches++;
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? OBLIVGM_OK : cuda_fail(e, "k_repack launch");
+}
+}  // namespace ogm

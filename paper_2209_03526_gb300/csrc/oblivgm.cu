@@ -605,6 +605,7 @@ oblivgm_status oblivgm_create(oblivgm_ctx** out, int32_t device, const oblivgm_c
     ctx->cfg = *cfg;
     oblivgm_status st = set_filter_attrs();
     if (st == OBLIVGM_OK) st = set_onehot_attrs();
+    if (st == OBLIVGM_OK) st = set_keygen_attrs();
     if (st != OBLIVGM_OK) { delete ctx; return st; }
     cudaError_t e = cudaMalloc(&ctx->d_te0, 256 * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemcpy(ctx->d_te0, aes_tables().te0, 256 * sizeof(uint32_t), cudaMemcpyHostToDevice);
@@ -660,7 +661,8 @@ oblivgm_status oblivgm_sync(oblivgm_ctx* ctx, void* stream) {
     OGM_CUDA(cudaMemcpy(&flag, ctx->d_error, sizeof flag, cudaMemcpyDeviceToHost), "read fault flag");
     if (flag) {
         cudaMemset(ctx->d_error, 0, sizeof flag);
-        return fail(OBLIVGM_EFAULT_DEVICE, "a bounded device wait expired (key staging)");
+        return fail(OBLIVGM_EFAULT_DEVICE, (flag & 1u) ? "a bounded device wait expired (key staging)"
+                                                       : "a device-resident key had a malformed header");
     }
     return OBLIVGM_OK;
 }
@@ -742,23 +744,30 @@ static oblivgm_status eval_batch(oblivgm_ctx* ctx, uint32_t kind, const uint8_t*
     if (st) return st;
     if (!keys || n_keys == 0 || (n_points && (!points || !out))) return fail(OBLIVGM_EINVAL, "NULL or empty argument");
     const bool all = (flags & OBLIVGM_ALL_PAIRS) != 0;
-    if (flags & ~OBLIVGM_ALL_PAIRS) return fail(OBLIVGM_EINVAL, "unknown flags");
+    const bool dev_keys = (flags & OBLIVGM_KEYS_DEVICE) != 0;
+    if (flags & ~(OBLIVGM_ALL_PAIRS | OBLIVGM_KEYS_DEVICE | 0xFF00u)) return fail(OBLIVGM_EINVAL, "unknown flags");
+    if (!dev_keys && (flags & 0xFF00u)) return fail(OBLIVGM_EINVAL, "key bit length in flags needs OBLIVGM_KEYS_DEVICE");
     if (!all && n_points && !key_of_point) return fail(OBLIVGM_EINVAL, "key_of_point is NULL");
     if (all && n_keys > 65535) return fail(OBLIVGM_EINVAL, "ALL_PAIRS takes at most 65535 keys");
     const uint64_t need = all ? (uint64_t)n_keys * n_points : n_points;
     if (n_out < need) return fail(OBLIVGM_ERANGE, "output buffer too small");
-    const int n = keys[1];
+    const int n = dev_keys ? (int)((flags >> 8) & 0xFFu) : keys[1];
     if (n < 1 || n > kMaxBits) return fail(OBLIVGM_EINVAL, "bad key bit length");
-    const size_t klen = key_bytes(kind, n);
-    std::vector<DevKey> dk(n_keys);
-    std::string err;
-    for (uint32_t k = 0; k < n_keys; k++)
-        if (!repack_key(keys + (size_t)k * klen, klen, kind, n, &dk[k], &err)) return fail(OBLIVGM_EINVAL, err);
     if (n_points == 0) return OBLIVGM_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     DevKey* d_keys = nullptr;
-    OGM_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_keys), dk.size() * sizeof(DevKey), s), "key buffer");
-    OGM_CUDA(cudaMemcpyAsync(d_keys, dk.data(), dk.size() * sizeof(DevKey), cudaMemcpyHostToDevice, s), "key upload");
+    OGM_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_keys), (size_t)n_keys * sizeof(DevKey), s), "key buffer");
+    if (dev_keys) {
+        st = repack_keys_device(ctx, keys, kind, (uint32_t)n, n_keys, d_keys, s);
+        if (st != OBLIVGM_OK) return st;
+    } else {
+        const size_t klen = key_bytes(kind, n);
+        std::vector<DevKey> dk(n_keys);
+        std::string err;
+        for (uint32_t k = 0; k < n_keys; k++)
+            if (!repack_key(keys + (size_t)k * klen, klen, kind, n, &dk[k], &err)) return fail(OBLIVGM_EINVAL, err);
+        OGM_CUDA(cudaMemcpyAsync(d_keys, dk.data(), dk.size() * sizeof(DevKey), cudaMemcpyHostToDevice, s), "key upload");
+    }
     RawParams P{};
     P.aes = ctx->aes;
     P.te0 = ctx->d_te0;
