@@ -86,6 +86,13 @@ def lib():
             l.orc_filter_onehot.argtypes = [u8p, u8p, u8p, ctypes.POINTER(ctypes.c_size_t), u32, u8p,
                                             ctypes.POINTER(_Table), u32, u32, u8p, u64, u8p]
             l.orc_reshare.argtypes = [u8p, u8p, u8p, u64, u32, u32, u32]
+            l.orc_fresh_token_len.argtypes = [ctypes.POINTER(_Pred), u32, ctypes.c_int, u8p, u32]
+            l.orc_fresh_token_len.restype = u64
+            l.orc_keygen_fresh.argtypes = [ctypes.POINTER(_Pred), u32, ctypes.c_int, u8p, u32, u8p, u8p, u8p, u8p,
+                                           u64]
+            l.orc_filter_fresh.argtypes = [u8p, u8p, u8p, u32, u8p, ctypes.POINTER(_Table), u32, u32, u8p, u64, u8p]
+            l.orc_fresh_direct.argtypes = [ctypes.POINTER(_Pred), u32, ctypes.c_int, u8p, u32, u8p, u32, u8p,
+                                           ctypes.POINTER(_Table), u32, u8p, u64, u8p]
             l.orc_init()
             _lib = l
     return _lib
@@ -424,3 +431,97 @@ def fetch_unique(x_shares, tables, table: int, attrs, query_id: int, group: int,
         for i in range(3):
             out[i, 1 + col] = r[i]
     return out.astype(np.uint32)
+
+
+# ---------------------------------------------------------------- fresh keys per element
+
+def _elems_arr(table_elems):
+    return np.ascontiguousarray(table_elems, dtype=np.uint64)
+
+
+def fresh_token_len(preds, n: int, table_elems) -> int:
+    te = _elems_arr(table_elems)
+    L = lib().orc_fresh_token_len(_preds(preds), len(preds), n, te.ctypes.data, len(te))
+    if L == 0:
+        raise ValueError("oracle rejected the fresh-key predicates")
+    return int(L)
+
+
+def keygen_fresh(preds, n: int, table_elems, seed: bytes):
+    """Fresh-key tokens (one mask and one key triple per element and predicate), three bytes objects."""
+    te = _elems_arr(table_elems)
+    L = fresh_token_len(preds, n, te)
+    bufs = [np.zeros(L, dtype=np.uint8) for _ in range(3)]
+    rc = lib().orc_keygen_fresh(_preds(preds), len(preds), n, te.ctypes.data, len(te), _addr(_buf(seed)),
+                                *[b.ctypes.data for b in bufs], L)
+    if rc != 0:
+        raise ValueError(f"oracle fresh keygen failed (code {rc})")
+    return tuple(b.tobytes() for b in bufs)
+
+
+def _run_split(fn, n_out_cols, elems, threads):
+    out = np.zeros((3, len(elems)), dtype=np.uint32)
+
+    def run(lo, hi):
+        part = np.ascontiguousarray(elems[lo:hi])
+        o = np.zeros((3, hi - lo), dtype=np.uint32)
+        rc = fn(part, o)
+        if rc != 0:
+            raise ValueError(f"oracle fresh filter failed (code {rc})")
+        out[:, lo:hi] = o
+
+    n = len(elems)
+    if threads <= 1 or n < 2 * threads:
+        if n:
+            run(0, n)
+    else:
+        cuts = np.linspace(0, n, threads + 1).astype(int)
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(lambda i: run(cuts[i], cuts[i + 1]), range(threads)))
+    return out
+
+
+def filter_fresh(tokens, query_id: int, prf_keys: bytes, tables, group: int, elems, threads: int = 1):
+    """Servers' secEval on fresh-key tokens: (3, len(elems)) RSS shares of the group's AND."""
+    elems = np.ascontiguousarray(elems, dtype=np.uint64)
+    tarr, keep = _tables(tables)
+    toks = [np.frombuffer(t, dtype=np.uint8) for t in tokens]
+    pk = _buf(prf_keys)
+
+    def fn(part, o):
+        return lib().orc_filter_fresh(*[t.ctypes.data for t in toks], query_id, _addr(pk), tarr, len(tables),
+                                      group, part.ctypes.data, len(part), o.ctypes.data)
+
+    out = _run_split(fn, 3, elems, threads)
+    del keep
+    return out
+
+
+def fresh_direct(preds, n: int, seed: bytes, query_id: int, prf_keys: bytes, tables, group: int, elems,
+                 threads: int = 1):
+    """The fresh-key result of one group computed from the client seed, keys made where used."""
+    elems = np.ascontiguousarray(elems, dtype=np.uint64)
+    tarr, keep = _tables(tables)
+    te = _elems_arr([t[0][0].shape[1] for t in tables])
+    pa, sd, pk = _preds(preds), _buf(seed), _buf(prf_keys)
+
+    def fn(part, o):
+        return lib().orc_fresh_direct(pa, len(preds), n, te.ctypes.data, len(te), _addr(sd), query_id, _addr(pk),
+                                      tarr, group, part.ctypes.data, len(part), o.ctypes.data)
+
+    out = _run_split(fn, 3, elems, threads)
+    del keep
+    return out
+
+
+def fresh_layout(kind: int, n: int, N: int):
+    """Byte offsets inside one predicate's data block of a fresh token (the documented layout):
+    dict with rA, rB, cb (RANGE), and per key block (half, sub) its seed/scw/tl/tr/vcw/cw offsets."""
+    N4 = (N + 3) // 4 * 4
+    eq = kind == PRED_EQ
+    kdcf = not eq
+    kb = 16 * N + 16 * n * N + 8 * N4 + 4 * N4 + (4 * n * N4 if kdcf else 0)
+    lay = {"rA": 0, "rB": 4 * N4, "keys_at": (8 if eq else 12) * N4, "key_block": kb, "N4": N4}
+    if not eq:
+        lay["cb"] = 8 * N4
+    return lay

@@ -867,3 +867,378 @@ int orc_filter_onehot(const uint8_t* tok1, const uint8_t* tok2, const uint8_t* t
     free(ev);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Fresh masks and keys per element (Sec. V-C, the basic masked approach)    */
+/* ------------------------------------------------------------------------ */
+/*
+ * The masked-input approach as the paper first describes it: every attribute
+ * value gets its own mask and its own keys.  For predicate p and element c of its
+ * table the client's randomness is AES_K of the block B(c, p, tag, j) =
+ * u64 c || u16 p || u16 tag || u32 j under the client seed K:
+ *   tag 1, j 0: r = bytes 0..3, <r>_1 = bytes 4..7, <r>_2 = bytes 8..11 (each mod
+ *               2^n), <r>_3 = r - <r>_1 - <r>_2 mod 2^n;
+ *   tag 2, j = 4 pair + 2 sub + b: root seed of party b for key `sub` of `pair`.
+ * The functions are those of the per-predicate token (EQ: DPF at lo + r; RANGE:
+ * DCF at hi + 1 + r with beta', DCF at lo + r with -beta', c beta' with
+ * c = [a1 <= a0]), and the servers combine, re-share and AND exactly as orc_filter.
+ *
+ * Token layout (per server i; little-endian; N4 = N rounded up to 4):
+ *   64 B header: u32 0x464D474F, u8 1, u8 i, u8 n, u8 0, u16 n_preds, u16 0,
+ *     u32 0, u64 total length, zeros;
+ *   32 B per predicate: u8 kind, u8 n, u16 table, u16 attr, u16 group, u64 N,
+ *     u64 offset of the data block, u64 0;
+ *   data block: u32 rA[N4], u32 rB[N4], (RANGE) u32 cb[N4], then key blocks
+ *     (A,0), (A,1), (B,0), (B,1) (sub 1 for RANGE only), each: 16-byte seed[N],
+ *     16-byte scw[n][N], u32 tl[N4], u32 tr[N4], (DCF) u32 vcw[n][N4], u32 cw[N4].
+ */
+#define FRESH_MAGIC 0x464D474Fu
+#define MAX_KEY (24 + 32 * 24 + 4)
+
+static uint64_t round4(uint64_t x) { return (x + 3u) & ~(uint64_t)3u; }
+
+static uint64_t fresh_key_block_len(int kind, int n, uint64_t N)
+{
+    uint64_t N4 = round4(N);
+    uint64_t len = 16u * N + 16u * (uint64_t)n * N + 8u * N4 + 4u * N4;
+    if (kind == KIND_DCF) len += 4u * (uint64_t)n * N4;
+    return len;
+}
+
+static uint64_t fresh_data_len(int pred_kind, int n, uint64_t N)
+{
+    uint64_t N4 = round4(N);
+    if (pred_kind == PRED_EQ) return 8u * N4 + 2u * fresh_key_block_len(KIND_DPF, n, N);
+    return 12u * N4 + 4u * fresh_key_block_len(KIND_DCF, n, N);
+}
+
+static int fresh_check(const orc_pred* preds, uint32_t n_preds, int n, const uint64_t* table_elems, uint32_t n_tables)
+{
+    if (n < 1 || n > 32 || n_preds == 0 || n_preds > 64) return -1;
+    uint32_t m = mask_n(n);
+    for (uint32_t p = 0; p < n_preds; p++) {
+        const orc_pred* q = &preds[p];
+        if (q->kind == PRED_EQ) { if (q->lo > m) return -1; }
+        else if (q->kind == PRED_RANGE) { if (q->lo > q->hi || q->hi > m) return -1; }
+        else return -1;
+        if (q->table >= n_tables || q->attr > 0xFFFF || q->group > 0xFFFF) return -1;
+    }
+    return 0;
+}
+
+uint64_t orc_fresh_token_len(const orc_pred* preds, uint32_t n_preds, int n, const uint64_t* table_elems,
+                             uint32_t n_tables)
+{
+    if (fresh_check(preds, n_preds, n, table_elems, n_tables)) return 0;
+    uint64_t len = 64u + 32u * n_preds;
+    for (uint32_t p = 0; p < n_preds; p++) len += fresh_data_len((int)preds[p].kind, n, table_elems[preds[p].table]);
+    return len;
+}
+
+static void client_block(const aes_ks* K, uint64_t c, uint32_t p, uint32_t tag, uint32_t j, uint8_t out[16])
+{
+    uint8_t b[16];
+    for (int i = 0; i < 8; i++) b[i] = (uint8_t)(c >> (8 * i));
+    b[8] = (uint8_t)p; b[9] = (uint8_t)(p >> 8);
+    b[10] = (uint8_t)tag; b[11] = (uint8_t)(tag >> 8);
+    put32(b + 12, j);
+    aes_encrypt(K, b, out);
+}
+
+/* element c's mask shares, c*beta', and its key pairs in wire format:
+ * keys[pair][sub][party] (sub 1 only for RANGE) */
+static void fresh_element(const aes_ks* K, const orc_pred* q, uint32_t p, int n, uint64_t c, uint32_t rs[3],
+                          uint32_t* cbeta, uint8_t keys[3][2][2][MAX_KEY])
+{
+    uint32_t m = mask_n(n);
+    uint8_t blk[16];
+    client_block(K, c, p, 1, 0, blk);
+    uint32_t r = le32(blk) & m;
+    rs[0] = le32(blk + 4) & m;
+    rs[1] = le32(blk + 8) & m;
+    rs[2] = (r - rs[0] - rs[1]) & m;
+    *cbeta = 0;
+    for (int pair = 0; pair < 3; pair++) {
+        uint8_t s0[16], s1[16];
+        if (q->kind == PRED_EQ) {
+            client_block(K, c, p, 2, 4u * pair + 0, s0);
+            client_block(K, c, p, 2, 4u * pair + 1, s1);
+            orc_dpf_gen(n, (q->lo + r) & m, BETA_PRIME, s0, s1, keys[pair][0][0], keys[pair][0][1]);
+        } else {
+            uint32_t a0 = (q->lo + r) & m, a1 = (q->hi + 1u + r) & m;
+            *cbeta = a1 <= a0 ? BETA_PRIME : 0u;
+            client_block(K, c, p, 2, 4u * pair + 0, s0);
+            client_block(K, c, p, 2, 4u * pair + 1, s1);
+            orc_dcf_gen(n, a1, BETA_PRIME, s0, s1, keys[pair][0][0], keys[pair][0][1]);
+            client_block(K, c, p, 2, 4u * pair + 2, s0);
+            client_block(K, c, p, 2, 4u * pair + 3, s1);
+            orc_dcf_gen(n, a0, 0u - BETA_PRIME, s0, s1, keys[pair][1][0], keys[pair][1][1]);
+        }
+    }
+}
+
+static void put_u64(uint8_t* p, uint64_t v)
+{
+    for (int i = 0; i < 8; i++) p[i] = (uint8_t)(v >> (8 * i));
+}
+
+static uint64_t get_u64(const uint8_t* p)
+{
+    uint64_t v = 0;
+    for (int i = 0; i < 8; i++) v |= (uint64_t)p[i] << (8 * i);
+    return v;
+}
+
+/* copy one wire-format key of element c into key block `blk` (layout above) */
+static void scatter_key(uint8_t* blk, int kind, int n, uint64_t N, uint64_t c, const uint8_t* key)
+{
+    uint64_t N4 = round4(N);
+    size_t lb = level_bytes(kind);
+    memcpy(blk + 16u * c, key + 8, 16);
+    uint8_t* scw = blk + 16u * N;
+    uint8_t* tl = scw + 16u * (uint64_t)n * N;
+    uint8_t* tr = tl + 4u * N4;
+    uint8_t* vcw = tr + 4u * N4;
+    uint8_t* cw = vcw + (kind == KIND_DCF ? 4u * (uint64_t)n * N4 : 0u);
+    uint32_t tlw = 0, trw = 0;
+    for (int l = 1; l <= n; l++) {
+        const uint8_t* rec = key + 24 + (size_t)(l - 1) * lb;
+        memcpy(scw + 16u * ((uint64_t)(l - 1) * N + c), rec, 16);
+        tlw |= (uint32_t)(rec[16] & 1u) << (l - 1);
+        trw |= (uint32_t)(rec[17] & 1u) << (l - 1);
+        if (kind == KIND_DCF) memcpy(vcw + 4u * ((uint64_t)(l - 1) * N4 + c), rec + 20, 4);
+    }
+    put32(tl + 4u * c, tlw);
+    put32(tr + 4u * c, trw);
+    memcpy(cw + 4u * c, key + 24 + (size_t)n * lb, 4);
+}
+
+/*
+ * Client key generation for the fresh-key mode, element by element.  Returns 0, -1
+ * on an invalid predicate, -2 if cap is smaller than orc_fresh_token_len.
+ */
+int orc_keygen_fresh(const orc_pred* preds, uint32_t n_preds, int n, const uint64_t* table_elems, uint32_t n_tables,
+                     const uint8_t seed[16], uint8_t* tok1, uint8_t* tok2, uint8_t* tok3, uint64_t cap)
+{
+    uint8_t* tok[3] = {tok1, tok2, tok3};
+    if (fresh_check(preds, n_preds, n, table_elems, n_tables)) return -1;
+    uint64_t total = orc_fresh_token_len(preds, n_preds, n, table_elems, n_tables);
+    if (cap < total) return -2;
+    aes_ks K;
+    key_expansion(seed, &K);
+    for (int i = 0; i < 3; i++) {
+        memset(tok[i], 0, (size_t)total);
+        put32(tok[i], FRESH_MAGIC);
+        tok[i][4] = 1; tok[i][5] = (uint8_t)(i + 1); tok[i][6] = (uint8_t)n;
+        tok[i][8] = (uint8_t)n_preds; tok[i][9] = (uint8_t)(n_preds >> 8);
+        put_u64(tok[i] + 16, total);
+    }
+    uint8_t keys[3][2][2][MAX_KEY];
+    uint64_t off = 64u + 32u * n_preds;
+    for (uint32_t p = 0; p < n_preds; p++) {
+        const orc_pred* q = &preds[p];
+        uint64_t N = table_elems[q->table], N4 = round4(N);
+        int eq = q->kind == PRED_EQ;
+        int kkind = eq ? KIND_DPF : KIND_DCF, nsub = eq ? 1 : 2;
+        uint64_t kb = fresh_key_block_len(kkind, n, N);
+        for (int i = 0; i < 3; i++) {
+            uint8_t* d = tok[i] + 64 + 32 * p;
+            d[0] = (uint8_t)q->kind; d[1] = (uint8_t)n;
+            d[2] = (uint8_t)q->table; d[3] = (uint8_t)(q->table >> 8);
+            d[4] = (uint8_t)q->attr; d[5] = (uint8_t)(q->attr >> 8);
+            d[6] = (uint8_t)q->group; d[7] = (uint8_t)(q->group >> 8);
+            put_u64(d + 8, N);
+            put_u64(d + 16, off);
+        }
+        uint64_t keys_at = (eq ? 8u : 12u) * N4;
+        for (uint64_t c = 0; c < N; c++) {
+            uint32_t rs[3], cbeta;
+            fresh_element(&K, q, p, n, c, rs, &cbeta, keys);
+            for (int i = 0; i < 3; i++) {
+                uint8_t* blk = tok[i] + off;
+                put32(blk + 4u * c, rs[i]);
+                put32(blk + 4u * N4 + 4u * c, rs[(i + 1) % 3]);
+                if (!eq) put32(blk + 8u * N4 + 4u * c, cbeta);
+                for (int h = 0; h < 2; h++) {
+                    int pair = HOLD_PAIR[i][h] - 1, b = HOLD_PARTY[i][h];
+                    for (int s = 0; s < nsub; s++)
+                        scatter_key(blk + keys_at + (uint64_t)(h * nsub + s) * kb, kkind, n, N, c, keys[pair][s][b]);
+                }
+            }
+        }
+        off += fresh_data_len((int)q->kind, n, N);
+    }
+    return 0;
+}
+
+/* rebuild the wire-format key of element c from key block `blk` */
+static void gather_key(const uint8_t* blk, int kind, int n, uint64_t N, uint64_t c, int party, uint8_t* key)
+{
+    uint64_t N4 = round4(N);
+    size_t lb = level_bytes(kind);
+    memset(key, 0, orc_key_len(kind, n));
+    key[0] = (uint8_t)kind; key[1] = (uint8_t)n; key[2] = (uint8_t)party;
+    memcpy(key + 8, blk + 16u * c, 16);
+    const uint8_t* scw = blk + 16u * N;
+    const uint8_t* tl = scw + 16u * (uint64_t)n * N;
+    const uint8_t* tr = tl + 4u * N4;
+    const uint8_t* vcw = tr + 4u * N4;
+    const uint8_t* cw = vcw + (kind == KIND_DCF ? 4u * (uint64_t)n * N4 : 0u);
+    uint32_t tlw = le32(tl + 4u * c), trw = le32(tr + 4u * c);
+    for (int l = 1; l <= n; l++) {
+        uint8_t* rec = key + 24 + (size_t)(l - 1) * lb;
+        memcpy(rec, scw + 16u * ((uint64_t)(l - 1) * N + c), 16);
+        rec[16] = (uint8_t)((tlw >> (l - 1)) & 1u);
+        rec[17] = (uint8_t)((trw >> (l - 1)) & 1u);
+        if (kind == KIND_DCF) memcpy(rec + 20, vcw + 4u * ((uint64_t)(l - 1) * N4 + c), 4);
+    }
+    memcpy(key + 24 + (size_t)n * lb, cw + 4u * c, 4);
+}
+
+/*
+ * The servers' side on fresh tokens: and-group `group` on the listed elements, out
+ * [3][n_sel] as orc_filter.  Element c reads its own mask shares and keys.
+ * Returns 0 or a negative code on malformed input.
+ */
+int orc_filter_fresh(const uint8_t* tok1, const uint8_t* tok2, const uint8_t* tok3, uint32_t query_id,
+                     const uint8_t prf_keys[48], const orc_table* tables, uint32_t n_tables, uint32_t group,
+                     const uint64_t* elems, uint64_t n_sel, uint32_t* out)
+{
+    const uint8_t* tok[3] = {tok1, tok2, tok3};
+    for (int i = 0; i < 3; i++) {
+        if (le32(tok[i]) != FRESH_MAGIC || tok[i][4] != 1 || tok[i][5] != i + 1) return -1;
+        if (memcmp(tok[i] + 6, tok[0] + 6, 4) != 0 || get_u64(tok[i] + 16) != get_u64(tok[0] + 16)) return -1;
+    }
+    int n = tok[0][6], np = tok[0][8] | (tok[0][9] << 8);
+    if (n < 1 || n > 32 || np < 1 || np > 64) return -1;
+    int members[64], nm = 0, table = -1;
+    for (int p = 0; p < np; p++) {
+        const uint8_t* d = tok[0] + 64 + 32 * p;
+        for (int i = 1; i < 3; i++)
+            if (memcmp(tok[i] + 64 + 32 * p, d, 32) != 0) return -1;
+        if ((uint32_t)(d[6] | (d[7] << 8)) != group) continue;
+        int t = d[2] | (d[3] << 8);
+        if (table >= 0 && t != table) return -3;
+        table = t;
+        members[nm++] = p;
+    }
+    if (nm == 0) return -2;
+    if ((uint32_t)table >= n_tables) return -3;
+    const orc_table* T = &tables[table];
+    aes_ks prf_ks[3];
+    for (int i = 0; i < 3; i++) key_expansion(prf_keys + 16 * i, &prf_ks[i]);
+    uint8_t key[MAX_KEY];
+    for (uint64_t s = 0; s < n_sel; s++) {
+        uint64_t e = elems[s];
+        if (e >= T->n_elems) return -4;
+        uint32_t acc[3] = {0, 0, 0};
+        for (int k = 0; k < nm; k++) {
+            int p = members[k];
+            const uint8_t* d = tok[0] + 64 + 32 * p;
+            int kind = d[0], attr = d[4] | (d[5] << 8);
+            uint64_t N = get_u64(d + 8), off = get_u64(d + 16), N4 = round4(N);
+            if (N != T->n_elems || (uint32_t)attr >= T->n_attrs || (uint32_t)n != T->n_bits) return -3;
+            int eq = kind == PRED_EQ;
+            int kkind = eq ? KIND_DPF : KIND_DCF, nsub = eq ? 1 : 2;
+            uint64_t kb = fresh_key_block_len(kkind, n, N), keys_at = (eq ? 8u : 12u) * N4;
+            /* open x^_e = x_e + r_e: server i contributes <x_e>_i + <r_e>_i */
+            uint32_t xhat = 0;
+            for (int i = 0; i < 3; i++)
+                xhat += T->share[i][(uint64_t)attr * T->n_elems + e] + le32(tok[i] + off + 4u * e);
+            xhat &= mask_n(n);
+            uint32_t z[3];
+            for (int i = 0; i < 3; i++) {
+                const uint8_t* blk = tok[i] + off;
+                z[i] = 0;
+                for (int h = 0; h < 2; h++) {
+                    int b = HOLD_PARTY[i][h];
+                    for (int sb = 0; sb < nsub; sb++) {
+                        gather_key(blk + keys_at + (uint64_t)(h * nsub + sb) * kb, kkind, n, N, e, b, key);
+                        z[i] += eq ? orc_dpf_eval(key, xhat) : orc_dcf_eval(key, xhat);
+                    }
+                    if (!eq && b == 0) z[i] += le32(blk + 8u * N4 + 4u * e);
+                }
+            }
+            uint32_t bsh[3];
+            reshare(prf_ks, z, bsh, e, (uint32_t)p, (uint32_t)table, query_id);
+            if (k == 0) {
+                memcpy(acc, bsh, sizeof acc);
+            } else {
+                uint32_t w[3];
+                for (int i = 0; i < 3; i++) {
+                    int i1 = (i + 1) % 3;
+                    w[i] = acc[i] * bsh[i] + acc[i] * bsh[i1] + acc[i1] * bsh[i];
+                }
+                reshare(prf_ks, w, acc, e, 64u + (uint32_t)p, (uint32_t)table, query_id);
+            }
+        }
+        for (int i = 0; i < 3; i++) out[(uint64_t)i * n_sel + s] = acc[i];
+    }
+    return 0;
+}
+
+/*
+ * The same result computed straight from the client seed, without a token: element
+ * e's keys are generated where they are used.  For sampled checks at sizes where a
+ * whole token is too slow to build here.
+ */
+int orc_fresh_direct(const orc_pred* preds, uint32_t n_preds, int n, const uint64_t* table_elems,
+                     uint32_t n_tables, const uint8_t seed[16], uint32_t query_id, const uint8_t prf_keys[48],
+                     const orc_table* tables, uint32_t group, const uint64_t* elems, uint64_t n_sel, uint32_t* out)
+{
+    if (fresh_check(preds, n_preds, n, table_elems, n_tables)) return -1;
+    int members[64], nm = 0, table = -1;
+    for (uint32_t p = 0; p < n_preds; p++) {
+        if (preds[p].group != group) continue;
+        if (table >= 0 && (int)preds[p].table != table) return -3;
+        table = (int)preds[p].table;
+        members[nm++] = (int)p;
+    }
+    if (nm == 0) return -2;
+    const orc_table* T = &tables[table];
+    if (T->n_elems != table_elems[table] || (uint32_t)n != T->n_bits) return -3;
+    aes_ks K, prf_ks[3];
+    key_expansion(seed, &K);
+    for (int i = 0; i < 3; i++) key_expansion(prf_keys + 16 * i, &prf_ks[i]);
+    uint8_t keys[3][2][2][MAX_KEY];
+    for (uint64_t s = 0; s < n_sel; s++) {
+        uint64_t e = elems[s];
+        if (e >= T->n_elems) return -4;
+        uint32_t acc[3] = {0, 0, 0};
+        for (int k = 0; k < nm; k++) {
+            int p = members[k];
+            const orc_pred* q = &preds[p];
+            if (q->attr >= T->n_attrs) return -3;
+            uint32_t rs[3], cbeta;
+            fresh_element(&K, q, (uint32_t)p, n, e, rs, &cbeta, keys);
+            uint32_t xhat = 0;
+            for (int i = 0; i < 3; i++) xhat += T->share[i][(uint64_t)q->attr * T->n_elems + e] + rs[i];
+            xhat &= mask_n(n);
+            int eq = q->kind == PRED_EQ, nsub = eq ? 1 : 2;
+            uint32_t z[3];
+            for (int i = 0; i < 3; i++) {
+                z[i] = 0;
+                for (int h = 0; h < 2; h++) {
+                    int pair = HOLD_PAIR[i][h] - 1, b = HOLD_PARTY[i][h];
+                    for (int sb = 0; sb < nsub; sb++)
+                        z[i] += eq ? orc_dpf_eval(keys[pair][sb][b], xhat) : orc_dcf_eval(keys[pair][sb][b], xhat);
+                    if (!eq && b == 0) z[i] += cbeta;
+                }
+            }
+            uint32_t bsh[3];
+            reshare(prf_ks, z, bsh, e, (uint32_t)p, (uint32_t)table, query_id);
+            if (k == 0) {
+                memcpy(acc, bsh, sizeof acc);
+            } else {
+                uint32_t w[3];
+                for (int i = 0; i < 3; i++) {
+                    int i1 = (i + 1) % 3;
+                    w[i] = acc[i] * bsh[i] + acc[i] * bsh[i1] + acc[i1] * bsh[i];
+                }
+                reshare(prf_ks, w, acc, e, 64u + (uint32_t)p, (uint32_t)table, query_id);
+            }
+        }
+        for (int i = 0; i < 3; i++) out[(uint64_t)i * n_sel + s] = acc[i];
+    }
+    return 0;
+}
