@@ -59,6 +59,15 @@ def lookups_per_element(preds, n_bits=32):
     return fss + 3 * (2 * len(preds) - 1) * LOOKUPS_PER_AES_W0
 
 
+def plain_and(preds, values):
+    """Plaintext AND of a group's predicates (Def. 2), for the checks of the timed modes."""
+    res = np.ones(values.shape[1], dtype=np.uint64)
+    for p in preds:
+        v = values[p["attr"]].astype(np.uint64)
+        res &= ((v == p["lo"]) if p["kind"] == W.PRED_EQ else ((v >= p["lo"]) & (v <= p["hi"]))).astype(np.uint64)
+    return res
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -588,6 +597,60 @@ def run_workload(args):
         print(json.dumps(line), flush=True)
         return 0
 
+    if args.workload == "fresh":
+        # the headline workload (1,048,576 vertices, 4 equality + 4 range predicates, n = 32)
+        # with a fresh mask and key triple per element and predicate: the client's GPU keygen
+        # and the servers' filter on the device-resident tokens, each timed alone
+        wl = W.bulk_vertex_filter(n_vertices=N_VERTICES, seed=2)
+        preds = wl["preds"]
+        n_v = N_VERTICES
+        ctx.load_shares(0, [torch.from_numpy(x.view(np.int32)).to(dev) for x in wl["tables"][0]["shares"]], 32)
+        L = P.fresh_token_size(preds, 32, [n_v])
+        toks = [torch.empty(L, dtype=torch.uint8, device=dev) for _ in range(3)]
+        outs = [[torch.empty(n_v, dtype=torch.int32, device=dev) for _ in range(3)]]
+
+        def timed(fn, reps):
+            ms = []
+            for k in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn(k)
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+            return float(np.mean(ms)) / 1e3
+
+        for _ in range(max(1, args.warmup)):
+            ctx.keygen_fresh(preds, 32, [n_v], KEY_SEED, toks, stream)
+        gen_s = timed(lambda k: ctx.keygen_fresh(preds, 32, [n_v], KEY_SEED, toks, stream), args.steps)
+        for _ in range(max(1, args.warmup)):
+            ctx.filter_fresh(1, toks, outs, stream)
+        ctx.sync(stream)
+        step_s = timed(lambda k: ctx.filter_fresh(2 + k, toks, outs, stream), args.steps)
+        ctx.sync(stream)
+        rec = (sum(o.cpu().numpy().view(np.uint32).astype(np.uint64) for o in outs[0]) & 0xFFFFFFFF)
+        ok = bool(np.array_equal(rec, plain_and(preds, wl["tables"][0]["values"])))
+        units = len(preds) * n_v
+        lookups = lookups_per_element(preds) * n_v
+        key_bytes = 3 * L                              # every token byte is read once per step
+        pairs = n_v * sum(3 if p["kind"] == W.PRED_EQ else 6 for p in preds)
+        peak_bw = float(peaks.get("hbm_gbs", 6800.0))
+        line.update({"value": units / step_s, "ms_per_step": step_s * 1e3, "steps": args.steps,
+                     "warmup": args.warmup,
+                     "config": {"workload": "fresh_keys_bulk_vertex_filter_1048576v_4attr_8pred_n32",
+                                "token_bytes_per_server": L, "element_predicates_per_step": units,
+                                "reconstructs_to_plaintext": ok,
+                                "launch": "one k_filter_fresh launch (servers); one k_keygen_fresh launch (client)"},
+                     "roofline": {"bound": "alu", "achieved": lookups / step_s / 1e9, "peak": peak_lu,
+                                  "unit": "Glookup/s", "frac": lookups / step_s / 1e9 / peak_lu,
+                                  "token_GB_per_s": key_bytes / step_s / 1e9,
+                                  "token_frac_of_hbm": key_bytes / step_s / 1e9 / peak_bw},
+                     "client_keygen": {"ms": gen_s * 1e3, "key_pairs_per_s": pairs / gen_s,
+                                       "token_GB_per_s": key_bytes / gen_s / 1e9}})
+        ctx.close()
+        print(json.dumps(line), flush=True)
+        return 0
+
     if args.workload == "keygen":
         # batched Gen on the device: 1,048,576 DPF pairs and 1,048,576 DCF pairs with n = 32
         # (one fresh pair per element of a 2^20-vertex column, the masked approach's per-value
@@ -789,7 +852,7 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-path and latency comparisons")
     ap.add_argument("--serve-queries", type=int, default=48, help="arrivals per rate in --workload serve")
     ap.add_argument("--plain-queries", type=int, default=6, help="plain-path queries per rate in --workload serve")
-    ap.add_argument("--workload", choices=["bulk", "tiny", "edges", "batch", "serve", "onehot", "fetch", "keygen"],
+    ap.add_argument("--workload", choices=["bulk", "tiny", "edges", "batch", "serve", "onehot", "fetch", "keygen", "fresh"],
                     default="bulk",
                     help="bulk (default, the headline line); the others print their own line")
     ap.add_argument("--schedule", default="", help="threads,elems_per_thread (skips the autotuner)")

@@ -305,6 +305,69 @@ oblivgm_status oblivgm_keygen_device(oblivgm_ctx* ctx, uint32_t kind, uint32_t n
                                      const uint32_t* alpha, const uint32_t* beta, const uint8_t seed[16],
                                      uint8_t* keys_out, uint64_t out_bytes, void* stream);
 
+/* ------------------------------------------ fresh masks and keys per element */
+
+/* The masked-input approach with a fresh mask and fresh keys for every
+ * attribute value (the basic approach of Sec. V-C): for predicate p and
+ * element c of its table the client draws its own mask r_{c,p} and generates
+ * the predicate's three key pairs at the shifted point(s), so the servers open
+ * x^_c = x_c + r_{c,p} and no two opened values share a mask.  The client's
+ * key generation runs on the GPU (oblivgm_keygen_fresh) and writes each
+ * server's token to device memory in the layout below; the servers' filter
+ * (oblivgm_filter_fresh) evaluates element c's own keys, then combines,
+ * re-shares and ANDs exactly as oblivgm_filter_and_combine does (same PRF
+ * counters: element, step p, table, query_id; AND step 64 + p).
+ *
+ * Client randomness: AES-128 under the 16-byte client seed of the block
+ * B(c, p, tag, j) = u64 c || u16 p || u16 tag || u32 j (little-endian):
+ *   tag 1, j 0: mask block; r = bytes 0..3, <r>_1 = bytes 4..7,
+ *               <r>_2 = bytes 8..11, each mod 2^n; <r>_3 = r - <r>_1 - <r>_2.
+ *   tag 2, j = 4 * pair + 2 * sub + b: root seed of party b of key `sub` of
+ *               pair `pair` (0..2).
+ * Keys (beta' = 3^{-1} mod 2^32): EQ: one DPF per pair at alpha = lo + r;
+ * RANGE: sub 0 = DCF at a1 = hi + 1 + r with +beta', sub 1 = DCF at
+ * a0 = lo + r with -beta', and c * beta' with c = [a1 <= a0] (all mod 2^n).
+ * Server i (1..3) holds half A = (pair i, party HA) and half B =
+ * (pair i + 1, party HB): (HA, HB) = (0, 0), (1, 0), (1, 1) for servers 1, 2, 3
+ * (pairs numbered 1..3 here, 0..2 in the block index).
+ *
+ * Fresh token of server i, device memory, little-endian, every array 16-byte
+ * aligned (N = the table's elements, N4 = N rounded up to a multiple of 4):
+ *   header 64 B: u32 magic 0x464D474F, u8 version 1, u8 i, u8 n, u8 0,
+ *     u16 n_preds, u16 0, u32 0, u64 total length, zero to byte 64;
+ *   per predicate a 32 B descriptor: u8 kind, u8 n, u16 table, u16 attr,
+ *     u16 group, u64 N, u64 byte offset of its data block, u64 0;
+ *   data block: u32 rA[N4] = <r_c>_i, u32 rB[N4] = <r_c>_{i+1}, RANGE only
+ *     u32 cb[N4] = c_c * beta'; then the key blocks (A, sub 0), (A, sub 1),
+ *     (B, sub 0), (B, sub 1) (sub 1 for RANGE only), each:
+ *     uint4 seed[N], uint4 scw[n][N] (level-major), u32 tl[N4], u32 tr[N4]
+ *     (bit l - 1 = t^L_CW / t^R_CW of level l), DCF only u32 vcw[n][N4],
+ *     u32 cw[N4] (CW_{n+1}).
+ * Seeds and correction words are the 16 bytes of the wire format's fields
+ * read as four little-endian u32 words. */
+
+/* Size in bytes of each server's fresh token (the same for the three).
+ * table_elems[t] = elements of table t (n_tables entries).  Errors: EINVAL
+ * (as oblivgm_keygen, or a predicate on a table >= n_tables). */
+oblivgm_status oblivgm_fresh_token_size(const oblivgm_pred* preds, uint32_t n_preds, uint32_t n_bits,
+                                        const uint64_t* table_elems, uint32_t n_tables, uint64_t* bytes);
+
+/* Client key generation on the GPU: writes the three servers' fresh tokens
+ * into tok[0..2] (device pointers, 16-byte aligned, cap bytes each).
+ * Asynchronous on stream.  Errors: EINVAL, ERANGE (cap too small), ECUDA. */
+oblivgm_status oblivgm_keygen_fresh(oblivgm_ctx* ctx, const oblivgm_pred* preds, uint32_t n_preds,
+                                    uint32_t n_bits, const uint64_t* table_elems, uint32_t n_tables,
+                                    const uint8_t seed[16], uint8_t* const tok[3], uint64_t cap, void* stream);
+
+/* The servers' secEval (Alg. 3, masked form of Eq. predEval, re-share, AND)
+ * on fresh tokens.  tok[i]: device pointer to server i+1's token; the headers
+ * are read back to the host to plan the launch.  out as in
+ * oblivgm_filter_and_combine.  Asynchronous on stream apart from that
+ * header read.  Errors: EINVAL (malformed or mismatched tokens, a predicate
+ * whose N, attribute or n disagrees with the loaded table), ENOENT, ECUDA. */
+oblivgm_status oblivgm_filter_fresh(oblivgm_ctx* ctx, uint32_t query_id, const uint8_t* const tok[3],
+                                    uint32_t n_groups, uint32_t* const* out, void* stream);
+
 /* ---------------------------------------------------------- secFetch case I */
 
 /* secFetch, case I (Alg. 4, Sec. V-D): obliviously fetch the one element of a

@@ -18,7 +18,7 @@ from ._native import (ALL_PAIRS, EAGAIN, EBUSY, EFAULT_DEVICE, EINVAL, ENOENT, E
 from .build import build
 
 __all__ = ["Context", "keygen", "keygen_onehot", "build", "OblivgmError", "PRED_EQ", "PRED_RANGE", "KEY_DPF", "KEY_DCF",
-           "ALL_PAIRS", "version", "token_len"]
+           "ALL_PAIRS", "version", "token_len", "fresh_token_size"]
 
 
 def _lib():
@@ -56,6 +56,16 @@ def keygen(preds, n_bits: int, seed: bytes):
     sb = ctypes.create_string_buffer(bytes(seed), 16)
     N.check(_lib().oblivgm_keygen(arr, len(preds), n_bits, ctypes.addressof(sb), ptrs, L, lens), "oblivgm_keygen")
     return tuple(b.raw[:lens[i]] for i, b in enumerate(bufs))
+
+
+def fresh_token_size(preds, n_bits: int, table_elems) -> int:
+    """oblivgm_fresh_token_size: bytes of each server's fresh-key token."""
+    arr = _pred_array(preds)
+    te = (ctypes.c_uint64 * len(table_elems))(*[int(v) for v in table_elems])
+    out = ctypes.c_uint64()
+    N.check(_lib().oblivgm_fresh_token_size(arr, len(preds), n_bits, ctypes.addressof(te), len(table_elems),
+                                            ctypes.byref(out)), "oblivgm_fresh_token_size")
+    return out.value
 
 
 def keygen_onehot(preds, n_bits: int, seed: bytes):
@@ -229,6 +239,25 @@ class Context:
         arr = (N.c_vp * len(flat))(*flat)
         N.check(self._lib.oblivgm_filter_and_combine(self._h, query_id, tp, tl, len(outs), arr,
                                                      _stream_handle(stream)), "oblivgm_filter_and_combine")
+
+    def keygen_fresh(self, preds, n_bits: int, table_elems, seed: bytes, toks, stream=None):
+        """oblivgm_keygen_fresh: the client's fresh-key tokens into three uint8 CUDA tensors."""
+        arr = _pred_array(preds)
+        te = (ctypes.c_uint64 * len(table_elems))(*[int(v) for v in table_elems])
+        sb = ctypes.create_string_buffer(bytes(seed), 16)
+        ptrs = (N.c_vp * 3)(*[t.data_ptr() for t in toks])
+        cap = min(t.numel() for t in toks)
+        N.check(self._lib.oblivgm_keygen_fresh(self._h, arr, len(preds), n_bits, ctypes.addressof(te),
+                                               len(table_elems), ctypes.addressof(sb), ptrs, cap,
+                                               _stream_handle(stream)), "oblivgm_keygen_fresh")
+
+    def filter_fresh(self, query_id: int, toks, outs, stream=None):
+        """oblivgm_filter_fresh on three device-resident fresh tokens (uint8 CUDA tensors)."""
+        ptrs = (N.c_vp * 3)(*[t.data_ptr() for t in toks])
+        flat = [t.data_ptr() for g in outs for t in g]
+        arr = (N.c_vp * len(flat))(*flat)
+        N.check(self._lib.oblivgm_filter_fresh(self._h, query_id, ptrs, len(outs), arr, _stream_handle(stream)),
+                "oblivgm_filter_fresh")
 
     def filter_plain(self, query_id: int, tokens, outs, stream=None):
         """The plain per-query path (one launch per key half, global-memory AES tables)."""

@@ -70,6 +70,10 @@ _SIGS = {
     "oblivgm_plan_launch": ([c_vp, c_vp], c_i32),
     "oblivgm_plan_destroy": ([c_vp], c_i32),
     "oblivgm_keygen_device": ([c_vp, c_u32, c_u32, c_u64, c_vp, c_vp, c_u8p, c_vp, c_u64, c_vp], c_i32),
+    "oblivgm_fresh_token_size": ([ctypes.POINTER(Pred), c_u32, c_u32, c_vp, c_u32, ctypes.POINTER(c_u64)], c_i32),
+    "oblivgm_keygen_fresh": ([c_vp, ctypes.POINTER(Pred), c_u32, c_u32, c_vp, c_u32, c_u8p, ctypes.POINTER(c_vp),
+                              c_u64, c_vp], c_i32),
+    "oblivgm_filter_fresh": ([c_vp, c_u32, ctypes.POINTER(c_vp), c_u32, ctypes.POINTER(c_vp), c_vp], c_i32),
     "oblivgm_fetch_unique": ([c_vp, c_u32, c_u32, c_u32, ctypes.POINTER(c_vp), c_u32, ctypes.POINTER(c_u32), c_vp,
                               c_vp], c_i32),
     "oblivgm_keygen_onehot": ([ctypes.POINTER(Pred), c_u32, c_u32, c_u8p, ctypes.POINTER(c_vp), c_size,

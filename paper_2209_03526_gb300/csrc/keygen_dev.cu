@@ -10,6 +10,7 @@
 #include <cstring>
 
 #include "device_fss.cuh"
+#include "gen_device.cuh"
 #include "host_crypto.h"
 #include "oblivgm.h"
 #include "runtime.h"
@@ -36,16 +37,33 @@ struct KeygenParams {
 
 __device__ __forceinline__ void st32(uint8_t* p, uint32_t v) { *reinterpret_cast<uint32_t*>(p) = v; }
 
-// child of a seed in direction dir: seed with bit 0 of byte 0 cleared, control bit apart
-__device__ __forceinline__ void expand_child(const SmemTab& T, const AesParams& A, uint32_t dir, const uint32_t s[4],
-                                             uint32_t cs[4], uint32_t& ct) {
-    uint32_t o[4];
-    aes_sel(T, A.rk_st, A.d_st, 0u - dir, s, o);
+// level records of the wire format, written to both keys of the pair
+struct WireSink {
+    uint8_t* k0;
+    uint8_t* k1;
+    uint32_t lvl;          // bytes per level record: 20 (DPF) or 24 (DCF)
+    bool dcf;
+    uint32_t n;
+    __device__ __forceinline__ void level(int lv, const uint32_t scw[4], uint32_t tl, uint32_t tr, uint32_t vcw) {
+        const uint32_t off = 24u + (uint32_t)lv * lvl;
 #pragma unroll
-    for (int w = 0; w < 4; w++) cs[w] = o[w] ^ s[w];
-    ct = cs[0] & 1u;
-    cs[0] &= ~1u;
-}
+        for (int w = 0; w < 4; w++) {
+            st32(k0 + off + 4 * w, scw[w]);
+            st32(k1 + off + 4 * w, scw[w]);
+        }
+        st32(k0 + off + 16, tl | (tr << 8));
+        st32(k1 + off + 16, tl | (tr << 8));
+        if (dcf) {
+            st32(k0 + off + 20, vcw);
+            st32(k1 + off + 20, vcw);
+        }
+    }
+    __device__ __forceinline__ void final(uint32_t cw) {
+        const uint32_t off = 24u + n * lvl;
+        st32(k0 + off, cw);
+        st32(k1 + off, cw);
+    }
+};
 
 template <int kThreads>
 __global__ void __launch_bounds__(kThreads) k_keygen(const __grid_constant__ KeygenParams P) {
@@ -54,7 +72,7 @@ __global__ void __launch_bounds__(kThreads) k_keygen(const __grid_constant__ Key
     __syncthreads();
     const SmemTab T{reinterpret_cast<const char*>(smem), lane_offset()};
     const bool dcf = P.kind == OBLIVGM_KEY_DCF;
-    const uint32_t L = P.key_len, lvl = dcf ? 24u : 20u;
+    const uint32_t L = P.key_len;
     const int n = (int)P.n;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.n_pairs;
          i += (uint64_t)gridDim.x * blockDim.x) {
@@ -76,58 +94,8 @@ __global__ void __launch_bounds__(kThreads) k_keygen(const __grid_constant__ Key
             st32(k0 + 8 + 4 * w, s0[w]);
             st32(k1 + 8 + 4 * w, s1[w]);
         }
-        const uint32_t alpha = P.alpha[i], beta = P.beta[i];
-        uint32_t t0 = 0u, t1 = 1u, valpha = 0u;
-        for (int lv = 1; lv <= n; lv++) {
-            // children of both parties' seeds in both directions (no runtime-indexed arrays)
-            uint32_t c0l[4], c0r[4], c1l[4], c1r[4], t0l, t0r, t1l, t1r;
-            expand_child(T, P.aes, 0u, s0, c0l, t0l);
-            expand_child(T, P.aes, 1u, s0, c0r, t0r);
-            expand_child(T, P.aes, 0u, s1, c1l, t1l);
-            expand_child(T, P.aes, 1u, s1, c1r, t1r);
-            const uint32_t a = (alpha >> (n - lv)) & 1u;
-            const uint32_t tl = t0l ^ t1l ^ a ^ 1u, tr = t0r ^ t1r ^ a;
-            uint32_t scw[4];
-#pragma unroll
-            for (int w = 0; w < 4; w++) scw[w] = a ? (c0l[w] ^ c1l[w]) : (c0r[w] ^ c1r[w]);   // CW on the lose side
-            const uint32_t off = 24u + (uint32_t)(lv - 1) * lvl;
-#pragma unroll
-            for (int w = 0; w < 4; w++) {
-                st32(k0 + off + 4 * w, scw[w]);
-                st32(k1 + off + 4 * w, scw[w]);
-            }
-            st32(k0 + off + 16, tl | (tr << 8));
-            st32(k1 + off + 16, tl | (tr << 8));
-            if (dcf) {
-                const uint32_t v0l = aes_sel_w0(T, P.aes.rk_v, P.aes.d_v, 0u, s0) ^ s0[0];
-                const uint32_t v0r = aes_sel_w0(T, P.aes.rk_v, P.aes.d_v, ~0u, s0) ^ s0[0];
-                const uint32_t v1l = aes_sel_w0(T, P.aes.rk_v, P.aes.d_v, 0u, s1) ^ s1[0];
-                const uint32_t v1r = aes_sel_w0(T, P.aes.rk_v, P.aes.d_v, ~0u, s1) ^ s1[0];
-                const uint32_t v0_lose = a ? v0l : v0r, v1_lose = a ? v1l : v1r;
-                const uint32_t v0_keep = a ? v0r : v0l, v1_keep = a ? v1r : v1l;
-                const bool neg = t1 != 0;
-                uint32_t vcw = v1_lose - v0_lose - valpha;
-                if (neg) vcw = 0u - vcw;
-                if (a) vcw += neg ? 0u - beta : beta;          // lose side is L: inputs below alpha
-                valpha = valpha - v1_keep + v0_keep + (neg ? 0u - vcw : vcw);
-                st32(k0 + off + 20, vcw);
-                st32(k1 + off + 20, vcw);
-            }
-            const uint32_t tkeep = a ? tr : tl;
-            const uint32_t m0 = 0u - t0, m1 = 0u - t1;
-#pragma unroll
-            for (int w = 0; w < 4; w++) {
-                s0[w] = (a ? c0r[w] : c0l[w]) ^ (scw[w] & m0);
-                s1[w] = (a ? c1r[w] : c1l[w]) ^ (scw[w] & m1);
-            }
-            t0 = (a ? t0r : t0l) ^ (t0 & tkeep);
-            t1 = (a ? t1r : t1l) ^ (t1 & tkeep);
-        }
-        uint32_t cw = dcf ? s1[1] - s0[1] - valpha : beta - s0[1] + s1[1];
-        if (t1) cw = 0u - cw;
-        const uint32_t off = 24u + (uint32_t)n * lvl;
-        st32(k0 + off, cw);
-        st32(k1 + off, cw);
+        WireSink sink{k0, k1, dcf ? 24u : 20u, dcf, (uint32_t)n};
+        gen_pair(T, P.aes, dcf, n, P.alpha[i], P.beta[i], s0, s1, sink);
     }
 }
 

@@ -104,3 +104,15 @@ def test_onehot_keygen_byte_identical_to_oracle(n):
         assert P.keygen_onehot(preds, n, seed) == oracle.keygen_onehot(preds, n, seed)
     with pytest.raises(P.OblivgmError):
         P.keygen_onehot([W.eq_pred(0, 0, 0, 1)], 17, bytes(16))
+
+
+def test_fresh_token_size_matches_oracle_layout():
+    preds = [W.eq_pred(0, 0, 0, 5), W.range_pred(1, 1, 1, 2, 9), W.range_pred(0, 2, 0, 0, 255)]
+    for n, elems in ((8, [1, 1]), (8, [1003, 17]), (32, [4096, 5])):
+        assert P.fresh_token_size(preds, n, elems) == oracle.fresh_token_len(preds, n, elems)
+    with pytest.raises(P.OblivgmError):
+        P.fresh_token_size(preds, 8, [10])                 # table 1 has no size
+    with pytest.raises(P.OblivgmError):
+        P.fresh_token_size([W.range_pred(0, 0, 0, 9, 2)], 8, [10])
+    with pytest.raises(P.OblivgmError):
+        P.fresh_token_size(preds, 33, [10, 10])
