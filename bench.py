@@ -601,9 +601,9 @@ def run_workload(args):
         # the headline workload (1,048,576 vertices, 4 equality + 4 range predicates, n = 32)
         # with a fresh mask and key triple per element and predicate: the client's GPU keygen
         # and the servers' filter on the device-resident tokens, each timed alone
-        wl = W.bulk_vertex_filter(n_vertices=N_VERTICES, seed=2)
+        n_v = args.elems or N_VERTICES
+        wl = W.bulk_vertex_filter(n_vertices=n_v, seed=2)
         preds = wl["preds"]
-        n_v = N_VERTICES
         ctx.load_shares(0, [torch.from_numpy(x.view(np.int32)).to(dev) for x in wl["tables"][0]["shares"]], 32)
         L = P.fresh_token_size(preds, 32, [n_v])
         toks = [torch.empty(L, dtype=torch.uint8, device=dev) for _ in range(3)]
@@ -637,7 +637,7 @@ def run_workload(args):
         peak_bw = float(peaks.get("hbm_gbs", 6800.0))
         line.update({"value": units / step_s, "ms_per_step": step_s * 1e3, "steps": args.steps,
                      "warmup": args.warmup,
-                     "config": {"workload": "fresh_keys_bulk_vertex_filter_1048576v_4attr_8pred_n32",
+                     "config": {"workload": f"fresh_keys_bulk_vertex_filter_{n_v}v_4attr_8pred_n32",
                                 "token_bytes_per_server": L, "element_predicates_per_step": units,
                                 "reconstructs_to_plaintext": ok,
                                 "launch": "one k_filter_fresh launch (servers); one k_keygen_fresh launch (client)"},
@@ -855,6 +855,7 @@ def main():
     ap.add_argument("--workload", choices=["bulk", "tiny", "edges", "batch", "serve", "onehot", "fetch", "keygen", "fresh"],
                     default="bulk",
                     help="bulk (default, the headline line); the others print their own line")
+    ap.add_argument("--elems", type=int, default=0, help="--workload fresh: vertices (default 1,048,576)")
     ap.add_argument("--schedule", default="", help="threads,elems_per_thread (skips the autotuner)")
     ap.add_argument("--profile-case", action="store_true",
                     help="one small fused launch for ncu: 4,194,304 elements, 1 attribute, 1 equality + 1 range "

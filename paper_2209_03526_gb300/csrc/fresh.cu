@@ -35,7 +35,10 @@ constexpr uint32_t kFreshMagic = 0x464D474Fu;
 constexpr int kFreshMaxPreds = 64;
 constexpr int kFreshMaxJobs = kFreshMaxPreds * 6;
 constexpr int kFreshGenThreads = 768;    // 80 registers: one 768-thread CTA per SM with the 128 KiB tables
-constexpr int kFreshEvalThreads = 512;
+#ifndef OGM_FRESH_EVAL_THREADS
+#define OGM_FRESH_EVAL_THREADS 768
+#endif
+constexpr int kFreshEvalThreads = OGM_FRESH_EVAL_THREADS;
 
 // halves held by server i (0-based): (pair, party) -- CS1 (1,0),(2,0); CS2 (2,1),(3,0); CS3 (3,1),(1,1)
 __constant__ uint8_t c_hold_pair[3][2] = {{0, 1}, {1, 2}, {2, 0}};
@@ -199,33 +202,38 @@ struct FreshEvalParams {
 __device__ __forceinline__ uint4 ldg4(const uint8_t* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
 __device__ __forceinline__ uint32_t ldg1(const uint8_t* p) { return __ldg(reinterpret_cast<const uint32_t*>(p)); }
 
-// DPF (dcf = false) or DCF Eval of element c's key in key block blk at input x; the
-// next level's correction word is loaded one level ahead of its use.
-__device__ __forceinline__ uint32_t walk_soa(const SmemTab& T, const AesParams& A, bool dcf, const uint8_t* blk,
-                                             uint64_t N, uint64_t N4, uint64_t c, uint32_t n, uint32_t party,
-                                             uint32_t x) {
-    const uint8_t* scwp = blk + 16 * N + 16 * c;
-    const uint8_t* tp = blk + 16 * N + 16 * (uint64_t)n * N + 4 * c;
-    const uint8_t* vp = tp + 8 * N4;
-    const uint8_t* cwp = vp + (dcf ? 4 * (uint64_t)n * N4 : 0);
-    const uint4 s4 = ldg4(blk + 16 * c);
+// DPF (DCF = false) or DCF Eval of element c's key in key block blk at input x.  The
+// level-major arrays are walked with pointer increments, and the next level's
+// correction word is loaded one level ahead of its use.
+template <bool DCF>
+__device__ __forceinline__ uint32_t walk_soa(const SmemTab& T, const AesParams& A, const uint8_t* blk, uint64_t N,
+                                             uint64_t N4, uint64_t c, uint32_t n, uint32_t party, uint32_t x) {
+    const uint4* scwp = reinterpret_cast<const uint4*>(blk + 16 * N) + c;
+    const uint32_t* tp = reinterpret_cast<const uint32_t*>(blk + 16 * N + 16 * (uint64_t)n * N) + c;
+    const uint32_t* vp = tp + 2 * N4;
+    const uint32_t* cwp = vp + (DCF ? (uint64_t)n * N4 : 0);
+    const uint4 s4 = __ldg(reinterpret_cast<const uint4*>(blk) + c);
     uint32_t s[4] = {s4.x, s4.y, s4.z, s4.w};
-    const uint32_t tl = ldg1(tp), tr = ldg1(tp + 4 * N4), cwf = ldg1(cwp);
+    const uint32_t tl = __ldg(tp), tr = __ldg(tp + N4), cwf = __ldg(cwp);
     uint32_t t = party, V = 0;
-    uint4 cw_next = ldg4(scwp);
-    uint32_t vcw_next = dcf ? ldg1(vp) : 0u;
+    uint4 cw_next = __ldg(scwp);
+    uint32_t vcw_next = DCF ? __ldg(vp) : 0u;
     for (uint32_t i = 0; i < n; i++) {
         const uint4 cw = cw_next;
         const uint32_t vcw = vcw_next;
         if (i + 1 < n) {
-            cw_next = ldg4(scwp + 16 * (uint64_t)(i + 1) * N);
-            if (dcf) vcw_next = ldg1(vp + 4 * (uint64_t)(i + 1) * N4);
+            scwp += N;
+            cw_next = __ldg(scwp);
+            if (DCF) {
+                vp += N4;
+                vcw_next = __ldg(vp);
+            }
         }
         const uint32_t dir = (x >> (n - 1 - i)) & 1u;
         const uint32_t msk = 0u - dir;
         uint32_t o[4];
         aes_sel(T, A.rk_st, A.d_st, msk, s, o);
-        if (dcf) {
+        if (DCF) {
             const uint32_t v0 = aes_sel_w0(T, A.rk_v, A.d_v, msk, s) ^ s[0];
             const uint32_t term = v0 + (t ? vcw : 0u);
             V += party ? 0u - term : term;
@@ -295,7 +303,8 @@ __global__ void __launch_bounds__(kFreshEvalThreads, 1) k_filter_fresh(const __g
                 const int i = kk / (2 * nsub), h = (kk / nsub) & 1, sub = kk % nsub;
                 const uint32_t party = c_hold_party[i][h];
                 const uint8_t* blk = Q.data[i] + L.keys_at + (uint64_t)(h * nsub + sub) * L.key_block;
-                uint32_t v = walk_soa(T, P.aes, !eq, blk, L.N, L.N4, c, n, party, xh);
+                uint32_t v = eq ? walk_soa<false>(T, P.aes, blk, L.N, L.N4, c, n, party, xh)
+                                : walk_soa<true>(T, P.aes, blk, L.N, L.N4, c, n, party, xh);
                 // RANGE: c * beta' joins party 0's half once
                 if (!eq && sub == 0 && party == 0) v += ldg1(Q.data[i] + 8 * L.N4 + 4 * c);
                 z[0] += i == 0 ? v : 0u;
