@@ -401,11 +401,18 @@ def run_profile_case(args):
 
 
 def kernel_hash() -> str:
+    """Hash of the k_filter source: the device AES/FSS header and the kernel's part of
+    oblivgm.cu (from the PTX helpers to the raw-batch section), so host-code edits
+    elsewhere do not invalidate a traffic capture."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("device_fss.cuh", "oblivgm.cu"):
-        with open(os.path.join(ROOT, "paper_2209_03526_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    with open(os.path.join(ROOT, "paper_2209_03526_gb300", "csrc", "device_fss.cuh"), "rb") as fh:
+        h.update(fh.read())
+    with open(os.path.join(ROOT, "paper_2209_03526_gb300", "csrc", "oblivgm.cu"), "rb") as fh:
+        src = fh.read()
+    a = src.index(b"// ------------------------------------------------------------------ PTX helpers")
+    b = src.index(b"// ------------------------------------------------------------------ raw batches")
+    h.update(src[a:b])
     return h.hexdigest()[:16]
 
 
@@ -547,9 +554,12 @@ def run_workload(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     ctx = P.Context(0, prf_keys=PRF)
-    sched = tuple(int(v) for v in args.schedule.split(",")) if args.schedule else ctx.autotune()
-    if args.schedule:
-        ctx.set_schedule(*sched)
+    if args.workload in ("fresh", "keygen", "fetch", "onehot"):
+        sched = ()                       # these modes do not launch k_filter
+    else:
+        sched = tuple(int(v) for v in args.schedule.split(",")) if args.schedule else ctx.autotune()
+        if args.schedule:
+            ctx.set_schedule(*sched)
     peaks = measured_peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_lu = sm_count * LDS_LANES_PER_CLK * float(peaks.get("sm_max_mhz", 2070.0)) / 1e3

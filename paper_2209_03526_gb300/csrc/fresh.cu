@@ -199,7 +199,6 @@ struct FreshEvalParams {
     FreshPred preds[kFreshMaxPreds];
 };
 
-__device__ __forceinline__ uint4 ldg4(const uint8_t* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
 __device__ __forceinline__ uint32_t ldg1(const uint8_t* p) { return __ldg(reinterpret_cast<const uint32_t*>(p)); }
 
 // DPF (DCF = false) or DCF Eval of element c's key in key block blk at input x.  The
