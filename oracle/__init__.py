@@ -91,6 +91,12 @@ def lib():
             l.orc_keygen_fresh.argtypes = [ctypes.POINTER(_Pred), u32, ctypes.c_int, u8p, u32, u8p, u8p, u8p, u8p,
                                            u64]
             l.orc_filter_fresh.argtypes = [u8p, u8p, u8p, u32, u8p, ctypes.POINTER(_Table), u32, u32, u8p, u64, u8p]
+            l.orc_prp.argtypes = [u8p, u64, u64]
+            l.orc_prp.restype = u64
+            l.orc_shuffle.argtypes = [ctypes.c_int, u64, u32, u8p, u8p, u8p, u8p, u8p, u8p, u8p, u8p, u8p]
+            l.orc_fetch_multi.argtypes = [u64, u8p, u8p, u8p, ctypes.POINTER(_Table), u32, u8p, u8p, u8p, u8p, u8p,
+                                          u64, u8p, u8p]
+            l.orc_fetch_multi.restype = ctypes.c_int64
             l.orc_fresh_direct.argtypes = [ctypes.POINTER(_Pred), u32, ctypes.c_int, u8p, u32, u8p, u32, u8p,
                                            ctypes.POINTER(_Table), u32, u8p, u64, u8p]
             l.orc_init()
@@ -525,3 +531,47 @@ def fresh_layout(kind: int, n: int, N: int):
     if not eq:
         lay["cb"] = 8 * N4
     return lay
+
+
+# ---------------------------------------------------------------- secShuffle / secFetch case II
+
+SHUF_ADD, SHUF_XOR = 0, 1
+
+
+def prp(seed: bytes, n: int, x: int) -> int:
+    """The pair's pseudo-random permutation of [0, n) at x (Feistel with cycle walking)."""
+    return int(lib().orc_prp(_addr(_buf(seed)), n, x))
+
+
+def shuffle(shares, seeds: bytes, group: int = SHUF_ADD):
+    """secShuffle (Alg. 5) of a 3-out-of-3 shared table: shares = three uint32 arrays [n, W];
+    seeds = s12 || s23 || s31 (48 bytes).  Returns the three output share arrays [n, W]."""
+    D = [np.ascontiguousarray(s, dtype=np.uint32) for s in shares]
+    n, W = D[0].shape
+    out = [np.zeros((n, W), dtype=np.uint32) for _ in range(3)]
+    scratch = np.zeros(max(1, 8 * n * W), dtype=np.uint32)
+    perm = np.zeros(max(1, 3 * n), dtype=np.uint64)
+    sd = _buf(seeds)
+    rc = lib().orc_shuffle(group, n, W, *[d.ctypes.data for d in D], _addr(sd), *[o.ctypes.data for o in out],
+                           scratch.ctypes.data, perm.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle shuffle failed")
+    return out
+
+
+def fetch_multi(x_shares, table, attrs, seeds: bytes, cap: int):
+    """secFetch case II: (count, [3 arrays (min(count, cap), 1 + len(attrs))]) of the kept records."""
+    x = [np.ascontiguousarray(v, dtype=np.uint32) for v in x_shares]
+    n = len(x[0])
+    tarr, keep = _tables([table])
+    at = np.ascontiguousarray(attrs, dtype=np.uint32)
+    W = 2 + len(at)
+    out = [np.zeros((max(1, cap), W - 1), dtype=np.uint32) for _ in range(3)]
+    scratch = np.zeros(max(1, 14 * n * W), dtype=np.uint32)
+    perm = np.zeros(max(1, 3 * n), dtype=np.uint64)
+    m = lib().orc_fetch_multi(n, *[v.ctypes.data for v in x], tarr, len(at), at.ctypes.data, _addr(_buf(seeds)),
+                              *[o.ctypes.data for o in out], cap, scratch.ctypes.data, perm.ctypes.data)
+    del keep
+    if m < 0:
+        raise ValueError("oracle fetch_multi rejected its arguments")
+    return int(m), [o[:min(m, cap)] for o in out]

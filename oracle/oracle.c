@@ -1242,3 +1242,206 @@ int orc_fresh_direct(const orc_pred* preds, uint32_t n_preds, int n, const uint6
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* secShuffle (Alg. 5, the protocol of Araki et al. the paper cites)         */
+/* ------------------------------------------------------------------------ */
+/*
+ * A table D of n rows of W uint32 words, 3-out-of-3 shared as D = D1 op D2 op D3,
+ * where op is XOR (binary RSS, as Alg. 5 is written) or addition mod 2^32 (the
+ * arithmetic RSS the masked filter produces).  CS1/CS2 share seed s12, CS2/CS3
+ * s23, CS3/CS1 s31.  From its seed a pair derives
+ *   pi_ab  a pseudo-random permutation of [0, n): a 4-round balanced Feistel
+ *          network on 2h bits (h = max(1, ceil(bits(n - 1) / 2))) with cycle
+ *          walking; round r maps (L, R) to (R, L xor F_r(R)),
+ *          F_r(R) = word 0 of AES_s(u64 R || u16 3 || u16 r || u32 n) mod 2^h;
+ *   tables T_ab, R_a: word w of row i is word (w mod 4) of
+ *          AES_s(u64 i || u16 tag || u16 (w / 4) || u32 0), tag 1 for T, 2 for R.
+ * A permutation moves row i to row pi(i).  The steps, in the order Alg. 5 gives
+ * them (X2 there is the X1 that CS2 receives), with "+"/"-" standing for XOR in
+ * the binary case:
+ *   CS1: X1 = pi31(pi12(D1 + D2 + T12) + T31)
+ *   CS2: Y1 = pi12(D3 - T12);  C1 = pi23(X1 + T23) - R2
+ *   CS3: C2 = pi23(pi31(Y1 - T31) - T23) - R1;  R3 = C1 + C2
+ * Output shares (R1, R2, R3): R1 + R2 + R3 = pi23(pi31(pi12(D))).
+ */
+#define SHUF_XOR 1
+#define SHUF_ADD 0
+
+static int ceil_half_bits(uint64_t n)
+{
+    int b = 0;
+    uint64_t v = n - 1;
+    while (v) { b++; v >>= 1; }
+    int h = (b + 1) / 2;
+    return h < 1 ? 1 : h;
+}
+
+static uint32_t feistel_round(const aes_ks* K, uint32_t R, int r, uint64_t n, int h)
+{
+    uint8_t b[16], o[16];
+    for (int i = 0; i < 8; i++) b[i] = (uint8_t)((uint64_t)R >> (8 * i));
+    b[8] = 3; b[9] = 0;
+    b[10] = (uint8_t)r; b[11] = 0;
+    put32(b + 12, (uint32_t)n);
+    aes_encrypt(K, b, o);
+    return le32(o) & ((1u << h) - 1u);
+}
+
+static uint64_t feistel(const aes_ks* K, uint64_t x, uint64_t n, int h)
+{
+    uint32_t mask = (1u << h) - 1u;
+    uint32_t L = (uint32_t)(x >> h) & mask, R = (uint32_t)x & mask;
+    for (int r = 0; r < 4; r++) {
+        uint32_t t = L ^ feistel_round(K, R, r, n, h);
+        L = R;
+        R = t;
+    }
+    return ((uint64_t)L << h) | R;
+}
+
+/* pi(x) for x < n: walk the Feistel cycle of x until it lands inside [0, n) */
+static uint64_t prp_ks(const aes_ks* K, uint64_t n, uint64_t x)
+{
+    if (n <= 1) return 0;
+    int h = ceil_half_bits(n);
+    uint64_t y = feistel(K, x, n, h);
+    while (y >= n) y = feistel(K, y, n, h);
+    return y;
+}
+
+uint64_t orc_prp(const uint8_t seed[16], uint64_t n, uint64_t x)
+{
+    aes_ks K;
+    key_expansion(seed, &K);
+    return prp_ks(&K, n, x);
+}
+
+static uint32_t table_word(const aes_ks* K, int tag, uint64_t i, uint32_t w)
+{
+    uint8_t b[16], o[16];
+    for (int k = 0; k < 8; k++) b[k] = (uint8_t)(i >> (8 * k));
+    b[8] = (uint8_t)tag; b[9] = 0;
+    b[10] = (uint8_t)(w / 4); b[11] = (uint8_t)(w / 4 >> 8);
+    put32(b + 12, 0);
+    aes_encrypt(K, b, o);
+    return le32(o + 4 * (w % 4));
+}
+
+static uint32_t op_add(int g, uint32_t a, uint32_t b) { return g == SHUF_XOR ? a ^ b : a + b; }
+static uint32_t op_sub(int g, uint32_t a, uint32_t b) { return g == SHUF_XOR ? a ^ b : a - b; }
+
+/* dst[pi(i)] = src[i] for every row */
+static void permute_rows(const uint64_t* pi, const uint32_t* src, uint32_t* dst, uint64_t n, uint32_t W)
+{
+    for (uint64_t i = 0; i < n; i++) memcpy(dst + pi[i] * W, src + i * W, W * sizeof(uint32_t));
+}
+
+static void fill_table(const aes_ks* K, int tag, uint32_t* t, uint64_t n, uint32_t W)
+{
+    for (uint64_t i = 0; i < n; i++)
+        for (uint32_t w = 0; w < W; w++) t[i * W + w] = table_word(K, tag, i, w);
+}
+
+/*
+ * in[j] / out[j]: share j+1 as n x W row-major words.  seeds: s12 || s23 || s31.
+ * scratch: 8 n W words.  Returns 0.
+ */
+int orc_shuffle(int group, uint64_t n, uint32_t W, const uint32_t* in1, const uint32_t* in2, const uint32_t* in3,
+                const uint8_t seeds[48], uint32_t* out1, uint32_t* out2, uint32_t* out3, uint32_t* scratch,
+                uint64_t* perm_scratch)
+{
+    uint64_t NW = n * W;
+    aes_ks K12, K23, K31;
+    key_expansion(seeds, &K12);
+    key_expansion(seeds + 16, &K23);
+    key_expansion(seeds + 32, &K31);
+    uint64_t* p12 = perm_scratch;
+    uint64_t* p23 = perm_scratch + n;
+    uint64_t* p31 = perm_scratch + 2 * n;
+    for (uint64_t i = 0; i < n; i++) {
+        p12[i] = prp_ks(&K12, n, i);
+        p23[i] = prp_ks(&K23, n, i);
+        p31[i] = prp_ks(&K31, n, i);
+    }
+    uint32_t* T12 = scratch;
+    uint32_t* T23 = scratch + NW;
+    uint32_t* T31 = scratch + 2 * NW;
+    uint32_t* R1 = out1;   /* R1 and R2 are the final shares of CS1 (with CS3 / CS2) */
+    uint32_t* R2 = out2;
+    uint32_t* A = scratch + 3 * NW;
+    uint32_t* X1 = scratch + 4 * NW;
+    uint32_t* Y1 = scratch + 5 * NW;
+    uint32_t* C1 = scratch + 6 * NW;
+    uint32_t* C2 = scratch + 7 * NW;
+    fill_table(&K12, 1, T12, n, W);   /* CS1, CS2 from s12: pi12, T12, R2 */
+    fill_table(&K12, 2, R2, n, W);
+    fill_table(&K23, 1, T23, n, W);   /* CS2, CS3 from s23: pi23, T23 */
+    fill_table(&K31, 1, T31, n, W);   /* CS3, CS1 from s31: pi31, T31, R1 */
+    fill_table(&K31, 2, R1, n, W);
+    /* CS1: X1 = pi31(pi12(D1 + D2 + T12) + T31) */
+    for (uint64_t k = 0; k < NW; k++) A[k] = op_add(group, op_add(group, in1[k], in2[k]), T12[k]);
+    permute_rows(p12, A, X1, n, W);
+    for (uint64_t k = 0; k < NW; k++) A[k] = op_add(group, X1[k], T31[k]);
+    permute_rows(p31, A, X1, n, W);
+    /* CS2: Y1 = pi12(D3 - T12); C1 = pi23(X1 + T23) - R2 */
+    for (uint64_t k = 0; k < NW; k++) A[k] = op_sub(group, in3[k], T12[k]);
+    permute_rows(p12, A, Y1, n, W);
+    for (uint64_t k = 0; k < NW; k++) A[k] = op_add(group, X1[k], T23[k]);
+    permute_rows(p23, A, C1, n, W);
+    for (uint64_t k = 0; k < NW; k++) C1[k] = op_sub(group, C1[k], R2[k]);
+    /* CS3: C2 = pi23(pi31(Y1 - T31) - T23) - R1; R3 = C1 + C2 */
+    for (uint64_t k = 0; k < NW; k++) A[k] = op_sub(group, Y1[k], T31[k]);
+    permute_rows(p31, A, C2, n, W);
+    for (uint64_t k = 0; k < NW; k++) A[k] = op_sub(group, C2[k], T23[k]);
+    permute_rows(p23, A, C2, n, W);
+    for (uint64_t k = 0; k < NW; k++) {
+        C2[k] = op_sub(group, C2[k], R1[k]);
+        out3[k] = op_add(group, C1[k], C2[k]);
+    }
+    return 0;
+}
+
+/*
+ * secFetch case II (Alg. 4): the candidates' records D_c = x_c || id_c || d_c are
+ * shuffled (secShuffle over Z_{2^32}, additive shares as the masked filter gives
+ * them), the shuffled x^ are opened, and the records whose x^ = 1 are kept, in
+ * shuffled order, still shared.  id_c = c is shared as (c, 0, 0).
+ * x[j]: filter result share j+1 (n values); attrs: the fetched attribute rows of T.
+ * out[j]: share j+1 of the kept records, cap rows of (1 + n_attrs) words
+ * (id, then the attributes).  Returns the number of kept records (it may exceed
+ * cap; then only cap rows are written), or -1 on bad arguments.
+ */
+int64_t orc_fetch_multi(uint64_t n, const uint32_t* x1, const uint32_t* x2, const uint32_t* x3,
+                        const orc_table* T, uint32_t n_attrs, const uint32_t* attrs, const uint8_t seeds[48],
+                        uint32_t* out1, uint32_t* out2, uint32_t* out3, uint64_t cap, uint32_t* scratch,
+                        uint64_t* perm_scratch)
+{
+    const uint32_t* x[3] = {x1, x2, x3};
+    uint32_t* out[3] = {out1, out2, out3};
+    if (T->n_elems != n) return -1;
+    for (uint32_t a = 0; a < n_attrs; a++)
+        if (attrs[a] >= T->n_attrs) return -1;
+    uint32_t W = 2 + n_attrs;
+    uint64_t NW = n * W;
+    /* scratch: D[3] then S[3] then the shuffle's 8 n W words */
+    uint32_t* D[3] = {scratch, scratch + NW, scratch + 2 * NW};
+    uint32_t* S[3] = {scratch + 3 * NW, scratch + 4 * NW, scratch + 5 * NW};
+    for (int j = 0; j < 3; j++)
+        for (uint64_t c = 0; c < n; c++) {
+            uint32_t* row = D[j] + c * W;
+            row[0] = x[j][c];
+            row[1] = j == 0 ? (uint32_t)c : 0u;
+            for (uint32_t a = 0; a < n_attrs; a++) row[2 + a] = T->share[j][(uint64_t)attrs[a] * n + c];
+        }
+    orc_shuffle(SHUF_ADD, n, W, D[0], D[1], D[2], seeds, S[0], S[1], S[2], scratch + 6 * NW, perm_scratch);
+    int64_t m = 0;
+    for (uint64_t l = 0; l < n; l++) {
+        uint32_t xh = S[0][l * W] + S[1][l * W] + S[2][l * W];
+        if (xh != 1u) continue;
+        if ((uint64_t)m < cap)
+            for (int j = 0; j < 3; j++) memcpy(out[j] + (uint64_t)m * (W - 1), S[j] + l * W + 1, (W - 1) * 4);
+        m++;
+    }
+    return m;
+}
