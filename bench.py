@@ -554,7 +554,7 @@ def run_workload(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     ctx = P.Context(0, prf_keys=PRF)
-    if args.workload in ("fresh", "keygen", "fetch", "onehot"):
+    if args.workload in ("fresh", "keygen", "fetch", "onehot", "shuffle"):
         sched = ()                       # these modes do not launch k_filter
     else:
         sched = tuple(int(v) for v in args.schedule.split(",")) if args.schedule else ctx.autotune()
@@ -657,6 +657,62 @@ def run_workload(args):
                                   "token_frac_of_hbm": key_bytes / step_s / 1e9 / peak_bw},
                      "client_keygen": {"ms": gen_s * 1e3, "key_pairs_per_s": pairs / gen_s,
                                        "token_GB_per_s": key_bytes / gen_s / 1e9}})
+        ctx.close()
+        print(json.dumps(line), flush=True)
+        return 0
+
+    if args.workload == "shuffle":
+        # secShuffle of 1,048,576 records of 6 words (x, id and 4 attributes: the records of
+        # secFetch case II on the bulk table) over additive shares, then secFetch case II on
+        # that table after a filter matching about 1 % of the vertices
+        n_v, width = N_VERTICES, 6
+        g = W.rng(13)
+        ins = [torch.from_numpy(g.integers(0, 1 << 32, (n_v, width), dtype=np.uint64).astype(np.uint32)
+                                .view(np.int32)).to(dev) for _ in range(3)]
+        outs = [torch.empty_like(ins[0]) for _ in range(3)]
+        seeds = bytes(range(48))
+        for _ in range(max(1, args.warmup)):
+            ctx.shuffle(ins, seeds, outs, 0, stream)
+        ctx.sync(stream)
+        ms = []
+        for k in range(args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.shuffle(ins, seeds, outs, 0, stream)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        shuf_s = float(np.mean(ms)) / 1e3
+        q = (width + 3) // 4
+        # per row: 3 permutations x 4 Feistel rounds (one evaluation each: n = 2^20 is the
+        # network's whole domain) of an output-word-0 AES, and 8 q mask blocks of full AES
+        lookups = n_v * (12 * LOOKUPS_PER_AES_W0 + 8 * q * LOOKUPS_PER_AES)
+        # fetch case II after a filter on the bulk table
+        wl = W.bulk_vertex_filter(n_vertices=n_v, seed=2)
+        vals = wl["tables"][0]["values"]
+        ctx.load_shares(0, [torch.from_numpy(x.view(np.int32)).to(dev) for x in wl["tables"][0]["shares"]], 32)
+        thr = int(np.quantile(vals[1], 0.01))
+        toks = P.keygen([W.range_pred(0, 1, 0, 0, thr)], 32, KEY_SEED)
+        x = [torch.empty(n_v, dtype=torch.int32, device=dev) for _ in range(3)]
+        ctx.filter_and_combine(1, toks, [x], stream)
+        fouts = [torch.empty((n_v, 5), dtype=torch.int32, device=dev) for _ in range(3)]
+        ctx.fetch_multi(0, x, [0, 1, 2, 3], seeds, fouts, stream)
+        fms = []
+        for k in range(args.steps):
+            t0 = time.perf_counter()
+            m = ctx.fetch_multi(0, x, [0, 1, 2, 3], seeds, fouts, stream)
+            fms.append(time.perf_counter() - t0)
+        rec = sum(f[:m, 0].cpu().numpy().view(np.uint32).astype(np.uint64) for f in fouts) & 0xFFFFFFFF
+        ok = sorted(rec.tolist()) == np.flatnonzero(vals[1] <= thr).tolist()
+        line.update({"metric": "secShuffle records/s", "unit": "records/s", "value": n_v / shuf_s,
+                     "ms_per_step": shuf_s * 1e3, "steps": args.steps, "warmup": args.warmup,
+                     "config": {"workload": "shuffle_1048576x6_add", "records": n_v, "words_per_record": width,
+                                "launch": "k_perms + one kernel per server (k_shuf_cs1..3)"},
+                     "roofline": {"bound": "alu", "achieved": lookups / shuf_s / 1e9, "peak": peak_lu,
+                                  "unit": "Glookup/s", "frac": lookups / shuf_s / 1e9 / peak_lu},
+                     "fetch_case_ii": {"candidates": n_v, "matches": int(m), "ms_host_clock": float(np.mean(fms)) * 1e3,
+                                       "candidates_per_s": n_v / float(np.mean(fms)),
+                                       "returns_the_matches": bool(ok)}})
         ctx.close()
         print(json.dumps(line), flush=True)
         return 0
@@ -862,7 +918,7 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-path and latency comparisons")
     ap.add_argument("--serve-queries", type=int, default=48, help="arrivals per rate in --workload serve")
     ap.add_argument("--plain-queries", type=int, default=6, help="plain-path queries per rate in --workload serve")
-    ap.add_argument("--workload", choices=["bulk", "tiny", "edges", "batch", "serve", "onehot", "fetch", "keygen", "fresh"],
+    ap.add_argument("--workload", choices=["bulk", "tiny", "edges", "batch", "serve", "onehot", "fetch", "keygen", "fresh", "shuffle"],
                     default="bulk",
                     help="bulk (default, the headline line); the others print their own line")
     ap.add_argument("--elems", type=int, default=0, help="--workload fresh: vertices (default 1,048,576)")

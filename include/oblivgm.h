@@ -368,6 +368,50 @@ oblivgm_status oblivgm_keygen_fresh(oblivgm_ctx* ctx, const oblivgm_pred* preds,
 oblivgm_status oblivgm_filter_fresh(oblivgm_ctx* ctx, uint32_t query_id, const uint8_t* const tok[3],
                                     uint32_t n_groups, uint32_t* const* out, void* stream);
 
+/* --------------------------------------------- secShuffle, secFetch case II */
+
+/* secShuffle (Alg. 5, the RSS shuffle of Araki et al. that the paper cites),
+ * the three servers simulated on this GPU.  A table D of n_rows rows of
+ * `width` uint32 words is 3-out-of-3 shared, D = D1 op D2 op D3, with op XOR
+ * (OBLIVGM_SHUFFLE_XOR, binary RSS as Alg. 5 is written) or addition mod 2^32
+ * (OBLIVGM_SHUFFLE_ADD, the arithmetic shares the masked filter produces).
+ * seeds = s12 || s23 || s31, the seed each pair of servers shares.  From its
+ * seed a pair derives
+ *   pi_ab: a pseudo-random permutation of [0, n_rows): a 4-round balanced
+ *     Feistel network on 2h bits, h = max(1, ceil(bits(n_rows - 1) / 2)),
+ *     with cycle walking; round r maps (L, R) to (R, L xor F_r(R)),
+ *     F_r(R) = word 0 of AES_s(u64 R || u16 3 || u16 r || u32 n_rows) mod 2^h;
+ *   T_ab (tag 1) and R_a (tag 2): word w of row i is word w mod 4 of
+ *     AES_s(u64 i || u16 tag || u16 w / 4 || u32 0).
+ * pi moves row i to row pi(i).  With "+"/"-" XOR in the binary case:
+ *   CS1: X1 = pi31(pi12(D1 + D2 + T12) + T31)                   (sent to CS2)
+ *   CS2: Y1 = pi12(D3 - T12); C1 = pi23(X1 + T23) - R2           (sent to CS3)
+ *   CS3: C2 = pi23(pi31(Y1 - T31) - T23) - R1; R3 = C1 + C2      (sent to CS2)
+ * out[0] = R1, out[1] = R2, out[2] = R3, and R1 + R2 + R3 = pi23(pi31(pi12(D))).
+ * in[j], out[j]: device pointers, n_rows x width row-major, 4-byte aligned;
+ * out must not overlap in.  1 <= width <= 64, n_rows < 2^31.  Asynchronous on
+ * stream.  Errors: EINVAL, ENOMEM, ECUDA. */
+#define OBLIVGM_SHUFFLE_ADD 0u
+#define OBLIVGM_SHUFFLE_XOR 1u
+oblivgm_status oblivgm_shuffle(oblivgm_ctx* ctx, uint32_t group, uint64_t n_rows, uint32_t width,
+                               const uint32_t* const in[3], const uint8_t seeds[48], uint32_t* const out[3],
+                               void* stream);
+
+/* secFetch case II (Alg. 4): fetch every matched element of a filter result
+ * obliviously.  The records D_c = x_c || id_c || d_c (x: the filter's RSS
+ * result over Z_{2^32}, three device share sets of the table's n_elems
+ * values; id_c = c shared as (c, 0, 0); d_c: the attributes `attrs` of table
+ * table_id) are shuffled with oblivgm_shuffle (additive), the shuffled x are
+ * opened, and the records whose x = 1 are kept in shuffled order, still
+ * shared.  out[j]: device pointer, cap rows of 1 + n_attrs uint32 (id, then
+ * the attributes; attribute shares stay additive mod 2^n).  *count: the
+ * number of matches (host pointer; may exceed cap, then cap rows are
+ * written).  Waits for the stream to read the count.  Errors: EINVAL,
+ * ENOENT, ENOMEM, ECUDA. */
+oblivgm_status oblivgm_fetch_multi(oblivgm_ctx* ctx, uint32_t table_id, const uint32_t* const x[3], uint32_t n_attrs,
+                                   const uint32_t* attrs, const uint8_t seeds[48], uint32_t* const out[3],
+                                   uint64_t cap, uint64_t* count, void* stream);
+
 /* ---------------------------------------------------------- secFetch case I */
 
 /* secFetch, case I (Alg. 4, Sec. V-D): obliviously fetch the one element of a

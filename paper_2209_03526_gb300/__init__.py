@@ -259,6 +259,28 @@ class Context:
         N.check(self._lib.oblivgm_filter_fresh(self._h, query_id, ptrs, len(outs), arr, _stream_handle(stream)),
                 "oblivgm_filter_fresh")
 
+    def shuffle(self, ins, seeds: bytes, outs, group: int = 0, stream=None):
+        """oblivgm_shuffle: ins / outs three int32 CUDA tensors [n_rows, width]; seeds s12 || s23 || s31."""
+        n, w = ins[0].shape
+        ip = (N.c_vp * 3)(*[t.data_ptr() for t in ins])
+        op = (N.c_vp * 3)(*[t.data_ptr() for t in outs])
+        sb = ctypes.create_string_buffer(bytes(seeds), 48)
+        N.check(self._lib.oblivgm_shuffle(self._h, group, n, w, ip, ctypes.addressof(sb), op, _stream_handle(stream)),
+                "oblivgm_shuffle")
+
+    def fetch_multi(self, table_id: int, x, attrs, seeds: bytes, outs, stream=None) -> int:
+        """oblivgm_fetch_multi (secFetch case II): outs three int32 CUDA tensors [cap, 1 + len(attrs)];
+        returns the number of matched records."""
+        xp = (N.c_vp * 3)(*[t.data_ptr() for t in x])
+        op = (N.c_vp * 3)(*[t.data_ptr() for t in outs])
+        at = (ctypes.c_uint32 * max(1, len(attrs)))(*attrs)
+        sb = ctypes.create_string_buffer(bytes(seeds), 48)
+        cnt = ctypes.c_uint64()
+        N.check(self._lib.oblivgm_fetch_multi(self._h, table_id, xp, len(attrs), ctypes.addressof(at),
+                                              ctypes.addressof(sb), op, outs[0].shape[0], ctypes.byref(cnt),
+                                              _stream_handle(stream)), "oblivgm_fetch_multi")
+        return cnt.value
+
     def filter_plain(self, query_id: int, tokens, outs, stream=None):
         """The plain per-query path (one launch per key half, global-memory AES tables)."""
         _, tp, tl = _tok_arrays(tokens)

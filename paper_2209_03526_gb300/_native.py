@@ -28,6 +28,7 @@ KEY_DPF, KEY_DCF = 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 ALL_PAIRS = 1
 KEYS_DEVICE = 2
+SHUFFLE_ADD, SHUFFLE_XOR = 0, 1
 MAX_GROUPS = 64
 NOALLOC_SCRATCH_BYTES = 256 * 1024
 
@@ -74,6 +75,9 @@ _SIGS = {
     "oblivgm_keygen_fresh": ([c_vp, ctypes.POINTER(Pred), c_u32, c_u32, c_vp, c_u32, c_u8p, ctypes.POINTER(c_vp),
                               c_u64, c_vp], c_i32),
     "oblivgm_filter_fresh": ([c_vp, c_u32, ctypes.POINTER(c_vp), c_u32, ctypes.POINTER(c_vp), c_vp], c_i32),
+    "oblivgm_shuffle": ([c_vp, c_u32, c_u64, c_u32, ctypes.POINTER(c_vp), c_u8p, ctypes.POINTER(c_vp), c_vp], c_i32),
+    "oblivgm_fetch_multi": ([c_vp, c_u32, ctypes.POINTER(c_vp), c_u32, c_vp, c_u8p, ctypes.POINTER(c_vp), c_u64,
+                             ctypes.POINTER(c_u64), c_vp], c_i32),
     "oblivgm_fetch_unique": ([c_vp, c_u32, c_u32, c_u32, ctypes.POINTER(c_vp), c_u32, ctypes.POINTER(c_u32), c_vp,
                               c_vp], c_i32),
     "oblivgm_keygen_onehot": ([ctypes.POINTER(Pred), c_u32, c_u32, c_u8p, ctypes.POINTER(c_vp), c_size,

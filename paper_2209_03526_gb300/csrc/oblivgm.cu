@@ -607,6 +607,7 @@ oblivgm_status oblivgm_create(oblivgm_ctx** out, int32_t device, const oblivgm_c
     if (st == OBLIVGM_OK) st = set_onehot_attrs();
     if (st == OBLIVGM_OK) st = set_keygen_attrs();
     if (st == OBLIVGM_OK) st = set_fresh_attrs();
+    if (st == OBLIVGM_OK) st = set_shuffle_attrs();
     if (st != OBLIVGM_OK) { delete ctx; return st; }
     cudaError_t e = cudaMalloc(&ctx->d_te0, 256 * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemcpy(ctx->d_te0, aes_tables().te0, 256 * sizeof(uint32_t), cudaMemcpyHostToDevice);

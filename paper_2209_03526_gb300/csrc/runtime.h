@@ -116,6 +116,7 @@ double now_ms();
 oblivgm_status set_onehot_attrs();
 oblivgm_status set_keygen_attrs();
 oblivgm_status set_fresh_attrs();
+oblivgm_status set_shuffle_attrs();
 oblivgm_status repack_keys_device(oblivgm_ctx* ctx, const uint8_t* wire, uint32_t kind, uint32_t n, uint32_t n_keys,
                                   DevKey* out, cudaStream_t s);
 
