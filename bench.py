@@ -684,9 +684,10 @@ def run_workload(args):
             ms.append(a.elapsed_time(b))
         shuf_s = float(np.mean(ms)) / 1e3
         q = (width + 3) // 4
-        # per row: 3 permutations x 4 Feistel rounds (one evaluation each: n = 2^20 is the
-        # network's whole domain) of an output-word-0 AES, and 8 q mask blocks of full AES
-        lookups = n_v * (12 * LOOKUPS_PER_AES_W0 + 8 * q * LOOKUPS_PER_AES)
+        # per row 8 q mask blocks of full AES (T12, T31 by CS1; T12, T23, R2 by CS2; T31, T23,
+        # R1 by CS3); plus each permutation's round table, 4 x 2^h output-word-0 AES (h = 10)
+        half = max(1, ((n_v - 1).bit_length() + 1) // 2)
+        lookups = n_v * 8 * q * LOOKUPS_PER_AES + 12 * (1 << half) * LOOKUPS_PER_AES_W0
         # fetch case II after a filter on the bulk table
         wl = W.bulk_vertex_filter(n_vertices=n_v, seed=2)
         vals = wl["tables"][0]["values"]
@@ -707,7 +708,7 @@ def run_workload(args):
         line.update({"metric": "secShuffle records/s", "unit": "records/s", "value": n_v / shuf_s,
                      "ms_per_step": shuf_s * 1e3, "steps": args.steps, "warmup": args.warmup,
                      "config": {"workload": "shuffle_1048576x6_add", "records": n_v, "words_per_record": width,
-                                "launch": "k_perms + one kernel per server (k_shuf_cs1..3)"},
+                                "launch": "k_feistel_tab + k_perms + one kernel per server (k_shuf_cs1..3)"},
                      "roofline": {"bound": "alu", "achieved": lookups / shuf_s / 1e9, "peak": peak_lu,
                                   "unit": "Glookup/s", "frac": lookups / shuf_s / 1e9 / peak_lu},
                      "fetch_case_ii": {"candidates": n_v, "matches": int(m), "ms_host_clock": float(np.mean(fms)) * 1e3,

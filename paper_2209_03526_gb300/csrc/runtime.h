@@ -89,8 +89,8 @@ struct oblivgm_ctx {
     void* h_stage = nullptr;
     std::map<uint32_t, ogm::Table> tables;
     std::map<uint32_t, ogm::OnehotTable> onehot_tables;
-    uint32_t threads = 256;
-    uint32_t elems_per_thread = 4;
+    uint32_t threads = 512;          // the autotuner's usual pick on GB300 (256 x 4 spills)
+    uint32_t elems_per_thread = 1;
     std::atomic<uint64_t> launches{0};
     bool test_expire_next = false;      // failure-path test hook, one-shot
     uint64_t test_wait_limit_ns = 0;

@@ -1,7 +1,8 @@
 // shuffle.cu -- secShuffle (Alg. 5) with the three servers simulated on one GPU, and
 // secFetch case II (Alg. 4) on top of it.
 //
-//   k_perms       pi12, pi23, pi31 as index arrays: 4-round Feistel PRP with cycle walking
+//   k_feistel_tab the round function of each pair's Feistel PRP at all 2^h half-words
+//   k_perms       pi12, pi23, pi31 as index arrays: 4 table lookups per round trip, cycle walking
 //   k_shuf_cs1    CS1: X1 = pi31(pi12(D1 + D2 + T12) + T31)
 //   k_shuf_cs2    CS2: Y1 = pi12(D3 - T12); C1 = pi23(X1 + T23) - R2; its output share R2
 //   k_shuf_cs3    CS3: C2 = pi23(pi31(Y1 - T31) - T23) - R1; R3 = C1 + C2; output shares R1, R3
@@ -23,7 +24,10 @@ namespace ogm {
 
 namespace {
 
-constexpr int kShufThreads = 512;
+#ifndef OGM_SHUF_THREADS
+#define OGM_SHUF_THREADS 512
+#endif
+constexpr int kShufThreads = OGM_SHUF_THREADS;
 constexpr uint32_t kShufMaxWidth = 64;
 
 struct ShufParams {
@@ -32,6 +36,7 @@ struct ShufParams {
     const uint32_t* d[3];       // input shares (rows of width words)
     uint32_t* s[3];             // output shares R1, R2, R3
     uint32_t* perm[3];          // pi12, pi23, pi31
+    uint32_t* ftab;             // [which][round][2^h] Feistel round values
     uint32_t* x1;
     uint32_t* y1;
     uint32_t* c1;
@@ -52,36 +57,49 @@ __device__ __forceinline__ void mask_block(const SmemTab& T, const uint32_t* rk,
     aes_one(T, rk, in, out);
 }
 
-__device__ __forceinline__ uint64_t feistel(const SmemTab& T, const uint32_t* rk, uint64_t x, uint64_t n, uint32_t h) {
-    const uint32_t mask = (1u << h) - 1u;
+// F_r(R) of the three permutations for every round r and every half-word R: the round
+// function sees only h bits, so 4 * 2^h AES calls per permutation cover all inputs
+__global__ void __launch_bounds__(kShufThreads, 1) k_feistel_tab(const __grid_constant__ ShufParams P) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    fill_tables(reinterpret_cast<uint32_t*>(smem), P.te0);
+    __syncthreads();
+    const SmemTab T{reinterpret_cast<const char*>(smem), lane_offset()};
+    const uint32_t h = P.half_bits, side = 1u << h, mask = side - 1u;
+    const uint64_t total = 12ull * side;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t which = (uint32_t)(t / (4ull * side)), rem = (uint32_t)(t % (4ull * side));
+        const uint32_t r = rem / side, R = rem % side;
+        const uint32_t in[4] = {R, 0u, 3u | (r << 16), (uint32_t)P.n};
+        P.ftab[t] = aes_one_w0(T, P.rk[which], in) & mask;
+    }
+}
+
+__device__ __forceinline__ uint64_t feistel(const uint32_t* __restrict__ ft, uint64_t x, uint32_t h) {
+    const uint32_t side = 1u << h, mask = side - 1u;
     uint32_t L = (uint32_t)(x >> h) & mask, R = (uint32_t)x & mask;
-#pragma unroll 1
+#pragma unroll
     for (uint32_t r = 0; r < 4; r++) {
-        const uint32_t in[4] = {R, 0u, 3u | (r << 16), (uint32_t)n};
-        const uint32_t f = aes_one_w0(T, rk, in) & mask;
-        const uint32_t t = L ^ f;
+        const uint32_t t = L ^ __ldg(ft + r * side + R);
         L = R;
         R = t;
     }
     return ((uint64_t)L << h) | R;
 }
 
-__global__ void __launch_bounds__(kShufThreads, 1) k_perms(const __grid_constant__ ShufParams P) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    fill_tables(reinterpret_cast<uint32_t*>(smem), P.te0);
-    __syncthreads();
-    const SmemTab T{reinterpret_cast<const char*>(smem), lane_offset()};
+__global__ void __launch_bounds__(256) k_perms(const __grid_constant__ ShufParams P) {
     const uint32_t h = P.half_bits;
     const uint64_t dom = 1ull << (2 * h);
     for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 3 * P.n;
          t += (uint64_t)gridDim.x * blockDim.x) {
         const int which = (int)(t / P.n);
         const uint64_t x = t - (uint64_t)which * P.n;
+        const uint32_t* ft = P.ftab + (uint64_t)which * 4 * (1ull << h);
         uint64_t y = 0;
         if (P.n > 1) {
-            y = feistel(T, P.rk[which], x, P.n, h);
+            y = feistel(ft, x, h);
             // the cycle through x re-enters [0, n) within dom steps
-            for (uint64_t guard = 0; y >= P.n && guard < dom; guard++) y = feistel(T, P.rk[which], y, P.n, h);
+            for (uint64_t guard = 0; y >= P.n && guard < dom; guard++) y = feistel(ft, y, h);
             if (y >= P.n) y = x;   // unreachable; keeps every later index inside the table
         }
         P.perm[which][x] = (uint32_t)y;
@@ -306,7 +324,9 @@ oblivgm_status shuffle_device(oblivgm_ctx* ctx, uint32_t group, uint64_t n, uint
     for (uint64_t v = n - 1; v; v >>= 1) bits++;
     P.half_bits = std::max<uint32_t>(1, (bits + 1) / 2);
     const size_t perm_bytes = (size_t)n * 4, tab_bytes = (size_t)n * width * 4;
-    const size_t total = 3 * ((perm_bytes + 255) & ~size_t(255)) + 3 * ((tab_bytes + 255) & ~size_t(255));
+    const size_t ftab_bytes = 12ull * (1ull << P.half_bits) * 4;
+    const size_t total = 3 * ((perm_bytes + 255) & ~size_t(255)) + 3 * ((tab_bytes + 255) & ~size_t(255)) +
+                         ((ftab_bytes + 255) & ~size_t(255));
     uint8_t* scratch = nullptr;
     cudaError_t ce = cudaMallocAsync(reinterpret_cast<void**>(&scratch), total, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "shuffle scratch");
@@ -320,14 +340,16 @@ oblivgm_status shuffle_device(oblivgm_ctx* ctx, uint32_t group, uint64_t n, uint
         *tabs[k] = reinterpret_cast<uint32_t*>(scratch + off);
         off += (tab_bytes + 255) & ~size_t(255);
     }
+    P.ftab = reinterpret_cast<uint32_t*>(scratch + off);
     auto grid = [&](uint64_t items) {
         return (unsigned)std::min<uint64_t>((items + kShufThreads - 1) / kShufThreads, (uint64_t)ctx->sm_count);
     };
-    k_perms<<<grid(3 * n), kShufThreads, kTableBytes, s>>>(P);
+    k_feistel_tab<<<grid(12ull << P.half_bits), kShufThreads, kTableBytes, s>>>(P);
+    k_perms<<<(unsigned)std::min<uint64_t>((3 * n + 255) / 256, 16ull * ctx->sm_count), 256, 0, s>>>(P);
     k_shuf_cs1<<<grid(n), kShufThreads, kTableBytes, s>>>(P);
     k_shuf_cs2<<<grid(2 * n), kShufThreads, kTableBytes, s>>>(P);
     k_shuf_cs3<<<grid(n), kShufThreads, kTableBytes, s>>>(P);
-    ctx->launches += 4;
+    ctx->launches += 5;
     ce = cudaGetLastError();
     const cudaError_t fe = cudaFreeAsync(scratch, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "shuffle launch");
@@ -336,7 +358,7 @@ oblivgm_status shuffle_device(oblivgm_ctx* ctx, uint32_t group, uint64_t n, uint
 }
 
 oblivgm_status set_shuffle_attrs() {
-    const void* fns[4] = {reinterpret_cast<const void*>(k_perms), reinterpret_cast<const void*>(k_shuf_cs1),
+    const void* fns[4] = {reinterpret_cast<const void*>(k_feistel_tab), reinterpret_cast<const void*>(k_shuf_cs1),
                           reinterpret_cast<const void*>(k_shuf_cs2), reinterpret_cast<const void*>(k_shuf_cs3)};
     for (const void* f : fns) {
         const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kTableBytes);

@@ -158,7 +158,7 @@ def test_every_schedule_gives_identical_shares(ctx):
                 assert np.array_equal(ref, want)
             assert np.array_equal(got, ref), (t, e)
     finally:
-        ctx.set_schedule(256, 4)
+        ctx.set_schedule(512, 1)
 
 
 def test_unaligned_outputs_and_tiny_tables(ctx):
@@ -168,13 +168,18 @@ def test_unaligned_outputs_and_tiny_tables(ctx):
                    W.eq_pred(1, 0, 1, int(wl["tables"][1]["values"][0, 6]))]
     load_tables(ctx, wl)
     toks = P.keygen(wl["preds"], 32, bytes(range(16)))
-    for offset in (0, 1):
-        outs = alloc_outs(wl, offset=offset)
-        ctx.filter_and_combine(3, toks, outs)
-        torch.cuda.synchronize()
-        for grp, n in ((0, 1), (1, 7)):
-            got = np.stack([from_dev(t) for t in outs[grp]])
-            assert np.array_equal(got, oracle_group(oracle, wl, toks, 3, grp, np.arange(n)))
+    try:
+        for sched in ((512, 1), (256, 4), (256, 2)):          # scalar, uint4 and uint2 output stores
+            ctx.set_schedule(*sched)
+            for offset in (0, 1):
+                outs = alloc_outs(wl, offset=offset)
+                ctx.filter_and_combine(3, toks, outs)
+                torch.cuda.synchronize()
+                for grp, n in ((0, 1), (1, 7)):
+                    got = np.stack([from_dev(t) for t in outs[grp]])
+                    assert np.array_equal(got, oracle_group(oracle, wl, toks, 3, grp, np.arange(n))), sched
+    finally:
+        ctx.set_schedule(512, 1)
 
 
 def test_empty_table_is_a_no_op(ctx):
