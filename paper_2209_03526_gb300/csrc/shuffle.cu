@@ -2,14 +2,16 @@
 // secFetch case II (Alg. 4) on top of it.
 //
 //   k_feistel_tab the round function of each pair's Feistel PRP at all 2^h half-words
-//   k_perms       pi12, pi23, pi31 as index arrays: 4 table lookups per round trip, cycle walking
+//   k_perms       the permutations (pi12, pi31 forward; all three inverse, the network run
+//                 backwards) as index arrays: 4 table lookups per pass, cycle walking
+//   k_compose     pi31 o pi12 (CS1's map) and pi31^-1 o pi23^-1 (CS3's map)
 //   k_shuf_cs1    CS1: X1 = pi31(pi12(D1 + D2 + T12) + T31)
 //   k_shuf_cs2    CS2: Y1 = pi12(D3 - T12); C1 = pi23(X1 + T23) - R2; its output share R2
 //   k_shuf_cs3    CS3: C2 = pi23(pi31(Y1 - T31) - T23) - R1; R3 = C1 + C2; output shares R1, R3
 //
-// Each server kernel reads only what that server holds or receives.  Rows are
-// row-major (width words), so a scattered row write is one contiguous run.  The masks
-// T and R are AES blocks of the pair's seed, four words per block, made where used.
+// Each server kernel reads only what that server holds or receives.  Rows are row-major
+// (width words), so a row read or written out of order is one contiguous run.  The masks T and R are AES
+// blocks of the pair's seed, four words per block, made where used.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,8 +37,11 @@ struct ShufParams {
     const uint32_t* te0;
     const uint32_t* d[3];       // input shares (rows of width words)
     uint32_t* s[3];             // output shares R1, R2, R3
-    uint32_t* perm[3];          // pi12, pi23, pi31
+    uint32_t* inv[3];           // pi12^-1, pi23^-1, pi31^-1
+    uint32_t* fwd[2];           // pi12, pi31
     uint32_t* ftab;             // [which][round][2^h] Feistel round values
+    uint32_t* comp1;            // pi31(pi12(i)): CS1 knows both permutations
+    uint32_t* comp3;            // pi31^-1(pi23^-1(l)): CS3 knows both permutations
     uint32_t* x1;
     uint32_t* y1;
     uint32_t* c1;
@@ -87,26 +92,59 @@ __device__ __forceinline__ uint64_t feistel(const uint32_t* __restrict__ ft, uin
     return ((uint64_t)L << h) | R;
 }
 
+// the inverse of the Feistel network: rounds 3..0, each (L', R') -> (R' xor F_r(L'), L')
+__device__ __forceinline__ uint64_t feistel_inv(const uint32_t* __restrict__ ft, uint64_t y, uint32_t h) {
+    const uint32_t side = 1u << h, mask = side - 1u;
+    uint32_t L = (uint32_t)(y >> h) & mask, R = (uint32_t)y & mask;
+#pragma unroll
+    for (int r = 3; r >= 0; r--) {
+        const uint32_t prevL = R ^ __ldg(ft + (uint32_t)r * side + L);
+        R = L;
+        L = prevL;
+    }
+    return ((uint64_t)L << h) | R;
+}
+
+// pi^-1 of the three permutations, and pi12, pi31 forward, as index arrays.  The inverse
+// of a cycle-walking permutation walks the inverse network until it re-enters [0, n).
+// Items: 5 n, array a = item / n: 0..2 inverse of (12, 23, 31), 3 forward 12, 4 forward 31.
 __global__ void __launch_bounds__(256) k_perms(const __grid_constant__ ShufParams P) {
     const uint32_t h = P.half_bits;
     const uint64_t dom = 1ull << (2 * h);
-    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 3 * P.n;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 5 * P.n;
          t += (uint64_t)gridDim.x * blockDim.x) {
-        const int which = (int)(t / P.n);
-        const uint64_t x = t - (uint64_t)which * P.n;
+        const int a = (int)(t / P.n);
+        const int which = a < 3 ? a : (a == 3 ? S12 : S31);
+        const bool fwd = a >= 3;
+        const uint64_t y = t - (uint64_t)a * P.n;
         const uint32_t* ft = P.ftab + (uint64_t)which * 4 * (1ull << h);
-        uint64_t y = 0;
+        uint64_t x = 0;
         if (P.n > 1) {
-            y = feistel(ft, x, h);
-            // the cycle through x re-enters [0, n) within dom steps
-            for (uint64_t guard = 0; y >= P.n && guard < dom; guard++) y = feistel(ft, y, h);
-            if (y >= P.n) y = x;   // unreachable; keeps every later index inside the table
+            x = fwd ? feistel(ft, y, h) : feistel_inv(ft, y, h);
+            // the cycle through y re-enters [0, n) within dom steps
+            for (uint64_t guard = 0; x >= P.n && guard < dom; guard++)
+                x = fwd ? feistel(ft, x, h) : feistel_inv(ft, x, h);
+            if (x >= P.n) x = y;   // unreachable; keeps every later index inside the table
         }
-        P.perm[which][x] = (uint32_t)y;
+        (fwd ? P.fwd[a - 3] : P.inv[which])[y] = (uint32_t)x;
     }
 }
 
-// CS1: row i -> j = pi12(i) -> k = pi31(j); X1[k] = (D1 + D2 + T12)[i] + T31[j]
+// CS1's map pi31(pi12(i)) and CS3's inverse map pi31^-1(pi23^-1(l)), so their row loops
+// read indices in order
+__global__ void __launch_bounds__(256) k_compose(const __grid_constant__ ShufParams P) {
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 2 * P.n;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        if (t < P.n) P.comp1[t] = P.fwd[1][P.fwd[0][t]];
+        else P.comp3[t - P.n] = P.inv[S31][P.inv[S23][t - P.n]];
+    }
+}
+
+// CS1 runs over its input rows (two rows of D read in order, one row of X1 written at
+// pi31(pi12(i))); CS2 and CS3 run over their output rows and gather the input row the
+// permutations bring there, so their index reads and row writes are in order.
+
+// CS1: X1[k] = (D1 + D2 + T12)[i] + T31[j], j = pi12(i), k = pi31(j)
 __global__ void __launch_bounds__(kShufThreads, 1) k_shuf_cs1(const __grid_constant__ ShufParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
     fill_tables(reinterpret_cast<uint32_t*>(smem), P.te0);
@@ -114,7 +152,7 @@ __global__ void __launch_bounds__(kShufThreads, 1) k_shuf_cs1(const __grid_const
     const SmemTab T{reinterpret_cast<const char*>(smem), lane_offset()};
     const uint32_t W = P.width, g = P.group;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t j = P.perm[S12][i], k = P.perm[S31][j];
+        const uint64_t j = P.fwd[0][i], k = P.comp1[i];
         for (uint32_t q = 0; q * 4 < W; q++) {
             uint32_t t12[4], t31[4];
             mask_block(T, P.rk[S12], 1u, i, q, t12);
@@ -124,7 +162,7 @@ __global__ void __launch_bounds__(kShufThreads, 1) k_shuf_cs1(const __grid_const
                 const uint32_t w = 4 * q + e;
                 if (w < W) {
                     const uint64_t src = i * W + w;
-                    const uint32_t a = op_add(g, op_add(g, P.d[0][src], P.d[1][src]), t12[e]);
+                    const uint32_t a = op_add(g, op_add(g, __ldg(P.d[0] + src), __ldg(P.d[1] + src)), t12[e]);
                     P.x1[k * W + w] = op_add(g, a, t31[e]);
                 }
             }
@@ -132,8 +170,8 @@ __global__ void __launch_bounds__(kShufThreads, 1) k_shuf_cs1(const __grid_const
     }
 }
 
-// CS2: items 0..n-1: Y1[pi12(i)] = D3[i] - T12[i];
-//      items n..2n-1 (k = item - n): l = pi23(k); C1[l] = X1[k] + T23[k] - R2[l]; out R2[l]
+// CS2: items 0..n-1: Y1[j] = D3[i] - T12[i], i = pi12^-1(j);
+//      items n..2n-1 (l = item - n): C1[l] = X1[k] + T23[k] - R2[l], k = pi23^-1(l); output R2[l]
 __global__ void __launch_bounds__(kShufThreads, 1) k_shuf_cs2(const __grid_constant__ ShufParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
     fill_tables(reinterpret_cast<uint32_t*>(smem), P.te0);
@@ -143,18 +181,18 @@ __global__ void __launch_bounds__(kShufThreads, 1) k_shuf_cs2(const __grid_const
     for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 2 * P.n;
          t += (uint64_t)gridDim.x * blockDim.x) {
         if (t < P.n) {
-            const uint64_t i = t, j = P.perm[S12][i];
+            const uint64_t j = t, i = P.inv[S12][j];
             for (uint32_t q = 0; q * 4 < W; q++) {
                 uint32_t t12[4];
                 mask_block(T, P.rk[S12], 1u, i, q, t12);
 #pragma unroll
                 for (int e = 0; e < 4; e++) {
                     const uint32_t w = 4 * q + e;
-                    if (w < W) P.y1[j * W + w] = op_sub(g, P.d[2][i * W + w], t12[e]);
+                    if (w < W) P.y1[j * W + w] = op_sub(g, __ldg(P.d[2] + i * W + w), t12[e]);
                 }
             }
         } else {
-            const uint64_t k = t - P.n, l = P.perm[S23][k];
+            const uint64_t l = t - P.n, k = P.inv[S23][l];
             for (uint32_t q = 0; q * 4 < W; q++) {
                 uint32_t t23[4], r2[4];
                 mask_block(T, P.rk[S23], 1u, k, q, t23);
@@ -172,15 +210,16 @@ __global__ void __launch_bounds__(kShufThreads, 1) k_shuf_cs2(const __grid_const
     }
 }
 
-// CS3: row j -> k = pi31(j) -> l = pi23(k); C2[l] = Y1[j] - T31[j] - T23[k] - R1[l]; R3[l] = C1[l] + C2[l]
+// CS3: C2[l] = Y1[j] - T31[j] - T23[k] - R1[l], R3[l] = C1[l] + C2[l], with k = pi23^-1(l),
+// j = pi31^-1(k); outputs R1[l] and R3[l]
 __global__ void __launch_bounds__(kShufThreads, 1) k_shuf_cs3(const __grid_constant__ ShufParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
     fill_tables(reinterpret_cast<uint32_t*>(smem), P.te0);
     __syncthreads();
     const SmemTab T{reinterpret_cast<const char*>(smem), lane_offset()};
     const uint32_t W = P.width, g = P.group;
-    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < P.n; j += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t k = P.perm[S31][j], l = P.perm[S23][k];
+    for (uint64_t l = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; l < P.n; l += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = P.inv[S23][l], j = P.comp3[l];
         for (uint32_t q = 0; q * 4 < W; q++) {
             uint32_t t31[4], t23[4], r1[4];
             mask_block(T, P.rk[S31], 1u, j, q, t31);
@@ -325,14 +364,14 @@ oblivgm_status shuffle_device(oblivgm_ctx* ctx, uint32_t group, uint64_t n, uint
     P.half_bits = std::max<uint32_t>(1, (bits + 1) / 2);
     const size_t perm_bytes = (size_t)n * 4, tab_bytes = (size_t)n * width * 4;
     const size_t ftab_bytes = 12ull * (1ull << P.half_bits) * 4;
-    const size_t total = 3 * ((perm_bytes + 255) & ~size_t(255)) + 3 * ((tab_bytes + 255) & ~size_t(255)) +
+    const size_t total = 7 * ((perm_bytes + 255) & ~size_t(255)) + 3 * ((tab_bytes + 255) & ~size_t(255)) +
                          ((ftab_bytes + 255) & ~size_t(255));
     uint8_t* scratch = nullptr;
     cudaError_t ce = cudaMallocAsync(reinterpret_cast<void**>(&scratch), total, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "shuffle scratch");
     size_t off = 0;
     for (int k = 0; k < 3; k++) {
-        P.perm[k] = reinterpret_cast<uint32_t*>(scratch + off);
+        P.inv[k] = reinterpret_cast<uint32_t*>(scratch + off);
         off += (perm_bytes + 255) & ~size_t(255);
     }
     uint32_t** tabs[3] = {&P.x1, &P.y1, &P.c1};
@@ -341,15 +380,24 @@ oblivgm_status shuffle_device(oblivgm_ctx* ctx, uint32_t group, uint64_t n, uint
         off += (tab_bytes + 255) & ~size_t(255);
     }
     P.ftab = reinterpret_cast<uint32_t*>(scratch + off);
+    off += (ftab_bytes + 255) & ~size_t(255);
+    P.comp1 = reinterpret_cast<uint32_t*>(scratch + off);
+    off += (perm_bytes + 255) & ~size_t(255);
+    P.comp3 = reinterpret_cast<uint32_t*>(scratch + off);
+    for (int k = 0; k < 2; k++) {
+        off += (perm_bytes + 255) & ~size_t(255);
+        P.fwd[k] = reinterpret_cast<uint32_t*>(scratch + off);
+    }
     auto grid = [&](uint64_t items) {
         return (unsigned)std::min<uint64_t>((items + kShufThreads - 1) / kShufThreads, (uint64_t)ctx->sm_count);
     };
     k_feistel_tab<<<grid(12ull << P.half_bits), kShufThreads, kTableBytes, s>>>(P);
-    k_perms<<<(unsigned)std::min<uint64_t>((3 * n + 255) / 256, 16ull * ctx->sm_count), 256, 0, s>>>(P);
+    k_perms<<<(unsigned)std::min<uint64_t>((5 * n + 255) / 256, 16ull * ctx->sm_count), 256, 0, s>>>(P);
+    k_compose<<<(unsigned)std::min<uint64_t>((2 * n + 255) / 256, 16ull * ctx->sm_count), 256, 0, s>>>(P);
     k_shuf_cs1<<<grid(n), kShufThreads, kTableBytes, s>>>(P);
     k_shuf_cs2<<<grid(2 * n), kShufThreads, kTableBytes, s>>>(P);
     k_shuf_cs3<<<grid(n), kShufThreads, kTableBytes, s>>>(P);
-    ctx->launches += 5;
+    ctx->launches += 6;
     ce = cudaGetLastError();
     const cudaError_t fe = cudaFreeAsync(scratch, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "shuffle launch");
