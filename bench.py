@@ -39,6 +39,7 @@ UNIT = "element-predicates/s"
 N_VERTICES = 1 << 20
 PRF = bytes(range(48))
 KEY_SEED = bytes(range(16))
+SEED_B = bytes(range(16, 32))
 LOOKUPS_PER_AES = 160          # T-table AES-128: 16 table reads per round, 10 rounds
 LOOKUPS_PER_AES_W0 = 148       # ... when only output word 0 is used (DCF value block, re-share PRF)
 LDS_LANES_PER_CLK = 32         # shared-memory data path: one 4-byte word per lane per clock per SM
@@ -172,6 +173,22 @@ def oracle_rate(wl, toks, seconds: float, threads: int, rng_seed: int = 0):
     oracle.filter_group(toks, 1, PRF, tabs, 0, sample, threads=threads)
     dt = time.perf_counter() - t0
     return size * len(wl["preds"]) / dt, size, dt
+
+
+def oracle_leg(run, units: float, unit: str, cores: int, sample: str, target_s: float = 4.0):
+    """Time the oracle as it stands on a bounded sample: run(scale) does `scale` units' worth of
+    oracle work (scale = 1 is the smallest sample); one probe, then a run of about target_s."""
+    t0 = time.perf_counter()
+    run(1)
+    dt = time.perf_counter() - t0
+    scale = 1
+    if dt < 0.5 * target_s:               # a probe that already took long enough is the measurement
+        scale = max(1, int(target_s / max(dt, 1e-6)))
+        t0 = time.perf_counter()
+        run(scale)
+        dt = time.perf_counter() - t0
+    return {"value": units * scale / dt, "unit": unit, "cores": cores, "kind": "oracle",
+            "sample": f"{sample}, x{scale} ({dt:.1f} s)"}
 
 
 def run_reference(args):
@@ -603,6 +620,13 @@ def run_workload(args):
                                 "reconstructs_to_the_match": ok},
                      "roofline": {"bound": "hbm", "achieved": algo_bytes / step_s / 1e9, "peak": peak_bw,
                                   "unit": "GB/s", "frac": algo_bytes / step_s / 1e9 / peak_bw}})
+        if not args.no_cpu_baseline:
+            import oracle
+            xs = [o.cpu().numpy().view(np.uint32) for o in outs[0]]
+            line["cpu_baseline"] = oracle_leg(
+                lambda k: [oracle.fetch_unique(xs, [(tab["shares"], 32)], 0, [0, 1, 2, 3], 1, 0, PRF)
+                           for _ in range(k)], n_v, "candidates/s", 1,
+                f"oracle secFetch case I over all {n_v} candidates, 4 attributes (numpy)")
         ctx.close()
         print(json.dumps(line), flush=True)
         return 0
@@ -657,6 +681,18 @@ def run_workload(args):
                                   "token_frac_of_hbm": key_bytes / step_s / 1e9 / peak_bw},
                      "client_keygen": {"ms": gen_s * 1e3, "key_pairs_per_s": pairs / gen_s,
                                        "token_GB_per_s": key_bytes / gen_s / 1e9}})
+        if not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            cores = os.cpu_count() or 1
+            m = 4 * cores                     # a slice of the table: its first m vertices
+            sub = [s_[:, :m].copy() for s_ in wl["tables"][0]["shares"]]
+            otoks = oracle.keygen_fresh(preds, 32, [m], KEY_SEED)
+            line["cpu_baseline"] = oracle_leg(
+                lambda k: [oracle.filter_fresh(otoks, 1, PRF, [(sub, 32)], 0, np.arange(m), threads=cores)
+                           for _ in range(k)],
+                m * len(preds), UNIT, cores,
+                f"servers' filter on the oracle's fresh tokens for {m} vertices of the table, all 8 predicates")
         ctx.close()
         print(json.dumps(line), flush=True)
         return 0
@@ -714,6 +750,14 @@ def run_workload(args):
                      "fetch_case_ii": {"candidates": n_v, "matches": int(m), "ms_host_clock": float(np.mean(fms)) * 1e3,
                                        "candidates_per_s": n_v / float(np.mean(fms)),
                                        "returns_the_matches": bool(ok)}})
+        if not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            m = 1 << 13
+            gs = W.rng(15)
+            osh = [gs.integers(0, 1 << 32, (m, width), dtype=np.uint64).astype(np.uint32) for _ in range(3)]
+            line["cpu_baseline"] = oracle_leg(lambda k: [oracle.shuffle(osh, seeds, 0) for _ in range(k)], m,
+                                              "records/s", 1, f"oracle secShuffle of {m} records x {width} words")
         ctx.close()
         print(json.dumps(line), flush=True)
         return 0
@@ -771,6 +815,20 @@ def run_workload(args):
                      "roofline": {"bound": "alu", "achieved": total_lu / total_s / 1e9, "peak": peak_lu,
                                   "unit": "Glookup/s", "frac": total_lu / total_s / 1e9 / peak_lu},
                      "table1_host_gentoken": table1})
+        if not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            ga = W.rng(14)
+            al = [int(v) for v in ga.integers(0, 1 << 32, 64, dtype=np.uint64)]
+
+            def gen_pairs(k):
+                for r in range(k):
+                    for i, a in enumerate(al):
+                        oracle.dpf_gen(32, a, a ^ 0x5A5A, KEY_SEED, SEED_B)
+                        oracle.dcf_gen(32, a, a ^ 0x5A5A, KEY_SEED, SEED_B)
+
+            line["cpu_baseline"] = oracle_leg(gen_pairs, 2 * len(al), "key-pairs/s", 1,
+                                              "oracle DPF and DCF Gen at n = 32, 64 pairs of each, one thread")
         ctx.close()
         print(json.dumps(line), flush=True)
         return 0
@@ -819,7 +877,15 @@ def run_workload(args):
                                   "what": "whole step (EvalAll + dot-product + fold launches) against the share "
                                           "rows of each column read (once for all predicates on it) and the packed "
                                           "outputs"}})
-        ctx.close()
+        if not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            m = 4096
+            sub = W.onehot_table(vals[:, :m], n, W.rng(16))["shares"]
+            # group 0 (one equality predicate): its EvalAll over the 2^16 positions, then m vertices
+            line["cpu_baseline"] = oracle_leg(
+                lambda k: [oracle.filter_onehot(toks, 1, PRF, [(sub, n)], 0, np.arange(m)) for _ in range(k)],
+                m, UNIT, 1, f"oracle one-hot secEval of group 0 (1 predicate) on {m} vertices", target_s=4.0)
         print(json.dumps(line), flush=True)
         return 0
 
