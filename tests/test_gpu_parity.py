@@ -369,3 +369,25 @@ def test_fetch_unique_matches_oracle(ctx):
     assert np.array_equal(got, want)
     rec = oracle.reconstruct(got)
     assert rec[0] == target and list(rec[1:]) == [vals[a, target] for a in (0, 1, 3)]
+
+
+@pytest.mark.parametrize("n_el,attrs,offset", [(1, [0], 0), (1003, [], 0), (1003, list(range(11)), 0),
+                                             (1003, list(range(11)), 1), (200_001, [3, 9, 1], 0),
+                                             (200_001, [3, 9, 1], 1)])
+def test_fetch_unique_column_groups_and_sizes(ctx, n_el, attrs, offset):
+    """secFetch case I on synthetic result shares (any values: the sums are linear in x):
+    no attribute, more attributes than one pass takes (8 columns), one candidate, many CTAs,
+    16-byte-aligned result shares (4-candidate loads) and shares one word off (scalar loads)."""
+    g = W.rng(72 + n_el)
+    bits = 32
+    vals = W.uniform_attrs(g, 12, n_el, bits)
+    wl = {"tables": [W.table(vals, bits, g)]}
+    load_tables(ctx, wl)
+    xs = [g.integers(0, 1 << 32, n_el, dtype=np.uint64).astype(np.uint32) for _ in range(3)]
+    res = torch.empty(3 * (1 + len(attrs)), dtype=torch.int32, device="cuda")
+    dx = [to_dev(np.concatenate([np.zeros(offset, dtype=np.uint32), x]))[offset:] for x in xs]
+    ctx.fetch_unique(8, 5, 0, dx, attrs, res)
+    ctx.sync()
+    got = from_dev(res).reshape(3, 1 + len(attrs))
+    want = oracle.fetch_unique(xs, [(wl["tables"][0]["shares"], bits)], 0, attrs, 8, 5, PRF)
+    assert np.array_equal(got, want)
