@@ -34,14 +34,15 @@ namespace {
 constexpr uint32_t kFreshMagic = 0x464D474Fu;
 constexpr int kFreshMaxPreds = 64;
 constexpr int kFreshMaxJobs = kFreshMaxPreds * 6;
-constexpr int kFreshGenThreads = 768;    // 80 registers: one 768-thread CTA per SM with the 128 KiB tables
+// client Gen: one CTA per SM (the tables take 128 KiB); both instances need more than the
+// 80 registers a 768-thread CTA leaves
+template <bool DCF> constexpr int fresh_gen_threads() { return 512; }
 #ifndef OGM_FRESH_EVAL_THREADS
 #define OGM_FRESH_EVAL_THREADS 768
 #endif
 constexpr int kFreshEvalThreads = OGM_FRESH_EVAL_THREADS;
 
 // halves held by server i (0-based): (pair, party) -- CS1 (1,0),(2,0); CS2 (2,1),(3,0); CS3 (3,1),(1,1)
-__constant__ uint8_t c_hold_pair[3][2] = {{0, 1}, {1, 2}, {2, 0}};
 __constant__ uint8_t c_hold_party[3][2] = {{0, 0}, {1, 0}, {1, 1}};
 
 struct FreshLayout {
@@ -126,26 +127,25 @@ __device__ __forceinline__ void client_block(const SmemTab& T, const uint32_t* r
     aes_one(T, rk, in, out);
 }
 
-__global__ void __launch_bounds__(kFreshGenThreads) k_keygen_fresh(const __grid_constant__ FreshGenParams P) {
+// one instance per predicate kind (EQ: DPF keys, RANGE: DCF keys), launched on its own jobs
+template <bool DCF>
+__global__ void __launch_bounds__(fresh_gen_threads<DCF>()) k_keygen_fresh(const __grid_constant__ FreshGenParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
     fill_tables(reinterpret_cast<uint32_t*>(smem), P.te0);
     __syncthreads();
     const SmemTab T{reinterpret_cast<const char*>(smem), lane_offset()};
     const GenJob J = P.jobs[blockIdx.y];
     const FreshPred& Q = P.preds[J.pred];
-    const bool eq = Q.kind == OBLIVGM_PRED_EQ;
+    constexpr bool eq = !DCF;
     const uint32_t n = P.n;
     const uint32_t m = n >= 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
     const FreshLayout& L = Q.lay;
-    const int nsub = eq ? 1 : 2;
-    // owners of the pair's two keys: (server, half) with that (pair, party)
-    int srv[2] = {0, 0}, half[2] = {0, 0};
-    for (int i = 0; i < 3; i++)
-        for (int h = 0; h < 2; h++)
-            if (c_hold_pair[i][h] == J.pair) {
-                srv[c_hold_party[i][h]] = i;
-                half[c_hold_party[i][h]] = h;
-            }
+    constexpr int nsub = eq ? 1 : 2;
+    // owners (server, half) of the pair's two keys, from the assignment
+    // CS1 (1,0),(2,0); CS2 (2,1),(3,0); CS3 (3,1),(1,1): party 0 of pairs 1, 2, 3 sits with
+    // CS1 A, CS1 B, CS2 B; party 1 with CS3 B, CS2 A, CS3 A
+    const uint32_t srv0 = J.pair == 2 ? 1u : 0u, half0 = J.pair == 0 ? 0u : 1u;
+    const uint32_t srv1 = J.pair == 1 ? 1u : 2u, half1 = J.pair == 0 ? 1u : 0u;
     for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < L.N; c += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t w[4];
         client_block(T, P.rk_client, c, Q.step, 1u, 0u, w);
@@ -166,8 +166,8 @@ __global__ void __launch_bounds__(kFreshGenThreads) k_keygen_fresh(const __grid_
         client_block(T, P.rk_client, c, Q.step, 2u, 4u * J.pair + 2u * J.sub + 0u, s0);
         client_block(T, P.rk_client, c, Q.step, 2u, 4u * J.pair + 2u * J.sub + 1u, s1);
         SoaSink sink;
-        for (int b = 0; b < 2; b++)
-            sink.b[b] = Q.data[srv[b]] + L.keys_at + (uint64_t)(half[b] * nsub + J.sub) * L.key_block;
+        sink.b[0] = Q.data[srv0] + L.keys_at + (uint64_t)(half0 * nsub + J.sub) * L.key_block;
+        sink.b[1] = Q.data[srv1] + L.keys_at + (uint64_t)(half1 * nsub + J.sub) * L.key_block;
         st_u128(sink.b[0] + 16 * c, s0);
         st_u128(sink.b[1] + 16 * c, s1);
         sink.N = L.N;
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(kFreshGenThreads) k_keygen_fresh(const __grid_
         sink.n = n;
         sink.tlw = sink.trw = 0;
         sink.dcf = !eq;
-        gen_pair(T, P.aes, !eq, (int)n, alpha, beta, s0, s1, sink);
+        gen_pair<DCF>(T, P.aes, (int)n, alpha, beta, s0, s1, sink);
     }
 }
 
@@ -412,6 +412,7 @@ extern "C" oblivgm_status oblivgm_keygen_fresh(oblivgm_ctx* ctx, const oblivgm_p
     P.n = n_bits;
     // headers and descriptors, written on the host and copied in front of each token
     const size_t head = 64 + 32 * (size_t)n_preds;
+    std::vector<GenJob> eq_jobs, range_jobs;
     std::vector<uint8_t> hdr(3 * head, 0);
     uint64_t off = head, n_max = 0;
     for (uint32_t p = 0; p < n_preds; p++) {
@@ -436,7 +437,10 @@ extern "C" oblivgm_status oblivgm_keygen_fresh(oblivgm_ctx* ctx, const oblivgm_p
             put_u64(d + 16, off);
         }
         for (uint8_t pair = 0; pair < 3; pair++)
-            for (uint8_t sub = 0; sub < (eq ? 1 : 2); sub++) P.jobs[P.n_jobs++] = GenJob{(uint16_t)p, pair, sub};
+            for (uint8_t sub = 0; sub < (eq ? 1 : 2); sub++) {
+                std::vector<GenJob>& jl = eq ? eq_jobs : range_jobs;
+                jl.push_back(GenJob{(uint16_t)p, pair, sub});
+            }
         n_max = std::max(n_max, F.lay.N);
         off += F.lay.data_len;
     }
@@ -455,13 +459,23 @@ extern "C" oblivgm_status oblivgm_keygen_fresh(oblivgm_ctx* ctx, const oblivgm_p
         if (ce != cudaSuccess) return cuda_fail(ce, "fresh token header copy");
     }
     if (n_max == 0) return OBLIVGM_OK;
-    // about two CTAs per SM in total, spread over the jobs; each CTA strides over its job's elements
-    const uint64_t per_job = std::max<uint64_t>(1, (2ull * ctx->sm_count + P.n_jobs - 1) / P.n_jobs);
-    const uint64_t bx = std::min<uint64_t>(per_job, (n_max + kFreshGenThreads - 1) / kFreshGenThreads);
-    k_keygen_fresh<<<dim3((unsigned)bx, P.n_jobs), kFreshGenThreads, kTableBytes, s>>>(P);
-    ctx->launches++;
-    ce = cudaGetLastError();
-    return ce == cudaSuccess ? OBLIVGM_OK : cuda_fail(ce, "k_keygen_fresh launch");
+    // one launch per kind; about two CTAs per SM in total, spread over the launch's jobs,
+    // each CTA striding over its job's elements
+    for (int kind = 0; kind < 2; kind++) {
+        const std::vector<GenJob>& jl = kind ? range_jobs : eq_jobs;
+        if (jl.empty()) continue;
+        P.n_jobs = (uint32_t)jl.size();
+        std::copy(jl.begin(), jl.end(), P.jobs);
+        const uint64_t threads = kind ? fresh_gen_threads<true>() : fresh_gen_threads<false>();
+        const uint64_t per_job = std::max<uint64_t>(1, (2ull * ctx->sm_count + P.n_jobs - 1) / P.n_jobs);
+        const uint64_t bx = std::min<uint64_t>(per_job, (n_max + threads - 1) / threads);
+        if (kind) k_keygen_fresh<true><<<dim3((unsigned)bx, P.n_jobs), (unsigned)threads, kTableBytes, s>>>(P);
+        else k_keygen_fresh<false><<<dim3((unsigned)bx, P.n_jobs), (unsigned)threads, kTableBytes, s>>>(P);
+        ctx->launches++;
+        ce = cudaGetLastError();
+        if (ce != cudaSuccess) return cuda_fail(ce, "k_keygen_fresh launch");
+    }
+    return OBLIVGM_OK;
 }
 
 extern "C" oblivgm_status oblivgm_filter_fresh(oblivgm_ctx* ctx, uint32_t query_id, const uint8_t* const tok[3],
@@ -573,7 +587,9 @@ extern "C" oblivgm_status oblivgm_filter_fresh(oblivgm_ctx* ctx, uint32_t query_
 
 namespace ogm {
 oblivgm_status set_fresh_attrs() {
-    cudaError_t e = cudaFuncSetAttribute(k_keygen_fresh, cudaFuncAttributeMaxDynamicSharedMemorySize, kTableBytes);
+    cudaError_t e = cudaFuncSetAttribute(k_keygen_fresh<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTableBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_keygen_fresh<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTableBytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_filter_fresh, cudaFuncAttributeMaxDynamicSharedMemorySize, kTableBytes);
     return e == cudaSuccess ? OBLIVGM_OK : cuda_fail(e, "fresh-key kernel attributes");

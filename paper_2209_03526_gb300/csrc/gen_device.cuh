@@ -24,12 +24,14 @@ __device__ __forceinline__ void gen_expand(const SmemTab& T, const AesParams& A,
     cs[0] &= ~1u;
 }
 
-// Gen of f^=_{alpha,beta} (dcf = false) or g^<_{alpha,beta} (dcf = true) over Z_{2^32}
+// Gen of f^=_{alpha,beta} (DCF = false) or g^<_{alpha,beta} (DCF = true) over Z_{2^32}
 // from the root seeds s0, s1 (overwritten).  No runtime-indexed arrays: the L/R and
-// keep/lose choices are selects, so everything stays in registers.
-template <class Sink>
-__device__ __forceinline__ void gen_pair(const SmemTab& T, const AesParams& A, bool dcf, int n, uint32_t alpha,
-                                         uint32_t beta, uint32_t s0[4], uint32_t s1[4], Sink& sink) {
+// keep/lose choices are selects, so everything stays in registers.  One instance per
+// kind keeps the DPF loop free of the DCF's value blocks.
+template <bool DCF, class Sink>
+__device__ __forceinline__ void gen_pair(const SmemTab& T, const AesParams& A, int n, uint32_t alpha, uint32_t beta,
+                                         uint32_t s0[4], uint32_t s1[4], Sink& sink) {
+    constexpr bool dcf = DCF;
     uint32_t t0 = 0u, t1 = 1u, valpha = 0u;
     for (int lv = 1; lv <= n; lv++) {
         uint32_t c0l[4], c0r[4], c1l[4], c1r[4], t0l, t0r, t1l, t1r;

@@ -23,6 +23,8 @@ namespace {
 #define OGM_KEYGEN_THREADS 768
 #endif
 constexpr int kKeygenThreads = OGM_KEYGEN_THREADS;   // one CTA per SM (the tables take 128 KiB)
+// tables, then a staging area of 32 records of 6 words per warp for the stores
+constexpr int kKeygenSmem = kTableBytes + (kKeygenThreads / 32) * 32 * 6 * 4;
 
 struct KeygenParams {
     AesParams aes;
@@ -37,45 +39,59 @@ struct KeygenParams {
 
 __device__ __forceinline__ void st32(uint8_t* p, uint32_t v) { *reinterpret_cast<uint32_t*>(p) = v; }
 
-// level records of the wire format, written to both keys of the pair
-struct WireSink {
-    uint8_t* k0;
-    uint8_t* k1;
-    uint32_t lvl;          // bytes per level record: 20 (DPF) or 24 (DCF)
-    bool dcf;
-    uint32_t n;
+// Level records of the wire format, written by the whole warp.  A warp's 32 consecutive
+// pairs own 64 consecutive keys; each level's record (the same for both keys of a pair)
+// goes through shared memory, and the warp then stores the 64 records with lanes on
+// consecutive words of a record, so a store instruction covers a few whole records
+// instead of 32 scattered words.
+template <bool DCF>
+struct WarpWireSink {
+    static constexpr uint32_t kWords = DCF ? 6 : 5;        // words per level record
+    uint8_t* base;         // first key of the warp's 64
+    uint32_t* stage;       // kWords words per lane
+    uint32_t L, lane, n, n_keys;   // key length, lane, levels, keys of the warp that exist
     __device__ __forceinline__ void level(int lv, const uint32_t scw[4], uint32_t tl, uint32_t tr, uint32_t vcw) {
-        const uint32_t off = 24u + (uint32_t)lv * lvl;
+        uint32_t* my = stage + lane * kWords;
+        my[0] = scw[0]; my[1] = scw[1]; my[2] = scw[2]; my[3] = scw[3];
+        my[4] = tl | (tr << 8);
+        if (DCF) my[5] = vcw;
+        __syncwarp();
+        const uint32_t off = 24u + (uint32_t)lv * kWords * 4;
 #pragma unroll
-        for (int w = 0; w < 4; w++) {
-            st32(k0 + off + 4 * w, scw[w]);
-            st32(k1 + off + 4 * w, scw[w]);
+        for (uint32_t j = 0; j < 2 * kWords; j++) {         // 64 records x kWords words
+            const uint32_t w = 32 * j + lane, r = w / kWords, word = w - r * kWords;
+            if (r < n_keys) st32(base + (uint64_t)r * L + off + 4 * word, stage[(r >> 1) * kWords + word]);
         }
-        st32(k0 + off + 16, tl | (tr << 8));
-        st32(k1 + off + 16, tl | (tr << 8));
-        if (dcf) {
-            st32(k0 + off + 20, vcw);
-            st32(k1 + off + 20, vcw);
-        }
+        __syncwarp();
     }
     __device__ __forceinline__ void final(uint32_t cw) {
-        const uint32_t off = 24u + n * lvl;
-        st32(k0 + off, cw);
-        st32(k1 + off, cw);
+        const uint32_t off = 24u + n * kWords * 4;
+        if (2 * lane < n_keys) {
+            st32(base + (uint64_t)(2 * lane) * L + off, cw);
+            st32(base + (uint64_t)(2 * lane + 1) * L + off, cw);
+        }
     }
 };
 
-template <int kThreads>
+// The loop runs over warp-sized chunks of pairs so that the whole warp stays together
+// for the cooperative stores; lanes past the last pair repeat the last pair's work and
+// store nothing.
+template <int kThreads, bool DCF>
 __global__ void __launch_bounds__(kThreads) k_keygen(const __grid_constant__ KeygenParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
     fill_tables(reinterpret_cast<uint32_t*>(smem), P.te0);
     __syncthreads();
     const SmemTab T{reinterpret_cast<const char*>(smem), lane_offset()};
-    const bool dcf = P.kind == OBLIVGM_KEY_DCF;
     const uint32_t L = P.key_len;
     const int n = (int)P.n;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.n_pairs;
-         i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* stage = reinterpret_cast<uint32_t*>(smem + kTableBytes) + warp * 32 * WarpWireSink<DCF>::kWords;
+    const uint64_t warps_total = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t chunk = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp; chunk * 32 < P.n_pairs;
+         chunk += warps_total) {
+        const uint64_t first = chunk * 32;
+        const uint64_t i = first + lane < P.n_pairs ? first + lane : P.n_pairs - 1;
+        const bool real = first + lane < P.n_pairs;
         uint32_t s0[4], s1[4];
         {
             const uint32_t c0[4] = {(uint32_t)(2 * i), (uint32_t)((2 * i) >> 32), 0u, 0u};
@@ -83,19 +99,27 @@ __global__ void __launch_bounds__(kThreads) k_keygen(const __grid_constant__ Key
             aes_one(T, P.rk_seed, c0, s0);
             aes_one(T, P.rk_seed, c1, s1);
         }
-        uint8_t* const k0 = P.out + (2 * i) * L;
-        uint8_t* const k1 = k0 + L;
-        st32(k0, (uint32_t)P.kind | ((uint32_t)n << 8));
-        st32(k1, (uint32_t)P.kind | ((uint32_t)n << 8) | (1u << 16));
-        st32(k0 + 4, 0u);
-        st32(k1 + 4, 0u);
+        if (real) {
+            uint8_t* const k0 = P.out + (2 * i) * L;
+            uint8_t* const k1 = k0 + L;
+            st32(k0, (uint32_t)P.kind | ((uint32_t)n << 8));
+            st32(k1, (uint32_t)P.kind | ((uint32_t)n << 8) | (1u << 16));
+            st32(k0 + 4, 0u);
+            st32(k1 + 4, 0u);
 #pragma unroll
-        for (int w = 0; w < 4; w++) {
-            st32(k0 + 8 + 4 * w, s0[w]);
-            st32(k1 + 8 + 4 * w, s1[w]);
+            for (int w = 0; w < 4; w++) {
+                st32(k0 + 8 + 4 * w, s0[w]);
+                st32(k1 + 8 + 4 * w, s1[w]);
+            }
         }
-        WireSink sink{k0, k1, dcf ? 24u : 20u, dcf, (uint32_t)n};
-        gen_pair(T, P.aes, dcf, n, P.alpha[i], P.beta[i], s0, s1, sink);
+        WarpWireSink<DCF> sink;
+        sink.base = P.out + 2 * first * L;
+        sink.stage = stage;
+        sink.L = L;
+        sink.lane = lane;
+        sink.n = (uint32_t)n;
+        sink.n_keys = (uint32_t)(P.n_pairs - first < 32 ? 2 * (P.n_pairs - first) : 64);
+        gen_pair<DCF>(T, P.aes, n, P.alpha[i], P.beta[i], s0, s1, sink);
     }
 }
 
@@ -131,7 +155,10 @@ extern "C" oblivgm_status oblivgm_keygen_device(oblivgm_ctx* ctx, uint32_t kind,
     P.key_len = L;
     const unsigned grid =
         (unsigned)std::min<uint64_t>((n_pairs + kKeygenThreads - 1) / kKeygenThreads, (uint64_t)ctx->sm_count);
-    k_keygen<kKeygenThreads><<<grid, kKeygenThreads, kTableBytes, static_cast<cudaStream_t>(stream)>>>(P);
+    if (kind == OBLIVGM_KEY_DCF)
+        k_keygen<kKeygenThreads, true><<<grid, kKeygenThreads, kKeygenSmem, static_cast<cudaStream_t>(stream)>>>(P);
+    else
+        k_keygen<kKeygenThreads, false><<<grid, kKeygenThreads, kKeygenSmem, static_cast<cudaStream_t>(stream)>>>(P);
     ctx->launches++;
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return cuda_fail(ce, "k_keygen launch");
@@ -140,7 +167,11 @@ extern "C" oblivgm_status oblivgm_keygen_device(oblivgm_ctx* ctx, uint32_t kind,
 
 namespace ogm {
 oblivgm_status set_keygen_attrs() {
-    cudaError_t e = cudaFuncSetAttribute(k_keygen<kKeygenThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTableBytes);
+    cudaError_t e = cudaFuncSetAttribute(k_keygen<kKeygenThreads, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kKeygenSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_keygen<kKeygenThreads, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kKeygenSmem);
     return e == cudaSuccess ? OBLIVGM_OK : cuda_fail(e, "keygen kernel attributes");
 }
 }  // namespace ogm
