@@ -388,6 +388,11 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{size} random vertices of the 1,048,576-vertex table, all 8 predicates, "
                                           f"{dt:.1f} s on {cores} threads"}
+    # context only (another method, machine and workload): the paper's Table 2 secEval time for
+    # 10,000 candidates with an equality predicate, one-hot keys, 3 V100 servers and a network
+    line["paper_context"] = {"secEval_10000_candidates_eq_s": 2.6, "candidate_predicates_per_s": 10000 / 2.6,
+                             "hardware": "3 x Tesla V100 (one per server), 2.5 Gbps network",
+                             "note": "not the same workload or metric; not used for vs_baseline"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
