@@ -141,6 +141,135 @@ __global__ void __launch_bounds__(1024, 1) k_onehot_evalall(const __grid_constan
     }
 }
 
+// ---- n >= 5: one work item per (key, 32 positions), one output word each
+
+// one level step with the key kind fixed at compile time
+template <bool DCF>
+__device__ __forceinline__ void step_k(const SmemTab& T, const AesParams& A, const DevKey& K, int i, uint32_t dir,
+                                       uint32_t s[4], uint32_t& t, uint32_t& V) {
+    // dir is opaque to the compiler here: otherwise it specialises the two-valued child
+    // loops of the depth-first expansion and keeps both selected key schedules in registers
+    asm volatile("" : "+r"(dir));
+    const uint32_t m = 0u - dir;
+    if (DCF) {
+        const uint32_t v0 = aes_sel_w0(T, A.rk_v, A.d_v, m, s);
+        V ^= ((v0 ^ s[0]) & 1u) ^ (t & K.vcw[i] & 1u);
+        // the seed block below starts after the value block: interleaving the two AES
+        // computations would double the live state
+        asm volatile("" : "+r"(s[0]), "+r"(s[1]), "+r"(s[2]), "+r"(s[3]) : "r"(V));
+    }
+    uint32_t o[4];
+    aes_sel(T, A.rk_st, A.d_st, m, s, o);
+#pragma unroll
+    for (int w = 0; w < 4; w++) o[w] ^= s[w];
+    uint32_t tn = o[0] & 1u;
+    o[0] &= ~1u;
+    const uint32_t tm = 0u - t;
+#pragma unroll
+    for (int w = 0; w < 4; w++) s[w] = o[w] ^ (K.scw[i][w] & tm);
+    tn ^= t & (((dir ? K.tr : K.tl) >> i) & 1u);
+    t = tn;
+}
+
+#ifndef OGM_DFS_DEPTH
+#define OGM_DFS_DEPTH 5
+#endif
+constexpr int kDfsDepth = OGM_DFS_DEPTH;   // positions per work item: 2^kDfsDepth (at most 5)
+constexpr int kNodeWords = 6;              // seed, control bit, DCF value bit
+
+// Eval of one key at the 2^D positions prefix * 2^D + j: the n - D shared levels once,
+// then the last D levels depth first, 2^(D+1) - 2 level steps for the 2^D positions.
+// The depth-first order keeps, for each depth below the block's root, the node on the
+// current path in a per-thread stack in shared memory (word w of depth d of thread x at
+// stack[(d * kNodeWords + w) * blockDim.x + x]), so one level step serves every depth.
+// Leaf j recomputes the levels below the highest bit in which j differs from j - 1.
+__device__ __forceinline__ uint32_t eval_block_d(const SmemTab& T, const AesParams& A, const DevKey& K,
+                                                 uint32_t prefix, bool dcf, uint32_t* stack) {
+    const int n = (int)K.n;
+    const uint32_t nt = blockDim.x;
+    uint32_t s[4] = {K.seed[0], K.seed[1], K.seed[2], K.seed[3]};
+    uint32_t t = K.party, V = 0;
+    for (int i = 0; i < n - kDfsDepth; i++)
+        level_step(T, A, K, i, (prefix >> (n - kDfsDepth - 1 - i)) & 1u, dcf, s, t, V);
+    const int lv0 = n - kDfsDepth;
+    const uint32_t cwf = K.cw_final & 1u;
+    auto save = [&](int d) {
+#pragma unroll
+        for (int w = 0; w < 4; w++) stack[(d * kNodeWords + w) * nt] = s[w];
+        stack[(d * kNodeWords + 4) * nt] = t;
+        stack[(d * kNodeWords + 5) * nt] = V;
+    };
+    auto load = [&](int d) {
+#pragma unroll
+        for (int w = 0; w < 4; w++) s[w] = stack[(d * kNodeWords + w) * nt];
+        t = stack[(d * kNodeWords + 4) * nt];
+        V = stack[(d * kNodeWords + 5) * nt];
+    };
+    save(0);
+    uint32_t bits = 0;
+#pragma unroll 1
+    for (uint32_t leaf = 0; leaf < (1u << kDfsDepth); leaf++) {
+        const int d0 = leaf == 0 ? 0 : kDfsDepth - 1 - (31 - __clz(leaf ^ (leaf - 1)));
+        if (leaf != 0) load(d0);
+#pragma unroll 1
+        for (int d = d0; d < kDfsDepth; d++) {
+            level_step(T, A, K, lv0 + d, (leaf >> (kDfsDepth - 1 - d)) & 1u, dcf, s, t, V);
+            if (d + 1 < kDfsDepth) save(d + 1);
+        }
+        bits |= (V ^ ((s[0] >> 1) & 1u) ^ (t & cwf)) << leaf;
+    }
+    return bits;
+}
+
+struct KeySlot {
+    uint32_t key;       // index into the keys
+    uint32_t half;      // the half vector it is XORed into
+    uint32_t cmask;     // all ones where party 0 of a range half adds the public constant
+    uint32_t dcf;
+};
+
+struct EvalWordParams {
+    AesParams aes;
+    const uint32_t* te0;
+    const DevKey* keys;
+    const KeySlot* slots;
+    uint32_t* hv;          // [half][words], zeroed before the launch
+    uint32_t words;        // 2^n / 32
+    uint32_t blocks;       // 2^(n - kDfsDepth) work items per key
+    uint32_t n_slots;
+};
+
+// Every key at every position, n >= 5.  Work item = (key slot, block of 2^D positions);
+// a range half's two DCF keys are separate items XORed into the same word.
+#ifndef OGM_EVALALL32_THREADS
+#define OGM_EVALALL32_THREADS 512
+#endif
+constexpr int kEvalAll32Threads = OGM_EVALALL32_THREADS;
+constexpr int kEvalAll32Smem = kTableBytes + kDfsDepth * kNodeWords * kEvalAll32Threads * 4;
+
+// The key kind is a runtime value: with it fixed at compile time the compiler keeps far
+// more state live in the DCF walk and spills.  Slots are ordered DPF first, so warps mix
+// kinds only at the boundary.
+__global__ void __launch_bounds__(kEvalAll32Threads, 1) k_onehot_evalall32(const __grid_constant__ EvalWordParams P) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    fill_tables(reinterpret_cast<uint32_t*>(smem), P.te0);
+    __syncthreads();
+    const SmemTab T{reinterpret_cast<const char*>(smem), lane_offset()};
+    uint32_t* stack = reinterpret_cast<uint32_t*>(smem + kTableBytes) + threadIdx.x;
+    const uint64_t items = (uint64_t)P.n_slots * P.blocks;
+    constexpr uint32_t kBits = 1u << kDfsDepth;
+    constexpr uint32_t kMask = kBits == 32 ? 0xFFFFFFFFu : ((1u << kBits) - 1u);
+    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < items;
+         idx += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t slot = (uint32_t)(idx / P.blocks), b = (uint32_t)(idx % P.blocks);
+        const KeySlot S = P.slots[slot];
+        const DevKey& K = P.keys[S.key];
+        const uint32_t bits = (eval_block_d(T, P.aes, K, b, S.dcf != 0, stack) ^ S.cmask) & kMask;
+        const uint32_t pos = b * kBits;
+        atomicXor(P.hv + (uint64_t)S.half * P.words + pos / 32, bits << (pos % 32));
+    }
+}
+
 constexpr int kDotPreds = 4;   // predicates one streaming pass over a column serves
 
 // Pass over one attribute column for up to kDotPreds predicates on it: every element's
@@ -462,7 +591,19 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
     const size_t off_h = up(keys.size() * sizeof(DevKey));
     const size_t off_o = off_h + up(halves.size() * sizeof(HalfDesc));
     const size_t off_s = off_o + up(np * sizeof(uint64_t));
-    const size_t off_v = off_s + up(np * sizeof(uint32_t));
+    std::vector<KeySlot> slots;             // DPF keys first, then DCF keys
+    for (uint32_t kind = 0; kind < 2; kind++)
+        for (uint32_t h = 0; h < halves.size(); h++) {
+            const HalfDesc& H = halves[h];
+            const uint32_t dcf = H.kind == OBLIVGM_KEY_DCF ? 1u : 0u;
+            if (dcf != kind) continue;
+            slots.push_back(KeySlot{H.key0, h, H.cbit ? 0xFFFFFFFFu : 0u, dcf});
+            if (H.key1 != kNoKey) slots.push_back(KeySlot{H.key1, h, 0u, dcf});
+        }
+    uint32_t n_dpf_slots = 0;
+    for (const KeySlot& k : slots) n_dpf_slots += k.dcf ? 0u : 1u;
+    const size_t off_k = off_s + up(np * sizeof(uint32_t));
+    const size_t off_v = off_k + up(slots.size() * sizeof(KeySlot));
     const size_t off_z = off_v + up(halves.size() * words * sizeof(uint32_t));
     const size_t total = off_z + zwords * sizeof(uint32_t);
     std::vector<unsigned char> img(off_v, 0);
@@ -470,6 +611,7 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
     std::memcpy(img.data() + off_h, halves.data(), halves.size() * sizeof(HalfDesc));
     std::memcpy(img.data() + off_o, gzoff.data(), np * sizeof(uint64_t));
     std::memcpy(img.data() + off_s, gstep.data(), np * sizeof(uint32_t));
+    std::memcpy(img.data() + off_k, slots.data(), slots.size() * sizeof(KeySlot));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned char* ws = nullptr;
     ce = cudaMallocAsync(reinterpret_cast<void**>(&ws), total, s);
@@ -489,7 +631,22 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
     E.log_block = (int)std::min<uint32_t>(3, n);
     ce = cudaMemsetAsync(E.hv, 0, halves.size() * words * sizeof(uint32_t), s);
     if (ce != cudaSuccess) return cuda_fail(ce, "half-vector clear");
-    {
+    if (n >= (uint32_t)kDfsDepth && n >= 5) {
+        EvalWordParams EW{};
+        EW.aes = ctx->aes;
+        EW.te0 = ctx->d_te0;
+        EW.keys = E.keys;
+        EW.slots = reinterpret_cast<const KeySlot*>(ws + off_k);
+        EW.hv = E.hv;
+        EW.words = words;
+        EW.blocks = domain >> kDfsDepth;
+        EW.slots = reinterpret_cast<const KeySlot*>(ws + off_k);
+        EW.n_slots = (uint32_t)slots.size();
+        const uint64_t items = (uint64_t)EW.n_slots * EW.blocks;
+        const unsigned grid = (unsigned)std::min<uint64_t>((items + kEvalAll32Threads - 1) / kEvalAll32Threads,
+                                                           (uint64_t)ctx->sm_count);
+        k_onehot_evalall32<<<grid, kEvalAll32Threads, kEvalAll32Smem, s>>>(EW);
+    } else {
         const uint64_t items = (uint64_t)halves.size() * (domain >> E.log_block);
         const unsigned grid = (unsigned)std::min<uint64_t>((items + 1023) / 1024, (uint64_t)ctx->sm_count);
         k_onehot_evalall<<<grid, 1024, kTableBytes, s>>>(E);
@@ -553,6 +710,8 @@ namespace ogm {
 
 oblivgm_status set_onehot_attrs() {
     cudaError_t e = cudaFuncSetAttribute(k_onehot_evalall, cudaFuncAttributeMaxDynamicSharedMemorySize, kTableBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_onehot_evalall32, cudaFuncAttributeMaxDynamicSharedMemorySize, kEvalAll32Smem);
     return e == cudaSuccess ? OBLIVGM_OK : cuda_fail(e, "one-hot kernel attributes");
 }
 
