@@ -143,34 +143,6 @@ __global__ void __launch_bounds__(1024, 1) k_onehot_evalall(const __grid_constan
 
 // ---- n >= 5: one work item per (key, 32 positions), one output word each
 
-// one level step with the key kind fixed at compile time
-template <bool DCF>
-__device__ __forceinline__ void step_k(const SmemTab& T, const AesParams& A, const DevKey& K, int i, uint32_t dir,
-                                       uint32_t s[4], uint32_t& t, uint32_t& V) {
-    // dir is opaque to the compiler here: otherwise it specialises the two-valued child
-    // loops of the depth-first expansion and keeps both selected key schedules in registers
-    asm volatile("" : "+r"(dir));
-    const uint32_t m = 0u - dir;
-    if (DCF) {
-        const uint32_t v0 = aes_sel_w0(T, A.rk_v, A.d_v, m, s);
-        V ^= ((v0 ^ s[0]) & 1u) ^ (t & K.vcw[i] & 1u);
-        // the seed block below starts after the value block: interleaving the two AES
-        // computations would double the live state
-        asm volatile("" : "+r"(s[0]), "+r"(s[1]), "+r"(s[2]), "+r"(s[3]) : "r"(V));
-    }
-    uint32_t o[4];
-    aes_sel(T, A.rk_st, A.d_st, m, s, o);
-#pragma unroll
-    for (int w = 0; w < 4; w++) o[w] ^= s[w];
-    uint32_t tn = o[0] & 1u;
-    o[0] &= ~1u;
-    const uint32_t tm = 0u - t;
-#pragma unroll
-    for (int w = 0; w < 4; w++) s[w] = o[w] ^ (K.scw[i][w] & tm);
-    tn ^= t & (((dir ? K.tr : K.tl) >> i) & 1u);
-    t = tn;
-}
-
 #ifndef OGM_DFS_DEPTH
 #define OGM_DFS_DEPTH 5
 #endif
