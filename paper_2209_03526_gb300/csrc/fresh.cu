@@ -36,7 +36,10 @@ constexpr int kFreshMaxPreds = 64;
 constexpr int kFreshMaxJobs = kFreshMaxPreds * 6;
 // client Gen: one CTA per SM (the tables take 128 KiB); both instances need more than the
 // 80 registers a 768-thread CTA leaves
-template <bool DCF> constexpr int fresh_gen_threads() { return 512; }
+#ifndef OGM_FRESH_GEN_THREADS
+#define OGM_FRESH_GEN_THREADS 512
+#endif
+template <bool DCF> constexpr int fresh_gen_threads() { return OGM_FRESH_GEN_THREADS; }
 #ifndef OGM_FRESH_EVAL_THREADS
 #define OGM_FRESH_EVAL_THREADS 768
 #endif
@@ -84,6 +87,7 @@ struct FreshGenParams {
     uint32_t n, n_jobs;
     FreshPred preds[kFreshMaxPreds];
     GenJob jobs[kFreshMaxJobs];
+    uint64_t job_start[kFreshMaxJobs + 1];   // prefix sums of the jobs' element counts
 };
 
 __device__ __forceinline__ void st_u32(uint8_t* p, uint32_t v) { *reinterpret_cast<uint32_t*>(p) = v; }
@@ -134,19 +138,29 @@ __global__ void __launch_bounds__(fresh_gen_threads<DCF>()) k_keygen_fresh(const
     fill_tables(reinterpret_cast<uint32_t*>(smem), P.te0);
     __syncthreads();
     const SmemTab T{reinterpret_cast<const char*>(smem), lane_offset()};
-    const GenJob J = P.jobs[blockIdx.y];
-    const FreshPred& Q = P.preds[J.pred];
     constexpr bool eq = !DCF;
     const uint32_t n = P.n;
     const uint32_t m = n >= 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
-    const FreshLayout& L = Q.lay;
     constexpr int nsub = eq ? 1 : 2;
-    // owners (server, half) of the pair's two keys, from the assignment
-    // CS1 (1,0),(2,0); CS2 (2,1),(3,0); CS3 (3,1),(1,1): party 0 of pairs 1, 2, 3 sits with
-    // CS1 A, CS1 B, CS2 B; party 1 with CS3 B, CS2 A, CS3 A
-    const uint32_t srv0 = J.pair == 2 ? 1u : 0u, half0 = J.pair == 0 ? 0u : 1u;
-    const uint32_t srv1 = J.pair == 1 ? 1u : 2u, half1 = J.pair == 0 ? 1u : 0u;
-    for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < L.N; c += (uint64_t)gridDim.x * blockDim.x) {
+    // one persistent grid over all (job, element) items of the launch, so no CTA waits on
+    // a short last wave
+    const uint64_t total = P.job_start[P.n_jobs];
+    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t lo = 0, hi = P.n_jobs - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (P.job_start[mid] <= idx) lo = mid; else hi = mid - 1;
+        }
+        const GenJob J = P.jobs[lo];
+        const FreshPred& Q = P.preds[J.pred];
+        const FreshLayout& L = Q.lay;
+        const uint64_t c = idx - P.job_start[lo];
+        // owners (server, half) of the pair's two keys, from the assignment
+        // CS1 (1,0),(2,0); CS2 (2,1),(3,0); CS3 (3,1),(1,1): party 0 of pairs 1, 2, 3 sits with
+        // CS1 A, CS1 B, CS2 B; party 1 with CS3 B, CS2 A, CS3 A
+        const uint32_t srv0 = J.pair == 2 ? 1u : 0u, half0 = J.pair == 0 ? 0u : 1u;
+        const uint32_t srv1 = J.pair == 1 ? 1u : 2u, half1 = J.pair == 0 ? 1u : 0u;
         uint32_t w[4];
         client_block(T, P.rk_client, c, Q.step, 1u, 0u, w);
         const uint32_t r = w[0] & m;
@@ -459,18 +473,19 @@ extern "C" oblivgm_status oblivgm_keygen_fresh(oblivgm_ctx* ctx, const oblivgm_p
         if (ce != cudaSuccess) return cuda_fail(ce, "fresh token header copy");
     }
     if (n_max == 0) return OBLIVGM_OK;
-    // one launch per kind; about two CTAs per SM in total, spread over the launch's jobs,
-    // each CTA striding over its job's elements
+    // one launch per kind, a persistent grid over the launch's (job, element) items
     for (int kind = 0; kind < 2; kind++) {
         const std::vector<GenJob>& jl = kind ? range_jobs : eq_jobs;
         if (jl.empty()) continue;
         P.n_jobs = (uint32_t)jl.size();
         std::copy(jl.begin(), jl.end(), P.jobs);
+        P.job_start[0] = 0;
+        for (uint32_t j = 0; j < P.n_jobs; j++) P.job_start[j + 1] = P.job_start[j] + P.preds[jl[j].pred].lay.N;
+        if (P.job_start[P.n_jobs] == 0) continue;
         const uint64_t threads = kind ? fresh_gen_threads<true>() : fresh_gen_threads<false>();
-        const uint64_t per_job = std::max<uint64_t>(1, (2ull * ctx->sm_count + P.n_jobs - 1) / P.n_jobs);
-        const uint64_t bx = std::min<uint64_t>(per_job, (n_max + threads - 1) / threads);
-        if (kind) k_keygen_fresh<true><<<dim3((unsigned)bx, P.n_jobs), (unsigned)threads, kTableBytes, s>>>(P);
-        else k_keygen_fresh<false><<<dim3((unsigned)bx, P.n_jobs), (unsigned)threads, kTableBytes, s>>>(P);
+        const uint64_t grid = std::min<uint64_t>((P.job_start[P.n_jobs] + threads - 1) / threads, ctx->sm_count);
+        if (kind) k_keygen_fresh<true><<<(unsigned)grid, (unsigned)threads, kTableBytes, s>>>(P);
+        else k_keygen_fresh<false><<<(unsigned)grid, (unsigned)threads, kTableBytes, s>>>(P);
         ctx->launches++;
         ce = cudaGetLastError();
         if (ce != cudaSuccess) return cuda_fail(ce, "k_keygen_fresh launch");
