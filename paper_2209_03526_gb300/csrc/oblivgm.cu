@@ -387,19 +387,23 @@ struct Plan {
 
 // Element tile per work item.  The items (group, tile) are taken by one persistent CTA
 // per SM in cost order; a tile width that leaves the last wave half empty wastes the
-// idle SMs' time, so widths from step_elems up to max_tile (in steps of a warp's worth
-// of elements, down to half the CTA's width) are tried by simulating that greedy schedule, and the width with the
-// shortest makespan wins (the widest on ties).  Large item counts skip the search: their
-// tail is already a small fraction.
+// idle SMs' time, and a query too small to give every SM a full-width tile leaves SMs
+// idle altogether, so widths from max_tile down to one warp's worth of elements
+// (step_elems) are tried by simulating that greedy schedule, and the width with the
+// shortest makespan wins (the widest on ties).  An item's time is modelled as its cost
+// times its element count, but never less than for kLatencyFloorElems elements: below
+// about two warps per SM the walks' own latency, not the shared-memory pipe, sets the
+// time.  Large item counts skip the search: their tail is already a small fraction.
 template <typename NF, typename CF>
 uint32_t choose_tile(size_t n_groups, NF n_elems_of, CF cost_of, uint32_t max_tile, uint32_t step_elems, int sm_count) {
     uint64_t items_at_max = 0;
     for (size_t g = 0; g < n_groups; g++) items_at_max += (n_elems_of(g) + max_tile - 1) / max_tile;
     if (items_at_max == 0 || items_at_max > 64ull * (uint64_t)sm_count || step_elems == 0) return max_tile;
+    constexpr uint64_t kLatencyFloorElems = 64;
     uint32_t best_tile = max_tile;
     double best = -1.0;
     std::vector<double> finish;
-    const uint32_t min_tile = std::max(step_elems, max_tile / 2 / step_elems * step_elems);
+    const uint32_t min_tile = step_elems;
     for (uint32_t t = max_tile; t >= min_tile; t -= step_elems) {
         finish.assign((size_t)sm_count, 0.0);
         std::make_heap(finish.begin(), finish.end(), std::greater<double>());
@@ -407,7 +411,7 @@ uint32_t choose_tile(size_t n_groups, NF n_elems_of, CF cost_of, uint32_t max_ti
             const uint64_t n = n_elems_of(g);
             for (uint64_t e = 0; e < n; e += t) {
                 const uint64_t width = std::min<uint64_t>(t, n - e);
-                const uint64_t warps_elems = (width + 31) / 32 * 32;
+                const uint64_t warps_elems = std::max<uint64_t>((width + 31) / 32 * 32, kLatencyFloorElems);
                 std::pop_heap(finish.begin(), finish.end(), std::greater<double>());
                 finish.back() += (double)cost_of(g) * (double)warps_elems;
                 std::push_heap(finish.begin(), finish.end(), std::greater<double>());
