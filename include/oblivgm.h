@@ -521,6 +521,12 @@ oblivgm_status oblivgm_sync(oblivgm_ctx* ctx, void* stream);
  * faults, traps or spins without a bound.  For tests only. */
 oblivgm_status oblivgm_test_expire_next_wait(oblivgm_ctx* ctx, uint32_t limit_us);
 
+/* Failure-path test hook: the context's next device workspace allocation is
+ * refused as if the device were out of memory, so that call returns ENOMEM
+ * (nothing is launched); later calls allocate normally.  The paper has no
+ * counterpart. */
+oblivgm_status oblivgm_test_fail_next_alloc(oblivgm_ctx* ctx);
+
 /* Count of this library's kernel launches so far on the context (for the
  * bench's launch accounting). */
 uint64_t oblivgm_launch_count(oblivgm_ctx* ctx);

@@ -13,7 +13,7 @@ import ctypes
 from typing import Sequence
 
 from . import _native as N
-from ._native import (ALL_PAIRS, EAGAIN, EBUSY, EFAULT_DEVICE, EINVAL, ENOENT, ERANGE, ETIMEOUT, KEY_DCF, KEY_DPF,
+from ._native import (ALL_PAIRS, EAGAIN, EBUSY, EFAULT_DEVICE, EINVAL, ENOENT, ENOMEM, ERANGE, ETIMEOUT, KEY_DCF, KEY_DPF,
                       OK, PRED_EQ, PRED_RANGE, OblivgmError)
 from .build import build
 
@@ -390,6 +390,10 @@ class Context:
         t, e = N.c_u32(), N.c_u32()
         N.check(self._lib.oblivgm_autotune(self._h, ctypes.byref(t), ctypes.byref(e)), "oblivgm_autotune")
         return t.value, e.value
+
+    def test_fail_next_alloc(self):
+        """Failure-path test hook: the next device workspace allocation reports ENOMEM."""
+        N.check(self._lib.oblivgm_test_fail_next_alloc(self._h), "oblivgm_test_fail_next_alloc")
 
     def test_expire_next_wait(self, limit_us: int):
         """Failure-path test hook: the next fused launch's key-staging waits run out after limit_us."""

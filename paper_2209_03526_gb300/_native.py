@@ -98,6 +98,7 @@ _SIGS = {
     "oblivgm_autotune": ([c_vp, ctypes.POINTER(c_u32), ctypes.POINTER(c_u32)], c_i32),
     "oblivgm_set_schedule": ([c_vp, c_u32, c_u32], c_i32),
     "oblivgm_test_expire_next_wait": ([c_vp, c_u32], c_i32),
+    "oblivgm_test_fail_next_alloc": ([c_vp], c_i32),
 }
 
 

@@ -167,6 +167,7 @@ using namespace ogm;
 extern "C" oblivgm_status oblivgm_fetch_unique(oblivgm_ctx* ctx, uint32_t query_id, uint32_t group,
                                                uint32_t table_id, const uint32_t* const x[3], uint32_t n_attrs,
                                                const uint32_t* attrs, uint32_t* out, void* stream) {
+    const NvtxRange nvtx_range("oblivgm_fetch_unique");
     if (!ctx || !x || !out || (n_attrs && !attrs)) return fail(OBLIVGM_EINVAL, "NULL argument");
     if (n_attrs > (uint32_t)kFetchMaxAttrs) return fail(OBLIVGM_EINVAL, "at most 64 attributes per fetch");
     if (group > 0xFFFF - kFetchStep) return fail(OBLIVGM_EINVAL, "group index too large");

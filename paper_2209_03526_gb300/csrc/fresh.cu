@@ -406,6 +406,7 @@ extern "C" oblivgm_status oblivgm_keygen_fresh(oblivgm_ctx* ctx, const oblivgm_p
                                                uint32_t n_bits, const uint64_t* table_elems, uint32_t n_tables,
                                                const uint8_t seed[16], uint8_t* const tok[3], uint64_t cap,
                                                void* stream) {
+    const NvtxRange nvtx_range("oblivgm_keygen_fresh");
     if (!ctx || !seed || !tok || !tok[0] || !tok[1] || !tok[2]) return fail(OBLIVGM_EINVAL, "NULL argument");
     oblivgm_status st = check_fresh_preds(preds, n_preds, n_bits, table_elems, n_tables);
     if (st) return st;
@@ -495,6 +496,7 @@ extern "C" oblivgm_status oblivgm_keygen_fresh(oblivgm_ctx* ctx, const oblivgm_p
 
 extern "C" oblivgm_status oblivgm_filter_fresh(oblivgm_ctx* ctx, uint32_t query_id, const uint8_t* const tok[3],
                                                uint32_t n_groups, uint32_t* const* out, void* stream) {
+    const NvtxRange nvtx_range("oblivgm_filter_fresh");
     if (!ctx || !tok || !tok[0] || !tok[1] || !tok[2] || !out) return fail(OBLIVGM_EINVAL, "NULL argument");
     if (n_groups == 0 || n_groups > OBLIVGM_MAX_GROUPS) return fail(OBLIVGM_EINVAL, "n_groups must be 1..64");
     for (int i = 0; i < 3; i++)

@@ -132,6 +132,7 @@ using namespace ogm;
 extern "C" oblivgm_status oblivgm_keygen_device(oblivgm_ctx* ctx, uint32_t kind, uint32_t n_bits, uint64_t n_pairs,
                                                 const uint32_t* alpha, const uint32_t* beta, const uint8_t seed[16],
                                                 uint8_t* keys_out, uint64_t out_bytes, void* stream) {
+    const NvtxRange nvtx_range("oblivgm_keygen_device");
     if (!ctx || !seed || (n_pairs && (!alpha || !beta || !keys_out))) return fail(OBLIVGM_EINVAL, "NULL argument");
     if (kind != OBLIVGM_KEY_DPF && kind != OBLIVGM_KEY_DCF) return fail(OBLIVGM_EINVAL, "unknown key kind");
     if (n_bits < 1 || n_bits > (uint32_t)kMaxBits) return fail(OBLIVGM_EINVAL, "n must be 1..32");

@@ -31,6 +31,17 @@ oblivgm_status cuda_fail(cudaError_t e, const char* what) {
     return e == cudaErrorMemoryAllocation ? OBLIVGM_ENOMEM : OBLIVGM_ECUDA;
 }
 
+oblivgm_status ws_alloc(oblivgm_ctx* ctx, void** p, size_t bytes, cudaStream_t s, const char* what) {
+    *p = nullptr;
+    if (ctx->test_fail_alloc.exchange(false)) return fail(OBLIVGM_ENOMEM, std::string(what) + ": refused (test hook)");
+    const cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(OBLIVGM_ENOMEM, std::string(what) + ": out of device memory");
+    }
+    return e == cudaSuccess ? OBLIVGM_OK : cuda_fail(e, what);
+}
+
 #define OGM_CUDA(call, what)                      \
     do {                                          \
         cudaError_t _e = (call);                  \
@@ -514,7 +525,8 @@ oblivgm_status launch_plan(oblivgm_ctx* ctx, const Plan& plan, cudaStream_t st, 
     std::memcpy(img.data() + off_keys, plan.keys.data(), plan.keys.size() * sizeof(DevKey));
     std::memcpy(img.data() + off_items, plan.item_start.data(), plan.item_start.size() * sizeof(uint64_t));
     unsigned char* ws = nullptr;
-    OGM_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&ws), total, st), "workspace allocation");
+    oblivgm_status as = ws_alloc(ctx, reinterpret_cast<void**>(&ws), total, st, "workspace allocation");
+    if (as != OBLIVGM_OK) return as;
     OGM_CUDA(cudaMemcpyAsync(ws, img.data(), total, cudaMemcpyHostToDevice, st), "descriptor upload");
     FilterParams P{};
     P.aes = ctx->aes;
@@ -678,6 +690,7 @@ uint64_t oblivgm_launch_count(oblivgm_ctx* ctx) { return ctx ? ctx->launches.loa
 oblivgm_status oblivgm_load_shares(oblivgm_ctx* ctx, uint32_t table_id, uint64_t n_elems, uint32_t n_attrs,
                                    uint32_t n_bits, const uint32_t* const share_sets[3], int32_t mem_kind,
                                    void* stream) {
+    const NvtxRange nvtx_range("oblivgm_load_shares");
     oblivgm_status st = check_ctx(ctx);
     if (st) return st;
     if (table_id > 0xFFFF || n_attrs == 0 || n_attrs > 65536 || n_bits < 1 || n_bits > 32 || !share_sets)
@@ -746,6 +759,7 @@ oblivgm_status oblivgm_keygen(const oblivgm_pred* preds, uint32_t n_preds, uint3
 static oblivgm_status eval_batch(oblivgm_ctx* ctx, uint32_t kind, const uint8_t* keys, uint32_t n_keys,
                                  const uint32_t* points, const uint32_t* key_of_point, uint64_t n_points,
                                  uint32_t flags, uint32_t* out, uint64_t n_out, void* stream) {
+    const NvtxRange nvtx_range(kind == OBLIVGM_KEY_DPF ? "oblivgm_eval_dpf_batch" : "oblivgm_eval_dcf_batch");
     oblivgm_status st = check_ctx(ctx);
     if (st) return st;
     if (!keys || n_keys == 0 || (n_points && (!points || !out))) return fail(OBLIVGM_EINVAL, "NULL or empty argument");
@@ -762,7 +776,8 @@ static oblivgm_status eval_batch(oblivgm_ctx* ctx, uint32_t kind, const uint8_t*
     if (n_points == 0) return OBLIVGM_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     DevKey* d_keys = nullptr;
-    OGM_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_keys), (size_t)n_keys * sizeof(DevKey), s), "key buffer");
+    st = ws_alloc(ctx, reinterpret_cast<void**>(&d_keys), (size_t)n_keys * sizeof(DevKey), s, "key buffer");
+    if (st != OBLIVGM_OK) return st;
     if (dev_keys) {
         st = repack_keys_device(ctx, keys, kind, (uint32_t)n, n_keys, d_keys, s);
         if (st != OBLIVGM_OK) return st;
@@ -811,6 +826,7 @@ oblivgm_status oblivgm_eval_dcf_batch(oblivgm_ctx* ctx, const uint8_t* keys, uin
 oblivgm_status oblivgm_filter_batch(oblivgm_ctx* ctx, uint32_t n_queries, const uint32_t* query_ids,
                                     const uint8_t* const* toks, const size_t* tok_lens, const uint32_t* n_groups,
                                     uint32_t* const* const* outs, void* stream) {
+    const NvtxRange nvtx_range("oblivgm_filter_batch");
     oblivgm_status st = check_ctx(ctx);
     if (st) return st;
     if (n_queries == 0) return OBLIVGM_OK;
@@ -829,6 +845,7 @@ oblivgm_status oblivgm_filter_batch(oblivgm_ctx* ctx, uint32_t n_queries, const 
 oblivgm_status oblivgm_filter_and_combine(oblivgm_ctx* ctx, uint32_t query_id, const uint8_t* const tok[3],
                                           const size_t tok_len[3], uint32_t n_groups, uint32_t* const* out,
                                           void* stream) {
+    const NvtxRange nvtx_range("oblivgm_filter_and_combine");
     if (!tok || !tok_len || !out) return fail(OBLIVGM_EINVAL, "NULL argument");
     const uint8_t* toks[3] = {tok[0], tok[1], tok[2]};
     uint32_t* const* outs[1] = {out};
@@ -836,6 +853,7 @@ oblivgm_status oblivgm_filter_and_combine(oblivgm_ctx* ctx, uint32_t query_id, c
 }
 
 oblivgm_status oblivgm_autotune(oblivgm_ctx* ctx, uint32_t* threads, uint32_t* elems_per_thread) {
+    const NvtxRange nvtx_range("oblivgm_autotune");
     oblivgm_status st = check_ctx(ctx);
     if (st) return st;
     // synthetic private table: 2^20 elements (every candidate shape gets at least one tile
@@ -908,6 +926,13 @@ oblivgm_status oblivgm_autotune(oblivgm_ctx* ctx, uint32_t* threads, uint32_t* e
     return OBLIVGM_OK;
 }
 
+oblivgm_status oblivgm_test_fail_next_alloc(oblivgm_ctx* ctx) {
+    oblivgm_status st = check_ctx(ctx);
+    if (st) return st;
+    ctx->test_fail_alloc = true;
+    return OBLIVGM_OK;
+}
+
 oblivgm_status oblivgm_test_expire_next_wait(oblivgm_ctx* ctx, uint32_t limit_us) {
     oblivgm_status st = check_ctx(ctx);
     if (st) return st;
@@ -973,6 +998,7 @@ oblivgm_status scratch_address(int device, unsigned char** out) {
 extern "C" oblivgm_status oblivgm_filter_and_combine_noalloc(oblivgm_ctx* ctx, uint32_t query_id,
                                                              const uint8_t* const tok[3], const size_t tok_len[3],
                                                              uint32_t n_groups, uint32_t* const* out, void* stream) {
+    const NvtxRange nvtx_range("oblivgm_filter_and_combine_noalloc");
     oblivgm_status st = check_ctx(ctx);   // also makes the context's device current
     if (st) return st;
     if (!tok || !tok_len || !out) return fail(OBLIVGM_EINVAL, "NULL argument");
@@ -1114,6 +1140,7 @@ extern "C" oblivgm_status oblivgm_plan_create(oblivgm_ctx* ctx, uint32_t n_queri
 }
 
 extern "C" oblivgm_status oblivgm_plan_launch(oblivgm_plan* p, void* stream) {
+    const NvtxRange nvtx_range("oblivgm_plan_launch");
     if (!p) return fail(OBLIVGM_EINVAL, "NULL plan");
     if (p->n_items == 0) return OBLIVGM_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

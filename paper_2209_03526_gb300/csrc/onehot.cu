@@ -446,6 +446,7 @@ using namespace ogm;
 extern "C" oblivgm_status oblivgm_keygen_onehot(const oblivgm_pred* preds, uint32_t n_preds, uint32_t n_bits,
                                                 const uint8_t seed[16], uint8_t* const tok[3], size_t cap,
                                                 size_t out_len[3]) {
+    const NvtxRange nvtx_range("oblivgm_keygen_onehot");
     std::string err;
     oblivgm_status st = keygen(preds, n_preds, n_bits, seed, tok, cap, out_len, &err, /*onehot=*/true);
     if (st != OBLIVGM_OK) return fail(st, err);
@@ -455,6 +456,7 @@ extern "C" oblivgm_status oblivgm_keygen_onehot(const oblivgm_pred* preds, uint3
 extern "C" oblivgm_status oblivgm_load_onehot(oblivgm_ctx* ctx, uint32_t table_id, uint64_t n_elems,
                                               uint32_t n_attrs, uint32_t n_bits,
                                               const uint32_t* const share_sets[3], int32_t mem_kind, void* stream) {
+    const NvtxRange nvtx_range("oblivgm_load_onehot");
     if (!ctx) return fail(OBLIVGM_EINVAL, "NULL context");
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
@@ -495,6 +497,7 @@ extern "C" oblivgm_status oblivgm_load_onehot(oblivgm_ctx* ctx, uint32_t table_i
 extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query_id, const uint8_t* const tok[3],
                                                 const size_t tok_len[3], uint32_t n_groups, uint32_t* const* out,
                                                 void* stream) {
+    const NvtxRange nvtx_range("oblivgm_filter_onehot");
     if (!ctx || !tok || !tok_len || !out) return fail(OBLIVGM_EINVAL, "NULL argument");
     cudaError_t ce = cudaSetDevice(ctx->device);
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaSetDevice");
@@ -586,8 +589,10 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
     std::memcpy(img.data() + off_k, slots.data(), slots.size() * sizeof(KeySlot));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned char* ws = nullptr;
-    ce = cudaMallocAsync(reinterpret_cast<void**>(&ws), total, s);
-    if (ce != cudaSuccess) return cuda_fail(ce, "one-hot scratch");
+    {
+        const oblivgm_status as = ws_alloc(ctx, reinterpret_cast<void**>(&ws), total, s, "one-hot scratch");
+        if (as != OBLIVGM_OK) return as;
+    }
     ce = cudaMemcpyAsync(ws, img.data(), off_v, cudaMemcpyHostToDevice, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "one-hot descriptor upload");
     uint32_t* zbase = reinterpret_cast<uint32_t*>(ws + off_z);

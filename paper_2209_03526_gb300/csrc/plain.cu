@@ -88,6 +88,7 @@ using namespace ogm;
 extern "C" oblivgm_status oblivgm_filter_plain(oblivgm_ctx* ctx, uint32_t query_id, const uint8_t* const tok[3],
                                                const size_t tok_len[3], uint32_t n_groups, uint32_t* const* out,
                                                void* stream) {
+    const NvtxRange nvtx_range("oblivgm_filter_plain");
     if (!ctx || !tok || !tok_len || !out) return fail(OBLIVGM_EINVAL, "NULL argument");
     cudaError_t ce = cudaSetDevice(ctx->device);
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaSetDevice");
@@ -124,8 +125,11 @@ extern "C" oblivgm_status oblivgm_filter_plain(oblivgm_ctx* ctx, uint32_t query_
         // scratch: xhat | y (12 n) | b (3 n) | 12 device keys
         const size_t words = n + 12 * n + 3 * n;
         unsigned char* ws = nullptr;
-        ce = cudaMallocAsync(reinterpret_cast<void**>(&ws), words * 4 + 12 * sizeof(DevKey) + 256, s);
-        if (ce != cudaSuccess) return cuda_fail(ce, "plain-path scratch");
+        {
+            const oblivgm_status as =
+                ws_alloc(ctx, reinterpret_cast<void**>(&ws), words * 4 + 12 * sizeof(DevKey) + 256, s, "plain-path scratch");
+            if (as != OBLIVGM_OK) return as;
+        }
         uint32_t* xhat = reinterpret_cast<uint32_t*>(ws);
         uint32_t* y = xhat + n;
         uint32_t* b = y + 12 * n;

@@ -15,10 +15,20 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "host_crypto.h"
 #include "oblivgm.h"
 
 namespace ogm {
+
+// NVTX range around an ABI call (header-only NVTX v3: a no-op unless a profiler is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct Table {
     uint32_t* dev = nullptr;   // [share set j][attr][stride] uint32
@@ -93,6 +103,7 @@ struct oblivgm_ctx {
     uint32_t elems_per_thread = 1;
     std::atomic<uint64_t> launches{0};
     bool test_expire_next = false;      // failure-path test hook, one-shot
+    std::atomic<bool> test_fail_alloc{false};   // failure-path test hook: refuse the next workspace allocation
     uint64_t test_wait_limit_ns = 0;
     ogm::ServeState serve;
 };
@@ -115,6 +126,8 @@ oblivgm_status launch_parsed(oblivgm_ctx* ctx, uint32_t n_queries, const uint32_
 double now_ms();
 oblivgm_status set_onehot_attrs();
 oblivgm_status set_keygen_attrs();
+// stream-ordered device workspace; ENOMEM when the allocator refuses (or the test hook says so)
+oblivgm_status ws_alloc(oblivgm_ctx* ctx, void** p, size_t bytes, cudaStream_t s, const char* what);
 oblivgm_status set_fresh_attrs();
 oblivgm_status set_shuffle_attrs();
 oblivgm_status repack_keys_device(oblivgm_ctx* ctx, const uint8_t* wire, uint32_t kind, uint32_t n, uint32_t n_keys,

@@ -101,9 +101,11 @@ void worker_main(oblivgm_ctx* ctx) {
             parsed.push_back(q->parsed);
             for (auto& kv : q->tables) tables[kv.first] = kv.second;
         }
-        if (st_code == OBLIVGM_OK)
+        if (st_code == OBLIVGM_OK) {
+            const NvtxRange nvtx_range("oblivgm_serve_batch");
             st_code = launch_parsed(ctx, (uint32_t)batch.size(), qids.data(), parsed.data(), ngroups.data(),
                                     outs.data(), tables, st);
+        }
         auto* cb = new ServeBatch{ctx, {}};
         for (ServeQuery* q : batch) cb->tickets.push_back(q->ticket);
         if (st_code != OBLIVGM_OK) {

@@ -367,8 +367,9 @@ oblivgm_status shuffle_device(oblivgm_ctx* ctx, uint32_t group, uint64_t n, uint
     const size_t total = 7 * ((perm_bytes + 255) & ~size_t(255)) + 3 * ((tab_bytes + 255) & ~size_t(255)) +
                          ((ftab_bytes + 255) & ~size_t(255));
     uint8_t* scratch = nullptr;
-    cudaError_t ce = cudaMallocAsync(reinterpret_cast<void**>(&scratch), total, s);
-    if (ce != cudaSuccess) return cuda_fail(ce, "shuffle scratch");
+    const oblivgm_status as = ws_alloc(ctx, reinterpret_cast<void**>(&scratch), total, s, "shuffle scratch");
+    if (as != OBLIVGM_OK) return as;
+    cudaError_t ce = cudaSuccess;
     size_t off = 0;
     for (int k = 0; k < 3; k++) {
         P.inv[k] = reinterpret_cast<uint32_t*>(scratch + off);
@@ -422,6 +423,7 @@ using namespace ogm;
 extern "C" oblivgm_status oblivgm_shuffle(oblivgm_ctx* ctx, uint32_t group, uint64_t n_rows, uint32_t width,
                                           const uint32_t* const in[3], const uint8_t seeds[48],
                                           uint32_t* const out[3], void* stream) {
+    const NvtxRange nvtx_range("oblivgm_shuffle");
     if (!ctx || !in || !out || !seeds) return fail(OBLIVGM_EINVAL, "NULL argument");
     if (group != OBLIVGM_SHUFFLE_ADD && group != OBLIVGM_SHUFFLE_XOR) return fail(OBLIVGM_EINVAL, "unknown share group");
     if (width < 1 || width > kShufMaxWidth) return fail(OBLIVGM_EINVAL, "width must be 1..64");
@@ -439,6 +441,7 @@ extern "C" oblivgm_status oblivgm_shuffle(oblivgm_ctx* ctx, uint32_t group, uint
 extern "C" oblivgm_status oblivgm_fetch_multi(oblivgm_ctx* ctx, uint32_t table_id, const uint32_t* const x[3],
                                               uint32_t n_attrs, const uint32_t* attrs, const uint8_t seeds[48],
                                               uint32_t* const out[3], uint64_t cap, uint64_t* count, void* stream) {
+    const NvtxRange nvtx_range("oblivgm_fetch_multi");
     if (!ctx || !x || !out || !seeds || !count || (n_attrs && !attrs)) return fail(OBLIVGM_EINVAL, "NULL argument");
     if (n_attrs + 2 > kShufMaxWidth) return fail(OBLIVGM_EINVAL, "at most 62 attributes");
     cudaError_t ce = cudaSetDevice(ctx->device);
@@ -460,8 +463,10 @@ extern "C" oblivgm_status oblivgm_fetch_multi(oblivgm_ctx* ctx, uint32_t table_i
     const size_t tab = ((size_t)n * W * 4 + 255) & ~size_t(255);
     const size_t total = 6 * tab + ((size_t)(n_blocks + 1) * 4 + 255);
     uint8_t* scratch = nullptr;
-    ce = cudaMallocAsync(reinterpret_cast<void**>(&scratch), total, s);
-    if (ce != cudaSuccess) return cuda_fail(ce, "fetch scratch");
+    {
+        const oblivgm_status as = ws_alloc(ctx, reinterpret_cast<void**>(&scratch), total, s, "fetch scratch");
+        if (as != OBLIVGM_OK) return as;
+    }
     PackParams K;
     std::memset(&K, 0, sizeof K);
     uint32_t* d[3];
