@@ -886,7 +886,7 @@ oblivgm_status oblivgm_autotune(oblivgm_ctx* ctx, uint32_t* threads, uint32_t* e
     const uint32_t qid = 1, ng = 1;
     uint32_t* const* outs[1] = {outs3};
     struct Cand { uint32_t t, e; };
-    const Cand cands[] = {{1024, 1}, {512, 1}, {512, 2}, {256, 2}, {512, 4}, {256, 4}, {128, 4}};
+    const Cand cands[] = {{1024, 1}, {768, 1}, {512, 1}, {512, 2}, {256, 2}, {512, 4}, {256, 4}, {128, 4}};
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);

@@ -99,7 +99,7 @@ struct oblivgm_ctx {
     void* h_stage = nullptr;
     std::map<uint32_t, ogm::Table> tables;
     std::map<uint32_t, ogm::OnehotTable> onehot_tables;
-    uint32_t threads = 512;          // the autotuner's usual pick on GB300 (256 x 4 spills)
+    uint32_t threads = 768;          // the autotuner's pick on GB300 (256 x 4 spills)
     uint32_t elems_per_thread = 1;
     std::atomic<uint64_t> launches{0};
     bool test_expire_next = false;      // failure-path test hook, one-shot

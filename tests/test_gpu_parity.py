@@ -139,7 +139,7 @@ def test_bulk_filter_ragged_full_parity(ctx, n_vertices):
     assert rec[wl["target"]] == 1
 
 
-SCHEDULES = [(1024, 1), (512, 1), (256, 2), (512, 2), (128, 4), (256, 4), (512, 4)]
+SCHEDULES = [(1024, 1), (768, 1), (512, 1), (256, 2), (512, 2), (128, 4), (256, 4), (512, 4)]
 
 
 def test_every_schedule_gives_identical_shares(ctx):
@@ -158,7 +158,7 @@ def test_every_schedule_gives_identical_shares(ctx):
                 assert np.array_equal(ref, want)
             assert np.array_equal(got, ref), (t, e)
     finally:
-        ctx.set_schedule(512, 1)
+        ctx.set_schedule(768, 1)
 
 
 def test_unaligned_outputs_and_tiny_tables(ctx):
@@ -179,7 +179,7 @@ def test_unaligned_outputs_and_tiny_tables(ctx):
                     got = np.stack([from_dev(t) for t in outs[grp]])
                     assert np.array_equal(got, oracle_group(oracle, wl, toks, 3, grp, np.arange(n))), sched
     finally:
-        ctx.set_schedule(512, 1)
+        ctx.set_schedule(768, 1)
 
 
 def test_empty_table_is_a_no_op(ctx):
