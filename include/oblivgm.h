@@ -360,13 +360,15 @@ oblivgm_status oblivgm_keygen_fresh(oblivgm_ctx* ctx, const oblivgm_pred* preds,
                                     const uint8_t seed[16], uint8_t* const tok[3], uint64_t cap, void* stream);
 
 /* The servers' secEval (Alg. 3, masked form of Eq. predEval, re-share, AND)
- * on fresh tokens.  tok[i]: device pointer to server i+1's token; the headers
- * are read back to the host to plan the launch.  out as in
- * oblivgm_filter_and_combine.  Asynchronous on stream apart from that
- * header read.  Errors: EINVAL (malformed or mismatched tokens, a predicate
- * whose N, attribute or n disagrees with the loaded table), ENOENT, ECUDA. */
+ * on fresh tokens.  tok[i]: device pointer to server i+1's token, tok_cap
+ * bytes readable at each (a token whose stated length exceeds tok_cap is
+ * rejected before any kernel reads it); the headers are read back to the
+ * host to plan the launch.  out as in oblivgm_filter_and_combine.
+ * Asynchronous on stream apart from that header read.  Errors: EINVAL
+ * (malformed, mismatched or truncated tokens, a predicate whose N, attribute
+ * or n disagrees with the loaded table), ENOENT, ECUDA. */
 oblivgm_status oblivgm_filter_fresh(oblivgm_ctx* ctx, uint32_t query_id, const uint8_t* const tok[3],
-                                    uint32_t n_groups, uint32_t* const* out, void* stream);
+                                    uint64_t tok_cap, uint32_t n_groups, uint32_t* const* out, void* stream);
 
 /* --------------------------------------------- secShuffle, secFetch case II */
 

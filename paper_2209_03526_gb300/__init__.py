@@ -256,7 +256,8 @@ class Context:
         ptrs = (N.c_vp * 3)(*[t.data_ptr() for t in toks])
         flat = [t.data_ptr() for g in outs for t in g]
         arr = (N.c_vp * len(flat))(*flat)
-        N.check(self._lib.oblivgm_filter_fresh(self._h, query_id, ptrs, len(outs), arr, _stream_handle(stream)),
+        cap = min(t.numel() * t.element_size() for t in toks)
+        N.check(self._lib.oblivgm_filter_fresh(self._h, query_id, ptrs, cap, len(outs), arr, _stream_handle(stream)),
                 "oblivgm_filter_fresh")
 
     def shuffle(self, ins, seeds: bytes, outs, group: int = 0, stream=None):

@@ -74,7 +74,7 @@ _SIGS = {
     "oblivgm_fresh_token_size": ([ctypes.POINTER(Pred), c_u32, c_u32, c_vp, c_u32, ctypes.POINTER(c_u64)], c_i32),
     "oblivgm_keygen_fresh": ([c_vp, ctypes.POINTER(Pred), c_u32, c_u32, c_vp, c_u32, c_u8p, ctypes.POINTER(c_vp),
                               c_u64, c_vp], c_i32),
-    "oblivgm_filter_fresh": ([c_vp, c_u32, ctypes.POINTER(c_vp), c_u32, ctypes.POINTER(c_vp), c_vp], c_i32),
+    "oblivgm_filter_fresh": ([c_vp, c_u32, ctypes.POINTER(c_vp), c_u64, c_u32, ctypes.POINTER(c_vp), c_vp], c_i32),
     "oblivgm_shuffle": ([c_vp, c_u32, c_u64, c_u32, ctypes.POINTER(c_vp), c_u8p, ctypes.POINTER(c_vp), c_vp], c_i32),
     "oblivgm_fetch_multi": ([c_vp, c_u32, ctypes.POINTER(c_vp), c_u32, c_vp, c_u8p, ctypes.POINTER(c_vp), c_u64,
                              ctypes.POINTER(c_u64), c_vp], c_i32),

@@ -495,7 +495,8 @@ extern "C" oblivgm_status oblivgm_keygen_fresh(oblivgm_ctx* ctx, const oblivgm_p
 }
 
 extern "C" oblivgm_status oblivgm_filter_fresh(oblivgm_ctx* ctx, uint32_t query_id, const uint8_t* const tok[3],
-                                               uint32_t n_groups, uint32_t* const* out, void* stream) {
+                                               uint64_t tok_cap, uint32_t n_groups, uint32_t* const* out,
+                                               void* stream) {
     const NvtxRange nvtx_range("oblivgm_filter_fresh");
     if (!ctx || !tok || !tok[0] || !tok[1] || !tok[2] || !out) return fail(OBLIVGM_EINVAL, "NULL argument");
     if (n_groups == 0 || n_groups > OBLIVGM_MAX_GROUPS) return fail(OBLIVGM_EINVAL, "n_groups must be 1..64");
@@ -504,6 +505,7 @@ extern "C" oblivgm_status oblivgm_filter_fresh(oblivgm_ctx* ctx, uint32_t query_
     cudaError_t ce = cudaSetDevice(ctx->device);
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaSetDevice");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (tok_cap < 64) return fail(OBLIVGM_EINVAL, "fresh token buffer shorter than a header");
     // read the three headers and descriptor tables back (ordered after work already on the stream)
     uint8_t h[3][64];
     for (int i = 0; i < 3; i++) {
@@ -523,6 +525,8 @@ extern "C" oblivgm_status oblivgm_filter_fresh(oblivgm_ctx* ctx, uint32_t query_
             return fail(OBLIVGM_EINVAL, "the three fresh tokens disagree");
     }
     if (n < 1 || n > 32 || np < 1 || np > (uint32_t)kFreshMaxPreds) return fail(OBLIVGM_EINVAL, "bad fresh token header");
+    if (get_u64(h[0] + 16) > tok_cap || 64 + 32 * (uint64_t)np > tok_cap)
+        return fail(OBLIVGM_EINVAL, "fresh token longer than its buffer");
     std::vector<uint8_t> desc(3 * 32 * (size_t)np);
     for (int i = 0; i < 3; i++) {
         ce = cudaMemcpyAsync(desc.data() + i * 32 * np, tok[i] + 64, 32 * np, cudaMemcpyDeviceToHost, s);

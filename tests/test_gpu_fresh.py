@@ -169,6 +169,10 @@ def test_gpu_fresh_rejects_bad_inputs(ctx):
     with pytest.raises(P.OblivgmError) as e:
         ctx.keygen_fresh(preds, bits, [1003, 517], SEED, [big[1:], toks[1], toks[2]])
     assert e.value.status == P.EINVAL
+    # a buffer shorter than the token says it is: rejected before any kernel reads it
+    with pytest.raises(P.OblivgmError) as e:
+        ctx.filter_fresh(1, [toks[0], toks[1][: L // 2], toks[2]], _outs([1003, 517]))
+    assert e.value.status == P.EINVAL
     # the context still works
     ctx.filter_fresh(2, toks, _outs([1003, 517]))
     ctx.sync()
