@@ -917,6 +917,7 @@ def run_workload(args):
         aes = sum(query_aes(q["preds"], table_n, n_bits) for q in queries)
         lookups = sum(query_lookups(q["preds"], table_n, n_bits) for q in queries)
         plan = ctx.plan_create(qids, toks, outs)
+        shape = ctx.plan_describe(plan)
         ms = _timed_graph(torch, ctx, plan, stream, args.warmup, args.steps)
         ctx.plan_destroy(plan)
         step_s = float(np.mean(ms)) / 1e3
@@ -928,7 +929,9 @@ def run_workload(args):
                      "warmup": args.warmup,
                      "config": {"workload": name, "queries": len(queries), "element_predicates_per_step": units,
                                 "aes_blocks_per_step": aes, "tables": {str(k): v for k, v in table_n.items()},
-                                "launch": "one persistent k_filter launch replayed from a CUDA graph"},
+                                "launch": f"one persistent {shape['kernel']} launch ({shape['grid']} CTAs x "
+                                          f"{shape['threads']} threads, {shape['items']} tiles of {shape['tile']} "
+                                          "elements) replayed from a CUDA graph"},
                      "roofline": {"bound": "alu", "achieved": lookups / step_s / 1e9, "peak": peak_lu,
                                   "unit": "Glookup/s", "frac": lookups / step_s / 1e9 / peak_lu,
                                   "aes_blocks_per_s": aes / step_s},

@@ -249,6 +249,13 @@ oblivgm_status oblivgm_plan_create(oblivgm_ctx* ctx, uint32_t n_queries, const u
 oblivgm_status oblivgm_plan_launch(oblivgm_plan* plan, void* stream);
 oblivgm_status oblivgm_plan_destroy(oblivgm_plan* plan);
 
+/* The launch a plan fixed: walk_parallel = 1 for the walk-parallel kernel
+ * (one thread per key walk), 0 for the per-element kernel; threads per CTA;
+ * elements per work item (tile); work items; CTAs launched (one per SM at
+ * most).  Any output pointer may be NULL.  Errors: EINVAL for a NULL plan. */
+oblivgm_status oblivgm_plan_describe(const oblivgm_plan* plan, uint32_t* walk_parallel, uint32_t* threads,
+                                     uint32_t* tile, uint64_t* n_items, uint32_t* grid);
+
 /* The plain per-query GPU path: the same computation and results as
  * oblivgm_filter_and_combine (Alg. 3 + Eq. predEval + re-share + AND), but
  * launched the straightforward way -- per predicate one mask-open launch, one
@@ -508,6 +515,17 @@ oblivgm_status oblivgm_serve_stats(oblivgm_ctx* ctx, uint64_t* admitted, uint64_
  * reported (and may be forced with oblivgm_set_schedule, 0 = keep). */
 oblivgm_status oblivgm_autotune(oblivgm_ctx* ctx, uint32_t* threads, uint32_t* elems_per_thread);
 oblivgm_status oblivgm_set_schedule(oblivgm_ctx* ctx, uint32_t threads, uint32_t elems_per_thread);
+
+/* Small batches (Alg. 3 over few elements): a batch whose AND-groups hold at
+ * most `max_elems` elements in all is evaluated by the walk-parallel kernel,
+ * one thread per key walk (six DPF or twelve DCF walks of an element side by
+ * side), instead of one thread per element.  Both kernels give identical
+ * output.  Default: 128 x the SM count; 0 turns the walk-parallel kernel off,
+ * UINT64_MAX uses it for every batch.  `previous` (may be NULL) receives the
+ * setting it replaces.  Applies to oblivgm_filter_and_combine,
+ * oblivgm_filter_batch, the no-alloc entry point, plans created afterwards and
+ * the serving loop.  Errors: EINVAL for a NULL context. */
+oblivgm_status oblivgm_set_walk_parallel(oblivgm_ctx* ctx, uint64_t max_elems, uint64_t* previous);
 
 /* Synchronise `stream` and report device-side faults recorded since the last
  * check: EFAULT_DEVICE if a bounded device wait (key staging) expired in a

@@ -332,6 +332,15 @@ class Context:
     def plan_launch(self, plan, stream=None):
         N.check(self._lib.oblivgm_plan_launch(plan, _stream_handle(stream)), "oblivgm_plan_launch")
 
+    def plan_describe(self, plan) -> dict:
+        """The launch a plan fixed (oblivgm_plan_describe)."""
+        wp, th, tile, grid = (ctypes.c_uint32() for _ in range(4))
+        items = ctypes.c_uint64()
+        N.check(self._lib.oblivgm_plan_describe(plan, ctypes.byref(wp), ctypes.byref(th), ctypes.byref(tile),
+                                                ctypes.byref(items), ctypes.byref(grid)), "oblivgm_plan_describe")
+        return {"kernel": "k_filter_wp" if wp.value else "k_filter", "threads": th.value, "tile": tile.value,
+                "items": items.value, "grid": grid.value}
+
     def plan_destroy(self, plan):
         N.check(self._lib.oblivgm_plan_destroy(plan), "oblivgm_plan_destroy")
 
@@ -402,6 +411,14 @@ class Context:
 
     def set_schedule(self, threads: int = 0, elems_per_thread: int = 0):
         N.check(self._lib.oblivgm_set_schedule(self._h, threads, elems_per_thread), "oblivgm_set_schedule")
+
+    def set_walk_parallel(self, max_elems: int) -> int:
+        """Batches of at most max_elems elements in all run the walk-parallel kernel (0: never,
+        2**64 - 1: always).  Returns the setting it replaces."""
+        prev = ctypes.c_uint64(0)
+        N.check(self._lib.oblivgm_set_walk_parallel(self._h, max_elems, ctypes.byref(prev)),
+                "oblivgm_set_walk_parallel")
+        return prev.value
 
 
 class _DeviceWords:

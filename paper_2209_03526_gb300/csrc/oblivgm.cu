@@ -369,6 +369,122 @@ using namespace ogm;
 
 namespace ogm {
 
+// ------------------------------------------------------------------ walk-parallel filter
+//
+// For queries too small to give every SM its own tiles: twelve threads per element, one
+// key walk each (the six DPF or twelve DCF keys of a predicate), so an element's walks
+// run side by side instead of one after another in one thread.  The keys are staged as
+// in k_filter; the walks' outputs meet in shared memory, and the element's first slot
+// thread sums them per server, re-shares and ANDs exactly as k_filter does.
+
+constexpr int kWpSlots = 12;                      // threads per element
+constexpr int kWpElems = 40;                      // elements per CTA (tile)
+constexpr int kWpThreads = kWpSlots * kWpElems;   // 480
+constexpr int kWpSmem = kFilterSmem + kWpElems * kWpSlots * 4;
+// default switch-over: batches of at most this many elements per SM in all
+constexpr uint64_t kWpDefaultElemsPerSm = 128;
+
+__global__ void __launch_bounds__(kWpThreads, 1) k_filter_wp(const __grid_constant__ FilterParams P) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const SmemTab T{reinterpret_cast<const char*>(smem), lane_offset()};
+    DevKey* kbuf = reinterpret_cast<DevKey*>(smem + kTableBytes);
+    uint32_t* part = reinterpret_cast<uint32_t*>(smem + kFilterSmem);   // [element][slot]
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ unsigned long long item_sh;
+
+    fill_tables(reinterpret_cast<uint32_t*>(smem), P.te0);
+    if (threadIdx.x == 0) mbar_init(&mbar);
+    __syncthreads();
+
+    const uint32_t el = threadIdx.x / kWpSlots, slot = threadIdx.x % kWpSlots;
+    uint32_t phase = 0;
+    const uint64_t n_items = P.item_start[P.n_groups];
+    for (;;) {
+        if (threadIdx.x == 0) item_sh = atomicAdd(P.counter, 1ull);
+        __syncthreads();
+        const uint64_t item = item_sh;
+        if (item >= n_items) break;
+        int lo = 0, hi = (int)P.n_groups - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (P.item_start[mid] <= item) lo = mid; else hi = mid - 1;
+        }
+        const GroupDesc& G = P.groups[lo];
+        const uint64_t e = (item - P.item_start[lo]) * P.tile + el;
+        const uint64_t n_elems = G.n_elems;
+        const bool valid = el < P.tile && e < n_elems;
+        const uint32_t table = G.table_id, query = G.query_id;
+        uint32_t acc[3][1] = {{0}, {0}, {0}};
+        for (uint32_t k = 0; k < G.n_preds; k++) {
+            const PredDesc& D = P.preds[G.pred_begin + k];
+            __syncthreads();   // everyone is done with the previous predicate's keys
+            if (threadIdx.x == 0) {
+                const uint32_t bytes = D.n_keys * (uint32_t)sizeof(DevKey);
+                mbar_expect_tx(&mbar, bytes + P.expect_extra);
+                bulk_g2s(kbuf, P.keys + D.key_begin, bytes, &mbar);
+            }
+            const bool ok = mbar_wait_bounded(&mbar, phase, P.wait_limit_ns);
+            phase ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) atomicOr(P.error, kErrKeyWait);
+                mbar_wait_bounded(&mbar, phase ^ 1u, P.wait_limit_ns);   // let an in-flight copy land
+                return;
+            }
+            const bool eq = D.kind == OBLIVGM_PRED_EQ;
+            const uint32_t nsub = eq ? 1u : 2u;
+            uint32_t y[1] = {0};
+            if (valid && slot < 6 * nsub) {
+                const uint32_t mask = D.n_bits >= 32 ? 0xFFFFFFFFu : ((1u << D.n_bits) - 1u);
+                const uint64_t row = (uint64_t)D.attr * G.stride;
+                uint32_t xh[1] = {D.r[0] + D.r[1] + D.r[2]};
+#pragma unroll
+                for (int j = 0; j < 3; j++) xh[0] += __ldg(G.share[j] + row + e);
+                xh[0] &= mask;
+                const DevKey& K = kbuf[slot];
+                if (eq) dpf_walk<1>(T, P.aes, K, xh, y);
+                else dcf_walk<1>(T, P.aes, K, xh, y);
+                // RANGE: the public constant c * beta' joins party 0's half once
+                if (!eq && (slot % nsub) == 0 && K.party == 0) y[0] += D.cbeta;
+            }
+            part[el * kWpSlots + slot] = y[0];
+            __syncthreads();
+            if (slot == 0 && valid) {
+                // keys are ordered [server i][half h][sub s]: server i owns slots [2 nsub i, 2 nsub (i + 1))
+                uint32_t z[3][1] = {{0}, {0}, {0}};
+                for (uint32_t kk = 0; kk < 6 * nsub; kk++) {
+                    const uint32_t v = part[el * kWpSlots + kk], i = kk / (2 * nsub);
+                    z[0][0] += i == 0 ? v : 0u;
+                    z[1][0] += i == 1 ? v : 0u;
+                    z[2][0] += i == 2 ? v : 0u;
+                }
+                uint32_t step = D.step;
+                const int passes = k == 0 ? 1 : 2;
+#pragma unroll 1
+                for (int pass = 0; pass < passes; pass++) {
+                    uint32_t r[3][1];
+                    reshare<1>(T, P.rk_prf, z, r, e, step, table, query);
+                    if (pass + 1 < passes) {
+#pragma unroll
+                        for (int i = 0; i < 3; i++) {
+                            const int i1 = (i + 1) % 3;
+                            z[i][0] = acc[i][0] * r[i][0] + acc[i][0] * r[i1][0] + acc[i1][0] * r[i][0];
+                        }
+                        step = 64u + D.step;
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 3; i++) acc[i][0] = r[i][0];
+                    }
+                }
+            }
+        }
+        if (slot == 0 && valid) {
+#pragma unroll
+            for (int i = 0; i < 3; i++) G.out[i][e] = acc[i][0];
+        }
+        __syncthreads();
+    }
+}
+
 void build_aes_params(AesParams* a) {
     const RoundKeys &L = fixed_key(0), &R = fixed_key(1), &VL = fixed_key(2), &VR = fixed_key(3);
     for (int i = 0; i < 44; i++) {
@@ -390,6 +506,7 @@ static oblivgm_status check_ctx(oblivgm_ctx* ctx) {
 // cost, most expensive first) into one contiguous host image.
 struct Plan {
     uint32_t tile = 0, elems_per_thread = 1, threads = 0;
+    bool wp = false;   // walk-parallel kernel (k_filter_wp)
     std::vector<GroupDesc> groups;
     std::vector<PredDesc> preds;
     std::vector<DevKey> keys;
@@ -399,46 +516,63 @@ struct Plan {
 // Element tile per work item.  The items (group, tile) are taken by one persistent CTA
 // per SM in cost order; a tile width that leaves the last wave half empty wastes the
 // idle SMs' time, and a query too small to give every SM a full-width tile leaves SMs
-// idle altogether, so widths from max_tile down to one warp's worth of elements
-// (step_elems) are tried by simulating that greedy schedule, and the width with the
-// shortest makespan wins (the widest on ties).  An item's time is modelled as its cost
-// times its element count, but never less than for kLatencyFloorElems elements: below
-// about two warps per SM the walks' own latency, not the shared-memory pipe, sets the
-// time.  Large item counts skip the search: their tail is already a small fraction.
-template <typename NF, typename CF>
-uint32_t choose_tile(size_t n_groups, NF n_elems_of, CF cost_of, uint32_t max_tile, uint32_t step_elems, int sm_count) {
+// idle altogether, so widths from max_tile down to `step` are tried by simulating that
+// greedy schedule, with item_time(group, width) as an item's time, and the width with
+// the shortest makespan wins (the widest on ties).  Large item counts skip the search:
+// their tail is already a small fraction.
+template <typename NF, typename TF>
+uint32_t choose_tile(size_t n_groups, NF n_elems_of, TF item_time, uint32_t max_tile, uint32_t step, int sm_count) {
     uint64_t items_at_max = 0;
     for (size_t g = 0; g < n_groups; g++) items_at_max += (n_elems_of(g) + max_tile - 1) / max_tile;
-    if (items_at_max == 0 || items_at_max > 64ull * (uint64_t)sm_count || step_elems == 0) return max_tile;
-    constexpr uint64_t kLatencyFloorElems = 64;
+    if (items_at_max == 0 || items_at_max > 64ull * (uint64_t)sm_count || step == 0) return max_tile;
     uint32_t best_tile = max_tile;
     double best = -1.0;
     std::vector<double> finish;
-    const uint32_t min_tile = step_elems;
-    for (uint32_t t = max_tile; t >= min_tile; t -= step_elems) {
+    for (uint32_t t = max_tile; t >= step; t -= step) {
         finish.assign((size_t)sm_count, 0.0);
         std::make_heap(finish.begin(), finish.end(), std::greater<double>());
         for (size_t g = 0; g < n_groups; g++) {
             const uint64_t n = n_elems_of(g);
             for (uint64_t e = 0; e < n; e += t) {
-                const uint64_t width = std::min<uint64_t>(t, n - e);
-                const uint64_t warps_elems = std::max<uint64_t>((width + 31) / 32 * 32, kLatencyFloorElems);
                 std::pop_heap(finish.begin(), finish.end(), std::greater<double>());
-                finish.back() += (double)cost_of(g) * (double)warps_elems;
+                finish.back() += item_time(g, std::min<uint64_t>(t, n - e));
                 std::push_heap(finish.begin(), finish.end(), std::greater<double>());
             }
         }
         const double makespan = *std::max_element(finish.begin(), finish.end());
         if (best < 0 || makespan < best * (1.0 - 1e-9)) { best = makespan; best_tile = t; }
-        if (t == min_tile) break;
+        if (t < 2 * step) break;
     }
     return best_tile;
 }
 
+// Item-time models (arbitrary units; only their ratios matter).
+//  k_filter: one thread per element, so the time follows the cost of the group's walks
+//  times the width rounded up to whole warps, but never less than for 64 elements: below
+//  about two warps per SM the walks' own latency, not the shared-memory pipe, sets it.
+//  k_filter_wp: one thread per walk; per predicate of n bits a fixed latency of its walk
+//  chain (about 0.55 n us for EQ, 0.97 n us for RANGE on GB300) plus, beyond 10 elements,
+//  a per-element term (31 n / 62 n ns: an EQ predicate leaves half of an element's twelve
+//  threads idle).  Fitted to single-predicate sweeps of widths 1..40 at n = 32.
+struct GroupCost {
+    uint64_t walk_cost = 0;            // k_filter: sum over predicates of 6 n (EQ) / 24 n (RANGE)
+    uint64_t wp_lat = 0, wp_slope = 0; // k_filter_wp: latency and per-element terms, ns
+};
+constexpr uint64_t kWpKnee = 10;
+
+double filter_item_time(const GroupCost& c, uint64_t width) {
+    const uint64_t busy = std::max<uint64_t>((width + 31) / 32 * 32, 64);
+    return (double)c.walk_cost * (double)busy;
+}
+
+double wp_item_time(const GroupCost& c, uint64_t width) {
+    return (double)c.wp_lat + (double)c.wp_slope * (double)(width > kWpKnee ? width - kWpKnee : 0);
+}
+
 oblivgm_status plan_queries(const std::map<uint32_t, Table>& tables, uint32_t n_queries, const uint32_t* query_ids,
                             const ParsedQuery* parsed, const uint32_t* n_groups, uint32_t* const* const* outs,
-                            uint32_t tile, uint32_t step_elems, int sm_count, Plan* plan) {
-    struct G { GroupDesc d; std::vector<const ParsedPred*> preds; uint64_t cost; };
+                            uint32_t tile, uint32_t step, bool wp, int sm_count, Plan* plan) {
+    struct G { GroupDesc d; std::vector<const ParsedPred*> preds; GroupCost cost; };
     std::vector<G> all;
     for (uint32_t q = 0; q < n_queries; q++) {
         const ParsedQuery& pq = parsed[q];
@@ -456,12 +590,15 @@ oblivgm_status plan_queries(const std::map<uint32_t, Table>& tables, uint32_t n_
             auto it = tables.find(tid);
             if (it == tables.end()) return fail(OBLIVGM_ENOENT, "predicate on a table that is not loaded");
             const Table& tb = it->second;
-            uint64_t cost = 0;
+            GroupCost cost;
             for (const ParsedPred* p : members[g]) {
                 if (p->table != tid) return fail(OBLIVGM_EINVAL, "an AND-group spans two tables");
                 if (p->attr >= tb.n_attrs) return fail(OBLIVGM_EINVAL, "predicate attribute outside its table");
                 if (p->n != tb.n_bits) return fail(OBLIVGM_EINVAL, "predicate bit length differs from its table's");
-                cost += p->kind == OBLIVGM_PRED_EQ ? 6ull * p->n : 24ull * p->n;
+                const bool eq = p->kind == OBLIVGM_PRED_EQ;
+                cost.walk_cost += (eq ? 6ull : 24ull) * p->n;
+                cost.wp_lat += (eq ? 550ull : 970ull) * p->n;
+                cost.wp_slope += (eq ? 31ull : 62ull) * p->n;
             }
             G gr{};
             for (int j = 0; j < 3; j++) {
@@ -481,9 +618,11 @@ oblivgm_status plan_queries(const std::map<uint32_t, Table>& tables, uint32_t n_
             all.push_back(std::move(gr));
         }
     }
-    std::stable_sort(all.begin(), all.end(), [](const G& a, const G& b) { return a.cost > b.cost; });
-    tile = choose_tile(all.size(), [&](size_t i) { return all[i].d.n_elems; }, [&](size_t i) { return all[i].cost; },
-                       tile, step_elems, sm_count);
+    std::stable_sort(all.begin(), all.end(), [](const G& a, const G& b) { return a.cost.walk_cost > b.cost.walk_cost; });
+    tile = choose_tile(
+        all.size(), [&](size_t i) { return all[i].d.n_elems; },
+        [&](size_t i, uint64_t w) { return wp ? wp_item_time(all[i].cost, w) : filter_item_time(all[i].cost, w); },
+        tile, step, sm_count);
     plan->groups.clear(); plan->preds.clear(); plan->keys.clear(); plan->item_start.clear();
     plan->tile = tile;
     uint64_t items = 0;
@@ -506,6 +645,46 @@ oblivgm_status plan_queries(const std::map<uint32_t, Table>& tables, uint32_t n_
     }
     plan->item_start.push_back(items);
     return OBLIVGM_OK;
+}
+
+// Plan a batch for the fused kernel in the context's launch shape; a batch whose groups
+// hold at most ctx->wp_max_elems elements in all goes to the walk-parallel kernel instead,
+// in tiles of kWpElems elements.
+oblivgm_status plan_filter(oblivgm_ctx* ctx, const std::map<uint32_t, Table>& tables, uint32_t n_queries,
+                           const uint32_t* query_ids, const ParsedQuery* parsed, const uint32_t* n_groups,
+                           uint32_t* const* const* outs, Plan* plan) {
+    const uint32_t threads = ctx->threads, E = ctx->elems_per_thread;
+    plan->elems_per_thread = E;
+    plan->threads = threads;
+    plan->wp = false;
+    oblivgm_status s = plan_queries(tables, n_queries, query_ids, parsed, n_groups, outs, threads * E, 32 * E,
+                                    false, ctx->sm_count, plan);
+    if (s != OBLIVGM_OK) return s;
+    uint64_t total = 0;
+    for (const GroupDesc& g : plan->groups) total += g.n_elems;
+    if (total == 0 || total > ctx->wp_max_elems) return OBLIVGM_OK;
+    s = plan_queries(tables, n_queries, query_ids, parsed, n_groups, outs, kWpElems, 1, true, ctx->sm_count, plan);
+    if (s != OBLIVGM_OK) return s;
+    plan->wp = true;
+    plan->threads = kWpThreads;
+    plan->elems_per_thread = 1;
+    return OBLIVGM_OK;
+}
+
+// One launch of the planned kernel: grid = min(work items, SMs), one persistent CTA per SM.
+cudaError_t launch_filter_kernel(const FilterParams& P, uint64_t n_items, int sm_count, uint32_t threads, uint32_t E,
+                                 bool wp, cudaStream_t st) {
+    const unsigned grid = (unsigned)std::min<uint64_t>(n_items, (uint64_t)sm_count);
+    if (wp) {
+        k_filter_wp<<<grid, kWpThreads, kWpSmem, st>>>(P);
+    } else {
+        switch (E) {
+            case 1: k_filter<1><<<grid, threads, kFilterSmem, st>>>(P); break;
+            case 2: k_filter<2><<<grid, threads, kFilterSmem, st>>>(P); break;
+            default: k_filter<4><<<grid, threads, kFilterSmem, st>>>(P); break;
+        }
+    }
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -546,16 +725,8 @@ oblivgm_status launch_plan(oblivgm_ctx* ctx, const Plan& plan, cudaStream_t st, 
         P.wait_limit_ns = ctx->test_wait_limit_ns;
         ctx->test_expire_next = false;
     }
-    const uint64_t n_items = plan.item_start.back();
-    const unsigned grid = (unsigned)std::min<uint64_t>(n_items, (uint64_t)ctx->sm_count);
-    const uint32_t E = plan.elems_per_thread, threads = plan.threads;
-    cudaError_t e = cudaSuccess;
-    switch (E) {
-        case 1: k_filter<1><<<grid, threads, kFilterSmem, st>>>(P); break;
-        case 2: k_filter<2><<<grid, threads, kFilterSmem, st>>>(P); break;
-        default: k_filter<4><<<grid, threads, kFilterSmem, st>>>(P); break;
-    }
-    e = cudaGetLastError();
+    const cudaError_t e = launch_filter_kernel(P, plan.item_start.back(), ctx->sm_count, plan.threads,
+                                               plan.elems_per_thread, plan.wp, st);
     if (e != cudaSuccess) return cuda_fail(e, "k_filter launch");
     ctx->launches++;
     OGM_CUDA(cudaFreeAsync(ws, st), "workspace release");
@@ -566,11 +737,7 @@ oblivgm_status launch_parsed(oblivgm_ctx* ctx, uint32_t n_queries, const uint32_
                              const ParsedQuery* parsed, const uint32_t* n_groups, uint32_t* const* const* outs,
                              const std::map<uint32_t, Table>& tables, cudaStream_t st) {
     Plan plan;
-    const uint32_t threads = ctx->threads, E = ctx->elems_per_thread;
-    plan.elems_per_thread = E;
-    plan.threads = threads;
-    oblivgm_status s = plan_queries(tables, n_queries, query_ids, parsed, n_groups, outs, threads * E, 32 * E,
-                                    ctx->sm_count, &plan);
+    oblivgm_status s = plan_filter(ctx, tables, n_queries, query_ids, parsed, n_groups, outs, &plan);
     if (s != OBLIVGM_OK) return s;
     return launch_plan(ctx, plan, st, ctx->d_error);
 }
@@ -579,6 +746,7 @@ oblivgm_status set_filter_attrs() {
     OGM_CUDA(cudaFuncSetAttribute(k_filter<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFilterSmem), "smem attr");
     OGM_CUDA(cudaFuncSetAttribute(k_filter<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFilterSmem), "smem attr");
     OGM_CUDA(cudaFuncSetAttribute(k_filter<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFilterSmem), "smem attr");
+    OGM_CUDA(cudaFuncSetAttribute(k_filter_wp, cudaFuncAttributeMaxDynamicSharedMemorySize, kWpSmem), "smem attr");
     OGM_CUDA(cudaFuncSetAttribute(k_eval_raw<OBLIVGM_KEY_DPF>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTableBytes), "smem attr");
     OGM_CUDA(cudaFuncSetAttribute(k_eval_raw<OBLIVGM_KEY_DCF>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTableBytes), "smem attr");
     return OBLIVGM_OK;
@@ -613,6 +781,7 @@ oblivgm_status oblivgm_create(oblivgm_ctx** out, int32_t device, const oblivgm_c
     if (!ctx) return fail(OBLIVGM_ENOMEM, "host allocation");
     ctx->device = device;
     ctx->sm_count = prop.multiProcessorCount;
+    ctx->wp_max_elems = (uint64_t)ctx->sm_count * kWpDefaultElemsPerSm;
     build_aes_params(&ctx->aes);
     for (int i = 0; i < 3; i++) {
         const RoundKeys rk = expand_key(cfg->prf_keys[i]);
@@ -955,6 +1124,14 @@ oblivgm_status oblivgm_set_schedule(oblivgm_ctx* ctx, uint32_t threads, uint32_t
     return OBLIVGM_OK;
 }
 
+oblivgm_status oblivgm_set_walk_parallel(oblivgm_ctx* ctx, uint64_t max_elems, uint64_t* previous) {
+    oblivgm_status st = check_ctx(ctx);
+    if (st) return st;
+    if (previous) *previous = ctx->wp_max_elems;
+    ctx->wp_max_elems = max_elems;
+    return OBLIVGM_OK;
+}
+
 }  // extern "C"
 
 // ====================================================================== no-allocation variant
@@ -1008,10 +1185,7 @@ extern "C" oblivgm_status oblivgm_filter_and_combine_noalloc(oblivgm_ctx* ctx, u
     if (st != OBLIVGM_OK) return fail(st, err);
     uint32_t* const* outs[1] = {out};
     Plan plan;
-    plan.elems_per_thread = ctx->elems_per_thread;
-    plan.threads = ctx->threads;
-    st = plan_queries(ctx->tables, 1, &query_id, &parsed, &n_groups, outs, ctx->threads * ctx->elems_per_thread,
-                      32 * ctx->elems_per_thread, ctx->sm_count, &plan);
+    st = plan_filter(ctx, ctx->tables, 1, &query_id, &parsed, &n_groups, outs, &plan);
     if (st != OBLIVGM_OK) return st;
     if (plan.item_start.back() == 0) return OBLIVGM_OK;
     // workspace image: counter (zeroed every call) | groups | preds | keys | tile offsets
@@ -1046,15 +1220,8 @@ extern "C" oblivgm_status oblivgm_filter_and_combine_noalloc(oblivgm_ctx* ctx, u
     P.n_groups = (uint32_t)plan.groups.size();
     P.tile = plan.tile;
     P.wait_limit_ns = kWaitLimitNs;
-    const uint64_t n_items = plan.item_start.back();
-    const unsigned grid = (unsigned)std::min<uint64_t>(n_items, (uint64_t)ctx->sm_count);
-    const uint32_t E = plan.elems_per_thread, threads = plan.threads;
-    switch (E) {
-        case 1: k_filter<1><<<grid, threads, kFilterSmem, s>>>(P); break;
-        case 2: k_filter<2><<<grid, threads, kFilterSmem, s>>>(P); break;
-        default: k_filter<4><<<grid, threads, kFilterSmem, s>>>(P); break;
-    }
-    cudaError_t e = cudaGetLastError();
+    const cudaError_t e = launch_filter_kernel(P, plan.item_start.back(), ctx->sm_count, plan.threads,
+                                               plan.elems_per_thread, plan.wp, s);
     if (e != cudaSuccess) return cuda_fail(e, "k_filter launch (no-alloc)");
     ctx->launches++;
     return OBLIVGM_OK;
@@ -1071,8 +1238,8 @@ struct oblivgm_plan {
     oblivgm_ctx* ctx = nullptr;
     unsigned char* ws = nullptr;
     FilterParams params{};
-    unsigned grid = 0;
     uint32_t threads = 0, E = 1;
+    bool wp = false;
     uint64_t n_items = 0;
 };
 
@@ -1093,10 +1260,7 @@ extern "C" oblivgm_status oblivgm_plan_create(oblivgm_ctx* ctx, uint32_t n_queri
         if (st != OBLIVGM_OK) return fail(st, err);
     }
     Plan plan;
-    plan.elems_per_thread = ctx->elems_per_thread;
-    plan.threads = ctx->threads;
-    st = plan_queries(ctx->tables, n_queries, query_ids, parsed.data(), n_groups, outs,
-                      ctx->threads * ctx->elems_per_thread, 32 * ctx->elems_per_thread, ctx->sm_count, &plan);
+    st = plan_filter(ctx, ctx->tables, n_queries, query_ids, parsed.data(), n_groups, outs, &plan);
     if (st != OBLIVGM_OK) return st;
     const size_t off_groups = 256;
     const size_t off_preds = off_groups + (plan.groups.size() * sizeof(GroupDesc) + 255) / 256 * 256;
@@ -1132,9 +1296,9 @@ extern "C" oblivgm_status oblivgm_plan_create(oblivgm_ctx* ctx, uint32_t n_queri
     P.tile = plan.tile;
     P.wait_limit_ns = kWaitLimitNs;
     p->n_items = plan.item_start.back();
-    p->grid = (unsigned)std::min<uint64_t>(p->n_items, (uint64_t)ctx->sm_count);
     p->threads = plan.threads;
     p->E = plan.elems_per_thread;
+    p->wp = plan.wp;
     *out_plan = p;
     return OBLIVGM_OK;
 }
@@ -1145,14 +1309,20 @@ extern "C" oblivgm_status oblivgm_plan_launch(oblivgm_plan* p, void* stream) {
     if (p->n_items == 0) return OBLIVGM_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     OGM_CUDA(cudaMemsetAsync(p->ws, 0, sizeof(unsigned long long), s), "plan counter reset");
-    switch (p->E) {
-        case 1: k_filter<1><<<p->grid, p->threads, kFilterSmem, s>>>(p->params); break;
-        case 2: k_filter<2><<<p->grid, p->threads, kFilterSmem, s>>>(p->params); break;
-        default: k_filter<4><<<p->grid, p->threads, kFilterSmem, s>>>(p->params); break;
-    }
-    cudaError_t e = cudaGetLastError();
+    const cudaError_t e = launch_filter_kernel(p->params, p->n_items, p->ctx->sm_count, p->threads, p->E, p->wp, s);
     if (e != cudaSuccess) return cuda_fail(e, "k_filter launch (plan)");
     p->ctx->launches++;
+    return OBLIVGM_OK;
+}
+
+extern "C" oblivgm_status oblivgm_plan_describe(const oblivgm_plan* p, uint32_t* walk_parallel, uint32_t* threads,
+                                                uint32_t* tile, uint64_t* n_items, uint32_t* grid) {
+    if (!p) return fail(OBLIVGM_EINVAL, "NULL plan");
+    if (walk_parallel) *walk_parallel = p->wp ? 1u : 0u;
+    if (threads) *threads = p->threads;
+    if (tile) *tile = p->params.tile;
+    if (n_items) *n_items = p->n_items;
+    if (grid) *grid = (uint32_t)std::min<uint64_t>(p->n_items, (uint64_t)p->ctx->sm_count);
     return OBLIVGM_OK;
 }
 

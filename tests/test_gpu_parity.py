@@ -148,6 +148,7 @@ def test_every_schedule_gives_identical_shares(ctx):
     load_tables(ctx, wl)
     toks = P.keygen(wl["preds"], 32, bytes(16))
     ref = None
+    prev = ctx.set_walk_parallel(0)   # the per-element kernel in every launch shape
     try:
         for t, e in SCHEDULES:
             ctx.set_schedule(t, e)
@@ -159,6 +160,7 @@ def test_every_schedule_gives_identical_shares(ctx):
             assert np.array_equal(got, ref), (t, e)
     finally:
         ctx.set_schedule(768, 1)
+        ctx.set_walk_parallel(prev)
 
 
 def test_unaligned_outputs_and_tiny_tables(ctx):
@@ -168,9 +170,12 @@ def test_unaligned_outputs_and_tiny_tables(ctx):
                    W.eq_pred(1, 0, 1, int(wl["tables"][1]["values"][0, 6]))]
     load_tables(ctx, wl)
     toks = P.keygen(wl["preds"], 32, bytes(range(16)))
+    prev = ctx.set_walk_parallel(0)
     try:
-        for sched in ((512, 1), (256, 4), (256, 2)):          # scalar, uint4 and uint2 output stores
+        # scalar, uint4 and uint2 stores of the per-element kernel, then the walk-parallel kernel
+        for sched, wp in (((512, 1), 0), ((256, 4), 0), ((256, 2), 0), ((768, 1), ALWAYS)):
             ctx.set_schedule(*sched)
+            ctx.set_walk_parallel(wp)
             for offset in (0, 1):
                 outs = alloc_outs(wl, offset=offset)
                 ctx.filter_and_combine(3, toks, outs)
@@ -180,6 +185,58 @@ def test_unaligned_outputs_and_tiny_tables(ctx):
                     assert np.array_equal(got, oracle_group(oracle, wl, toks, 3, grp, np.arange(n))), sched
     finally:
         ctx.set_schedule(768, 1)
+        ctx.set_walk_parallel(prev)
+
+
+ALWAYS = (1 << 64) - 1
+
+
+def test_walk_parallel_kernel_equals_oracle(ctx):
+    """The walk-parallel kernel (one thread per key walk, 40-element tiles) gives the
+    oracle's shares: the tiny path query (EQ + RANGE ANDs, two tables), a bulk filter of
+    4,099 elements (102 full tiles and a ragged one; EQ and RANGE over n = 32), and a
+    batch of queries; the default switch-over picks it for the tiny query and the
+    per-element kernel for the large one, with the same shares either way."""
+    wl = W.tiny_path(seed=1)
+    load_tables(ctx, wl)
+    toks = P.keygen(wl["preds"], wl["n_bits"], bytes(range(16)))
+    want = [oracle_group(oracle, wl, toks, 11, 0, np.arange(1000)),
+            oracle_group(oracle, wl, toks, 11, 1, np.arange(4000))]
+    prev = ctx.set_walk_parallel(ALWAYS)
+    try:
+        ctx.set_walk_parallel(prev)
+        outs = alloc_outs(wl)
+        plan = ctx.plan_create([11], [toks], [outs])      # 5,000 elements: under the default switch-over
+        assert ctx.plan_describe(plan)["kernel"] == "k_filter_wp"
+        ctx.plan_destroy(plan)
+        for wp in (ALWAYS, 0, prev):
+            ctx.set_walk_parallel(wp)
+            got = _filter(ctx, wl, toks, 11)
+            assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1]), wp
+        bulk = W.bulk_vertex_filter(n_vertices=4099, seed=13)
+        load_tables(ctx, bulk)
+        btoks = P.keygen(bulk["preds"], 32, bytes(range(5, 21)))
+        ctx.set_walk_parallel(ALWAYS)
+        got = _filter(ctx, bulk, btoks, 6)[0]
+        assert np.array_equal(got, oracle_group(oracle, bulk, btoks, 6, 0, np.arange(4099), threads=16))
+        ctx.set_walk_parallel(0)
+        assert np.array_equal(_filter(ctx, bulk, btoks, 6)[0], got)
+        graph = W.edge_graph(700, 3000, 4, 2, seed=71)
+        load_tables(ctx, graph)
+        qs = W.query_mix(graph, 4, seed=72)
+        qtoks = [P.keygen(q["preds"], 32, bytes([i + 3]) * 16) for i, q in enumerate(qs)]
+        res = {}
+        for wp in (ALWAYS, 0):
+            ctx.set_walk_parallel(wp)
+            outs = [alloc_outs(graph, preds=q["preds"]) for q in qs]
+            ctx.filter_batch(list(range(40, 44)), qtoks, outs)
+            ctx.sync()
+            res[wp] = [[np.stack([from_dev(t) for t in grp]) for grp in q] for q in outs]
+        for qa, qb in zip(res[ALWAYS], res[0]):
+            for a, b in zip(qa, qb):
+                assert np.array_equal(a, b)
+    finally:
+        ctx.set_walk_parallel(prev)
 
 
 def test_empty_table_is_a_no_op(ctx):
@@ -281,9 +338,18 @@ def test_plain_path_equals_fused_and_oracle(ctx):
     assert np.array_equal(got, oracle_group(oracle, bulk, toks, 22, 0, np.arange(2053), threads=16))
 
 
-def test_prepared_plan_and_cuda_graph_replay(ctx):
+@pytest.mark.parametrize("walk_parallel", [False, True])
+def test_prepared_plan_and_cuda_graph_replay(ctx, walk_parallel):
     """A prepared batch launched directly, then captured into a CUDA graph and replayed twice,
-    gives the shares of filter_batch for the same queries."""
+    gives the shares of filter_batch for the same queries (per-element and walk-parallel plans)."""
+    prev = ctx.set_walk_parallel((1 << 64) - 1 if walk_parallel else 0)
+    try:
+        _plan_and_graph(ctx, walk_parallel)
+    finally:
+        ctx.set_walk_parallel(prev)
+
+
+def _plan_and_graph(ctx, walk_parallel):
     graph = W.edge_graph(6000, 20000, 4, 2, seed=61)
     load_tables(ctx, graph)
     qs = W.query_mix(graph, 5, seed=62)
@@ -306,6 +372,9 @@ def test_prepared_plan_and_cuda_graph_replay(ctx):
 
     plan = ctx.plan_create(qids, toks, got)
     try:
+        d = ctx.plan_describe(plan)
+        assert d["kernel"] == ("k_filter_wp" if walk_parallel else "k_filter")
+        assert d["tile"] <= (40 if walk_parallel else d["threads"]) and 0 < d["grid"] <= d["items"]
         s = torch.cuda.Stream()
         ctx.plan_launch(plan, s)
         s.synchronize()
