@@ -7,7 +7,7 @@
  * compute in secEval (Alg. 3): every predicate of a query on every element
  * (vertex or edge) of a resident, secret-shared table, by DPF Eval (equality)
  * or DCF Eval (range) over masked attribute values, followed by the re-share
- * of Sec. III-B and the AND aggregation of Sec. V-D.  The three servers are
+ * of Sec. III-B and the aggregation of Sec. V-D.  The three servers are
  * simulated as three share sets in one address space; "sending" a share is a
  * read of another share set.
  *
@@ -52,6 +52,19 @@ typedef int32_t oblivgm_status;
 #define OBLIVGM_PRED_EQ    1u
 #define OBLIVGM_PRED_RANGE 2u
 
+/* How a predicate's result joins its group's result (Sec. V-D, aggregation of
+ * several predicates of one target vertex): the group's predicates are folded
+ * left to right in list order, acc <- acc OP x_p, each step an RSS product
+ * (Sec. III-B) plus local linear terms, then a re-share.  Over 0/1 values:
+ *   AND  acc * x                 (all predicates hold; the paper's product)
+ *   XOR  acc + x - 2 acc x       (the paper's "one of", written with XOR)
+ *   OR   acc + x - acc x         (at least one holds)
+ * In the one-hot mode (shares over Z_2) the same three are a b, a ^ b and
+ * a ^ b ^ a b.  A group's first predicate must carry AND (0). */
+#define OBLIVGM_COMBINE_AND 0u
+#define OBLIVGM_COMBINE_XOR 1u
+#define OBLIVGM_COMBINE_OR  2u
+
 /* key kinds in the key wire format */
 #define OBLIVGM_KEY_DPF 1u
 #define OBLIVGM_KEY_DCF 2u
@@ -83,13 +96,16 @@ typedef struct {
     uint32_t kind;    /* OBLIVGM_PRED_EQ or OBLIVGM_PRED_RANGE                      */
     uint32_t table;   /* id of the element table the predicate reads (< 65536)      */
     uint32_t attr;    /* attribute row within that table (< 65536)                  */
-    uint32_t group;   /* AND-group of the query: all predicates of a group are on
-                         the same table and their results are ANDed (Sec. V-D)     */
+    uint32_t group;   /* group of the query: all predicates of a group are on the
+                         same table and their results are folded into one 0/1
+                         result per element (Sec. V-D)                              */
     uint32_t lo;      /* EQ: the value alpha; RANGE: inclusive lower bound          */
     uint32_t hi;      /* RANGE: inclusive upper bound (lo <= hi); ignored for EQ    */
+    uint32_t combine; /* OBLIVGM_COMBINE_*: how this result joins the group's result
+                         so far; AND (0) for a group's first predicate              */
 } oblivgm_pred;
 
-/* Result of a served query: per AND-group g, three device arrays of n_elems[g]
+/* Result of a served query: per group g, three device arrays of n_elems[g]
  * uint32 each, the RSS share sets 1..3 of the group's 0/1 result.  The memory
  * belongs to the library until oblivgm_release(). */
 #define OBLIVGM_MAX_GROUPS 64
@@ -158,14 +174,16 @@ oblivgm_status oblivgm_unload_shares(oblivgm_ctx* ctx, uint32_t table_id);
  *     u8 0, u16 n_preds, u16 0, u32 total length;
  *   per predicate a 24 B record: u8 kind, u8 n, u16 table, u16 attr,
  *     u16 group, u32 <r>_i, u32 <r>_{i+1}, u32 c*beta' (RANGE, c = [a1 <= a0];
- *     0 for EQ), u32 0; then key half A and key half B, each one DPF key (EQ)
+ *     0 for EQ), u8 combine, 3 zero bytes; then key half A and key half B,
+ *     each one DPF key (EQ)
  *     or two DCF keys, a1 = hi + 1 + r first, then a0 = lo + r (RANGE).
  *   key: u8 kind (1 DPF, 2 DCF), u8 n, u8 party b, u8 0, u32 0, seed[16],
  *     per level i = 1..n: s_CW[16], u8 t^L_CW, u8 t^R_CW, u16 0 and for DCF
  *     u32 V_CW; then u32 CW_{n+1}.
  * tok[i] may be NULL to query the size: out_len[i] is always set.  Errors:
  * EINVAL (0 or more than 64 predicates, empty range, value outside 2^n,
- * n outside 1..32, ids >= 65536), ERANGE (cap < out_len[i]). */
+ * n outside 1..32, ids >= 65536, combine above 2 or not AND on a group's
+ * first predicate), ERANGE (cap < out_len[i]). */
 oblivgm_status oblivgm_keygen(const oblivgm_pred* preds, uint32_t n_preds, uint32_t n_bits,
                               const uint8_t seed[16], uint8_t* const tok[3], size_t cap, size_t out_len[3]);
 
@@ -206,9 +224,9 @@ oblivgm_status oblivgm_eval_dcf_batch(oblivgm_ctx* ctx, const uint8_t* keys, uin
  * approach of Sec. V-C), evaluate the six key halves of each predicate
  * (Eq. predEval, masked form: CS_i sums its two halves), re-share each
  * predicate's 3-out-of-3 sum to RSS with the PRF zero-sharing (Sec. III-B,
- * counter = element, step p, table, query_id), and AND the group's
- * predicates in token order with RSS multiplication plus re-share (step
- * 64 + p) (Sec. V-D).
+ * counter = element, step p, table, query_id), and fold the group's
+ * predicates in token order (AND, XOR or OR per predicate, OBLIVGM_COMBINE_*)
+ * with RSS multiplication plus re-share (step 64 + p) (Sec. V-D).
  * tok[i], tok_len[i]: host pointers to server i+1's token from
  *       oblivgm_keygen (all three must come from the same keygen call).
  * out: host array of 3 * n_groups device pointers; out[3 g + i] receives
@@ -343,7 +361,8 @@ oblivgm_status oblivgm_keygen_device(oblivgm_ctx* ctx, uint32_t kind, uint32_t n
  *   header 64 B: u32 magic 0x464D474F, u8 version 1, u8 i, u8 n, u8 0,
  *     u16 n_preds, u16 0, u32 0, u64 total length, zero to byte 64;
  *   per predicate a 32 B descriptor: u8 kind, u8 n, u16 table, u16 attr,
- *     u16 group, u64 N, u64 byte offset of its data block, u64 0;
+ *     u16 group, u64 N, u64 byte offset of its data block, u8 combine,
+ *     7 zero bytes;
  *   data block: u32 rA[N4] = <r_c>_i, u32 rB[N4] = <r_c>_{i+1}, RANGE only
  *     u32 cb[N4] = c_c * beta'; then the key blocks (A, sub 0), (A, sub 1),
  *     (B, sub 0), (B, sub 1) (sub 1 for RANGE only), each:
@@ -424,7 +443,7 @@ oblivgm_status oblivgm_fetch_multi(oblivgm_ctx* ctx, uint32_t table_id, const ui
 /* ---------------------------------------------------------- secFetch case I */
 
 /* secFetch, case I (Alg. 4, Sec. V-D): obliviously fetch the one element of a
- * table that an AND-group matched.  x[0..2] are device pointers to the
+ * table that a group matched.  x[0..2] are device pointers to the
  * group's RSS result (the three share sets written by
  * oblivgm_filter_and_combine for that group, n_elems of table_id each); the
  * result assumes exactly one x_c = 1 (with none it is 0, with several the
@@ -472,8 +491,8 @@ oblivgm_status oblivgm_load_onehot(oblivgm_ctx* ctx, uint32_t table_id, uint64_t
  * key halves at all 2^n positions (EvalAll) and takes the parity of their AND
  * with the binary share its key pair is tied to (CS_i: shares i and i+1);
  * it XORs its two bits, re-shares in binary RSS (F = bit 0 of AES_k(ctr),
- * same counters as the masked mode) and the group's predicates are ANDed in
- * binary RSS.  out[3 g + i] receives share set i+1 of group g packed 32
+ * same counters as the masked mode) and the group's predicates are folded
+ * in binary RSS (AND, XOR or OR per predicate).  out[3 g + i] receives share set i+1 of group g packed 32
  * elements per word (element e in bit e % 32 of word e / 32; ceil(n_elems / 32)
  * words; bits past n_elems are 0).  Asynchronous on stream.  Errors as
  * oblivgm_filter_and_combine; EINVAL for a masked-mode token. */
@@ -516,7 +535,7 @@ oblivgm_status oblivgm_serve_stats(oblivgm_ctx* ctx, uint64_t* admitted, uint64_
 oblivgm_status oblivgm_autotune(oblivgm_ctx* ctx, uint32_t* threads, uint32_t* elems_per_thread);
 oblivgm_status oblivgm_set_schedule(oblivgm_ctx* ctx, uint32_t threads, uint32_t elems_per_thread);
 
-/* Small batches (Alg. 3 over few elements): a batch whose AND-groups hold at
+/* Small batches (Alg. 3 over few elements): a batch whose groups hold at
  * most `max_elems` elements in all is evaluated by the walk-parallel kernel,
  * one thread per key walk (six DPF or twelve DCF walks of an element side by
  * side), instead of one thread per element.  Both kernels give identical

@@ -30,6 +30,7 @@ _SO = os.path.join(_OUT_DIR, "liboblivgm_oracle.so")
 
 KIND_DPF, KIND_DCF = 1, 2
 PRED_EQ, PRED_RANGE = 1, 2
+COMBINE_AND, COMBINE_XOR, COMBINE_OR = 0, 1, 2
 BETA_PRIME = 0xAAAAAAAB        # 3^{-1} mod 2^32
 MASK32 = 0xFFFFFFFF
 
@@ -53,7 +54,7 @@ class _Table(ctypes.Structure):
 
 
 class _Pred(ctypes.Structure):
-    _fields_ = [(f, ctypes.c_uint32) for f in ("kind", "table", "attr", "group", "lo", "hi")]
+    _fields_ = [(f, ctypes.c_uint32) for f in ("kind", "table", "attr", "group", "lo", "hi", "combine")]
 
 
 def lib():
@@ -187,6 +188,7 @@ def _preds(preds):
     for i, p in enumerate(preds):
         arr[i].kind, arr[i].table, arr[i].attr = p["kind"], p["table"], p["attr"]
         arr[i].group, arr[i].lo, arr[i].hi = p.get("group", 0), p["lo"], p.get("hi", p["lo"])
+        arr[i].combine = p.get("combine", COMBINE_AND)
     return arr
 
 
@@ -342,14 +344,24 @@ def plain_pred(pred, values) -> np.ndarray:
 
 
 def plain_group(preds, group: int, attrs) -> np.ndarray:
-    """AND over the group's predicates on plaintext attribute rows attrs[attr][elem]."""
+    """The group's predicates on plaintext attribute rows attrs[attr][elem], folded left to
+    right as Boolean values (Sec. V-D): all hold (AND), the paper's "one of" written with
+    XOR, or at least one (OR), per predicate's "combine"."""
     res = None
     for p in preds:
         if p.get("group", 0) != group:
             continue
-        b = plain_pred(p, attrs[p["attr"]])
-        res = b if res is None else res & b
-    return res
+        b = plain_pred(p, attrs[p["attr"]]).astype(bool)
+        op = p.get("combine", COMBINE_AND)
+        if res is None:
+            res = b
+        elif op == COMBINE_AND:
+            res = res & b
+        elif op == COMBINE_XOR:
+            res = res != b
+        else:
+            res = res | b
+    return None if res is None else res.astype(np.uint32)
 
 
 def match(n_vertices: int, edges, query_vertices: int, query_edges, vertex_ok, edge_ok):

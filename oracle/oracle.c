@@ -19,7 +19,9 @@
  *     predicate, handed to CS1..CS3 as (k^1_1,k^2_1), (k^2_2,k^3_1), (k^3_2,k^1_2).
  *   - secEval (Alg. 3) on additively masked inputs (Sec. V-C, the masked-input
  *     approach), the per-server sum of Eq. (predEval), the PRF re-share of
- *     Sec. III-B and the RSS AND fold of Sec. V-D, all over Z_{2^32}.
+ *     Sec. III-B and the aggregation of a target's predicates of Sec. V-D
+ *     (all hold: the RSS product; "one of": the paper's XOR; or the inclusive
+ *     OR), all over Z_{2^32}.
  *
  * Every step is written in the order the construction states it; nothing is
  * blocked, fused or reordered.  Eval computes only the child the input bit
@@ -434,9 +436,22 @@ void orc_prg(int which, const uint8_t s[16], uint8_t out[16]) { prg_h(which, s, 
 #define BETA_PRIME 0xAAAAAAABu   /* 3 * 0xAAAAAAAB = 1 mod 2^32 */
 #define MAX_HALF (2 * (24 + 32 * 24 + 4))   /* two DCF keys at n = 32 */
 
+#define COMBINE_AND 0
+#define COMBINE_XOR 1
+#define COMBINE_OR 2
+
 typedef struct {
     uint32_t kind, table, attr, group, lo, hi;
+    uint32_t combine;   /* how the predicate's result joins its group's: COMBINE_* */
 } orc_pred;
+
+/* 1 if predicate p is the first of its group in list order */
+static int first_of_group(const orc_pred* preds, uint32_t p)
+{
+    for (uint32_t e = 0; e < p; e++)
+        if (preds[e].group == preds[p].group) return 0;
+    return 1;
+}
 
 static const int HOLD_PAIR[3][2] = {{1, 2}, {2, 3}, {3, 1}};
 static const int HOLD_PARTY[3][2] = {{0, 0}, {1, 0}, {1, 1}};
@@ -486,6 +501,7 @@ static int keygen_impl(const orc_pred* preds, uint32_t n_preds, int n, const uin
         else if (q->kind == PRED_RANGE) { if (q->lo > q->hi || q->hi > m) return -1; }
         else return -1;
         if (q->table > 0xFFFF || q->attr > 0xFFFF || q->group > 0xFFFF) return -1;
+        if (q->combine > COMBINE_OR || (first_of_group(preds, p) && q->combine != COMBINE_AND)) return -1;
     }
     size_t total = orc_token_len(preds, n_preds, n);
     if (cap < total) return -2;
@@ -552,6 +568,7 @@ static int keygen_impl(const orc_pred* preds, uint32_t n_preds, int n, const uin
             put32(rec + 8, rs[i]);
             put32(rec + 12, rs[(i + 1) % 3]);
             put32(rec + 16, cbeta);
+            rec[20] = (uint8_t)q->combine;
             for (int h = 0; h < 2; h++) {
                 int j = HOLD_PAIR[i][h] - 1, b = HOLD_PARTY[i][h];
                 memcpy(rec + 24 + (size_t)h * half_len, keys[j][b], half_len);
@@ -588,6 +605,7 @@ typedef struct {
 typedef struct {
     const uint8_t* rec[3];      /* the predicate's record in each server's token */
     int kind, n, table, attr, group;
+    int combine;                /* COMBINE_* */
     int out_group;              /* 0 = Z_{2^32} (masked mode), 1 = Z_2 (one-hot mode) */
 } pred_view;
 
@@ -617,10 +635,16 @@ static int parse_tokens(const uint8_t* const tok[3], const size_t tok_len[3], pr
         pv[p].table = r0[2] | (r0[3] << 8);
         pv[p].attr = r0[4] | (r0[5] << 8);
         pv[p].group = r0[6] | (r0[7] << 8);
+        pv[p].combine = r0[20];
         pv[p].out_group = tok[0][7];
+        if (r0[20] > COMBINE_OR || r0[21] || r0[22] || r0[23]) return -1;
+        int first = 1;
+        for (int e = 0; e < p; e++)
+            if (pv[e].group == pv[p].group) first = 0;
+        if (first && pv[p].combine != COMBINE_AND) return -1;
         for (int i = 0; i < 3; i++) {
             pv[p].rec[i] = tok[i] + off;
-            if (memcmp(tok[i] + off, r0, 8) != 0) return -1;
+            if (memcmp(tok[i] + off, r0, 8) != 0 || memcmp(tok[i] + off + 20, r0 + 20, 4) != 0) return -1;
         }
         off += 24 + 2 * half_len;
     }
@@ -647,6 +671,38 @@ static void reshare(const aes_ks prf_ks[3], const uint32_t z[3], uint32_t out[3]
     uint32_t f[3];
     for (int i = 0; i < 3; i++) f[i] = prf(&prf_ks[i], elem, step, table, query);
     for (int i = 0; i < 3; i++) out[i] = z[i] + f[i] - f[(i + 2) % 3];
+}
+
+/*
+ * Aggregation of a target's predicates (Sec. V-D) over RSS shares of 0/1 values in
+ * Z_{2^32}: acc = (a_i, a_{i+1}) and b = (b_i, b_{i+1}) held by CS_i.  Server i's
+ * additive share of the product a b is a_i b_i + a_i b_{i+1} + a_{i+1} b_i (Sec. III-B).
+ *   all predicates hold:   a b
+ *   "one of" (paper's XOR): a XOR b = a + b - 2 a b
+ *   at least one (OR):     a OR b  = a + b - a b
+ * The result is 3-out-of-3 additive and is re-shared by the caller.
+ */
+static void fold_z2_32(int combine, const uint32_t a[3], const uint32_t b[3], uint32_t w[3])
+{
+    for (int i = 0; i < 3; i++) {
+        int i1 = (i + 1) % 3;
+        uint32_t ab = a[i] * b[i] + a[i] * b[i1] + a[i1] * b[i];
+        if (combine == COMBINE_AND) w[i] = ab;
+        else if (combine == COMBINE_XOR) w[i] = a[i] + b[i] - 2u * ab;
+        else w[i] = a[i] + b[i] - ab;
+    }
+}
+
+/* the same over binary RSS (one-hot mode, Z_2): a b, a ^ b, a ^ b ^ a b */
+static void fold_z2(int combine, const uint32_t a[3], const uint32_t b[3], uint32_t w[3])
+{
+    for (int i = 0; i < 3; i++) {
+        int i1 = (i + 1) % 3;
+        uint32_t ab = (a[i] & b[i]) ^ (a[i] & b[i1]) ^ (a[i1] & b[i]);
+        if (combine == COMBINE_AND) w[i] = ab;
+        else if (combine == COMBINE_XOR) w[i] = a[i] ^ b[i];
+        else w[i] = a[i] ^ b[i] ^ ab;
+    }
 }
 
 /* y for one key half held by a server: DPF (EQ) or two DCFs plus c*beta' for party 0 (RANGE) */
@@ -713,10 +769,7 @@ int orc_filter(const uint8_t* tok1, const uint8_t* tok2, const uint8_t* tok3, co
                 memcpy(acc, bsh, sizeof acc);
             } else {
                 uint32_t w[3];
-                for (int i = 0; i < 3; i++) {
-                    int i1 = (i + 1) % 3;
-                    w[i] = acc[i] * bsh[i] + acc[i] * bsh[i1] + acc[i1] * bsh[i];
-                }
+                fold_z2_32(q->combine, acc, bsh, w);
                 reshare(prf_ks, w, acc, e, 64u + (uint32_t)p, (uint32_t)table, query_id);
             }
         }
@@ -855,10 +908,7 @@ int orc_filter_onehot(const uint8_t* tok1, const uint8_t* tok2, const uint8_t* t
                 memcpy(acc, bsh, sizeof acc);
             } else {
                 uint32_t w[3];
-                for (int i = 0; i < 3; i++) {
-                    int i1 = (i + 1) % 3;
-                    w[i] = (acc[i] & bsh[i]) ^ (acc[i] & bsh[i1]) ^ (acc[i1] & bsh[i]);
-                }
+                fold_z2(q->combine, acc, bsh, w);
                 reshare_bin(prf_ks, w, acc, e, 64u + (uint32_t)p, (uint32_t)table, query_id);
             }
         }
@@ -922,6 +972,7 @@ static int fresh_check(const orc_pred* preds, uint32_t n_preds, int n, const uin
         else if (q->kind == PRED_RANGE) { if (q->lo > q->hi || q->hi > m) return -1; }
         else return -1;
         if (q->table >= n_tables || q->attr > 0xFFFF || q->group > 0xFFFF) return -1;
+        if (q->combine > COMBINE_OR || (first_of_group(preds, p) && q->combine != COMBINE_AND)) return -1;
     }
     return 0;
 }
@@ -1049,6 +1100,7 @@ int orc_keygen_fresh(const orc_pred* preds, uint32_t n_preds, int n, const uint6
             d[6] = (uint8_t)q->group; d[7] = (uint8_t)(q->group >> 8);
             put_u64(d + 8, N);
             put_u64(d + 16, off);
+            d[24] = (uint8_t)q->combine;
         }
         uint64_t keys_at = (eq ? 8u : 12u) * N4;
         for (uint64_t c = 0; c < N; c++) {
@@ -1116,7 +1168,11 @@ int orc_filter_fresh(const uint8_t* tok1, const uint8_t* tok2, const uint8_t* to
         const uint8_t* d = tok[0] + 64 + 32 * p;
         for (int i = 1; i < 3; i++)
             if (memcmp(tok[i] + 64 + 32 * p, d, 32) != 0) return -1;
+        if (d[24] > COMBINE_OR) return -1;
+        for (int b = 25; b < 32; b++)
+            if (d[b]) return -1;
         if ((uint32_t)(d[6] | (d[7] << 8)) != group) continue;
+        if (nm == 0 && d[24] != COMBINE_AND) return -1;
         int t = d[2] | (d[3] << 8);
         if (table >= 0 && t != table) return -3;
         table = t;
@@ -1165,10 +1221,7 @@ int orc_filter_fresh(const uint8_t* tok1, const uint8_t* tok2, const uint8_t* to
                 memcpy(acc, bsh, sizeof acc);
             } else {
                 uint32_t w[3];
-                for (int i = 0; i < 3; i++) {
-                    int i1 = (i + 1) % 3;
-                    w[i] = acc[i] * bsh[i] + acc[i] * bsh[i1] + acc[i1] * bsh[i];
-                }
+                fold_z2_32(d[24], acc, bsh, w);
                 reshare(prf_ks, w, acc, e, 64u + (uint32_t)p, (uint32_t)table, query_id);
             }
         }
@@ -1231,10 +1284,7 @@ int orc_fresh_direct(const orc_pred* preds, uint32_t n_preds, int n, const uint6
                 memcpy(acc, bsh, sizeof acc);
             } else {
                 uint32_t w[3];
-                for (int i = 0; i < 3; i++) {
-                    int i1 = (i + 1) % 3;
-                    w[i] = acc[i] * bsh[i] + acc[i] * bsh[i1] + acc[i1] * bsh[i];
-                }
+                fold_z2_32(q->combine, acc, bsh, w);
                 reshare(prf_ks, w, acc, e, 64u + (uint32_t)p, (uint32_t)table, query_id);
             }
         }

@@ -13,11 +13,13 @@ import ctypes
 from typing import Sequence
 
 from . import _native as N
-from ._native import (ALL_PAIRS, EAGAIN, EBUSY, EFAULT_DEVICE, EINVAL, ENOENT, ENOMEM, ERANGE, ETIMEOUT, KEY_DCF, KEY_DPF,
+from ._native import (ALL_PAIRS, COMBINE_AND, COMBINE_OR, COMBINE_XOR, EAGAIN, EBUSY, EFAULT_DEVICE, EINVAL, ENOENT,
+                      ENOMEM, ERANGE, ETIMEOUT, KEY_DCF, KEY_DPF,
                       OK, PRED_EQ, PRED_RANGE, OblivgmError)
 from .build import build
 
 __all__ = ["Context", "keygen", "keygen_onehot", "build", "OblivgmError", "PRED_EQ", "PRED_RANGE", "KEY_DPF", "KEY_DCF",
+           "COMBINE_AND", "COMBINE_XOR", "COMBINE_OR",
            "ALL_PAIRS", "version", "token_len", "fresh_token_size"]
 
 
@@ -34,6 +36,7 @@ def _pred_array(preds):
     for i, p in enumerate(preds):
         arr[i].kind, arr[i].table, arr[i].attr = int(p["kind"]), int(p["table"]), int(p["attr"])
         arr[i].group, arr[i].lo, arr[i].hi = int(p.get("group", 0)), int(p["lo"]), int(p.get("hi", p["lo"]))
+        arr[i].combine = int(p.get("combine", COMBINE_AND))
     return arr
 
 

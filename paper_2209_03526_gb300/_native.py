@@ -24,6 +24,7 @@ c_vp = ctypes.c_void_p
 OK, EINVAL, ENOMEM, ECUDA, EARCH, ERANGE, EBUSY, EAGAIN, ETIMEOUT, ENOENT, EFAULT_DEVICE = (
     0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10)
 PRED_EQ, PRED_RANGE = 1, 2
+COMBINE_AND, COMBINE_XOR, COMBINE_OR = 0, 1, 2
 KEY_DPF, KEY_DCF = 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 ALL_PAIRS = 1
@@ -43,7 +44,7 @@ class Config(ctypes.Structure):
 
 
 class Pred(ctypes.Structure):
-    _fields_ = [(f, c_u32) for f in ("kind", "table", "attr", "group", "lo", "hi")]
+    _fields_ = [(f, c_u32) for f in ("kind", "table", "attr", "group", "lo", "hi", "combine")]
 
 
 class Result(ctypes.Structure):

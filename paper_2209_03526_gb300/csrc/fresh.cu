@@ -68,7 +68,7 @@ __host__ __device__ inline FreshLayout fresh_layout(bool eq, uint32_t n, uint64_
 struct FreshPred {
     uint32_t kind, attr, lo, hi;
     uint32_t step;         // the predicate's index p in the query
-    uint32_t pad;
+    uint32_t combine;      // OBLIVGM_COMBINE_*: how the result joins the group's
     FreshLayout lay;
     uint8_t* data[3];      // the predicate's data block in each server token
 };
@@ -331,10 +331,15 @@ __global__ void __launch_bounds__(kFreshEvalThreads, 1) k_filter_fresh(const __g
                 uint32_t r[3];
                 reshare1(T, P.rk_prf, z, r, c, step, G.table, P.query);
                 if (pass + 1 < passes) {
+                    // fold (Sec. V-D): w = lin (a + b) + prod a b over 0/1 values
+                    const uint32_t lin = Q.combine == OBLIVGM_COMBINE_AND ? 0u : 1u;
+                    const uint32_t prod = Q.combine == OBLIVGM_COMBINE_AND   ? 1u
+                                          : Q.combine == OBLIVGM_COMBINE_XOR ? 0xFFFFFFFEu
+                                                                             : 0xFFFFFFFFu;
 #pragma unroll
                     for (int i = 0; i < 3; i++) {
                         const int i1 = (i + 1) % 3;
-                        z[i] = acc[i] * r[i] + acc[i] * r[i1] + acc[i1] * r[i];
+                        z[i] = lin * (acc[i] + r[i]) + prod * (acc[i] * r[i] + acc[i] * r[i1] + acc[i1] * r[i]);
                     }
                     step = 64u + Q.step;
                 } else {
@@ -377,6 +382,8 @@ oblivgm_status check_fresh_preds(const oblivgm_pred* preds, uint32_t n_preds, ui
         if (q.attr > 0xFFFF || q.group > 0xFFFF) return fail(OBLIVGM_EINVAL, "id above 65535");
         if (table_elems[q.table] >= (1ull << 40)) return fail(OBLIVGM_EINVAL, "table too large");
     }
+    std::string err;
+    if (!check_combine(preds, n_preds, &err)) return fail(OBLIVGM_EINVAL, err);
     return OBLIVGM_OK;
 }
 
@@ -439,10 +446,12 @@ extern "C" oblivgm_status oblivgm_keygen_fresh(oblivgm_ctx* ctx, const oblivgm_p
         F.lo = q.lo;
         F.hi = q.hi;
         F.step = p;
+        F.combine = q.combine;
         F.lay = fresh_layout(eq, n_bits, table_elems[q.table]);
         for (int i = 0; i < 3; i++) {
             F.data[i] = tok[i] + off;
             uint8_t* d = hdr.data() + i * head + 64 + 32 * p;
+            d[24] = (uint8_t)q.combine;
             d[0] = (uint8_t)q.kind;
             d[1] = (uint8_t)n_bits;
             d[2] = (uint8_t)q.table; d[3] = (uint8_t)(q.table >> 8);
@@ -563,6 +572,12 @@ extern "C" oblivgm_status oblivgm_filter_fresh(oblivgm_ctx* ctx, uint32_t query_
         if (N != tb.n_elems || attr >= tb.n_attrs || n != tb.n_bits)
             return fail(OBLIVGM_EINVAL, "predicate disagrees with the loaded table (elements, attribute or n)");
         if (get_u64(d + 16) != off) return fail(OBLIVGM_EINVAL, "fresh token layout offsets do not match");
+        const uint32_t combine = d[24];
+        for (int b = 25; b < 32; b++)
+            if (d[b]) return fail(OBLIVGM_EINVAL, "bad fresh predicate descriptor");
+        if (combine > OBLIVGM_COMBINE_OR) return fail(OBLIVGM_EINVAL, "bad combine field");
+        if (members[group].empty() && combine != OBLIVGM_COMBINE_AND)
+            return fail(OBLIVGM_EINVAL, "a group's first predicate must combine with AND");
         if (gtable[group] >= 0 && gtable[group] != (int)table)
             return fail(OBLIVGM_EINVAL, "an AND-group spans two tables");
         gtable[group] = (int)table;
@@ -571,6 +586,7 @@ extern "C" oblivgm_status oblivgm_filter_fresh(oblivgm_ctx* ctx, uint32_t query_
         F.kind = kind;
         F.attr = attr;
         F.step = p;
+        F.combine = combine;
         F.lay = fresh_layout(kind == OBLIVGM_PRED_EQ, n, N);
         for (int i = 0; i < 3; i++) F.data[i] = const_cast<uint8_t*>(tok[i]) + off;
         off += F.lay.data_len;

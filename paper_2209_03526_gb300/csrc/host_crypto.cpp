@@ -326,6 +326,16 @@ oblivgm_status parse_tokens(const uint8_t* const tok[3], const size_t tok_len[3]
         for (int i = 0; i < 3; i++)
             if (ld32(tok[i] + off + 12) != pp.r[(i + 1) % 3]) { *err = "mask shares are not replicated"; return OBLIVGM_EINVAL; }
         pp.cbeta = ld32(r0 + 16);
+        for (int i = 1; i < 3; i++)
+            if (ld32(tok[i] + off + 20) != ld32(r0 + 20)) { *err = "tokens disagree on the combine field"; return OBLIVGM_EINVAL; }
+        pp.combine = r0[20];
+        if (pp.combine > OBLIVGM_COMBINE_OR || r0[21] || r0[22] || r0[23]) { *err = "bad combine field"; return OBLIVGM_EINVAL; }
+        bool first_of_group = true;
+        for (const ParsedPred& e : q->preds) first_of_group = first_of_group && e.group != pp.group;
+        if (first_of_group && pp.combine != OBLIVGM_COMBINE_AND) {
+            *err = "a group's first predicate must combine with AND";
+            return OBLIVGM_EINVAL;
+        }
         pp.keys.resize(6 * nsub);
         for (int i = 0; i < 3; i++)
             for (int h = 0; h < 2; h++)
@@ -342,6 +352,19 @@ oblivgm_status parse_tokens(const uint8_t* const tok[3], const size_t tok_len[3]
     for (int i = 0; i < 3; i++)
         if (off != tok_len[i]) { *err = "trailing bytes in token"; return OBLIVGM_EINVAL; }
     return OBLIVGM_OK;
+}
+
+bool check_combine(const oblivgm_pred* preds, uint32_t n_preds, std::string* err) {
+    for (uint32_t p = 0; p < n_preds; p++) {
+        if (preds[p].combine > OBLIVGM_COMBINE_OR) { *err = "combine must be AND, XOR or OR"; return false; }
+        bool first_of_group = true;
+        for (uint32_t e = 0; e < p; e++) first_of_group = first_of_group && preds[e].group != preds[p].group;
+        if (first_of_group && preds[p].combine != OBLIVGM_COMBINE_AND) {
+            *err = "a group's first predicate must combine with AND";
+            return false;
+        }
+    }
+    return true;
 }
 
 oblivgm_status keygen(const oblivgm_pred* preds, uint32_t n_preds, uint32_t n_bits, const uint8_t seed[16],
@@ -371,6 +394,7 @@ oblivgm_status keygen(const oblivgm_pred* preds, uint32_t n_preds, uint32_t n_bi
         }
         if (q.table > 0xFFFF || q.attr > 0xFFFF || q.group > 0xFFFF) { *err = "id above 65535"; return OBLIVGM_EINVAL; }
     }
+    if (!check_combine(preds, n_preds, err)) return OBLIVGM_EINVAL;
     for (int i = 0; i < 3; i++) out_len[i] = total;
     if (!tok || !tok[0] || !tok[1] || !tok[2]) return OBLIVGM_OK;   // size query
     if (cap < total) { *err = "token buffer too small"; return OBLIVGM_ERANGE; }
@@ -447,6 +471,7 @@ oblivgm_status keygen(const oblivgm_pred* preds, uint32_t n_preds, uint32_t n_bi
             st32(rec + 8, rs[i]);
             st32(rec + 12, rs[(i + 1) % 3]);
             st32(rec + 16, cbeta);
+            rec[20] = (uint8_t)q.combine;
             for (int h = 0; h < 2; h++)
                 std::memcpy(rec + 24 + h * half, keys.data() + (kPair[i][h] * 2 + kParty[i][h]) * half, half);
         }

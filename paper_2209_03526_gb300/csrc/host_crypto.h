@@ -62,10 +62,23 @@ bool repack_key(const uint8_t* wire, size_t avail, uint32_t want_kind, int want_
 // One predicate as the servers see it after parsing the three tokens.
 struct ParsedPred {
     uint32_t kind, n, table, attr, group, step;
+    uint32_t combine = 0;       // OBLIVGM_COMBINE_*: how the result joins the group's
     uint32_t r[3];        // <r>_1, <r>_2, <r>_3 (each server's own share)
     uint32_t cbeta;
     std::vector<DevKey> keys;   // [server][half][sub]: 6 (EQ) or 12 (RANGE)
 };
+
+// Fold of a group's result a with a predicate's result b (Sec. V-D), over 0/1 values in
+// Z_{2^32}: w = lin (a + b) + prod a b, with (lin, prod) = AND (0, 1), XOR (1, -2),
+// OR (1, -1).
+inline void combine_coeffs(uint32_t op, uint32_t* lin, uint32_t* prod) {
+    *lin = op == OBLIVGM_COMBINE_AND ? 0u : 1u;
+    *prod = op == OBLIVGM_COMBINE_AND ? 1u : op == OBLIVGM_COMBINE_XOR ? 0xFFFFFFFEu : 0xFFFFFFFFu;
+}
+
+// Checks the combine fields of a predicate list: each at most OR, and AND on the
+// first predicate of every group.  Returns false with *err set otherwise.
+bool check_combine(const oblivgm_pred* preds, uint32_t n_preds, std::string* err);
 
 struct ParsedQuery {
     uint32_t n_bits = 0;

@@ -115,7 +115,8 @@ struct PredDesc {
     uint32_t r[3];
     uint32_t cbeta;
     uint32_t key_begin, n_keys;
-    uint32_t pad[2];
+    // fold into the group's result: w_i = lin (a_i + b_i) + prod (a_i b_i + a_i b_{i+1} + a_{i+1} b_i)
+    uint32_t lin, prod;
 };
 
 struct FilterParams {
@@ -294,8 +295,9 @@ __global__ void __launch_bounds__(max_threads<E>(), 1) k_filter(const __grid_con
                 }
             }
             // re-share the predicate's sum to RSS (step p); from the second predicate on,
-            // AND it into the accumulator (Sec. III-B: w_i = a_i b_i + a_i b_{i+1} + a_{i+1} b_i)
-            // and re-share the product (step 64 + p).  One re-share call site, two passes.
+            // fold it into the accumulator -- the RSS product (Sec. III-B: a_i b_i + a_i b_{i+1}
+            // + a_{i+1} b_i) plus, for XOR / OR, the linear terms (Sec. V-D) -- and re-share
+            // the result (step 64 + p).  One re-share call site, two passes.
             uint32_t step = D.step;
             const int passes = k == 0 ? 1 : 2;
 #pragma unroll 1
@@ -308,7 +310,8 @@ __global__ void __launch_bounds__(max_threads<E>(), 1) k_filter(const __grid_con
 #pragma unroll
                         for (int e = 0; e < E; e++) {
                             const int i1 = (i + 1) % 3;
-                            z[i][e] = acc[i][e] * r[i][e] + acc[i][e] * r[i1][e] + acc[i1][e] * r[i][e];
+                            const uint32_t pr = acc[i][e] * r[i][e] + acc[i][e] * r[i1][e] + acc[i1][e] * r[i][e];
+                            z[i][e] = D.lin * (acc[i][e] + r[i][e]) + D.prod * pr;
                         }
                     step = 64u + D.step;
                 } else {
@@ -375,7 +378,7 @@ namespace ogm {
 // key walk each (the six DPF or twelve DCF keys of a predicate), so an element's walks
 // run side by side instead of one after another in one thread.  The keys are staged as
 // in k_filter; the walks' outputs meet in shared memory, and the element's first slot
-// thread sums them per server, re-shares and ANDs exactly as k_filter does.
+// thread sums them per server, re-shares and folds exactly as k_filter does.
 
 constexpr int kWpSlots = 12;                      // threads per element
 constexpr int kWpElems = 40;                      // elements per CTA (tile)
@@ -467,7 +470,8 @@ __global__ void __launch_bounds__(kWpThreads, 1) k_filter_wp(const __grid_consta
 #pragma unroll
                         for (int i = 0; i < 3; i++) {
                             const int i1 = (i + 1) % 3;
-                            z[i][0] = acc[i][0] * r[i][0] + acc[i][0] * r[i1][0] + acc[i1][0] * r[i][0];
+                            const uint32_t pr = acc[i][0] * r[i][0] + acc[i][0] * r[i1][0] + acc[i1][0] * r[i][0];
+                            z[i][0] = D.lin * (acc[i][0] + r[i][0]) + D.prod * pr;
                         }
                         step = 64u + D.step;
                     } else {
@@ -634,6 +638,7 @@ oblivgm_status plan_queries(const std::map<uint32_t, Table>& tables, uint32_t n_
             d.kind = p->kind; d.n_bits = p->n; d.attr = p->attr; d.step = p->step;
             for (int i = 0; i < 3; i++) d.r[i] = p->r[i];
             d.cbeta = p->cbeta;
+            combine_coeffs(p->combine, &d.lin, &d.prod);
             d.key_begin = (uint32_t)plan->keys.size();
             d.n_keys = (uint32_t)p->keys.size();
             plan->keys.insert(plan->keys.end(), p->keys.begin(), p->keys.end());

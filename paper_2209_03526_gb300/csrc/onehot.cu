@@ -5,7 +5,7 @@
 // outputs, beta = 1) at every public position l and computes
 //     x = XOR_l Eval(k, l) AND <e_v>_j[l]
 // for the share j its key pair is tied to; it XORs its two results, re-shares them
-// in binary RSS and the query element's predicates are ANDed in binary RSS.
+// in binary RSS and the query element's predicates are folded (AND, XOR or OR) in binary RSS.
 //
 // Three kernels per query:
 //  * k_onehot_evalall: every key half at every position (the walk code of the masked
@@ -15,8 +15,8 @@
 //    rows serves up to 4 predicates on that column: a CTA per 32 elements, its warps
 //    splitting the rows, each lane holding its slice of the half vectors in
 //    registers; parities are reduced by ballots and each server's bit written packed;
-//  * k_onehot_fold: per AND-group, each element's bits are re-shared in binary RSS
-//    and ANDed in token order; results are packed 32 elements per word.
+//  * k_onehot_fold: per group, each element's bits are re-shared in binary RSS
+//    and folded in token order; results are packed 32 elements per word.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -370,14 +370,14 @@ void launch_dots(const DotParams& D, uint64_t nwords, int /*sm_count*/, cudaStre
     k_onehot_dots<<<(unsigned)nwords, warps * 32, 0, s>>>(D);
 }
 
-// Per AND-group: each element's predicate bits are re-shared in binary RSS and ANDed in
+// Per group: each element's predicate bits are re-shared in binary RSS and folded in
 // token order; one thread per element, results packed by warp ballots.
 struct FoldParams {
     uint32_t rk_prf[3][44];
     const uint32_t* te4;               // global-memory T-tables for the PRF
     const uint32_t* zbase;             // the query's packed predicate bits
     const uint64_t* zoff;              // per predicate of the group: word offset of its [3][nwords] block
-    const uint32_t* steps;             // per predicate: its index in the token
+    const uint32_t* steps;             // per predicate: its index in the token | combine << 16
     uint32_t* out[3];
     uint64_t n_elems;
     uint32_t n_preds;
@@ -414,17 +414,22 @@ __global__ void __launch_bounds__(256) k_onehot_fold(const __grid_constant__ Fol
             uint32_t z[3], b[3];
 #pragma unroll
             for (int i = 0; i < 3; i++) z[i] = valid ? (P.zbase[P.zoff[k] + (uint64_t)i * nwords + wd] >> lane) & 1u : 0u;
-            reshare_bits(T, P, z, b, e, P.steps[k]);
+            const uint32_t step = P.steps[k] & 0xFFFFu, combine = P.steps[k] >> 16;
+            reshare_bits(T, P, z, b, e, step);
             if (k == 0) {
                 acc[0] = b[0]; acc[1] = b[1]; acc[2] = b[2];
             } else {
+                // fold over Z_2 (Sec. V-D): AND = a b, XOR = a ^ b, OR = a ^ b ^ a b
+                const uint32_t lin = combine == OBLIVGM_COMBINE_AND ? 0u : 1u;
+                const uint32_t prod = combine == OBLIVGM_COMBINE_XOR ? 0u : 1u;
                 uint32_t w[3];
 #pragma unroll
                 for (int i = 0; i < 3; i++) {
                     const int i1 = (i + 1) % 3;
-                    w[i] = (acc[i] & b[i]) ^ (acc[i] & b[i1]) ^ (acc[i1] & b[i]);
+                    const uint32_t pr = (acc[i] & b[i]) ^ (acc[i] & b[i1]) ^ (acc[i1] & b[i]);
+                    w[i] = ((acc[i] ^ b[i]) & (0u - lin)) ^ (pr & (0u - prod));
                 }
-                reshare_bits(T, P, w, acc, e, 64u + P.steps[k]);
+                reshare_bits(T, P, w, acc, e, 64u + step);
             }
         }
 #pragma unroll
@@ -557,7 +562,7 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
         gbegin.push_back(gzoff.size());
         for (uint32_t p : members[g]) {
             gzoff.push_back(zoff[p]);
-            gstep.push_back(q.preds[p].step);
+            gstep.push_back(q.preds[p].step | q.preds[p].combine << 16);
         }
     }
     const size_t np = gzoff.size();

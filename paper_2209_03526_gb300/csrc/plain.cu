@@ -62,10 +62,10 @@ __global__ void k_plain_sum_reshare(const __grid_constant__ PrfKeys K, const uin
     for (int s = 0; s < 3; s++) b[(uint64_t)s * n + i] = z[s] + f[s] - f[(s + 2) % 3];
 }
 
-// acc <- reshare(acc AND b), w_i = a_i b_i + a_i b_{i+1} + a_{i+1} b_i
+// acc <- reshare(acc OP b): w_i = lin (a_i + b_i) + prod (a_i b_i + a_i b_{i+1} + a_{i+1} b_i)
 __global__ void k_plain_and(const __grid_constant__ PrfKeys K, const uint32_t* __restrict__ te,
                             const uint32_t* __restrict__ b, uint64_t n, uint32_t step, uint32_t table,
-                            uint32_t query, uint32_t* __restrict__ acc) {
+                            uint32_t query, uint32_t lin, uint32_t prod, uint32_t* __restrict__ acc) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const GlobalTab T{te};
@@ -73,7 +73,7 @@ __global__ void k_plain_and(const __grid_constant__ PrfKeys K, const uint32_t* _
     for (int s = 0; s < 3; s++) { a[s] = acc[(uint64_t)s * n + i]; bb[s] = b[(uint64_t)s * n + i]; }
     for (int s = 0; s < 3; s++) {
         const int s1 = (s + 1) % 3;
-        w[s] = a[s] * bb[s] + a[s] * bb[s1] + a[s1] * bb[s];
+        w[s] = lin * (a[s] + bb[s]) + prod * (a[s] * bb[s] + a[s] * bb[s1] + a[s1] * bb[s]);
     }
     for (int s = 0; s < 3; s++) f[s] = prf(T, K.rk[s], i, step, table, query);
     for (int s = 0; s < 3; s++) acc[(uint64_t)s * n + i] = w[s] + f[s] - f[(s + 2) % 3];
@@ -154,7 +154,7 @@ extern "C" oblivgm_status oblivgm_filter_plain(oblivgm_ctx* ctx, uint32_t query_
                 ctx->launches++;
             }
             // the predicate's RSS bit into b; the group's first predicate becomes the accumulator,
-            // later ones are ANDed into it (the accumulator is staged through y's space)
+            // later ones are folded into it (the accumulator is staged through y's space)
             k_plain_sum_reshare<<<blocks, 256, 0, s>>>(K, ctx->d_te4, y, nsub, n, p->step, tid, query_id, b);
             ctx->launches++;
             if (first) {
@@ -167,7 +167,9 @@ extern "C" oblivgm_status oblivgm_filter_plain(oblivgm_ctx* ctx, uint32_t query_
                     ce = cudaMemcpyAsync(y + (uint64_t)j * n, acc[j], n * 4, cudaMemcpyDeviceToDevice, s);
                     if (ce != cudaSuccess) return cuda_fail(ce, "plain-path copy");
                 }
-                k_plain_and<<<blocks, 256, 0, s>>>(K, ctx->d_te4, b, n, 64u + p->step, tid, query_id, y);
+                uint32_t lin, prod;
+                combine_coeffs(p->combine, &lin, &prod);
+                k_plain_and<<<blocks, 256, 0, s>>>(K, ctx->d_te4, b, n, 64u + p->step, tid, query_id, lin, prod, y);
                 ctx->launches++;
                 for (int j = 0; j < 3; j++) {
                     ce = cudaMemcpyAsync(acc[j], y + (uint64_t)j * n, n * 4, cudaMemcpyDeviceToDevice, s);

@@ -23,6 +23,7 @@ from __future__ import annotations
 import numpy as np
 
 PRED_EQ, PRED_RANGE = 1, 2
+COMBINE_AND, COMBINE_XOR, COMBINE_OR = 0, 1, 2
 
 
 def rng(seed: int) -> np.random.Generator:
@@ -88,12 +89,14 @@ def share3(g: np.random.Generator, values: np.ndarray, bits: int):
     return s1.astype(np.uint32), s2.astype(np.uint32), s3.astype(np.uint32)
 
 
-def eq_pred(table: int, attr: int, group: int, value: int):
-    return {"kind": PRED_EQ, "table": table, "attr": attr, "group": group, "lo": int(value), "hi": int(value)}
+def eq_pred(table: int, attr: int, group: int, value: int, combine: int = COMBINE_AND):
+    return {"kind": PRED_EQ, "table": table, "attr": attr, "group": group, "lo": int(value), "hi": int(value),
+            "combine": combine}
 
 
-def range_pred(table: int, attr: int, group: int, lo: int, hi: int):
-    return {"kind": PRED_RANGE, "table": table, "attr": attr, "group": group, "lo": int(lo), "hi": int(hi)}
+def range_pred(table: int, attr: int, group: int, lo: int, hi: int, combine: int = COMBINE_AND):
+    return {"kind": PRED_RANGE, "table": table, "attr": attr, "group": group, "lo": int(lo), "hi": int(hi),
+            "combine": combine}
 
 
 def range_around(g: np.random.Generator, value: int, bits: int, width_frac: float):
