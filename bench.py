@@ -254,7 +254,7 @@ def run_ours(args):
         threads, ept = ctx.autotune()
     outs = [[torch.empty(N_VERTICES, dtype=torch.int32, device=dev) for _ in range(3)]]
     stream = torch.cuda.current_stream(dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    flush = L2Flush(torch, dev, stream)
 
     for _ in range(args.warmup):
         ctx.filter_and_combine(1, toks, outs, stream)
@@ -274,7 +274,7 @@ def run_ours(args):
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier()
     for k in range(args.steps):
-        flush.fill_(k & 0xFF)                      # evict the shares from L2 between timed steps
+        flush()                                    # evict the shares from L2 between timed steps
         evs[k][0].record(stream)
         ctx.filter_and_combine(1 + k, toks, outs, stream)
         evs[k][1].record(stream)
@@ -423,13 +423,14 @@ def run_profile_case(args):
 
 
 def kernel_hash() -> str:
-    """Hash of the k_filter source: the device AES/FSS header and the kernel's part of
-    oblivgm.cu (from the PTX helpers to the raw-batch section), so host-code edits
+    """Hash of the k_filter source: the device AES/FSS and async-copy headers and the kernel's
+    part of oblivgm.cu (from the PTX helpers to the raw-batch section), so host-code edits
     elsewhere do not invalidate a traffic capture."""
     import hashlib
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_2209_03526_gb300", "csrc", "device_fss.cuh"), "rb") as fh:
-        h.update(fh.read())
+    for hdr in ("device_fss.cuh", "ptx_async.cuh"):
+        with open(os.path.join(ROOT, "paper_2209_03526_gb300", "csrc", hdr), "rb") as fh:
+            h.update(fh.read())
     with open(os.path.join(ROOT, "paper_2209_03526_gb300", "csrc", "oblivgm.cu"), "rb") as fh:
         src = fh.read()
     a = src.index(b"// ------------------------------------------------------------------ PTX helpers")
@@ -524,6 +525,22 @@ def pct(xs, q):
     return float(np.percentile(np.asarray(xs) * 1e3, q))
 
 
+class L2Flush:
+    """Reads a buffer larger than the 129 MB L2 on `stream` (None: the current stream), so
+    that the next timed step starts with its inputs in HBM; called between timed steps,
+    outside the events.  A read leaves clean lines behind: a write would leave the L2 full
+    of dirty lines whose write-back the next step would pay for."""
+
+    def __init__(self, torch, dev, stream=None):
+        self.torch, self.stream = torch, stream
+        self.buf = torch.zeros(64 << 20, dtype=torch.int32, device=dev)     # 256 MB
+
+    def __call__(self):
+        s = self.stream if self.stream is not None else self.torch.cuda.current_stream()
+        with self.torch.cuda.stream(s):
+            self.buf.max()
+
+
 def time_plain(ctx, toks_list, outs_list, stream, reps=1):
     """Seconds the plain path takes for the listed queries, run one after another."""
     import torch
@@ -552,8 +569,10 @@ def _timed_graph(torch, ctx, plan, stream, warmup, steps):
     with torch.cuda.graph(g):
         ctx.plan_launch(plan, torch.cuda.current_stream())
     torch.cuda.synchronize()
+    flush = L2Flush(torch, torch.device("cuda", torch.cuda.current_device()))
     ms = []
     for _ in range(steps):
+        flush()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         g.replay()
@@ -606,12 +625,29 @@ def run_workload(args):
         for _ in range(max(1, args.warmup)):
             ctx.fetch_unique(1, 0, 0, outs[0], [0, 1, 2, 3], res, stream)
         ctx.sync(stream)
-        ms = []
+        flush = L2Flush(torch, dev, stream)
+        call_ms = []                               # the call as a host program makes it
         for k in range(args.steps):
+            flush()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             ctx.fetch_unique(1, 0, 0, outs[0], [0, 1, 2, 3], res, stream)
             b.record(stream)
+            b.synchronize()
+            call_ms.append(a.elapsed_time(b))
+        # the device's time: the call (output clear + k_fetch) captured once in a CUDA graph
+        g_fetch = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g_fetch):
+            ctx.fetch_unique(1, 0, 0, outs[0], [0, 1, 2, 3], res, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        flush_cur = L2Flush(torch, dev)
+        ms = []
+        for k in range(args.steps):
+            flush_cur()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            g_fetch.replay()
+            b.record()
             b.synchronize()
             ms.append(a.elapsed_time(b))
         rec = (res.cpu().numpy().view(np.uint32).reshape(3, 5).astype(np.uint64).sum(axis=0)) & 0xFFFFFFFF
@@ -622,7 +658,9 @@ def run_workload(args):
         line.update({"value": n_v / step_s, "unit": "candidates/s", "metric": "secFetch case I candidates/s",
                      "ms_per_step": step_s * 1e3, "steps": args.steps, "warmup": args.warmup,
                      "config": {"workload": "fetch_unique_1048576v_4attr", "attributes_fetched": 4,
-                                "reconstructs_to_the_match": ok},
+                                "reconstructs_to_the_match": ok, "l2": "flushed between timed steps",
+                                "launch": "output clear + one k_fetch, replayed from a CUDA graph",
+                                "direct_call_ms": float(np.mean(call_ms))},
                      "roofline": {"bound": "hbm", "achieved": algo_bytes / step_s / 1e9, "peak": peak_bw,
                                   "unit": "GB/s", "frac": algo_bytes / step_s / 1e9 / peak_bw}})
         if not args.no_cpu_baseline:
@@ -648,9 +686,12 @@ def run_workload(args):
         toks = [torch.empty(L, dtype=torch.uint8, device=dev) for _ in range(3)]
         outs = [[torch.empty(n_v, dtype=torch.int32, device=dev) for _ in range(3)]]
 
+        flush = L2Flush(torch, dev, stream)
+
         def timed(fn, reps):
             ms = []
             for k in range(reps):
+                flush()
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
                 fn(k)
@@ -676,7 +717,7 @@ def run_workload(args):
         peak_bw = float(peaks.get("hbm_gbs", 6800.0))
         line.update({"value": units / step_s, "ms_per_step": step_s * 1e3, "steps": args.steps,
                      "warmup": args.warmup,
-                     "config": {"workload": f"fresh_keys_bulk_vertex_filter_{n_v}v_4attr_8pred_n32",
+                     "config": {"l2": "flushed between timed steps", "workload": f"fresh_keys_bulk_vertex_filter_{n_v}v_4attr_8pred_n32",
                                 "token_bytes_per_server": L, "element_predicates_per_step": units,
                                 "reconstructs_to_plaintext": ok,
                                 "launch": "one k_filter_fresh launch (servers); one k_keygen_fresh launch (client)"},
@@ -715,8 +756,10 @@ def run_workload(args):
         for _ in range(max(1, args.warmup)):
             ctx.shuffle(ins, seeds, outs, 0, stream)
         ctx.sync(stream)
+        flush = L2Flush(torch, dev, stream)
         ms = []
         for k in range(args.steps):
+            flush()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             ctx.shuffle(ins, seeds, outs, 0, stream)
@@ -748,7 +791,7 @@ def run_workload(args):
         ok = sorted(rec.tolist()) == np.flatnonzero(vals[1] <= thr).tolist()
         line.update({"metric": "secShuffle records/s", "unit": "records/s", "value": n_v / shuf_s,
                      "ms_per_step": shuf_s * 1e3, "steps": args.steps, "warmup": args.warmup,
-                     "config": {"workload": "shuffle_1048576x6_add", "records": n_v, "words_per_record": width,
+                     "config": {"l2": "flushed between timed steps", "workload": "shuffle_1048576x6_add", "records": n_v, "words_per_record": width,
                                 "launch": "k_feistel_tab + k_perms + one kernel per server (k_shuf_cs1..3)"},
                      "roofline": {"bound": "alu", "achieved": lookups / shuf_s / 1e9, "peak": peak_lu,
                                   "unit": "Glookup/s", "frac": lookups / shuf_s / 1e9 / peak_lu},
@@ -782,8 +825,10 @@ def run_workload(args):
             out = torch.empty(2 * m * L, dtype=torch.uint8, device=dev)
             for _ in range(max(1, args.warmup)):
                 ctx.keygen_device(kind, n, alpha, beta, KEY_SEED, out, stream)
+            flush = L2Flush(torch, dev, stream)
             ms = []
             for k in range(args.steps):
+                flush()
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
                 ctx.keygen_device(kind, n, alpha, beta, KEY_SEED, out, stream)
@@ -814,7 +859,7 @@ def run_workload(args):
         line.update({"metric": "FSS key pairs generated/s (n = 32)", "unit": "key-pairs/s",
                      "value": total_pairs / total_s, "ms_per_step": total_s * 1e3, "steps": args.steps,
                      "warmup": args.warmup,
-                     "config": {"workload": "keygen_1048576_dpf_1048576_dcf_n32", "pairs_per_kind": m,
+                     "config": {"l2": "flushed between timed steps", "workload": "keygen_1048576_dpf_1048576_dcf_n32", "pairs_per_kind": m,
                                 "launch": "one k_keygen launch per kind"},
                      "kinds": kinds,
                      "roofline": {"bound": "alu", "achieved": total_lu / total_s / 1e9, "peak": peak_lu,
@@ -856,8 +901,10 @@ def run_workload(args):
         for _ in range(max(1, args.warmup)):
             ctx.filter_onehot(1, toks, outs, stream)
         ctx.sync(stream)
+        flush = L2Flush(torch, dev, stream)
         ms = []
         for k in range(args.steps):
+            flush()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             ctx.filter_onehot(2 + k, toks, outs, stream)
@@ -874,7 +921,7 @@ def run_workload(args):
         peak_bw = float(peaks.get("hbm_gbs", 6800.0))
         line.update({"value": units / step_s, "ms_per_step": step_s * 1e3, "steps": args.steps,
                      "warmup": args.warmup,
-                     "config": {"workload": "onehot_107614v_n16_4pred", "elements": n_v, "one_hot_bits": 1 << n,
+                     "config": {"l2": "flushed between timed steps", "workload": "onehot_107614v_n16_4pred", "elements": n_v, "one_hot_bits": 1 << n,
                                 "groups": "EQ | RANGE | EQ AND RANGE", "element_predicates_per_step": units,
                                 "share_row_bytes_per_element": row_bytes, "columns_read": columns},
                      "roofline": {"bound": "hbm", "achieved": algo_bytes / step_s / 1e9, "peak": peak_bw,
@@ -927,7 +974,7 @@ def run_workload(args):
         e2e_s = time.perf_counter() - t0
         line.update({"value": units / step_s, "ms_per_step": step_s * 1e3, "steps": args.steps,
                      "warmup": args.warmup,
-                     "config": {"workload": name, "queries": len(queries), "element_predicates_per_step": units,
+                     "config": {"l2": "flushed between timed steps", "workload": name, "queries": len(queries), "element_predicates_per_step": units,
                                 "aes_blocks_per_step": aes, "tables": {str(k): v for k, v in table_n.items()},
                                 "launch": f"one persistent {shape['kernel']} launch ({shape['grid']} CTAs x "
                                           f"{shape['threads']} threads, {shape['items']} tiles of {shape['tile']} "

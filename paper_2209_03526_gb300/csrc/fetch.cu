@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <numeric>
 
 #include "host_crypto.h"
 #include "oblivgm.h"
@@ -20,16 +21,8 @@ namespace {
 
 constexpr int kFetchMaxAttrs = 64;
 constexpr uint32_t kFetchStep = 256;
-
-#ifndef OGM_FETCH_COLS
-#define OGM_FETCH_COLS 6
-#endif
-#ifndef OGM_FETCH_CTAS_PER_SM
-#define OGM_FETCH_CTAS_PER_SM 2
-#endif
-constexpr int kFetchThreads = 512;
-constexpr uint32_t kFetchCols = OGM_FETCH_COLS;
-constexpr int kFetchCtasPerSm = OGM_FETCH_CTAS_PER_SM;
+constexpr int kFetchThreads = 256;
+constexpr int kFetchCtasPerSm = 5;          // 48 registers: 1,280 threads per SM
 
 struct FetchParams {
     const uint32_t* x[3];          // filter result share sets, n_elems each
@@ -49,112 +42,92 @@ __device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
     return v;
 }
 
-// sum of a value over the CTA (every thread gets it); red holds one word per warp
-__device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t* red) {
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    v = warp_sum(v);
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    uint32_t t = 0;
-    for (uint32_t w = 0; w < blockDim.x / 32; w++) t += red[w];
-    return t;
+// one candidate's contribution to column k: the index row adds c * <x_c>_i, an attribute
+// row the RSS product share w_i = v_i x_i + v_i x_{i+1} + v_{i+1} x_i
+__device__ __forceinline__ void fetch_add(uint32_t acc[3], bool index_col, uint32_t c, const uint32_t x[3],
+                                          const uint32_t v[3]) {
+    if (index_col) {
+        acc[0] += c * x[0]; acc[1] += c * x[1]; acc[2] += c * x[2];
+    } else {
+        acc[0] += v[0] * x[0] + v[0] * x[1] + v[1] * x[0];
+        acc[1] += v[1] * x[1] + v[1] * x[2] + v[2] * x[1];
+        acc[2] += v[2] * x[2] + v[2] * x[0] + v[0] * x[2];
+    }
 }
 
 // Every output word is a sum mod 2^32, so each CTA adds its part straight into the
 // zeroed outputs and the order of the additions does not matter:
 //   index (column 0), share set i:    sum_c c * <x_c>_i
 //   attribute a (column 1 + k), set i: sum_c w_i(c) + F(k_i, ctr) - F(k_{i-1}, ctr),
-//   w_i = v_i x_i + v_i x_{i+1} + v_{i+1} x_i (the RSS product), ctr = (a, 256 + group, table, query).
+//   ctr = (a, 256 + group, table, query).
 // CTA 0 adds the re-share masks (PRF blocks the host computes: they depend only on the
-// attribute, the step, the table and the query); the index has public weights and needs none.  One pass over the candidates per group of up to 8 columns:
-// each thread loads an element's result shares and every attribute share first, then sums.
+// attribute, the step, the table and the query); the index has public weights and needs none.
+// Work split: the launch has a multiple of `cols` warps, and warp w always serves column
+// w % cols, for blocks of 32 x 4 candidates w / cols, w / cols + W / cols, ... (W warps):
+// each lane issues six 16-byte loads (its four candidates' result shares and the column's
+// attribute shares) per step, every SM streams many such steps, and a warp keeps three
+// accumulators.  The result shares are read once per column; the other columns' reads of
+// the same block come from warps of the same CTA, mostly out of L1 / L2.
 __global__ void __launch_bounds__(kFetchThreads, kFetchCtasPerSm) k_fetch(const __grid_constant__ FetchParams P) {
-    __shared__ uint32_t red[kFetchThreads / 32];
+    __shared__ uint32_t part[1 + kFetchMaxAttrs][3];
     const uint32_t cols = 1 + P.n_attrs;
+    for (uint32_t t = threadIdx.x; t < 3 * cols; t += blockDim.x) part[t / 3][t % 3] = 0;
     if (blockIdx.x == 0)
         for (uint32_t t = threadIdx.x; t < 3 * P.n_attrs; t += blockDim.x)
             atomicAdd(P.out + (t / P.n_attrs) * cols + 1 + t % P.n_attrs, P.mask[t / P.n_attrs][t % P.n_attrs]);
-    for (uint32_t c0 = 0; c0 < cols; c0 += kFetchCols) {
-        uint32_t acc[kFetchCols][3];
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t k = (uint32_t)(warp % cols);
+    const uint64_t b0 = warp / cols, bstep = n_warps / cols;
+    const bool index_col = k == 0;
+    const uint64_t arow = index_col ? 0 : (uint64_t)P.attrs[k - 1] * P.stride;
+    uint32_t acc[3] = {0, 0, 0};
+    // 16-byte loads of four candidates while the result shares are 16-byte aligned (the
+    // table rows always are), then one candidate at a time for the rest
+    const uint64_t nq = P.vec4 ? P.n_elems / 4 : 0;
+    for (uint64_t b = b0; b * 32 < nq; b += bstep) {
+        const uint64_t q = b * 32 + lane;
+        if (q < nq) {
+            uint4 X[3], A[3];
 #pragma unroll
-        for (uint32_t k = 0; k < kFetchCols; k++) acc[k][0] = acc[k][1] = acc[k][2] = 0;
-        // 16-byte loads of four candidates while the result shares are 16-byte aligned (the
-        // table rows always are), then one candidate at a time for the rest
-        uint64_t c_begin = P.n_elems;
-        if (P.vec4) {
-            const uint64_t n4 = P.n_elems / 4;
-            for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4;
-                 q += (uint64_t)gridDim.x * blockDim.x) {
-                const uint4 X0 = __ldg(reinterpret_cast<const uint4*>(P.x[0]) + q);
-                const uint4 X1 = __ldg(reinterpret_cast<const uint4*>(P.x[1]) + q);
-                const uint4 X2 = __ldg(reinterpret_cast<const uint4*>(P.x[2]) + q);
-                const uint32_t xs[3][4] = {{X0.x, X0.y, X0.z, X0.w}, {X1.x, X1.y, X1.z, X1.w},
-                                           {X2.x, X2.y, X2.z, X2.w}};
+            for (int j = 0; j < 3; j++) X[j] = __ldg(reinterpret_cast<const uint4*>(P.x[j]) + q);
+            if (!index_col) {
 #pragma unroll
-                for (uint32_t k = 0; k < kFetchCols; k++) {
-                    const uint32_t col = c0 + k;
-                    if (col == 0) {
+                for (int j = 0; j < 3; j++) A[j] = __ldg(reinterpret_cast<const uint4*>(P.v[j] + arow) + q);
+            } else {
 #pragma unroll
-                        for (int e = 0; e < 4; e++) {
-                            const uint32_t cw = (uint32_t)(4 * q + e);
-                            acc[k][0] += cw * xs[0][e]; acc[k][1] += cw * xs[1][e]; acc[k][2] += cw * xs[2][e];
-                        }
-                    } else if (col < cols) {
-                        const uint64_t off = ((uint64_t)P.attrs[col - 1] * P.stride) / 4 + q;
-                        const uint4 A0 = __ldg(reinterpret_cast<const uint4*>(P.v[0]) + off);
-                        const uint4 A1 = __ldg(reinterpret_cast<const uint4*>(P.v[1]) + off);
-                        const uint4 A2 = __ldg(reinterpret_cast<const uint4*>(P.v[2]) + off);
-                        const uint32_t as[3][4] = {{A0.x, A0.y, A0.z, A0.w}, {A1.x, A1.y, A1.z, A1.w},
-                                                   {A2.x, A2.y, A2.z, A2.w}};
-#pragma unroll
-                        for (int e = 0; e < 4; e++) {
-                            acc[k][0] += as[0][e] * xs[0][e] + as[0][e] * xs[1][e] + as[1][e] * xs[0][e];
-                            acc[k][1] += as[1][e] * xs[1][e] + as[1][e] * xs[2][e] + as[2][e] * xs[1][e];
-                            acc[k][2] += as[2][e] * xs[2][e] + as[2][e] * xs[0][e] + as[0][e] * xs[2][e];
-                        }
-                    }
-                }
+                for (int j = 0; j < 3; j++) A[j] = make_uint4(0, 0, 0, 0);
             }
-            c_begin = 4 * n4;
-        } else {
-            c_begin = 0;
+            const uint32_t c = (uint32_t)(4 * q);
+            { const uint32_t x[3] = {X[0].x, X[1].x, X[2].x}, v[3] = {A[0].x, A[1].x, A[2].x}; fetch_add(acc, index_col, c, x, v); }
+            { const uint32_t x[3] = {X[0].y, X[1].y, X[2].y}, v[3] = {A[0].y, A[1].y, A[2].y}; fetch_add(acc, index_col, c + 1, x, v); }
+            { const uint32_t x[3] = {X[0].z, X[1].z, X[2].z}, v[3] = {A[0].z, A[1].z, A[2].z}; fetch_add(acc, index_col, c + 2, x, v); }
+            { const uint32_t x[3] = {X[0].w, X[1].w, X[2].w}, v[3] = {A[0].w, A[1].w, A[2].w}; fetch_add(acc, index_col, c + 3, x, v); }
         }
-        for (uint64_t c = c_begin + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < P.n_elems;
-             c += (uint64_t)gridDim.x * blockDim.x) {
-            const uint32_t x0 = __ldg(P.x[0] + c), x1 = __ldg(P.x[1] + c), x2 = __ldg(P.x[2] + c);
-            uint32_t a[kFetchCols][3];
+    }
+    for (uint64_t b = b0; 4 * nq + b * 32 < P.n_elems; b += bstep) {
+        const uint64_t c = 4 * nq + b * 32 + lane;
+        if (c < P.n_elems) {
+            uint32_t x[3], v[3] = {0, 0, 0};
 #pragma unroll
-            for (uint32_t k = 0; k < kFetchCols; k++) {
-                const uint32_t col = c0 + k;
-                a[k][0] = a[k][1] = a[k][2] = 0;
-                if (col >= 1 && col < cols) {
-                    const uint64_t off = (uint64_t)P.attrs[col - 1] * P.stride + c;
-                    a[k][0] = __ldg(P.v[0] + off);
-                    a[k][1] = __ldg(P.v[1] + off);
-                    a[k][2] = __ldg(P.v[2] + off);
-                }
-            }
+            for (int j = 0; j < 3; j++) x[j] = __ldg(P.x[j] + c);
+            if (!index_col)
 #pragma unroll
-            for (uint32_t k = 0; k < kFetchCols; k++) {
-                if (c0 + k == 0) {
-                    const uint32_t cw = (uint32_t)c;   // weights mod 2^32
-                    acc[k][0] += cw * x0; acc[k][1] += cw * x1; acc[k][2] += cw * x2;
-                } else {                               // zero for columns past the last
-                    acc[k][0] += a[k][0] * x0 + a[k][0] * x1 + a[k][1] * x0;
-                    acc[k][1] += a[k][1] * x1 + a[k][1] * x2 + a[k][2] * x1;
-                    acc[k][2] += a[k][2] * x2 + a[k][2] * x0 + a[k][0] * x2;
-                }
-            }
+                for (int j = 0; j < 3; j++) v[j] = __ldg(P.v[j] + arow + c);
+            fetch_add(acc, index_col, (uint32_t)c, x, v);   // weights mod 2^32
         }
+    }
 #pragma unroll
-        for (uint32_t k = 0; k < kFetchCols; k++) {
-            if (c0 + k >= cols) break;
-            for (int i = 0; i < 3; i++) {
-                const uint32_t t = block_sum(acc[k][i], red);
-                if (threadIdx.x == 0) atomicAdd(P.out + i * cols + c0 + k, t);
-            }
-        }
+    for (int i = 0; i < 3; i++) {
+        const uint32_t t = warp_sum(acc[i]);
+        if (lane == 0) atomicAdd(&part[k][i], t);
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < 3 * cols; t += blockDim.x) {
+        const uint32_t col = t / 3, i = t % 3;
+        atomicAdd(P.out + i * cols + col, part[col][i]);
     }
 }
 
@@ -184,10 +157,14 @@ extern "C" oblivgm_status oblivgm_fetch_unique(oblivgm_ctx* ctx, uint32_t query_
     const uint32_t cols = 1 + n_attrs;
     ce = cudaMemsetAsync(out, 0, 3 * cols * sizeof(uint32_t), s);
     if (ce != cudaSuccess) return cuda_fail(ce, "fetch output clear");
-    // two 512-thread CTAs per SM (64 registers)
-    const uint64_t blocks = std::max<uint64_t>(
-        1, std::min<uint64_t>((tb.n_elems + kFetchThreads - 1) / kFetchThreads,
-                              (uint64_t)kFetchCtasPerSm * ctx->sm_count));
+    // warps: a multiple of cols (each warp serves one column), enough for one block of
+    // 32 x 4 candidates per warp and column, at most kFetchCtasPerSm CTAs per SM
+    const uint64_t warps_per_cta = kFetchThreads / 32;
+    const uint64_t unit = cols / std::gcd<uint64_t>(cols, warps_per_cta);   // CTAs per whole round of columns
+    const uint64_t blocks32 = std::max<uint64_t>(1, (tb.n_elems + 127) / 128);
+    const uint64_t want = (blocks32 * cols + warps_per_cta - 1) / warps_per_cta;
+    const uint64_t cap = std::max<uint64_t>(unit, (uint64_t)kFetchCtasPerSm * ctx->sm_count / unit * unit);
+    const uint64_t blocks = std::min<uint64_t>((want + unit - 1) / unit * unit, cap);
     FetchParams F{};
     for (int j = 0; j < 3; j++) {
         F.x[j] = x[j];

@@ -14,6 +14,7 @@
 
 #include "device_fss.cuh"
 #include "host_crypto.h"
+#include "ptx_async.cuh"
 #include "oblivgm.h"
 #include "runtime.h"
 
@@ -49,54 +50,7 @@ oblivgm_status ws_alloc(oblivgm_ctx* ctx, void** p, size_t bytes, cudaStream_t s
     } while (0)
 
 // ------------------------------------------------------------------ PTX helpers
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-// bulk (non-tensor) TMA copy global -> shared, completion counted on the mbarrier
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(phase)
-        : "memory");
-    return ok != 0;
-}
-
-// bounded wait: gives up after limit_ns of wall time
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase, uint64_t limit_ns) {
-    const uint64_t t0 = global_ns();
-    while (!mbar_try_wait(bar, phase)) {
-        if (global_ns() - t0 > limit_ns) return false;
-    }
-    return true;
-}
-
-constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
-constexpr uint32_t kErrKeyWait = 1u;
+// (mbarriers, bulk copies and the bounded wait are in ptx_async.cuh)
 
 // ------------------------------------------------------------------ fused secEval
 
