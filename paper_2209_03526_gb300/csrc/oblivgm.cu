@@ -1,6 +1,9 @@
 // oblivgm.cu -- context, resident share store, raw DPF/DCF batches and the
-// fused secEval kernel (mask-open, six key-half walks per predicate, per-server
-// sums, PRF re-share, RSS AND fold, output write) of the oblivgm library.
+// fused secEval kernels (mask-open, six key-half walks per predicate, per-server
+// sums, PRF re-share, RSS fold of a group's predicates, output write) of the
+// oblivgm library: k_filter (one thread per element) and k_filter_wp (one thread
+// per key walk, for small batches), the batch planner that picks between them,
+// prepared plans and the no-allocation entry point.
 #include <cuda_runtime.h>
 
 #include <algorithm>
