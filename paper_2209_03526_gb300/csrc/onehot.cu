@@ -28,6 +28,7 @@
 #include "device_fss.cuh"
 #include "host_crypto.h"
 #include "oblivgm.h"
+#include "ptx_async.cuh"
 #include "runtime.h"
 
 namespace ogm {
@@ -287,11 +288,13 @@ __global__ void __launch_bounds__(512) k_onehot_dots(const __grid_constant__ Dot
     const uint64_t nwords = (P.n_elems + 31) / 32;
     const uint64_t wd = blockIdx.x;
     const uint64_t base = wd * 32;
-    uint32_t mask[kDotPreds][3][2];
+    // lane 0 of each warp owns the warp's slots: cleared here, XORed into below
+    if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < kDotPreds; k++)
+        for (int k = 0; k < kDotPreds; k++)
 #pragma unroll
-        for (int j = 0; j < 3; j++) mask[k][j][0] = mask[k][j][1] = 0;
+            for (int j = 0; j < 3; j++) zs[warp][k][j][0] = zs[warp][k][j][1] = 0;
+    }
     // a lane's words: w0 .. w0 + 3 (vector path) or lane + 32 r (scalar path); the vector
     // path loops over the row in steps of 128 * warps words
     for (uint32_t w0 = vec ? warp * 128 + lane * 4 : 0; w0 < (vec ? W : 1u); w0 += vec ? warps * 128 : 1u) {
@@ -308,7 +311,10 @@ __global__ void __launch_bounds__(512) k_onehot_dots(const __grid_constant__ Dot
                     for (int r = 0; r < 4; r++) h[k][0][r] = h[k][1][r] = 0;
                 }
             }
-            // lane-local parity bits, bit c = element base + c; XOR-reduced over the warp below
+            // Lane-local parity bits of the 32 elements, XOR-reduced over the warp below.
+            // Element c = 4 q + f sits at bit 8 f + q: a batch's popcounts (at most 32 each)
+            // are added into the bytes of two words by shift-adds, and their low bits are
+            // moved into place with one mask and one shift per four elements.
             uint32_t pl[kDotPreds][2];
 #pragma unroll
             for (int k = 0; k < kDotPreds; k++) pl[k][0] = pl[k][1] = 0;
@@ -321,17 +327,22 @@ __global__ void __launch_bounds__(512) k_onehot_dots(const __grid_constant__ Dot
                     else v[b][0] = v[b][1] = v[b][2] = v[b][3] = 0;
                 }
 #pragma unroll
-                for (int b = 0; b < kDotBatch; b++)
+                for (int k = 0; k < kDotPreds; k++) {
+                    if ((uint32_t)k >= np) break;
 #pragma unroll
-                    for (int k = 0; k < kDotPreds; k++) {
-                        if ((uint32_t)k >= np) break;
+                    for (int hh = 0; hh < 2; hh++) {
+                        uint32_t cnt[kDotBatch / 4] = {};
 #pragma unroll
-                        for (int hh = 0; hh < 2; hh++) {
+                        for (int b = 0; b < kDotBatch; b++) {
                             const uint32_t a = (v[b][0] & h[k][hh][0]) ^ (v[b][1] & h[k][hh][1]) ^
                                                (v[b][2] & h[k][hh][2]) ^ (v[b][3] & h[k][hh][3]);
-                            pl[k][hh] ^= (__popc(a) & 1u) << (c0 + b);
+                            cnt[b / 4] += (uint32_t)__popc(a) << (8 * (b % 4));
                         }
+#pragma unroll
+                        for (int q = 0; q < kDotBatch / 4; q++)
+                            pl[k][hh] ^= (cnt[q] & 0x01010101u) << (c0 / 4 + q);
                     }
+                }
             }
 #pragma unroll
             for (int k = 0; k < kDotPreds; k++) {
@@ -341,31 +352,159 @@ __global__ void __launch_bounds__(512) k_onehot_dots(const __grid_constant__ Dot
                     uint32_t m = pl[k][hh];
 #pragma unroll
                     for (int off = 16; off > 0; off >>= 1) m ^= __shfl_xor_sync(0xFFFFFFFFu, m, off);
-                    mask[k][j][hh] ^= m;
+                    if (lane == 0) zs[warp][k][j][hh] ^= m;
                 }
             }
         }
     }
+    __syncthreads();
+    // server i: first half with share i, second half with share i + 1; element c leaves
+    // bit 8 (c % 4) + c / 4 for bit c of the packed output word
+    if (threadIdx.x < np * 3) {
+        const uint32_t k = threadIdx.x / 3, i = threadIdx.x % 3;
+        uint32_t zp = 0;
+        for (uint32_t q = 0; q < warps; q++) zp ^= zs[q][k][i][0] ^ zs[q][k][(i + 1) % 3][1];
+        uint32_t z = 0;
+#pragma unroll
+        for (uint32_t c = 0; c < 32; c++) z |= ((zp >> (8 * (c % 4) + c / 4)) & 1u) << c;
+        P.zbits[k][(uint64_t)i * nwords + wd] = z;
+    }
+}
+
+// The same pass for rows of W = 128 * warps words (2^12 <= D <= 2^16), with the element
+// rows staged through shared memory so that two batches are always in flight while a
+// third is combined.  Lane l of warp q owns words [128 q + 4 l, 128 q + 4 l + 4) of every
+// row: it copies them with its own 16-byte cp.async into its own slots and reads back
+// only those, so the pipeline needs no barrier.  A step is one share set and 8 elements;
+// the CTA's 32 elements and 3 share sets take 12 steps.  The next share set's half-vector
+// slices are loaded into registers during the last step of the current one.
+constexpr int kPipeStages = 3;
+constexpr int kPipeSteps = 3 * (32 / kDotBatch);
+constexpr uint32_t kPipeSmemPerWarp = kPipeStages * kDotBatch * 32 * 16;
+
+__device__ __forceinline__ void load_halves(const DotParams& P, uint32_t W, uint32_t w0, uint32_t np, int j,
+                                            uint32_t h[kDotPreds][2][4]) {
+#pragma unroll
+    for (int k = 0; k < kDotPreds; k++) {
+        if ((uint32_t)k < np) {
+            const uint4 a = __ldg(reinterpret_cast<const uint4*>(P.hv + (uint64_t)(P.half_base[k] + j * 2) * W + w0));
+            const uint4 b = __ldg(reinterpret_cast<const uint4*>(
+                P.hv + (uint64_t)(P.half_base[k] + ((j + 2) % 3) * 2 + 1) * W + w0));
+            h[k][0][0] = a.x; h[k][0][1] = a.y; h[k][0][2] = a.z; h[k][0][3] = a.w;
+            h[k][1][0] = b.x; h[k][1][1] = b.y; h[k][1][2] = b.z; h[k][1][3] = b.w;
+        } else {
+#pragma unroll
+            for (int r = 0; r < 4; r++) h[k][0][r] = h[k][1][r] = 0;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(512) k_onehot_dots_pipe(const __grid_constant__ DotParams P) {
+    extern __shared__ __align__(16) unsigned char dsmem[];
+    __shared__ uint32_t zs[16][kDotPreds][3][2];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+    const uint32_t W = P.words, np = P.n_preds;
+    const uint64_t nwords = (P.n_elems + 31) / 32;
+    const uint64_t wd = blockIdx.x;
+    const uint64_t base = wd * 32;
+    const uint32_t w0 = warp * 128 + lane * 4;
+    // slot (stage s, element b) of this lane: mine[(s * kDotBatch + b) * 32]
+    uint4* mine = reinterpret_cast<uint4*>(dsmem + (size_t)warp * kPipeSmemPerWarp) + lane;
     if (lane == 0) {
 #pragma unroll
         for (int k = 0; k < kDotPreds; k++)
 #pragma unroll
-            for (int j = 0; j < 3; j++) {
-                zs[warp][k][j][0] = mask[k][j][0];
-                zs[warp][k][j][1] = mask[k][j][1];
-            }
+            for (int j = 0; j < 3; j++) zs[warp][k][j][0] = zs[warp][k][j][1] = 0;
     }
+    auto issue = [&](int t) {
+        const int j = t / (32 / kDotBatch), c0 = (t % (32 / kDotBatch)) * kDotBatch, st = t % kPipeStages;
+#pragma unroll
+        for (int b = 0; b < kDotBatch; b++) {
+            const uint64_t e = base + c0 + b;
+            const bool ok = e < P.n_elems;     // past the table's end: zero-filled, nothing read
+            cp_async16(mine + (st * kDotBatch + b) * 32, P.share[j] + (ok ? e : base) * W + w0, ok ? 16u : 0u);
+        }
+        cp_async_commit();
+    };
+    issue(0);
+    issue(1);
+    uint32_t h[kDotPreds][2][4], hn[kDotPreds][2][4];
+    load_halves(P, W, w0, np, 0, h);
+    uint32_t pl[kDotPreds][2];
+#pragma unroll 1
+    for (int t = 0; t < kPipeSteps; t++) {
+        if (t + 2 < kPipeSteps) issue(t + 2);
+        else cp_async_commit();                       // an empty group keeps the count uniform
+        cp_async_wait<2>();                           // this lane's copies of step t have landed
+        const int j = t / (32 / kDotBatch), cb = t % (32 / kDotBatch), st = t % kPipeStages;
+        if (cb == 0) {
+#pragma unroll
+            for (int k = 0; k < kDotPreds; k++) pl[k][0] = pl[k][1] = 0;
+        }
+        const bool last = cb == 32 / kDotBatch - 1;
+        if (last && j < 2) load_halves(P, W, w0, np, j + 1, hn);
+        uint32_t v[kDotBatch][4];
+#pragma unroll
+        for (int b = 0; b < kDotBatch; b++) {
+            const uint4 x = mine[(st * kDotBatch + b) * 32];
+            v[b][0] = x.x; v[b][1] = x.y; v[b][2] = x.z; v[b][3] = x.w;
+        }
+#pragma unroll
+        for (int k = 0; k < kDotPreds; k++) {
+            if ((uint32_t)k >= np) break;
+#pragma unroll
+            for (int hh = 0; hh < 2; hh++) {
+                uint32_t cnt[kDotBatch / 4] = {};
+#pragma unroll
+                for (int b = 0; b < kDotBatch; b++) {
+                    const uint32_t a = (v[b][0] & h[k][hh][0]) ^ (v[b][1] & h[k][hh][1]) ^
+                                       (v[b][2] & h[k][hh][2]) ^ (v[b][3] & h[k][hh][3]);
+                    cnt[b / 4] += (uint32_t)__popc(a) << (8 * (b % 4));
+                }
+#pragma unroll
+                for (int q = 0; q < kDotBatch / 4; q++)
+                    pl[k][hh] ^= (cnt[q] & 0x01010101u) << (cb * (kDotBatch / 4) + q);
+            }
+        }
+        if (last) {
+#pragma unroll
+            for (int k = 0; k < kDotPreds; k++) {
+                if ((uint32_t)k >= np) break;
+#pragma unroll
+                for (int hh = 0; hh < 2; hh++) {
+                    uint32_t m = pl[k][hh];
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) m ^= __shfl_xor_sync(0xFFFFFFFFu, m, off);
+                    if (lane == 0) zs[warp][k][j][hh] ^= m;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kDotPreds; k++)
+#pragma unroll
+                for (int hh = 0; hh < 2; hh++)
+#pragma unroll
+                    for (int r = 0; r < 4; r++) h[k][hh][r] = hn[k][hh][r];
+        }
+    }
+    cp_async_wait<0>();
     __syncthreads();
-    // server i: first half with share i, second half with share i + 1
     if (threadIdx.x < np * 3) {
         const uint32_t k = threadIdx.x / 3, i = threadIdx.x % 3;
+        uint32_t zp = 0;
+        for (uint32_t q = 0; q < warps; q++) zp ^= zs[q][k][i][0] ^ zs[q][k][(i + 1) % 3][1];
         uint32_t z = 0;
-        for (uint32_t q = 0; q < warps; q++) z ^= zs[q][k][i][0] ^ zs[q][k][(i + 1) % 3][1];
+#pragma unroll
+        for (uint32_t c = 0; c < 32; c++) z |= ((zp >> (8 * (c % 4) + c / 4)) & 1u) << c;
         P.zbits[k][(uint64_t)i * nwords + wd] = z;
     }
 }
 
 void launch_dots(const DotParams& D, uint64_t nwords, int /*sm_count*/, cudaStream_t s) {
+    if (D.words >= 128 && D.words <= 128 * 16) {
+        const uint32_t warps = D.words / 128;
+        k_onehot_dots_pipe<<<(unsigned)nwords, warps * 32, warps * kPipeSmemPerWarp, s>>>(D);
+        return;
+    }
     const uint32_t warps = D.words >= 128 ? std::min<uint32_t>(16, D.words / 128) : 1u;
     k_onehot_dots<<<(unsigned)nwords, warps * 32, 0, s>>>(D);
 }
@@ -694,6 +833,8 @@ oblivgm_status set_onehot_attrs() {
     cudaError_t e = cudaFuncSetAttribute(k_onehot_evalall, cudaFuncAttributeMaxDynamicSharedMemorySize, kTableBytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_onehot_evalall32, cudaFuncAttributeMaxDynamicSharedMemorySize, kEvalAll32Smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_onehot_dots_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 * kPipeSmemPerWarp);
     return e == cudaSuccess ? OBLIVGM_OK : cuda_fail(e, "one-hot kernel attributes");
 }
 
