@@ -371,13 +371,15 @@ __global__ void __launch_bounds__(512) k_onehot_dots(const __grid_constant__ Dot
     }
 }
 
-// The same pass for rows of W = 128 * warps words (2^12 <= D <= 2^16), with the element
+// The same pass for rows of W = 128 * warps words (2^12 <= D <= 2^16), persistent (one
+// CTA per SM walks the 32-element words wd = blockIdx.x, + gridDim.x, ...) with the element
 // rows staged through shared memory so that two batches are always in flight while a
-// third is combined.  Lane l of warp q owns words [128 q + 4 l, 128 q + 4 l + 4) of every
-// row: it copies them with its own 16-byte cp.async into its own slots and reads back
-// only those, so the pipeline needs no barrier.  A step is one share set and 8 elements;
-// the CTA's 32 elements and 3 share sets take 12 steps.  The next share set's half-vector
-// slices are loaded into registers during the last step of the current one.
+// third is combined, across word boundaries too.  Lane l of warp q owns words
+// [128 q + 4 l, 128 q + 4 l + 4) of every row: it copies them with its own 16-byte
+// cp.async into its own slots and reads back only those, so the pipeline needs no
+// barrier.  A step is one share set and 8 elements; a word's 32 elements and 3 share sets
+// take 12 steps.  The next share set's half-vector slices are loaded into registers
+// during the last step of the current one.
 constexpr int kPipeStages = 3;
 constexpr int kPipeSteps = 3 * (32 / kDotBatch);
 constexpr uint32_t kPipeSmemPerWarp = kPipeStages * kDotBatch * 32 * 16;
@@ -401,23 +403,21 @@ __device__ __forceinline__ void load_halves(const DotParams& P, uint32_t W, uint
 
 __global__ void __launch_bounds__(512) k_onehot_dots_pipe(const __grid_constant__ DotParams P) {
     extern __shared__ __align__(16) unsigned char dsmem[];
-    __shared__ uint32_t zs[16][kDotPreds][3][2];
+    __shared__ uint32_t zs[2][16][kDotPreds][3][2];    // by word parity: per warp, masks per (pred, share, half)
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
     const uint32_t W = P.words, np = P.n_preds;
     const uint64_t nwords = (P.n_elems + 31) / 32;
-    const uint64_t wd = blockIdx.x;
-    const uint64_t base = wd * 32;
+    if (blockIdx.x >= nwords) return;
+    const uint64_t my_words = (nwords - 1 - blockIdx.x) / gridDim.x + 1;
+    const uint64_t total = my_words * kPipeSteps;
     const uint32_t w0 = warp * 128 + lane * 4;
     // slot (stage s, element b) of this lane: mine[(s * kDotBatch + b) * 32]
     uint4* mine = reinterpret_cast<uint4*>(dsmem + (size_t)warp * kPipeSmemPerWarp) + lane;
-    if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < kDotPreds; k++)
-#pragma unroll
-            for (int j = 0; j < 3; j++) zs[warp][k][j][0] = zs[warp][k][j][1] = 0;
-    }
-    auto issue = [&](int t) {
-        const int j = t / (32 / kDotBatch), c0 = (t % (32 / kDotBatch)) * kDotBatch, st = t % kPipeStages;
+    // step T: word blockIdx.x + (T / 12) gridDim.x, share set (T % 12) / 4, elements 8 (T % 4) ..
+    auto issue = [&](uint64_t T) {
+        const int t = (int)(T % kPipeSteps), st = (int)(T % kPipeStages);
+        const int j = t / (32 / kDotBatch), c0 = (t % (32 / kDotBatch)) * kDotBatch;
+        const uint64_t base = (blockIdx.x + (T / kPipeSteps) * gridDim.x) * 32;
 #pragma unroll
         for (int b = 0; b < kDotBatch; b++) {
             const uint64_t e = base + c0 + b;
@@ -427,22 +427,25 @@ __global__ void __launch_bounds__(512) k_onehot_dots_pipe(const __grid_constant_
         cp_async_commit();
     };
     issue(0);
-    issue(1);
+    if (total > 1) issue(1);
+    else cp_async_commit();
     uint32_t h[kDotPreds][2][4], hn[kDotPreds][2][4];
     load_halves(P, W, w0, np, 0, h);
     uint32_t pl[kDotPreds][2];
 #pragma unroll 1
-    for (int t = 0; t < kPipeSteps; t++) {
-        if (t + 2 < kPipeSteps) issue(t + 2);
+    for (uint64_t T = 0; T < total; T++) {
+        if (T + 2 < total) issue(T + 2);
         else cp_async_commit();                       // an empty group keeps the count uniform
-        cp_async_wait<2>();                           // this lane's copies of step t have landed
-        const int j = t / (32 / kDotBatch), cb = t % (32 / kDotBatch), st = t % kPipeStages;
+        cp_async_wait<2>();                           // this lane's copies of step T have landed
+        const int t = (int)(T % kPipeSteps), st = (int)(T % kPipeStages);
+        const int j = t / (32 / kDotBatch), cb = t % (32 / kDotBatch);
+        const uint32_t par = (uint32_t)(T / kPipeSteps) & 1u;
         if (cb == 0) {
 #pragma unroll
             for (int k = 0; k < kDotPreds; k++) pl[k][0] = pl[k][1] = 0;
         }
         const bool last = cb == 32 / kDotBatch - 1;
-        if (last && j < 2) load_halves(P, W, w0, np, j + 1, hn);
+        if (last) load_halves(P, W, w0, np, j < 2 ? j + 1 : 0, hn);
         uint32_t v[kDotBatch][4];
 #pragma unroll
         for (int b = 0; b < kDotBatch; b++) {
@@ -475,7 +478,7 @@ __global__ void __launch_bounds__(512) k_onehot_dots_pipe(const __grid_constant_
                     uint32_t m = pl[k][hh];
 #pragma unroll
                     for (int off = 16; off > 0; off >>= 1) m ^= __shfl_xor_sync(0xFFFFFFFFu, m, off);
-                    if (lane == 0) zs[warp][k][j][hh] ^= m;
+                    if (lane == 0) zs[par][warp][k][j][hh] = m;
                 }
             }
 #pragma unroll
@@ -485,24 +488,33 @@ __global__ void __launch_bounds__(512) k_onehot_dots_pipe(const __grid_constant_
 #pragma unroll
                     for (int r = 0; r < 4; r++) h[k][hh][r] = hn[k][hh][r];
         }
+        if (t == kPipeSteps - 1) {
+            // the word's masks are complete: combine the warps' and write the packed bits.
+            // zs is double-buffered by word parity, so one barrier per word suffices.
+            __syncthreads();
+            if (threadIdx.x < np * 3) {
+                const uint64_t wd = blockIdx.x + (T / kPipeSteps) * gridDim.x;
+                const uint32_t k = threadIdx.x / 3, i = threadIdx.x % 3;
+                uint32_t zp = 0;
+                for (uint32_t q = 0; q < warps; q++) zp ^= zs[par][q][k][i][0] ^ zs[par][q][k][(i + 1) % 3][1];
+                // element c sits at bit 8 (c % 4) + c / 4
+                uint32_t z = 0;
+#pragma unroll
+                for (uint32_t c = 0; c < 32; c++) z |= ((zp >> (8 * (c % 4) + c / 4)) & 1u) << c;
+                P.zbits[k][(uint64_t)i * nwords + wd] = z;
+            }
+        }
     }
     cp_async_wait<0>();
-    __syncthreads();
-    if (threadIdx.x < np * 3) {
-        const uint32_t k = threadIdx.x / 3, i = threadIdx.x % 3;
-        uint32_t zp = 0;
-        for (uint32_t q = 0; q < warps; q++) zp ^= zs[q][k][i][0] ^ zs[q][k][(i + 1) % 3][1];
-        uint32_t z = 0;
-#pragma unroll
-        for (uint32_t c = 0; c < 32; c++) z |= ((zp >> (8 * (c % 4) + c / 4)) & 1u) << c;
-        P.zbits[k][(uint64_t)i * nwords + wd] = z;
-    }
 }
 
-void launch_dots(const DotParams& D, uint64_t nwords, int /*sm_count*/, cudaStream_t s) {
+void launch_dots(const DotParams& D, uint64_t nwords, int sm_count, cudaStream_t s) {
     if (D.words >= 128 && D.words <= 128 * 16) {
+        // persistent: as many CTAs as fit on the SMs (one of 16 warps per SM at D = 2^16)
         const uint32_t warps = D.words / 128;
-        k_onehot_dots_pipe<<<(unsigned)nwords, warps * 32, warps * kPipeSmemPerWarp, s>>>(D);
+        const uint32_t per_sm = std::max<uint32_t>(1, std::min<uint32_t>(227u * 1024 / (warps * kPipeSmemPerWarp + 4096), 32 / warps));
+        const uint64_t grid = std::min<uint64_t>(nwords, (uint64_t)sm_count * per_sm);
+        k_onehot_dots_pipe<<<(unsigned)grid, warps * 32, warps * kPipeSmemPerWarp, s>>>(D);
         return;
     }
     const uint32_t warps = D.words >= 128 ? std::min<uint32_t>(16, D.words / 128) : 1u;

@@ -2,7 +2,10 @@
 
 Every compared share bit is equal; the reconstruction equals the plaintext
 predicates; domains cover one partial word (n = 3), a few words (n = 6),
-whole warps of words (n = 10) and the vector-load path (n = 12)."""
+whole warps of words (n = 10), the staged path with one warp per 32 elements
+(n = 12), with two warps and more words than the persistent grid has CTAs
+(n = 13, 70,001 elements), and the bench's domain (n = 16) with a ragged last
+word and CTAs that each take two words."""
 import numpy as np
 import pytest
 
@@ -63,6 +66,33 @@ def test_onehot_parity(ctx, n, n_elems):
         last = from_dev(outs[grp][0])[-1]
         if n_elems % 32:
             assert last >> (n_elems % 32) == 0
+
+
+@pytest.mark.parametrize("n,n_elems", [(13, 70_001), (16, 5_003)])
+def test_onehot_parity_persistent_grid(ctx, n, n_elems):
+    """More 32-element words than the dot pass's persistent grid has CTAs, so CTAs carry
+    their copy pipeline from one word into the next.  Every element of every group is
+    checked against the plaintext; group 0's shares against the oracle on a sample that
+    covers the first words, words across the table and the ragged last word (the
+    oracle's EvalAll over 2^16 positions is too slow for all three groups)."""
+    g = W.rng(100 + n)
+    top = (1 << n) - 1
+    vals = W.uniform_attrs(g, 2, n_elems, n)
+    tab = W.onehot_table(vals, n, g)
+    _load(ctx, 0, tab)
+    preds = [W.eq_pred(0, 0, 0, int(vals[0, 3])),
+             W.range_pred(0, 1, 1, top // 4, top), W.eq_pred(0, 0, 1, int(vals[0, 5])),
+             W.range_pred(0, 0, 2, 0, top // 2)]
+    toks = P.keygen_onehot(preds, n, bytes([n]) * 16)
+    got, outs = _run(ctx, toks, 3, [n_elems] * 3, 17)
+    for grp in range(3):
+        assert np.array_equal(oracle.reconstruct_bits(got[grp]), oracle.plain_group(preds, grp, vals)), grp
+        last = from_dev(outs[grp][0])[-1]
+        assert last >> (n_elems % 32) == 0
+    idx = np.unique(np.concatenate([np.arange(0, 64), np.arange(0, n_elems, n_elems // 24),
+                                    np.arange(n_elems - 40, n_elems)]))
+    want = oracle.filter_onehot(toks, 17, PRF, [(tab["shares"], n)], 0, idx)
+    assert np.array_equal(got[0][:, idx], want)
 
 
 def test_onehot_fig1_example(ctx):
