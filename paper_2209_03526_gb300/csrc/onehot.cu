@@ -417,83 +417,96 @@ __global__ void __launch_bounds__(512) k_onehot_dots_pipe(const __grid_constant_
     auto issue = [&](uint64_t T) {
         const int t = (int)(T % kPipeSteps), st = (int)(T % kPipeStages);
         const int j = t / (32 / kDotBatch), c0 = (t % (32 / kDotBatch)) * kDotBatch;
-        const uint64_t base = (blockIdx.x + (T / kPipeSteps) * gridDim.x) * 32;
+        const uint64_t e0 = (blockIdx.x + (T / kPipeSteps) * gridDim.x) * 32 + c0;
+        uint4* dst = mine + st * kDotBatch * 32;
+        const uint32_t* src = P.share[j] + e0 * W + w0;
+        if (e0 + kDotBatch <= P.n_elems) {
 #pragma unroll
-        for (int b = 0; b < kDotBatch; b++) {
-            const uint64_t e = base + c0 + b;
-            const bool ok = e < P.n_elems;     // past the table's end: zero-filled, nothing read
-            cp_async16(mine + (st * kDotBatch + b) * 32, P.share[j] + (ok ? e : base) * W + w0, ok ? 16u : 0u);
+            for (int b = 0; b < kDotBatch; b++) cp_async16(dst + b * 32, src + (size_t)b * W, 16u);
+        } else {
+            // the table's last word: rows past its end are zero-filled, nothing read
+            const uint32_t* row0 = P.share[j] + (e0 - c0) * W + w0;
+#pragma unroll
+            for (int b = 0; b < kDotBatch; b++) {
+                const bool ok = e0 + b < P.n_elems;
+                cp_async16(dst + b * 32, ok ? src + (size_t)b * W : row0, ok ? 16u : 0u);
+            }
         }
         cp_async_commit();
     };
-    issue(0);
-    if (total > 1) issue(1);
-    else cp_async_commit();
+    for (int d = 0; d < kPipeStages - 1; d++) {
+        if ((uint64_t)d < total) issue(d);
+        else cp_async_commit();                       // an empty group keeps the count uniform
+    }
     uint32_t h[kDotPreds][2][4], hn[kDotPreds][2][4];
     load_halves(P, W, w0, np, 0, h);
-    uint32_t pl[kDotPreds][2];
+    constexpr int kBatches = 32 / kDotBatch;          // steps per (word, share set)
 #pragma unroll 1
-    for (uint64_t T = 0; T < total; T++) {
-        if (T + 2 < total) issue(T + 2);
-        else cp_async_commit();                       // an empty group keeps the count uniform
-        cp_async_wait<2>();                           // this lane's copies of step T have landed
-        const int t = (int)(T % kPipeSteps), st = (int)(T % kPipeStages);
-        const int j = t / (32 / kDotBatch), cb = t % (32 / kDotBatch);
-        const uint32_t par = (uint32_t)(T / kPipeSteps) & 1u;
-        if (cb == 0) {
+    for (uint64_t T4 = 0; T4 < total; T4 += kBatches) {
+        const int j = (int)((T4 / kBatches) % 3);
+        const uint32_t par = (uint32_t)(T4 / kPipeSteps) & 1u;
+        uint32_t pl[kDotPreds][2];
 #pragma unroll
-            for (int k = 0; k < kDotPreds; k++) pl[k][0] = pl[k][1] = 0;
-        }
-        const bool last = cb == 32 / kDotBatch - 1;
-        if (last) load_halves(P, W, w0, np, j < 2 ? j + 1 : 0, hn);
-        uint32_t v[kDotBatch][4];
+        for (int k = 0; k < kDotPreds; k++) pl[k][0] = pl[k][1] = 0;
 #pragma unroll
-        for (int b = 0; b < kDotBatch; b++) {
-            const uint4 x = mine[(st * kDotBatch + b) * 32];
-            v[b][0] = x.x; v[b][1] = x.y; v[b][2] = x.z; v[b][3] = x.w;
+        for (int cb = 0; cb < kBatches; cb++) {
+            const uint64_t T = T4 + cb;
+            if (T + kPipeStages - 1 < total) issue(T + kPipeStages - 1);
+            else cp_async_commit();
+            cp_async_wait<kPipeStages - 1>();         // this lane's copies of step T have landed
+            if (cb == kBatches - 1) load_halves(P, W, w0, np, j < 2 ? j + 1 : 0, hn);
+            const uint4* slot = mine + (int)(T % kPipeStages) * kDotBatch * 32;
+            uint32_t v[kDotBatch][4];
+#pragma unroll
+            for (int b = 0; b < kDotBatch; b++) {
+                const uint4 x = slot[b * 32];
+                v[b][0] = x.x; v[b][1] = x.y; v[b][2] = x.z; v[b][3] = x.w;
+            }
+#pragma unroll
+            for (int k = 0; k < kDotPreds; k++) {
+                if ((uint32_t)k >= np) break;
+#pragma unroll
+                for (int hh = 0; hh < 2; hh++) {
+                    uint32_t cnt[kDotBatch / 4] = {};
+#pragma unroll
+                    for (int b = 0; b < kDotBatch; b++) {
+                        const uint32_t a = (v[b][0] & h[k][hh][0]) ^ (v[b][1] & h[k][hh][1]) ^
+                                           (v[b][2] & h[k][hh][2]) ^ (v[b][3] & h[k][hh][3]);
+                        cnt[b / 4] += (uint32_t)__popc(a) << (8 * (b % 4));
+                    }
+                    // bit 8 f + q, q = cb * (kDotBatch / 4) + (b / 4), a compile-time shift
+#pragma unroll
+                    for (int q = 0; q < kDotBatch / 4; q++) {
+                        constexpr uint32_t M = 0x01010101u;
+                        const int sh = cb * (kDotBatch / 4) + q;
+                        pl[k][hh] ^= (cnt[q] << sh) & (M << sh);
+                    }
+                }
+            }
         }
 #pragma unroll
         for (int k = 0; k < kDotPreds; k++) {
             if ((uint32_t)k >= np) break;
 #pragma unroll
             for (int hh = 0; hh < 2; hh++) {
-                uint32_t cnt[kDotBatch / 4] = {};
+                uint32_t m = pl[k][hh];
 #pragma unroll
-                for (int b = 0; b < kDotBatch; b++) {
-                    const uint32_t a = (v[b][0] & h[k][hh][0]) ^ (v[b][1] & h[k][hh][1]) ^
-                                       (v[b][2] & h[k][hh][2]) ^ (v[b][3] & h[k][hh][3]);
-                    cnt[b / 4] += (uint32_t)__popc(a) << (8 * (b % 4));
-                }
-#pragma unroll
-                for (int q = 0; q < kDotBatch / 4; q++)
-                    pl[k][hh] ^= (cnt[q] & 0x01010101u) << (cb * (kDotBatch / 4) + q);
+                for (int off = 16; off > 0; off >>= 1) m ^= __shfl_xor_sync(0xFFFFFFFFu, m, off);
+                if (lane == 0) zs[par][warp][k][j][hh] = m;
             }
         }
-        if (last) {
 #pragma unroll
-            for (int k = 0; k < kDotPreds; k++) {
-                if ((uint32_t)k >= np) break;
+        for (int k = 0; k < kDotPreds; k++)
 #pragma unroll
-                for (int hh = 0; hh < 2; hh++) {
-                    uint32_t m = pl[k][hh];
+            for (int hh = 0; hh < 2; hh++)
 #pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) m ^= __shfl_xor_sync(0xFFFFFFFFu, m, off);
-                    if (lane == 0) zs[par][warp][k][j][hh] = m;
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < kDotPreds; k++)
-#pragma unroll
-                for (int hh = 0; hh < 2; hh++)
-#pragma unroll
-                    for (int r = 0; r < 4; r++) h[k][hh][r] = hn[k][hh][r];
-        }
-        if (t == kPipeSteps - 1) {
+                for (int r = 0; r < 4; r++) h[k][hh][r] = hn[k][hh][r];
+        if (j == 2) {
             // the word's masks are complete: combine the warps' and write the packed bits.
             // zs is double-buffered by word parity, so one barrier per word suffices.
             __syncthreads();
             if (threadIdx.x < np * 3) {
-                const uint64_t wd = blockIdx.x + (T / kPipeSteps) * gridDim.x;
+                const uint64_t wd = blockIdx.x + (T4 / kPipeSteps) * gridDim.x;
                 const uint32_t k = threadIdx.x / 3, i = threadIdx.x % 3;
                 uint32_t zp = 0;
                 for (uint32_t q = 0; q < warps; q++) zp ^= zs[par][q][k][i][0] ^ zs[par][q][k][(i + 1) % 3][1];
