@@ -7,16 +7,18 @@
 // for the share j its key pair is tied to; it XORs its two results, re-shares them
 // in binary RSS and the query element's predicates are folded (AND, XOR or OR) in binary RSS.
 //
-// Three kernels per query:
-//  * k_onehot_evalall: every key half at every position (the walk code of the masked
-//    mode with Z_2 outputs): the shared top levels are walked once per block of 8
-//    positions and the last 3 levels expanded depth first;
-//  * k_onehot_dots: per attribute column, one pass over the elements' three share
-//    rows serves up to 4 predicates on that column: a CTA per 32 elements, its warps
-//    splitting the rows, each lane holding its slice of the half vectors in
-//    registers; parities are reduced by ballots and each server's bit written packed;
-//  * k_onehot_fold: per group, each element's bits are re-shared in binary RSS
-//    and folded in token order; results are packed 32 elements per word.
+// Three steps per query:
+//  * EvalAll, every key half at every position: k_onehot_evalall32 (n >= 5) walks the
+//    shared top levels once per block of 32 positions and expands the last 5 depth
+//    first; k_onehot_evalall (n < 5) covers blocks of up to 8 positions;
+//  * the dot pass, one streaming pass over an attribute column's three share rows for
+//    up to 4 predicates on that column: k_onehot_dots_pipe (D >= 2^12, persistent,
+//    rows staged by per-lane cp.async, warps splitting the rows, each lane holding its
+//    slice of the half vectors in registers) or k_onehot_dots (smaller D); parities
+//    are XOR-reduced over the warp and each server's bit written packed;
+//  * k_onehot_fold: every group in one launch, each element's bits re-shared in
+//    binary RSS and folded in token order (PRF AES from shared-memory T-tables);
+//    results are packed 32 elements per word.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -534,52 +536,75 @@ void launch_dots(const DotParams& D, uint64_t nwords, int sm_count, cudaStream_t
     k_onehot_dots<<<(unsigned)nwords, warps * 32, 0, s>>>(D);
 }
 
-// Per group: each element's predicate bits are re-shared in binary RSS and folded in
-// token order; one thread per element, results packed by warp ballots.
-struct FoldParams {
-    uint32_t rk_prf[3][44];
-    const uint32_t* te4;               // global-memory T-tables for the PRF
-    const uint32_t* zbase;             // the query's packed predicate bits
-    const uint64_t* zoff;              // per predicate of the group: word offset of its [3][nwords] block
-    const uint32_t* steps;             // per predicate: its index in the token | combine << 16
+// All groups of a query in one launch: each element's predicate bits are re-shared in
+// binary RSS and folded in token order.  A warp takes one (group, 32-element word) item
+// at a time, one lane per element, results packed by warp ballots.  The PRF's AES reads
+// the bank-replicated shared-memory T-tables (one persistent CTA per SM).
+struct FoldGroup {
     uint32_t* out[3];
     uint64_t n_elems;
+    uint64_t word_begin;     // first item of the group in the launch's item space
+    uint32_t first;          // index of the group's first predicate in zoff / steps
     uint32_t n_preds;
-    uint32_t table_id, query_id;
+    uint32_t table_id;
+    uint32_t pad;
 };
 
-__device__ __forceinline__ uint32_t prf_bit(const GlobalTab& T, const uint32_t* rk, uint64_t el, uint32_t step,
+struct FoldParams {
+    uint32_t rk_prf[3][44];
+    const uint32_t* te0;
+    const uint32_t* zbase;             // the query's packed predicate bits
+    const uint64_t* zoff;              // per predicate (group order): word offset of its [3][nwords] block
+    const uint32_t* steps;             // per predicate: its index in the token | combine << 16
+    const FoldGroup* groups;
+    uint64_t total_words;
+    uint32_t n_groups;
+    uint32_t query_id;
+};
+
+template <class Tab>
+__device__ __forceinline__ uint32_t prf_bit(const Tab& T, const uint32_t* rk, uint64_t el, uint32_t step,
                                             uint32_t table, uint32_t query) {
     const uint32_t ctr[4] = {(uint32_t)el, (uint32_t)(el >> 32), step | (table << 16), query};
     return aes_one_w0(T, rk, ctr) & 1u;
 }
 
 // binary re-share: r_i = z_i xor F(k_i) xor F(k_{i-1})
-__device__ __forceinline__ void reshare_bits(const GlobalTab& T, const FoldParams& P, const uint32_t z[3],
+template <class Tab>
+__device__ __forceinline__ void reshare_bits(const Tab& T, const FoldParams& P, uint32_t table, const uint32_t z[3],
                                              uint32_t out[3], uint64_t el, uint32_t step) {
     uint32_t f[3];
 #pragma unroll 1
-    for (int i = 0; i < 3; i++) f[i] = prf_bit(T, P.rk_prf[i], el, step, P.table_id, P.query_id);
+    for (int i = 0; i < 3; i++) f[i] = prf_bit(T, P.rk_prf[i], el, step, table, P.query_id);
     out[0] = z[0] ^ f[0] ^ f[2];
     out[1] = z[1] ^ f[1] ^ f[0];
     out[2] = z[2] ^ f[2] ^ f[1];
 }
 
-__global__ void __launch_bounds__(256) k_onehot_fold(const __grid_constant__ FoldParams P) {
-    const GlobalTab T{P.te4};
-    const uint64_t nwords = (P.n_elems + 31) / 32;
-    const uint32_t lane = threadIdx.x & 31;
-    for (uint64_t e0 = (uint64_t)blockIdx.x * blockDim.x; e0 < nwords * 32; e0 += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t e = e0 + threadIdx.x;
-        const uint64_t wd = e / 32;
-        const bool valid = e < P.n_elems;
+__global__ void __launch_bounds__(512, 1) k_onehot_fold(const __grid_constant__ FoldParams P) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    fill_tables(reinterpret_cast<uint32_t*>(smem), P.te0);
+    __syncthreads();
+    const SmemTab T{reinterpret_cast<const char*>(smem), lane_offset()};
+    const uint32_t lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+    for (uint64_t item = (uint64_t)blockIdx.x * warps + (threadIdx.x >> 5); item < P.total_words;
+         item += (uint64_t)gridDim.x * warps) {
+        uint32_t g = 0;
+        while (g + 1 < P.n_groups && P.groups[g + 1].word_begin <= item) g++;
+        const FoldGroup& G = P.groups[g];
+        const uint64_t nwords = (G.n_elems + 31) / 32;
+        const uint64_t wd = item - G.word_begin;
+        const uint64_t e = wd * 32 + lane;
+        const bool valid = e < G.n_elems;
         uint32_t acc[3] = {0, 0, 0};
-        for (uint32_t k = 0; k < P.n_preds; k++) {
+        for (uint32_t k = 0; k < G.n_preds; k++) {
+            const uint64_t zo = P.zoff[G.first + k];
+            const uint32_t sc = P.steps[G.first + k];
             uint32_t z[3], b[3];
 #pragma unroll
-            for (int i = 0; i < 3; i++) z[i] = valid ? (P.zbase[P.zoff[k] + (uint64_t)i * nwords + wd] >> lane) & 1u : 0u;
-            const uint32_t step = P.steps[k] & 0xFFFFu, combine = P.steps[k] >> 16;
-            reshare_bits(T, P, z, b, e, step);
+            for (int i = 0; i < 3; i++) z[i] = (P.zbase[zo + (uint64_t)i * nwords + wd] >> lane) & 1u;
+            const uint32_t step = sc & 0xFFFFu, combine = sc >> 16;
+            reshare_bits(T, P, G.table_id, z, b, e, step);
             if (k == 0) {
                 acc[0] = b[0]; acc[1] = b[1]; acc[2] = b[2];
             } else {
@@ -593,13 +618,13 @@ __global__ void __launch_bounds__(256) k_onehot_fold(const __grid_constant__ Fol
                     const uint32_t pr = (acc[i] & b[i]) ^ (acc[i] & b[i1]) ^ (acc[i1] & b[i]);
                     w[i] = ((acc[i] ^ b[i]) & (0u - lin)) ^ (pr & (0u - prod));
                 }
-                reshare_bits(T, P, w, acc, e, 64u + step);
+                reshare_bits(T, P, G.table_id, w, acc, e, 64u + step);
             }
         }
 #pragma unroll
         for (int i = 0; i < 3; i++) {
             const uint32_t word = __ballot_sync(0xFFFFFFFFu, valid && (acc[i] & 1u));
-            if (lane == 0 && wd < nwords) P.out[i][wd] = word;
+            if (lane == 0) G.out[i][wd] = word;
         }
     }
 }
@@ -730,7 +755,27 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
         }
     }
     const size_t np = gzoff.size();
-    // scratch: keys | halves | group offsets | group steps | half vectors | predicate bits
+    // fold descriptors: the groups with elements, each with its first item
+    std::vector<FoldGroup> fg;
+    uint64_t fold_items = 0;
+    for (uint32_t g = 0; g < n_groups; g++) {
+        const OnehotTable& tb = ctx->onehot_tables.at(q.preds[members[g][0]].table);
+        if (tb.n_elems == 0) continue;
+        FoldGroup G{};
+        for (int j = 0; j < 3; j++) {
+            G.out[j] = out[3 * g + j];
+            if (!G.out[j]) return fail(OBLIVGM_EINVAL, "NULL output pointer");
+        }
+        G.n_elems = tb.n_elems;
+        G.word_begin = fold_items;
+        G.first = (uint32_t)gbegin[g];
+        G.n_preds = (uint32_t)members[g].size();
+        G.table_id = q.preds[members[g][0]].table;
+        fg.push_back(G);
+        fold_items += (tb.n_elems + 31) / 32;
+    }
+    // scratch: keys | halves | group offsets | group steps | key slots | fold groups | half vectors |
+    // predicate bits
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t off_h = up(keys.size() * sizeof(DevKey));
     const size_t off_o = off_h + up(halves.size() * sizeof(HalfDesc));
@@ -747,7 +792,8 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
     uint32_t n_dpf_slots = 0;
     for (const KeySlot& k : slots) n_dpf_slots += k.dcf ? 0u : 1u;
     const size_t off_k = off_s + up(np * sizeof(uint32_t));
-    const size_t off_v = off_k + up(slots.size() * sizeof(KeySlot));
+    const size_t off_g = off_k + up(slots.size() * sizeof(KeySlot));
+    const size_t off_v = off_g + up(fg.size() * sizeof(FoldGroup));
     const size_t off_z = off_v + up(halves.size() * words * sizeof(uint32_t));
     const size_t total = off_z + zwords * sizeof(uint32_t);
     std::vector<unsigned char> img(off_v, 0);
@@ -756,6 +802,7 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
     std::memcpy(img.data() + off_o, gzoff.data(), np * sizeof(uint64_t));
     std::memcpy(img.data() + off_s, gstep.data(), np * sizeof(uint32_t));
     std::memcpy(img.data() + off_k, slots.data(), slots.size() * sizeof(KeySlot));
+    if (!fg.empty()) std::memcpy(img.data() + off_g, fg.data(), fg.size() * sizeof(FoldGroup));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned char* ws = nullptr;
     {
@@ -822,27 +869,20 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
             ctx->launches++;
         }
     }
-    // per AND-group: binary re-share and AND fold, packed outputs
-    for (uint32_t g = 0; g < n_groups; g++) {
-        const OnehotTable& tb = ctx->onehot_tables.at(q.preds[members[g][0]].table);
-        if (tb.n_elems == 0) continue;
+    // every AND-group in one launch: binary re-share and fold, packed outputs
+    if (!fg.empty()) {
         FoldParams F{};
         std::memcpy(F.rk_prf, ctx->rk_prf, sizeof F.rk_prf);
-        F.te4 = ctx->d_te4;
+        F.te0 = ctx->d_te0;
         F.zbase = zbase;
-        F.zoff = reinterpret_cast<const uint64_t*>(ws + off_o) + gbegin[g];
-        F.steps = reinterpret_cast<const uint32_t*>(ws + off_s) + gbegin[g];
-        for (int j = 0; j < 3; j++) {
-            F.out[j] = out[3 * g + j];
-            if (!F.out[j]) return fail(OBLIVGM_EINVAL, "NULL output pointer");
-        }
-        F.n_elems = tb.n_elems;
-        F.n_preds = (uint32_t)members[g].size();
-        F.table_id = q.preds[members[g][0]].table;
+        F.zoff = reinterpret_cast<const uint64_t*>(ws + off_o);
+        F.steps = reinterpret_cast<const uint32_t*>(ws + off_s);
+        F.groups = reinterpret_cast<const FoldGroup*>(ws + off_g);
+        F.total_words = fold_items;
+        F.n_groups = (uint32_t)fg.size();
         F.query_id = query_id;
-        const uint64_t nwords = (tb.n_elems + 31) / 32;
-        const unsigned grid = (unsigned)std::min<uint64_t>((nwords * 32 + 255) / 256, (uint64_t)ctx->sm_count * 8);
-        k_onehot_fold<<<grid, 256, 0, s>>>(F);
+        const unsigned grid = (unsigned)std::min<uint64_t>((fold_items + 15) / 16, (uint64_t)ctx->sm_count);
+        k_onehot_fold<<<grid, 512, kTableBytes, s>>>(F);
         ctx->launches++;
     }
     ce = cudaGetLastError();
@@ -860,6 +900,8 @@ oblivgm_status set_onehot_attrs() {
         e = cudaFuncSetAttribute(k_onehot_evalall32, cudaFuncAttributeMaxDynamicSharedMemorySize, kEvalAll32Smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_onehot_dots_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 * kPipeSmemPerWarp);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_onehot_fold, cudaFuncAttributeMaxDynamicSharedMemorySize, kTableBytes);
     return e == cudaSuccess ? OBLIVGM_OK : cuda_fail(e, "one-hot kernel attributes");
 }
 
