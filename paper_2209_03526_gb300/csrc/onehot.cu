@@ -210,14 +210,14 @@ struct EvalWordParams {
     const KeySlot* slots;
     uint32_t* hv;          // [half][words], zeroed before the launch
     uint32_t words;        // 2^n / 32
-    uint32_t blocks;       // 2^(n - kDfsDepth) work items per key
+    uint32_t blocks;       // 2^(n - kDfsDepth) blocks of positions per key
     uint32_t n_slots;
 };
 
 // Every key at every position, n >= 5.  Work item = (key slot, block of 2^D positions);
 // a range half's two DCF keys are separate items XORed into the same word.
 #ifndef OGM_EVALALL32_THREADS
-#define OGM_EVALALL32_THREADS 512
+#define OGM_EVALALL32_THREADS 768
 #endif
 constexpr int kEvalAll32Threads = OGM_EVALALL32_THREADS;
 constexpr int kEvalAll32Smem = kTableBytes + kDfsDepth * kNodeWords * kEvalAll32Threads * 4;
@@ -231,10 +231,12 @@ __global__ void __launch_bounds__(kEvalAll32Threads, 1) k_onehot_evalall32(const
     __syncthreads();
     const SmemTab T{reinterpret_cast<const char*>(smem), lane_offset()};
     uint32_t* stack = reinterpret_cast<uint32_t*>(smem + kTableBytes) + threadIdx.x;
-    const uint64_t items = (uint64_t)P.n_slots * P.blocks;
     constexpr uint32_t kBits = 1u << kDfsDepth;
     constexpr uint32_t kMask = kBits == 32 ? 0xFFFFFFFFu : ((1u << kBits) - 1u);
-    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < items;
+    // Item x goes to thread x / gridDim.x of CTA x % gridDim.x, which spreads the items,
+    // and the DPF / DCF mix, evenly over the SMs.
+    const uint64_t items = (uint64_t)P.n_slots * P.blocks;
+    for (uint64_t idx = (uint64_t)threadIdx.x * gridDim.x + blockIdx.x; idx < items;
          idx += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t slot = (uint32_t)(idx / P.blocks), b = (uint32_t)(idx % P.blocks);
         const KeySlot S = P.slots[slot];
@@ -581,7 +583,9 @@ __device__ __forceinline__ void reshare_bits(const Tab& T, const FoldParams& P, 
     out[2] = z[2] ^ f[2] ^ f[1];
 }
 
-__global__ void __launch_bounds__(512, 1) k_onehot_fold(const __grid_constant__ FoldParams P) {
+constexpr int kFoldThreads = 768;
+
+__global__ void __launch_bounds__(kFoldThreads, 1) k_onehot_fold(const __grid_constant__ FoldParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
     fill_tables(reinterpret_cast<uint32_t*>(smem), P.te0);
     __syncthreads();
@@ -789,8 +793,6 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
             slots.push_back(KeySlot{H.key0, h, H.cbit ? 0xFFFFFFFFu : 0u, dcf});
             if (H.key1 != kNoKey) slots.push_back(KeySlot{H.key1, h, 0u, dcf});
         }
-    uint32_t n_dpf_slots = 0;
-    for (const KeySlot& k : slots) n_dpf_slots += k.dcf ? 0u : 1u;
     const size_t off_k = off_s + up(np * sizeof(uint32_t));
     const size_t off_g = off_k + up(slots.size() * sizeof(KeySlot));
     const size_t off_v = off_g + up(fg.size() * sizeof(FoldGroup));
@@ -836,8 +838,9 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
         EW.slots = reinterpret_cast<const KeySlot*>(ws + off_k);
         EW.n_slots = (uint32_t)slots.size();
         const uint64_t items = (uint64_t)EW.n_slots * EW.blocks;
-        const unsigned grid = (unsigned)std::min<uint64_t>((items + kEvalAll32Threads - 1) / kEvalAll32Threads,
-                                                           (uint64_t)ctx->sm_count);
+        // every SM, each with an equal share of the items (at least a warp's worth)
+        const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((items + 31) / 32,
+                                                                                 (uint64_t)ctx->sm_count));
         k_onehot_evalall32<<<grid, kEvalAll32Threads, kEvalAll32Smem, s>>>(EW);
     } else {
         const uint64_t items = (uint64_t)halves.size() * (domain >> E.log_block);
@@ -881,8 +884,9 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
         F.total_words = fold_items;
         F.n_groups = (uint32_t)fg.size();
         F.query_id = query_id;
-        const unsigned grid = (unsigned)std::min<uint64_t>((fold_items + 15) / 16, (uint64_t)ctx->sm_count);
-        k_onehot_fold<<<grid, 512, kTableBytes, s>>>(F);
+        const uint64_t warps = kFoldThreads / 32;
+        const unsigned grid = (unsigned)std::min<uint64_t>((fold_items + warps - 1) / warps, (uint64_t)ctx->sm_count);
+        k_onehot_fold<<<grid, kFoldThreads, kTableBytes, s>>>(F);
         ctx->launches++;
     }
     ce = cudaGetLastError();
