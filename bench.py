@@ -340,7 +340,12 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},
             "gpu_launches": launches,
-            "clocks": clocks}
+            "clocks": clocks,
+            # per element: 6 DPF key-half walks per equality predicate, 12 DCF walks per range
+            "secondary_units": {
+                "key_half_walks_per_s": sum(6 if p["kind"] == W.PRED_EQ else 12 for p in preds) * N_VERTICES
+                / (ms_per_step / 1e3),
+                "aes_blocks_per_s": achieved_aes * 1e9}}
     # ---- the plain per-query GPU path on the same step (same shares, parity-tested)
     if not args.no_compare:
         l0 = ctx.launch_count()

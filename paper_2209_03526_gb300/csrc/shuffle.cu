@@ -27,7 +27,7 @@ namespace ogm {
 namespace {
 
 #ifndef OGM_SHUF_THREADS
-#define OGM_SHUF_THREADS 512
+#define OGM_SHUF_THREADS 768
 #endif
 constexpr int kShufThreads = OGM_SHUF_THREADS;
 constexpr uint32_t kShufMaxWidth = 64;

@@ -68,7 +68,7 @@ def test_onehot_parity(ctx, n, n_elems):
             assert last >> (n_elems % 32) == 0
 
 
-@pytest.mark.parametrize("n,n_elems", [(13, 70_001), (16, 5_003)])
+@pytest.mark.parametrize("n,n_elems", [(13, 70_001), (14, 20_011), (16, 5_003)])
 def test_onehot_parity_persistent_grid(ctx, n, n_elems):
     """More 32-element words than the dot pass's persistent grid has CTAs, so CTAs carry
     their copy pipeline from one word into the next.  Every element of every group is
