@@ -263,13 +263,12 @@ struct DotParams {
     uint32_t n_preds;
 };
 
-
-
-// One CTA per 32 elements (one packed output word).  The CTA's warps split each share
-// row: with W >= 128 words warp q covers words [128 q, 128 q + 128) of every row in steps
-// of W' = 128 * warps (one uint4 per lane when W' = W); with W < 128 one warp reads the
-// row word by word.  A lane keeps its slice of the predicates' half vectors in registers
-// for all 32 elements and streams 8 elements' rows at a time; its parity bits of the 32
+// The unstaged pass, launched for domains below 2^12 and general in W.  One CTA per 32
+// elements (one packed output word).  The CTA's warps split each share row: with
+// W >= 128 words warp q covers words [128 q, 128 q + 128) of every row in steps of
+// W' = 128 * warps (one uint4 per lane when W' = W); with W < 128 one warp reads the row
+// word by word.  A lane keeps its slice of the predicates' half vectors in registers for
+// all 32 elements and streams 8 elements' rows at a time; its parity bits of the 32
 // elements are XORed over the warp by shuffles and over the warps through shared memory.
 constexpr int kDotBatch = 8;
 
