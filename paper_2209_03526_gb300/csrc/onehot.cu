@@ -80,6 +80,36 @@ __device__ __forceinline__ void level_step(const SmemTab& T, const AesParams& A,
     t = tn;
 }
 
+// The fixed PRG round keys of both directions, for level steps whose direction the whole
+// warp shares (the depth-first part of EvalAll): st[dir] for the seed / control-bit
+// block, v[dir] for the DCF value block.
+struct FixedKeys {
+    uint32_t st[2][44];
+    uint32_t v[2][44];
+};
+
+// level_step with the direction DIR known at compile time: plain AES under fixed round
+// keys instead of a per-lane key selection in every round.
+template <uint32_t DIR>
+__device__ __forceinline__ void level_step_fixed(const SmemTab& T, const FixedKeys& F, const DevKey& K, int i,
+                                                 bool dcf, uint32_t s[4], uint32_t& t, uint32_t& V) {
+    uint32_t o[4];
+    aes_one(T, F.st[DIR], s, o);
+    if (dcf) {
+        const uint32_t v0 = aes_one_w0(T, F.v[DIR], s);
+        V ^= ((v0 ^ s[0]) & 1u) ^ (t & K.vcw[i] & 1u);
+    }
+#pragma unroll
+    for (int w = 0; w < 4; w++) o[w] ^= s[w];
+    uint32_t tn = o[0] & 1u;
+    o[0] &= ~1u;
+    const uint32_t tm = 0u - t;
+#pragma unroll
+    for (int w = 0; w < 4; w++) s[w] = o[w] ^ (K.scw[i][w] & tm);
+    tn ^= t & (((DIR ? K.tr : K.tl) >> i) & 1u);
+    t = tn;
+}
+
 // Eval of one key at the 2^m consecutive positions prefix * 2^m + j, j < 2^m (m <= 3):
 // walk the n - m shared levels once, then expand the last m levels depth first
 // (2^(m+1) - 2 more levels instead of m per position).  Bit j of the result is
@@ -158,8 +188,8 @@ constexpr int kNodeWords = 6;              // seed, control bit, DCF value bit
 // current path in a per-thread stack in shared memory (word w of depth d of thread x at
 // stack[(d * kNodeWords + w) * blockDim.x + x]), so one level step serves every depth.
 // Leaf j recomputes the levels below the highest bit in which j differs from j - 1.
-__device__ __forceinline__ uint32_t eval_block_d(const SmemTab& T, const AesParams& A, const DevKey& K,
-                                                 uint32_t prefix, bool dcf, uint32_t* stack) {
+__device__ __forceinline__ uint32_t eval_block_d(const SmemTab& T, const AesParams& A, const FixedKeys& F,
+                                                 const DevKey& K, uint32_t prefix, bool dcf, uint32_t* stack) {
     const int n = (int)K.n;
     const uint32_t nt = blockDim.x;
     uint32_t s[4] = {K.seed[0], K.seed[1], K.seed[2], K.seed[3]};
@@ -188,7 +218,9 @@ __device__ __forceinline__ uint32_t eval_block_d(const SmemTab& T, const AesPara
         if (leaf != 0) load(d0);
 #pragma unroll 1
         for (int d = d0; d < kDfsDepth; d++) {
-            level_step(T, A, K, lv0 + d, (leaf >> (kDfsDepth - 1 - d)) & 1u, dcf, s, t, V);
+            // the same leaf sequence in every lane: the direction is warp-uniform here
+            if ((leaf >> (kDfsDepth - 1 - d)) & 1u) level_step_fixed<1>(T, F, K, lv0 + d, dcf, s, t, V);
+            else level_step_fixed<0>(T, F, K, lv0 + d, dcf, s, t, V);
             if (d + 1 < kDfsDepth) save(d + 1);
         }
         bits |= (V ^ ((s[0] >> 1) & 1u) ^ (t & cwf)) << leaf;
@@ -205,6 +237,7 @@ struct KeySlot {
 
 struct EvalWordParams {
     AesParams aes;
+    FixedKeys fixed;
     const uint32_t* te0;
     const DevKey* keys;
     const KeySlot* slots;
@@ -241,7 +274,7 @@ __global__ void __launch_bounds__(kEvalAll32Threads, 1) k_onehot_evalall32(const
         const uint32_t slot = (uint32_t)(idx / P.blocks), b = (uint32_t)(idx % P.blocks);
         const KeySlot S = P.slots[slot];
         const DevKey& K = P.keys[S.key];
-        const uint32_t bits = (eval_block_d(T, P.aes, K, b, S.dcf != 0, stack) ^ S.cmask) & kMask;
+        const uint32_t bits = (eval_block_d(T, P.aes, P.fixed, K, b, S.dcf != 0, stack) ^ S.cmask) & kMask;
         const uint32_t pos = b * kBits;
         atomicXor(P.hv + (uint64_t)S.half * P.words + pos / 32, bits << (pos % 32));
     }
@@ -828,6 +861,12 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
     if (n >= (uint32_t)kDfsDepth && n >= 5) {
         EvalWordParams EW{};
         EW.aes = ctx->aes;
+        for (int w = 0; w < 44; w++) {
+            EW.fixed.st[0][w] = ctx->aes.rk_st[w];
+            EW.fixed.st[1][w] = ctx->aes.rk_st[w] ^ ctx->aes.d_st[w];
+            EW.fixed.v[0][w] = ctx->aes.rk_v[w];
+            EW.fixed.v[1][w] = ctx->aes.rk_v[w] ^ ctx->aes.d_v[w];
+        }
         EW.te0 = ctx->d_te0;
         EW.keys = E.keys;
         EW.slots = reinterpret_cast<const KeySlot*>(ws + off_k);
