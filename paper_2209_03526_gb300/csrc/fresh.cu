@@ -82,6 +82,7 @@ struct GenJob {
 
 struct FreshGenParams {
     AesParams aes;
+    GenRightKeys right;
     uint32_t rk_client[44];
     const uint32_t* te0;
     uint32_t n, n_jobs;
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(fresh_gen_threads<DCF>()) k_keygen_fresh(const
         sink.n = n;
         sink.tlw = sink.trw = 0;
         sink.dcf = !eq;
-        gen_pair<DCF>(T, P.aes, (int)n, alpha, beta, s0, s1, sink);
+        gen_pair<DCF>(T, P.aes, P.right, (int)n, alpha, beta, s0, s1, sink);
     }
 }
 
@@ -428,6 +429,10 @@ extern "C" oblivgm_status oblivgm_keygen_fresh(oblivgm_ctx* ctx, const oblivgm_p
     FreshGenParams P;
     std::memset(&P, 0, sizeof P);
     P.aes = ctx->aes;
+    for (int w = 0; w < 44; w++) {
+        P.right.st[w] = ctx->aes.rk_st[w] ^ ctx->aes.d_st[w];
+        P.right.v[w] = ctx->aes.rk_v[w] ^ ctx->aes.d_v[w];
+    }
     const RoundKeys rk = expand_key(seed);
     std::memcpy(P.rk_client, rk.w, sizeof P.rk_client);
     P.te0 = ctx->d_te0;

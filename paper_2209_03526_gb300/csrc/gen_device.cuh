@@ -13,11 +13,20 @@
 
 namespace ogm {
 
-// child of a seed in direction dir: seed with bit 0 of byte 0 cleared, control bit apart
-__device__ __forceinline__ void gen_expand(const SmemTab& T, const AesParams& A, uint32_t dir, const uint32_t s[4],
-                                           uint32_t cs[4], uint32_t& ct) {
+// The round keys of the right-child PRG keys (K_R for the seed / control-bit block, K_vR
+// for the DCF value block); the left-child ones are AesParams::rk_st and rk_v.  Gen
+// expands both children of every node, so each AES runs under a fixed key.
+struct GenRightKeys {
+    uint32_t st[44];
+    uint32_t v[44];
+};
+
+// child of a seed under the round keys rk of its direction: seed with bit 0 of byte 0
+// cleared, control bit apart
+__device__ __forceinline__ void gen_expand(const SmemTab& T, const uint32_t* rk, const uint32_t s[4], uint32_t cs[4],
+                                           uint32_t& ct) {
     uint32_t o[4];
-    aes_sel(T, A.rk_st, A.d_st, 0u - dir, s, o);
+    aes_one(T, rk, s, o);
 #pragma unroll
     for (int w = 0; w < 4; w++) cs[w] = o[w] ^ s[w];
     ct = cs[0] & 1u;
@@ -29,16 +38,16 @@ __device__ __forceinline__ void gen_expand(const SmemTab& T, const AesParams& A,
 // keep/lose choices are selects, so everything stays in registers.  One instance per
 // kind keeps the DPF loop free of the DCF's value blocks.
 template <bool DCF, class Sink>
-__device__ __forceinline__ void gen_pair(const SmemTab& T, const AesParams& A, int n, uint32_t alpha, uint32_t beta,
-                                         uint32_t s0[4], uint32_t s1[4], Sink& sink) {
+__device__ __forceinline__ void gen_pair(const SmemTab& T, const AesParams& A, const GenRightKeys& R, int n,
+                                         uint32_t alpha, uint32_t beta, uint32_t s0[4], uint32_t s1[4], Sink& sink) {
     constexpr bool dcf = DCF;
     uint32_t t0 = 0u, t1 = 1u, valpha = 0u;
     for (int lv = 1; lv <= n; lv++) {
         uint32_t c0l[4], c0r[4], c1l[4], c1r[4], t0l, t0r, t1l, t1r;
-        gen_expand(T, A, 0u, s0, c0l, t0l);
-        gen_expand(T, A, 1u, s0, c0r, t0r);
-        gen_expand(T, A, 0u, s1, c1l, t1l);
-        gen_expand(T, A, 1u, s1, c1r, t1r);
+        gen_expand(T, A.rk_st, s0, c0l, t0l);
+        gen_expand(T, R.st, s0, c0r, t0r);
+        gen_expand(T, A.rk_st, s1, c1l, t1l);
+        gen_expand(T, R.st, s1, c1r, t1r);
         const uint32_t a = (alpha >> (n - lv)) & 1u;
         const uint32_t tl = t0l ^ t1l ^ a ^ 1u, tr = t0r ^ t1r ^ a;
         uint32_t scw[4];
@@ -46,10 +55,10 @@ __device__ __forceinline__ void gen_pair(const SmemTab& T, const AesParams& A, i
         for (int w = 0; w < 4; w++) scw[w] = a ? (c0l[w] ^ c1l[w]) : (c0r[w] ^ c1r[w]);   // CW on the lose side
         uint32_t vcw = 0u;
         if (dcf) {
-            const uint32_t v0l = aes_sel_w0(T, A.rk_v, A.d_v, 0u, s0) ^ s0[0];
-            const uint32_t v0r = aes_sel_w0(T, A.rk_v, A.d_v, ~0u, s0) ^ s0[0];
-            const uint32_t v1l = aes_sel_w0(T, A.rk_v, A.d_v, 0u, s1) ^ s1[0];
-            const uint32_t v1r = aes_sel_w0(T, A.rk_v, A.d_v, ~0u, s1) ^ s1[0];
+            const uint32_t v0l = aes_one_w0(T, A.rk_v, s0) ^ s0[0];
+            const uint32_t v0r = aes_one_w0(T, R.v, s0) ^ s0[0];
+            const uint32_t v1l = aes_one_w0(T, A.rk_v, s1) ^ s1[0];
+            const uint32_t v1r = aes_one_w0(T, R.v, s1) ^ s1[0];
             const uint32_t v0_lose = a ? v0l : v0r, v1_lose = a ? v1l : v1r;
             const uint32_t v0_keep = a ? v0r : v0l, v1_keep = a ? v1r : v1l;
             const bool neg = t1 != 0;

@@ -28,6 +28,7 @@ constexpr int kKeygenSmem = kTableBytes + (kKeygenThreads / 32) * 32 * 6 * 4;
 
 struct KeygenParams {
     AesParams aes;
+    GenRightKeys right;
     uint32_t rk_seed[44];          // round keys of the client's seed (root-seed stream)
     const uint32_t* te0;
     const uint32_t* alpha;         // per pair (device)
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(kThreads) k_keygen(const __grid_constant__ Key
         sink.lane = lane;
         sink.n = (uint32_t)n;
         sink.n_keys = (uint32_t)(P.n_pairs - first < 32 ? 2 * (P.n_pairs - first) : 64);
-        gen_pair<DCF>(T, P.aes, n, P.alpha[i], P.beta[i], s0, s1, sink);
+        gen_pair<DCF>(T, P.aes, P.right, n, P.alpha[i], P.beta[i], s0, s1, sink);
     }
 }
 
@@ -144,6 +145,10 @@ extern "C" oblivgm_status oblivgm_keygen_device(oblivgm_ctx* ctx, uint32_t kind,
     if (n_pairs == 0) return OBLIVGM_OK;
     KeygenParams P{};
     P.aes = ctx->aes;
+    for (int w = 0; w < 44; w++) {
+        P.right.st[w] = ctx->aes.rk_st[w] ^ ctx->aes.d_st[w];
+        P.right.v[w] = ctx->aes.rk_v[w] ^ ctx->aes.d_v[w];
+    }
     const RoundKeys rk = expand_key(seed);
     std::memcpy(P.rk_seed, rk.w, sizeof P.rk_seed);
     P.te0 = ctx->d_te0;
