@@ -340,7 +340,8 @@ namespace ogm {
 constexpr int kWpSlots = 12;                      // threads per element
 constexpr int kWpElems = 40;                      // elements per CTA (tile)
 constexpr int kWpThreads = kWpSlots * kWpElems;   // 480
-constexpr int kWpSmem = kFilterSmem + kWpElems * kWpSlots * 4;
+constexpr int kWpPrf = 6;                         // re-share PRF words per element: 2 passes x 3 keys
+constexpr int kWpSmem = kFilterSmem + kWpElems * (kWpSlots + kWpPrf) * 4;
 // default switch-over: batches of at most this many elements per SM in all
 constexpr uint64_t kWpDefaultElemsPerSm = 128;
 
@@ -349,6 +350,7 @@ __global__ void __launch_bounds__(kWpThreads, 1) k_filter_wp(const __grid_consta
     const SmemTab T{reinterpret_cast<const char*>(smem), lane_offset()};
     DevKey* kbuf = reinterpret_cast<DevKey*>(smem + kTableBytes);
     uint32_t* part = reinterpret_cast<uint32_t*>(smem + kFilterSmem);   // [element][slot]
+    uint32_t* fprf = part + kWpElems * kWpSlots;                           // [element][pass * 3 + key]
     __shared__ __align__(8) uint64_t mbar;
     __shared__ unsigned long long item_sh;
 
@@ -407,6 +409,16 @@ __global__ void __launch_bounds__(kWpThreads, 1) k_filter_wp(const __grid_consta
                 if (!eq && (slot % nsub) == 0 && K.party == 0) y[0] += D.cbeta;
             }
             part[el * kWpSlots + slot] = y[0];
+            // The re-share PRF words depend only on (element, step, table, query), so six
+            // slots compute the (pass, key) pairs side by side: pass p re-shares with step
+            // D.step + 64 p (the fold's re-share, for every predicate after the first).
+            const int passes = k == 0 ? 1 : 2;
+            if (valid && slot < 3u * passes) {
+                const uint32_t pass = slot / 3, i = slot % 3;
+                const uint32_t ctr[4] = {(uint32_t)e, (uint32_t)(e >> 32), (D.step + 64u * pass) | (table << 16),
+                                         query};
+                fprf[el * kWpPrf + slot] = aes_one_w0(T, P.rk_prf[i], ctr);   // F keeps bytes 0..3
+            }
             __syncthreads();
             if (slot == 0 && valid) {
                 // keys are ordered [server i][half h][sub s]: server i owns slots [2 nsub i, 2 nsub (i + 1))
@@ -417,12 +429,13 @@ __global__ void __launch_bounds__(kWpThreads, 1) k_filter_wp(const __grid_consta
                     z[1][0] += i == 1 ? v : 0u;
                     z[2][0] += i == 2 ? v : 0u;
                 }
-                uint32_t step = D.step;
-                const int passes = k == 0 ? 1 : 2;
 #pragma unroll 1
                 for (int pass = 0; pass < passes; pass++) {
+                    // r_i = z_i + F(k_i) - F(k_{i-1}), as reshare() computes it
+                    const uint32_t* f = fprf + el * kWpPrf + 3 * pass;
                     uint32_t r[3][1];
-                    reshare<1>(T, P.rk_prf, z, r, e, step, table, query);
+#pragma unroll
+                    for (int i = 0; i < 3; i++) r[i][0] = z[i][0] + f[i] - f[(i + 2) % 3];
                     if (pass + 1 < passes) {
 #pragma unroll
                         for (int i = 0; i < 3; i++) {
@@ -430,7 +443,6 @@ __global__ void __launch_bounds__(kWpThreads, 1) k_filter_wp(const __grid_consta
                             const uint32_t pr = acc[i][0] * r[i][0] + acc[i][0] * r[i1][0] + acc[i1][0] * r[i][0];
                             z[i][0] = D.lin * (acc[i][0] + r[i][0]) + D.prod * pr;
                         }
-                        step = 64u + D.step;
                     } else {
 #pragma unroll
                         for (int i = 0; i < 3; i++) acc[i][0] = r[i][0];
