@@ -5,7 +5,7 @@
   through the per-element kernel, the walk-parallel kernel and the plain path,
   the fresh-key mode and the one-hot mode;
 * 64 groups (the maximum) of one predicate each over two tables, 192 output
-  arrays;
+  arrays, in the masked and in the one-hot mode;
 * one predicate more than the maximum, or one group more, is rejected.
 """
 import numpy as np
@@ -145,3 +145,40 @@ def test_64_groups(ctx):
     with pytest.raises(P.OblivgmError) as e:
         ctx.filter_and_combine(4, toks, outs + _outs([5]))        # 65 groups
     assert e.value.status == P.EINVAL
+
+
+def test_64_groups_onehot(ctx):
+    """64 one-hot groups over two tables of different sizes (22 and 11 packed words), at
+    n = 12 so every column goes through the staged dot pass, several passes per column;
+    the single fold launch maps its items back to 64 groups of two word counts."""
+    n = 12
+    g = W.rng(63)
+    sizes = (700, 333)
+    vals = [W.uniform_attrs(g, 2, sizes[0], n), W.uniform_attrs(g, 1, sizes[1], n)]
+    tabs = [W.onehot_table(v, n, g) for v in vals]
+    for tid, t in enumerate(tabs):
+        ctx.load_onehot(tid, [to_dev(s) for s in t["shares"]], n)
+    preds = []
+    for grp in range(64):
+        t = grp % 2
+        v = vals[t]
+        if grp % 3 == 0:
+            preds.append(W.range_pred(t, grp % v.shape[0], grp, grp, grp + 900))
+        else:
+            preds.append(W.eq_pred(t, grp % v.shape[0], grp, int(v[grp % v.shape[0], grp])))
+    toks = P.keygen_onehot(preds, n, SEED)
+    outs = _outs([(sizes[grp % 2] + 31) // 32 for grp in range(64)])
+    ctx.filter_onehot(5, toks, outs)
+    ctx.sync()
+    shares = [(t["shares"], n) for t in tabs]
+    for grp in range(64):
+        m = sizes[grp % 2]
+        words = np.stack([from_dev(x) for x in outs[grp]]).view(np.uint32)
+        bits = ((words[:, :, None] >> np.arange(32, dtype=np.uint32)) & 1).reshape(3, -1)[:, :m]
+        assert np.array_equal(oracle.reconstruct_bits(bits), oracle.plain_group(preds, grp, vals[grp % 2])), grp
+        assert words[0, -1] >> (m % 32) == 0, grp
+        # share for share on groups at both ends and in the middle of the fold's item space
+        # (the oracle's one-hot filter takes about two seconds a group here)
+        if grp in (0, 1, 2, 31, 62, 63):
+            want = oracle.filter_onehot(toks, 5, PRF, shares, grp, np.arange(m))
+            assert np.array_equal(bits, want), grp
