@@ -1015,7 +1015,8 @@ oblivgm_status oblivgm_autotune(oblivgm_ctx* ctx, uint32_t* threads, uint32_t* e
     tabs[0] = tb;
     uint32_t* outp = tb.dev + 3 * n;
     uint32_t* outs3[3] = {outp, outp, outp};   // timing only: the three sets may overlap
-    oblivgm_pred preds[2] = {{OBLIVGM_PRED_EQ, 0, 0, 0, 12345u, 0}, {OBLIVGM_PRED_RANGE, 0, 0, 0, 1000u, 0x7FFFFFFFu}};
+    oblivgm_pred preds[2] = {{OBLIVGM_PRED_EQ, 0, 0, 0, 12345u, 0, OBLIVGM_COMBINE_AND},
+                             {OBLIVGM_PRED_RANGE, 0, 0, 0, 1000u, 0x7FFFFFFFu, OBLIVGM_COMBINE_AND}};
     uint8_t seed[16] = {0};
     size_t len[3];
     std::string err;
