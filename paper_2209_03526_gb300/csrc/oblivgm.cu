@@ -680,6 +680,7 @@ oblivgm_status launch_plan(oblivgm_ctx* ctx, const Plan& plan, cudaStream_t st, 
     unsigned char* ws = nullptr;
     oblivgm_status as = ws_alloc(ctx, reinterpret_cast<void**>(&ws), total, st, "workspace allocation");
     if (as != OBLIVGM_OK) return as;
+    ScratchGuard guard(ws, st);
     OGM_CUDA(cudaMemcpyAsync(ws, img.data(), total, cudaMemcpyHostToDevice, st), "descriptor upload");
     FilterParams P{};
     P.aes = ctx->aes;
@@ -703,6 +704,7 @@ oblivgm_status launch_plan(oblivgm_ctx* ctx, const Plan& plan, cudaStream_t st, 
                                                plan.elems_per_thread, plan.wp, st);
     if (e != cudaSuccess) return cuda_fail(e, "k_filter launch");
     ctx->launches++;
+    guard.done();
     OGM_CUDA(cudaFreeAsync(ws, st), "workspace release");
     return OBLIVGM_OK;
 }
@@ -921,6 +923,7 @@ static oblivgm_status eval_batch(oblivgm_ctx* ctx, uint32_t kind, const uint8_t*
     DevKey* d_keys = nullptr;
     st = ws_alloc(ctx, reinterpret_cast<void**>(&d_keys), (size_t)n_keys * sizeof(DevKey), s, "key buffer");
     if (st != OBLIVGM_OK) return st;
+    ScratchGuard guard(d_keys, s);
     if (dev_keys) {
         st = repack_keys_device(ctx, keys, kind, (uint32_t)n, n_keys, d_keys, s);
         if (st != OBLIVGM_OK) return st;
@@ -950,6 +953,7 @@ static oblivgm_status eval_batch(oblivgm_ctx* ctx, uint32_t kind, const uint8_t*
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "k_eval_raw launch");
     ctx->launches++;
+    guard.done();
     OGM_CUDA(cudaFreeAsync(d_keys, s), "key buffer release");
     return OBLIVGM_OK;
 }

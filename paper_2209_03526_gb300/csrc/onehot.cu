@@ -843,6 +843,7 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
         const oblivgm_status as = ws_alloc(ctx, reinterpret_cast<void**>(&ws), total, s, "one-hot scratch");
         if (as != OBLIVGM_OK) return as;
     }
+    ScratchGuard guard(ws, s);
     ce = cudaMemcpyAsync(ws, img.data(), off_v, cudaMemcpyHostToDevice, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "one-hot descriptor upload");
     uint32_t* zbase = reinterpret_cast<uint32_t*>(ws + off_z);
@@ -929,6 +930,7 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
     }
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return cuda_fail(ce, "one-hot launch");
+    guard.done();
     ce = cudaFreeAsync(ws, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "one-hot scratch release");
     return OBLIVGM_OK;

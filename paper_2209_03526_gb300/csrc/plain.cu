@@ -130,6 +130,7 @@ extern "C" oblivgm_status oblivgm_filter_plain(oblivgm_ctx* ctx, uint32_t query_
                 ws_alloc(ctx, reinterpret_cast<void**>(&ws), words * 4 + 12 * sizeof(DevKey) + 256, s, "plain-path scratch");
             if (as != OBLIVGM_OK) return as;
         }
+        ScratchGuard guard(ws, s);
         uint32_t* xhat = reinterpret_cast<uint32_t*>(ws);
         uint32_t* y = xhat + n;
         uint32_t* b = y + 12 * n;
@@ -180,6 +181,7 @@ extern "C" oblivgm_status oblivgm_filter_plain(oblivgm_ctx* ctx, uint32_t query_
         }
         ce = cudaGetLastError();
         if (ce != cudaSuccess) return cuda_fail(ce, "plain-path launch");
+        guard.done();
         ce = cudaFreeAsync(ws, s);
         if (ce != cudaSuccess) return cuda_fail(ce, "plain-path scratch release");
     }

@@ -30,6 +30,20 @@ struct NvtxRange {
     NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
+// Releases a stream-ordered workspace (from ws_alloc) when an entry point returns early
+// on an error; the normal path releases it itself, checking the result, after done().
+struct ScratchGuard {
+    void* p;
+    cudaStream_t s;
+    ScratchGuard(void* p_, cudaStream_t s_) : p(p_), s(s_) {}
+    ~ScratchGuard() {
+        if (p) cudaFreeAsync(p, s);
+    }
+    void done() { p = nullptr; }
+    ScratchGuard(const ScratchGuard&) = delete;
+    ScratchGuard& operator=(const ScratchGuard&) = delete;
+};
+
 struct Table {
     uint32_t* dev = nullptr;   // [share set j][attr][stride] uint32
     uint64_t n_elems = 0;

@@ -515,7 +515,10 @@ extern "C" oblivgm_status oblivgm_fetch_multi(oblivgm_ctx* ctx, uint32_t table_i
     }
     uint32_t total_count = 0;
     ce = cudaMemcpyAsync(&total_count, counts + n_blocks, 4, cudaMemcpyDeviceToHost, s);
-    if (ce != cudaSuccess) return cuda_fail(ce, "fetch count read");
+    if (ce != cudaSuccess) {
+        cudaFreeAsync(scratch, s);
+        return cuda_fail(ce, "fetch count read");
+    }
     ce = cudaFreeAsync(scratch, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "fetch scratch release");
     ce = cudaStreamSynchronize(s);
