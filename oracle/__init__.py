@@ -100,6 +100,7 @@ def lib():
             l.orc_fetch_multi.restype = ctypes.c_int64
             l.orc_fresh_direct.argtypes = [ctypes.POINTER(_Pred), u32, ctypes.c_int, u8p, u32, u8p, u32, u8p,
                                            ctypes.POINTER(_Table), u32, u8p, u64, u8p]
+            l.orc_aes_blocks.restype = u64
             l.orc_init()
             _lib = l
     return _lib
@@ -120,6 +121,17 @@ def aes128(key: bytes, block: bytes) -> bytes:
     out = ctypes.create_string_buffer(16)
     lib().orc_aes128(_addr(_buf(key)), _addr(_buf(block)), _addr(out))
     return out.raw
+
+
+def aes_blocks_reset() -> None:
+    """Zero the calling thread's count of AES-128 blocks the oracle has encrypted."""
+    lib().orc_aes_blocks_reset()
+
+
+def aes_blocks() -> int:
+    """AES-128 blocks the oracle has encrypted on the calling thread since the last reset
+    (test instrumentation: the benchmark's algorithmic block counts are checked against it)."""
+    return int(lib().orc_aes_blocks())
 
 
 def prg(which: int, seed: bytes) -> bytes:

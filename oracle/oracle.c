@@ -129,9 +129,17 @@ static void mix_columns(uint8_t st[4][4])
     }
 }
 
+/* Test instrumentation: the AES-128 blocks the calling thread has encrypted, so that the
+ * tests can check the benchmark's algorithmic block counts against the oracle's own work. */
+static __thread uint64_t AES_BLOCKS;
+
+uint64_t orc_aes_blocks(void) { return AES_BLOCKS; }
+void orc_aes_blocks_reset(void) { AES_BLOCKS = 0; }
+
 static void aes_encrypt(const aes_ks* ks, const uint8_t in[16], uint8_t out[16])
 {
     uint8_t st[4][4];
+    AES_BLOCKS++;
     for (int i = 0; i < 16; i++) st[i % 4][i / 4] = in[i];
     add_round_key(st, ks, 0);
     for (int round = 1; round < 10; round++) {
