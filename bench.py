@@ -60,6 +60,13 @@ def lookups_per_element(preds, n_bits=32):
     return fss + 3 * (2 * len(preds) - 1) * LOOKUPS_PER_AES_W0
 
 
+def keygen_blocks_per_pair(dcf: bool, n_bits: int = 32):
+    """AES blocks (full, value-word-only) of one key pair's Gen on the GPU: the two root seeds
+    from the client seed, then per level both parties' seeds expanded in both directions
+    (4 blocks) and, for a DCF, the 4 value words of those children."""
+    return 2 + 4 * n_bits, (4 * n_bits if dcf else 0)
+
+
 def plain_and(preds, values):
     """Plaintext AND of a group's predicates (Def. 2), for the checks of the timed modes."""
     res = np.ones(values.shape[1], dtype=np.uint64)
@@ -842,9 +849,8 @@ def run_workload(args):
                 ms.append(a.elapsed_time(b))
             ctx.sync(stream)
             s_ = float(np.mean(ms)) / 1e3
-            # two root seeds, then per level 2 parties x 2 children (+ 2 x 2 value words for DCF)
-            lu = m * (2 * LOOKUPS_PER_AES + n * 4 * LOOKUPS_PER_AES
-                      + (n * 4 * LOOKUPS_PER_AES_W0 if kind == P.KEY_DCF else 0))
+            full, w0 = keygen_blocks_per_pair(kind == P.KEY_DCF, n)
+            lu = m * (full * LOOKUPS_PER_AES + w0 * LOOKUPS_PER_AES_W0)
             kinds[name] = {"pairs_per_s": m / s_, "ms": s_ * 1e3, "key_bytes": L,
                            "key_GB_per_s": 2 * m * L / s_ / 1e9, "glookup_per_s": lu / s_ / 1e9}
             total_s += s_

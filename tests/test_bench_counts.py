@@ -6,7 +6,8 @@ equality predicate, 12 DCF walks of n levels (two blocks per level: seed / contr
 value) per range predicate, and 3 PRF blocks per re-share, of which an AND-group of P
 predicates has 2P - 1.  Here the oracle, which runs the constructions step by step, counts
 the AES-128 blocks it encrypts while filtering one element, and the two must agree.  A
-dropped or doubled PRG call on either side changes the number.
+dropped or doubled PRG call on either side changes the number.  The keygen line's count
+per key pair is checked the same way against the oracle's Gen.
 """
 import numpy as np
 import pytest
@@ -49,3 +50,15 @@ def test_counter_counts_blocks():
     for _ in range(5):
         oracle.aes128(bytes(16), bytes(16))
     assert oracle.aes_blocks() == 5
+
+
+@pytest.mark.parametrize("n_bits", [5, 16, 32])
+@pytest.mark.parametrize("dcf", [False, True])
+def test_keygen_blocks_per_pair(n_bits, dcf):
+    """bench.py's keygen line counts a pair's Gen as 2 root-seed blocks plus the tree's
+    blocks; the oracle's Gen, given the root seeds, encrypts exactly the tree's."""
+    gen = oracle.dcf_gen if dcf else oracle.dpf_gen
+    oracle.aes_blocks_reset()
+    gen(n_bits, 11, 1, bytes(range(16)), bytes(range(16, 32)))
+    full, w0 = bench.keygen_blocks_per_pair(dcf, n_bits)
+    assert oracle.aes_blocks() + 2 == full + w0
