@@ -429,6 +429,19 @@ def match(n_vertices: int, edges, query_vertices: int, query_edges, vertex_ok, e
     return sorted(out)
 
 
+def distinct_matches(embeddings, query_edges) -> int:
+    """Number of distinct matched subgraphs among ordered embeddings (Def. 2).
+
+    Two embeddings that differ by an automorphism of the query graph map it onto the same
+    subgraph, and two embeddings with the same vertex set and the same image of the query's
+    edges differ by such an automorphism; so the orbits are counted by their images."""
+    seen = set()
+    for emb in embeddings:
+        image = frozenset(frozenset((emb[a], emb[b])) for a, b in query_edges)
+        seen.add((frozenset(emb), image))
+    return len(seen)
+
+
 # ---------------------------------------------------------------- secFetch, case I
 
 FETCH_STEP = 256

@@ -89,3 +89,35 @@ def test_tiny_path_workload_oblivious_equals_plaintext():
                         [oracle.plain_group(wl["preds"], 0, vt["values"]).astype(bool), None, None],
                         [None, oracle.plain_group(wl["preds"], 1, et["values"]).astype(bool)])
     assert got == want and len(got) > 0
+
+
+def test_distinct_matches_closed_forms():
+    """Ordered embeddings against distinct subgraphs: |Aut(query)| embeddings per subgraph."""
+    k4 = np.array([(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)], dtype=np.uint32)
+    k5 = np.array([(a, b) for a in range(5) for b in range(a + 1, 5)], dtype=np.uint32)
+    tri = [(0, 1), (1, 2), (2, 0)]
+    sq = [(0, 1), (1, 2), (2, 3), (3, 0)]
+    path = [(0, 1), (1, 2)]
+    none3, none4 = [None] * 3, [None] * 4
+    # triangles: C(4, 3) = 4 in K4, C(5, 3) = 10 in K5, each 6 times (|Aut(C3)| = 6)
+    e = oracle.match(4, k4, 3, tri, none3, none3)
+    assert (len(e), oracle.distinct_matches(e, tri)) == (24, 4)
+    e = oracle.match(5, k5, 3, tri, none3, none3)
+    assert (len(e), oracle.distinct_matches(e, tri)) == (60, 10)
+    # 4-cycles in K4: 3, each 8 times (|Aut(C4)| = 8)
+    e = oracle.match(4, k4, 4, sq, none4, none4)
+    assert (len(e), oracle.distinct_matches(e, sq)) == (24, 3)
+    # 2-edge paths in K4: 4 centres x C(3, 2) leaf pairs = 12, each twice
+    e = oracle.match(4, k4, 3, path, none3, [None] * 2)
+    assert (len(e), oracle.distinct_matches(e, path)) == (24, 12)
+    # a predicate on one end breaks the path's symmetry: no two embeddings share an image
+    ok0 = np.array([True, False, False, False])
+    e = oracle.match(4, k4, 3, path, [ok0, None, None], [None] * 2)
+    assert len(e) == oracle.distinct_matches(e, path) == 6
+
+
+def test_fig1_results_are_distinct_subgraphs():
+    attrs, edges = _fig1_graph()
+    ok = [oracle.plain_group(Q_PREDS, q, attrs).astype(bool) for q in range(5)]
+    got = oracle.match(9, edges, 5, Q_EDGES, ok, [None] * 4)
+    assert oracle.distinct_matches(got, Q_EDGES) == len(PAPER_RESULTS)
