@@ -27,6 +27,12 @@
  * blocked, fused or reordered.  Eval computes only the child the input bit
  * selects: the other half of G(s) is computed and then discarded by the
  * construction, so leaving it out changes no output.
+ *
+ * Parity unpinned (conventions the paper leaves open; they fix individual share
+ * values, while every reconstructed result is pinned by the tests): the fixed
+ * keys K_R, K_vL, K_vR (K_L is FIPS-pinned), the token byte layout, the keygen
+ * random streams, the PRF counter layout, and secShuffle's derivation of each
+ * pair's permutation and masks from its seed.
  */
 #include <stdint.h>
 #include <stddef.h>
