@@ -303,9 +303,14 @@ oblivgm_status oblivgm_filter_plain(oblivgm_ctx* ctx, uint32_t query_id, const u
  *  - all calls share the one array: the call overwrites it (and zeroes the
  *    work counter) in stream order, so calls that can overlap on the GPU --
  *    on different streams, or from several threads or contexts on the same
- *    device -- race and give wrong results; issue them on one stream;
+ *    device -- race and give wrong results; issue them on one stream (calls
+ *    back to back on one stream are safe);
  *  - the first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *    (cudaGetSymbolAddress);
+ *  - the call uploads its workspace from a host buffer that lives only for
+ *    the call, so it must not be captured into a CUDA graph: on a stream under
+ *    capture (or the legacy stream while another stream captures) it returns
+ *    EINVAL before doing anything.  Use oblivgm_plan_* for graphs.
  * Errors as oblivgm_filter_and_combine, plus ERANGE. */
 #define OBLIVGM_NOALLOC_SCRATCH_BYTES (256u * 1024u)
 oblivgm_status oblivgm_filter_and_combine_noalloc(oblivgm_ctx* ctx, uint32_t query_id, const uint8_t* const tok[3],
@@ -512,11 +517,22 @@ oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query_id, const 
 oblivgm_status oblivgm_submit(oblivgm_ctx* ctx, const uint8_t* const tok[3], const size_t tok_len[3],
                               uint64_t* ticket);
 
-/* Wait up to timeout_ms (0 = just check, < 0 = no limit) for a ticket.
+/* Wait for a ticket: timeout_ms = 0 only checks; a positive timeout waits at
+ * most that long; a negative one waits at most the context's poll limit
+ * (oblivgm_set_poll_limit, default OBLIVGM_POLL_LIMIT_DEFAULT_MS = 10 min),
+ * which also caps positive timeouts.  No poll blocks longer than its timeout
+ * or that limit.
  * OK: *out describes the result (library-owned until oblivgm_release).
- * EAGAIN (timeout_ms == 0 and not finished), ETIMEOUT, ENOENT (unknown or
- * already released ticket), EFAULT_DEVICE. */
+ * EAGAIN (timeout_ms == 0 and not finished), ETIMEOUT (the wait ran out, the
+ * query keeps running and may be polled again), ENOENT (unknown or already
+ * released ticket), ECUDA (its batch failed to launch; the text says why). */
+#define OBLIVGM_POLL_LIMIT_DEFAULT_MS 600000u
 oblivgm_status oblivgm_poll(oblivgm_ctx* ctx, uint64_t ticket, int32_t timeout_ms, oblivgm_result* out);
+
+/* Longest wait of any oblivgm_poll on this context, in milliseconds (>= 1).
+ * `previous` (may be NULL) receives the limit it replaces.  Errors: EINVAL
+ * (NULL context, max_ms 0). */
+oblivgm_status oblivgm_set_poll_limit(oblivgm_ctx* ctx, uint32_t max_ms, uint32_t* previous);
 
 /* Return a served result's memory to the arena (re-admits waiting work). */
 oblivgm_status oblivgm_release(oblivgm_ctx* ctx, uint64_t ticket);
@@ -552,7 +568,7 @@ oblivgm_status oblivgm_set_walk_parallel(oblivgm_ctx* ctx, uint64_t max_elems, u
 oblivgm_status oblivgm_sync(oblivgm_ctx* ctx, void* stream);
 
 /* Failure-path test hook.  The next fused launch of this context (filter,
- * batch or served batch) asks its first key-staging barrier for 16 bytes
+ * batch, served batch or no-alloc call) asks its first key-staging barrier for 16 bytes
  * more than the copy delivers, so every CTA's bounded wait runs out after
  * limit_us microseconds (1..2,000,000) instead of the normal 2 s.  Each CTA
  * then records the fault and returns without touching its outputs, and

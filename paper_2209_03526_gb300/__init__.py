@@ -13,8 +13,8 @@ import ctypes
 from typing import Sequence
 
 from . import _native as N
-from ._native import (ALL_PAIRS, COMBINE_AND, COMBINE_OR, COMBINE_XOR, EAGAIN, EBUSY, EFAULT_DEVICE, EINVAL, ENOENT,
-                      ENOMEM, ERANGE, ETIMEOUT, KEY_DCF, KEY_DPF,
+from ._native import (ALL_PAIRS, COMBINE_AND, COMBINE_OR, COMBINE_XOR, EAGAIN, EBUSY, ECUDA, EFAULT_DEVICE, EINVAL,
+                      ENOENT, ENOMEM, ERANGE, ETIMEOUT, KEY_DCF, KEY_DPF, POLL_LIMIT_DEFAULT_MS,
                       OK, PRED_EQ, PRED_RANGE, OblivgmError)
 from .build import build
 
@@ -389,6 +389,12 @@ class Context:
         for g in range(r.n_groups):
             groups.append({"table": r.table[g], "n_elems": r.n_elems[g], "shares": [r.shares[g][j] for j in range(3)]})
         return {"ticket": r.ticket, "latency_ms": r.latency_ms, "groups": groups}
+
+    def set_poll_limit(self, max_ms: int) -> int:
+        """Longest wait of any poll (a negative timeout waits this long); returns the old limit."""
+        prev = ctypes.c_uint32(0)
+        N.check(self._lib.oblivgm_set_poll_limit(self._h, max_ms, ctypes.byref(prev)), "oblivgm_set_poll_limit")
+        return prev.value
 
     def release(self, ticket: int):
         N.check(self._lib.oblivgm_release(self._h, ticket), "oblivgm_release")

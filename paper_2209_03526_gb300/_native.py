@@ -32,6 +32,7 @@ KEYS_DEVICE = 2
 SHUFFLE_ADD, SHUFFLE_XOR = 0, 1
 MAX_GROUPS = 64
 NOALLOC_SCRATCH_BYTES = 256 * 1024
+POLL_LIMIT_DEFAULT_MS = 600000
 
 STATUS_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EARCH: "EARCH", ERANGE: "ERANGE",
                 EBUSY: "EBUSY", EAGAIN: "EAGAIN", ETIMEOUT: "ETIMEOUT", ENOENT: "ENOENT",
@@ -95,6 +96,7 @@ _SIGS = {
     "oblivgm_submit": ([c_vp, ctypes.POINTER(c_vp), ctypes.POINTER(c_size), ctypes.POINTER(c_u64)], c_i32),
     "oblivgm_poll": ([c_vp, c_u64, c_i32, ctypes.POINTER(Result)], c_i32),
     "oblivgm_release": ([c_vp, c_u64], c_i32),
+    "oblivgm_set_poll_limit": ([c_vp, c_u32, ctypes.POINTER(c_u32)], c_i32),
     "oblivgm_serve_stats": ([c_vp] + [ctypes.POINTER(c_u64)] * 4, c_i32),
     "oblivgm_autotune": ([c_vp, ctypes.POINTER(c_u32), ctypes.POINTER(c_u32)], c_i32),
     "oblivgm_set_schedule": ([c_vp, c_u32, c_u32], c_i32),

@@ -30,6 +30,8 @@ oblivgm_status fail(oblivgm_status st, const std::string& msg) {
     return st;
 }
 
+const std::string& last_error_text() { return g_last_error; }
+
 oblivgm_status cuda_fail(cudaError_t e, const char* what) {
     g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? OBLIVGM_ENOMEM : OBLIVGM_ECUDA;
@@ -661,45 +663,67 @@ cudaError_t launch_filter_kernel(const FilterParams& P, uint64_t n_items, int sm
     return cudaGetLastError();
 }
 
-template <typename T>
-static size_t align_up(size_t x) { return (x + alignof(T) - 1) / alignof(T) * alignof(T); }
+// Device workspace of one fused launch: work counter | groups | preds | keys | tile offsets,
+// each part 256-byte aligned.  The image is built on the host; its first 8 bytes (the work
+// counter) are zero.
+struct WsImage {
+    size_t off_groups = 0, off_preds = 0, off_keys = 0, off_items = 0, total = 0;
+    std::vector<unsigned char> bytes;
+};
 
-oblivgm_status launch_plan(oblivgm_ctx* ctx, const Plan& plan, cudaStream_t st, uint32_t* error_flag) {
-    if (plan.item_start.back() == 0) return OBLIVGM_OK;   // nothing to evaluate
-    // one stream-ordered workspace: counter | groups | preds | keys | item_start
-    const size_t off_groups = 256;
-    const size_t off_preds = off_groups + (plan.groups.size() * sizeof(GroupDesc) + 255) / 256 * 256;
-    const size_t off_keys = off_preds + (plan.preds.size() * sizeof(PredDesc) + 255) / 256 * 256;
-    const size_t off_items = off_keys + (plan.keys.size() * sizeof(DevKey) + 255) / 256 * 256;
-    const size_t total = off_items + plan.item_start.size() * sizeof(uint64_t);
-    std::vector<unsigned char> img(total, 0);
-    std::memcpy(img.data() + off_groups, plan.groups.data(), plan.groups.size() * sizeof(GroupDesc));
-    std::memcpy(img.data() + off_preds, plan.preds.data(), plan.preds.size() * sizeof(PredDesc));
-    std::memcpy(img.data() + off_keys, plan.keys.data(), plan.keys.size() * sizeof(DevKey));
-    std::memcpy(img.data() + off_items, plan.item_start.data(), plan.item_start.size() * sizeof(uint64_t));
-    unsigned char* ws = nullptr;
-    oblivgm_status as = ws_alloc(ctx, reinterpret_cast<void**>(&ws), total, st, "workspace allocation");
-    if (as != OBLIVGM_OK) return as;
-    ScratchGuard guard(ws, st);
-    OGM_CUDA(cudaMemcpyAsync(ws, img.data(), total, cudaMemcpyHostToDevice, st), "descriptor upload");
+WsImage build_ws_image(const Plan& plan) {
+    WsImage im;
+    im.off_groups = 256;
+    im.off_preds = im.off_groups + (plan.groups.size() * sizeof(GroupDesc) + 255) / 256 * 256;
+    im.off_keys = im.off_preds + (plan.preds.size() * sizeof(PredDesc) + 255) / 256 * 256;
+    im.off_items = im.off_keys + (plan.keys.size() * sizeof(DevKey) + 255) / 256 * 256;
+    im.total = im.off_items + plan.item_start.size() * sizeof(uint64_t);
+    im.bytes.assign(im.total, 0);
+    std::memcpy(im.bytes.data() + im.off_groups, plan.groups.data(), plan.groups.size() * sizeof(GroupDesc));
+    std::memcpy(im.bytes.data() + im.off_preds, plan.preds.data(), plan.preds.size() * sizeof(PredDesc));
+    std::memcpy(im.bytes.data() + im.off_keys, plan.keys.data(), plan.keys.size() * sizeof(DevKey));
+    std::memcpy(im.bytes.data() + im.off_items, plan.item_start.data(), plan.item_start.size() * sizeof(uint64_t));
+    return im;
+}
+
+// Fused-kernel parameters of a plan whose workspace image lives at device address `ws`.
+FilterParams filter_params(const oblivgm_ctx* ctx, const Plan& plan, const WsImage& im, unsigned char* ws,
+                           uint32_t* error_flag) {
     FilterParams P{};
     P.aes = ctx->aes;
     std::memcpy(P.rk_prf, ctx->rk_prf, sizeof P.rk_prf);
     P.te0 = ctx->d_te0;
-    P.groups = reinterpret_cast<const GroupDesc*>(ws + off_groups);
-    P.preds = reinterpret_cast<const PredDesc*>(ws + off_preds);
-    P.keys = reinterpret_cast<const DevKey*>(ws + off_keys);
-    P.item_start = reinterpret_cast<const uint64_t*>(ws + off_items);
+    P.groups = reinterpret_cast<const GroupDesc*>(ws + im.off_groups);
+    P.preds = reinterpret_cast<const PredDesc*>(ws + im.off_preds);
+    P.keys = reinterpret_cast<const DevKey*>(ws + im.off_keys);
+    P.item_start = reinterpret_cast<const uint64_t*>(ws + im.off_items);
     P.counter = reinterpret_cast<unsigned long long*>(ws);
     P.error = error_flag;
     P.n_groups = (uint32_t)plan.groups.size();
     P.tile = plan.tile;
     P.wait_limit_ns = kWaitLimitNs;
-    if (ctx->test_expire_next) {   // one-shot failure-path test (oblivgm_test_expire_next_wait)
-        P.expect_extra = 16;
-        P.wait_limit_ns = ctx->test_wait_limit_ns;
-        ctx->test_expire_next = false;
-    }
+    return P;
+}
+
+// one-shot failure-path test (oblivgm_test_expire_next_wait): the next launch's first key
+// staging expects 16 bytes more than it gets, under a short wait bound
+void apply_test_expiry(oblivgm_ctx* ctx, FilterParams* P) {
+    if (!ctx->test_expire_next) return;
+    P->expect_extra = 16;
+    P->wait_limit_ns = ctx->test_wait_limit_ns;
+    ctx->test_expire_next = false;
+}
+
+oblivgm_status launch_plan(oblivgm_ctx* ctx, const Plan& plan, cudaStream_t st, uint32_t* error_flag) {
+    if (plan.item_start.back() == 0) return OBLIVGM_OK;   // nothing to evaluate
+    const WsImage im = build_ws_image(plan);
+    unsigned char* ws = nullptr;
+    oblivgm_status as = ws_alloc(ctx, reinterpret_cast<void**>(&ws), im.total, st, "workspace allocation");
+    if (as != OBLIVGM_OK) return as;
+    ScratchGuard guard(ws, st);
+    OGM_CUDA(cudaMemcpyAsync(ws, im.bytes.data(), im.total, cudaMemcpyHostToDevice, st), "descriptor upload");
+    FilterParams P = filter_params(ctx, plan, im, ws, error_flag);
+    apply_test_expiry(ctx, &P);
     const cudaError_t e = launch_filter_kernel(P, plan.item_start.back(), ctx->sm_count, plan.threads,
                                                plan.elems_per_thread, plan.wp, st);
     if (e != cudaSuccess) return cuda_fail(e, "k_filter launch");
@@ -1158,6 +1182,19 @@ extern "C" oblivgm_status oblivgm_filter_and_combine_noalloc(oblivgm_ctx* ctx, u
     oblivgm_status st = check_ctx(ctx);   // also makes the context's device current
     if (st) return st;
     if (!tok || !tok_len || !out) return fail(OBLIVGM_EINVAL, "NULL argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // The workspace upload reads a host buffer that lives only for this call, so a graph
+    // replay of a captured call would copy freed memory: refuse a capturing stream.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+    if (ce == cudaErrorStreamCaptureImplicit) {   // the legacy stream while another stream captures
+        cudaGetLastError();
+        cap = cudaStreamCaptureStatusActive;
+    } else if (ce != cudaSuccess) {
+        return cuda_fail(ce, "cudaStreamIsCapturing");
+    }
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(OBLIVGM_EINVAL, "the no-alloc entry point must not be called on a stream under capture");
     ParsedQuery parsed;
     std::string err;
     st = parse_tokens(tok, tok_len, &parsed, &err);
@@ -1167,38 +1204,17 @@ extern "C" oblivgm_status oblivgm_filter_and_combine_noalloc(oblivgm_ctx* ctx, u
     st = plan_filter(ctx, ctx->tables, 1, &query_id, &parsed, &n_groups, outs, &plan);
     if (st != OBLIVGM_OK) return st;
     if (plan.item_start.back() == 0) return OBLIVGM_OK;
-    // workspace image: counter (zeroed every call) | groups | preds | keys | tile offsets
-    const size_t off_groups = 256;
-    const size_t off_preds = off_groups + (plan.groups.size() * sizeof(GroupDesc) + 255) / 256 * 256;
-    const size_t off_keys = off_preds + (plan.preds.size() * sizeof(PredDesc) + 255) / 256 * 256;
-    const size_t off_items = off_keys + (plan.keys.size() * sizeof(DevKey) + 255) / 256 * 256;
-    const size_t total = off_items + plan.item_start.size() * sizeof(uint64_t);
-    if (total > OBLIVGM_NOALLOC_SCRATCH_BYTES)
-        return fail(OBLIVGM_ERANGE, "query needs " + std::to_string(total) + " workspace bytes; the no-alloc entry point holds " +
+    const WsImage im = build_ws_image(plan);
+    if (im.total > OBLIVGM_NOALLOC_SCRATCH_BYTES)
+        return fail(OBLIVGM_ERANGE, "query needs " + std::to_string(im.total) +
+                                        " workspace bytes; the no-alloc entry point holds " +
                                         std::to_string(OBLIVGM_NOALLOC_SCRATCH_BYTES));
     unsigned char* ws = nullptr;
     st = scratch_address(ctx->device, &ws);
     if (st != OBLIVGM_OK) return st;
-    std::vector<unsigned char> img(total, 0);
-    std::memcpy(img.data() + off_groups, plan.groups.data(), plan.groups.size() * sizeof(GroupDesc));
-    std::memcpy(img.data() + off_preds, plan.preds.data(), plan.preds.size() * sizeof(PredDesc));
-    std::memcpy(img.data() + off_keys, plan.keys.data(), plan.keys.size() * sizeof(DevKey));
-    std::memcpy(img.data() + off_items, plan.item_start.data(), plan.item_start.size() * sizeof(uint64_t));
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    OGM_CUDA(cudaMemcpyAsync(ws, img.data(), total, cudaMemcpyHostToDevice, s), "no-alloc workspace upload");
-    FilterParams P{};
-    P.aes = ctx->aes;
-    std::memcpy(P.rk_prf, ctx->rk_prf, sizeof P.rk_prf);
-    P.te0 = ctx->d_te0;
-    P.groups = reinterpret_cast<const GroupDesc*>(ws + off_groups);
-    P.preds = reinterpret_cast<const PredDesc*>(ws + off_preds);
-    P.keys = reinterpret_cast<const DevKey*>(ws + off_keys);
-    P.item_start = reinterpret_cast<const uint64_t*>(ws + off_items);
-    P.counter = reinterpret_cast<unsigned long long*>(ws);
-    P.error = ctx->d_error;
-    P.n_groups = (uint32_t)plan.groups.size();
-    P.tile = plan.tile;
-    P.wait_limit_ns = kWaitLimitNs;
+    OGM_CUDA(cudaMemcpyAsync(ws, im.bytes.data(), im.total, cudaMemcpyHostToDevice, s), "no-alloc workspace upload");
+    FilterParams P = filter_params(ctx, plan, im, ws, ctx->d_error);
+    apply_test_expiry(ctx, &P);
     const cudaError_t e = launch_filter_kernel(P, plan.item_start.back(), ctx->sm_count, plan.threads,
                                                plan.elems_per_thread, plan.wp, s);
     if (e != cudaSuccess) return cuda_fail(e, "k_filter launch (no-alloc)");
@@ -1241,39 +1257,18 @@ extern "C" oblivgm_status oblivgm_plan_create(oblivgm_ctx* ctx, uint32_t n_queri
     Plan plan;
     st = plan_filter(ctx, ctx->tables, n_queries, query_ids, parsed.data(), n_groups, outs, &plan);
     if (st != OBLIVGM_OK) return st;
-    const size_t off_groups = 256;
-    const size_t off_preds = off_groups + (plan.groups.size() * sizeof(GroupDesc) + 255) / 256 * 256;
-    const size_t off_keys = off_preds + (plan.preds.size() * sizeof(PredDesc) + 255) / 256 * 256;
-    const size_t off_items = off_keys + (plan.keys.size() * sizeof(DevKey) + 255) / 256 * 256;
-    const size_t total = off_items + plan.item_start.size() * sizeof(uint64_t);
-    std::vector<unsigned char> img(total, 0);
-    std::memcpy(img.data() + off_groups, plan.groups.data(), plan.groups.size() * sizeof(GroupDesc));
-    std::memcpy(img.data() + off_preds, plan.preds.data(), plan.preds.size() * sizeof(PredDesc));
-    std::memcpy(img.data() + off_keys, plan.keys.data(), plan.keys.size() * sizeof(DevKey));
-    std::memcpy(img.data() + off_items, plan.item_start.data(), plan.item_start.size() * sizeof(uint64_t));
+    const WsImage im = build_ws_image(plan);
     auto* p = new (std::nothrow) oblivgm_plan();
     if (!p) return fail(OBLIVGM_ENOMEM, "host allocation");
-    cudaError_t e = cudaMalloc(&p->ws, total);
-    if (e == cudaSuccess) e = cudaMemcpy(p->ws, img.data(), total, cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMalloc(&p->ws, im.total);
+    if (e == cudaSuccess) e = cudaMemcpy(p->ws, im.bytes.data(), im.total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         if (p->ws) cudaFree(p->ws);
         delete p;
         return cuda_fail(e, "plan buffer");
     }
     p->ctx = ctx;
-    FilterParams& P = p->params;
-    P.aes = ctx->aes;
-    std::memcpy(P.rk_prf, ctx->rk_prf, sizeof P.rk_prf);
-    P.te0 = ctx->d_te0;
-    P.groups = reinterpret_cast<const GroupDesc*>(p->ws + off_groups);
-    P.preds = reinterpret_cast<const PredDesc*>(p->ws + off_preds);
-    P.keys = reinterpret_cast<const DevKey*>(p->ws + off_keys);
-    P.item_start = reinterpret_cast<const uint64_t*>(p->ws + off_items);
-    P.counter = reinterpret_cast<unsigned long long*>(p->ws);
-    P.error = ctx->d_error;
-    P.n_groups = (uint32_t)plan.groups.size();
-    P.tile = plan.tile;
-    P.wait_limit_ns = kWaitLimitNs;
+    p->params = filter_params(ctx, plan, im, p->ws, ctx->d_error);
     p->n_items = plan.item_start.back();
     p->threads = plan.threads;
     p->E = plan.elems_per_thread;

@@ -93,6 +93,7 @@ struct ServeState {
     uint64_t admitted = 0, completed = 0, rejected = 0;
     int running_batches = 0;
     double batch_aes_target = 3e9;     // a batch closes once it holds this much work
+    uint32_t poll_limit_ms = OBLIVGM_POLL_LIMIT_DEFAULT_MS;   // longest wait of any poll
     bool stop = false;
     static constexpr int kStreams = 2;
     cudaStream_t streams[kStreams] = {};
@@ -126,6 +127,7 @@ struct oblivgm_ctx {
 namespace ogm {
 
 oblivgm_status fail(oblivgm_status st, const std::string& msg);
+const std::string& last_error_text();   // the calling thread's last failure text
 oblivgm_status cuda_fail(cudaError_t e, const char* what);
 
 struct Plan;

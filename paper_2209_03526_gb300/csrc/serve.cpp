@@ -10,6 +10,7 @@
 // Each query's shares depend only on its tokens, ticket and tables (the PRF
 // counters carry element, step, table and query id), never on the batch it ran
 // in.
+#include <algorithm>
 #include <chrono>
 #include <cstring>
 
@@ -105,6 +106,7 @@ void worker_main(oblivgm_ctx* ctx) {
             const NvtxRange nvtx_range("oblivgm_serve_batch");
             st_code = launch_parsed(ctx, (uint32_t)batch.size(), qids.data(), parsed.data(), ngroups.data(),
                                     outs.data(), tables, st);
+            if (st_code != OBLIVGM_OK) err = last_error_text();   // this thread's failure text
         }
         auto* cb = new ServeBatch{ctx, {}};
         for (ServeQuery* q : batch) cb->tickets.push_back(q->ticket);
@@ -231,9 +233,13 @@ oblivgm_status oblivgm_poll(oblivgm_ctx* ctx, uint64_t ticket, int32_t timeout_m
     auto done = [&] { return q->state >= 2; };
     if (!done()) {
         if (timeout_ms == 0) return OBLIVGM_EAGAIN;
-        if (timeout_ms < 0) S.cv_done.wait(lk, done);
-        else if (!S.cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done))
-            return fail(OBLIVGM_ETIMEOUT, "query not finished within the timeout");
+        // a negative timeout waits up to the context's poll limit; so does a longer one
+        const uint32_t wait_ms = timeout_ms < 0 ? S.poll_limit_ms : std::min<uint32_t>((uint32_t)timeout_ms,
+                                                                                        S.poll_limit_ms);
+        if (!S.cv_done.wait_for(lk, std::chrono::milliseconds(wait_ms), done))
+            return fail(OBLIVGM_ETIMEOUT, timeout_ms < 0 || (uint32_t)timeout_ms > S.poll_limit_ms
+                                              ? "query not finished within the context's poll limit"
+                                              : "query not finished within the timeout");
     }
     if (q->state == 3) return fail(OBLIVGM_ECUDA, q->error);
     std::memset(out, 0, sizeof *out);
@@ -267,6 +273,15 @@ oblivgm_status oblivgm_release(oblivgm_ctx* ctx, uint64_t ticket) {
     for (uint32_t* p : q->outs)
         if (p) cudaFreeAsync(p, S.streams[q->stream]);
     S.cv_work.notify_all();
+    return OBLIVGM_OK;
+}
+
+oblivgm_status oblivgm_set_poll_limit(oblivgm_ctx* ctx, uint32_t max_ms, uint32_t* previous) {
+    if (!ctx) return fail(OBLIVGM_EINVAL, "NULL argument");
+    if (max_ms == 0) return fail(OBLIVGM_EINVAL, "the poll limit must be at least 1 ms");
+    std::lock_guard<std::mutex> lk(ctx->serve.mu);
+    if (previous) *previous = ctx->serve.poll_limit_ms;
+    ctx->serve.poll_limit_ms = max_ms;
     return OBLIVGM_OK;
 }
 

@@ -122,3 +122,56 @@ def test_admission_by_memory():
         c.release(tk)
         st = c.serve_stats()
         assert st["reserved_bytes"] == 0 and st["rejected"] == 1 and st["completed"] == 1
+
+
+def test_poll_waits_at_most_the_context_limit():
+    """A negative timeout waits up to the context's poll limit, not without end: with the limit
+    at 2 ms a poll on a query that runs for tens of milliseconds returns ETIMEOUT at once; the
+    query keeps running and a later poll under the default limit gets its result."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    g = W.rng(46)
+    n = 1 << 20
+    tab = W.table(W.uniform_attrs(g, 1, n, 32), 32, g)
+    preds = [W.range_pred(0, 0, 0, 1000 * k, 0xF0000000) for k in range(8)]   # ~60 ms on one GB300
+    with P.Context(0, prf_keys=PRF) as c:
+        from tests._helpers import to_dev
+        c.load_shares(0, [to_dev(s) for s in tab["shares"]], 32)
+        assert c.set_poll_limit(2) == P.POLL_LIMIT_DEFAULT_MS
+        tk = c.submit(P.keygen(preds, 32, bytes(16)))
+        t0 = time.time()
+        with pytest.raises(P.OblivgmError) as e:
+            c.poll(tk, -1)
+        assert e.value.status == P.ETIMEOUT and time.time() - t0 < 1.0
+        with pytest.raises(P.OblivgmError) as e:
+            c.poll(tk, 60000)              # a longer timeout is capped by the limit too
+        assert e.value.status == P.ETIMEOUT
+        assert c.set_poll_limit(P.POLL_LIMIT_DEFAULT_MS) == 2
+        r = c.poll(tk, -1)
+        assert r is not None and r["groups"][0]["n_elems"] == n
+        c.release(tk)
+        with pytest.raises(P.OblivgmError) as e:
+            c.set_poll_limit(0)
+        assert e.value.status == P.EINVAL
+
+
+def test_a_failed_served_batch_reports_why():
+    """When a served batch cannot launch (its workspace allocation is refused through the test
+    hook) the poll reports the failure with the launch's own reason, not an empty text."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    g = W.rng(47)
+    tab = W.table(W.uniform_attrs(g, 1, 5000, 32), 32, g)
+    with P.Context(0, prf_keys=PRF) as c:
+        from tests._helpers import to_dev
+        c.load_shares(0, [to_dev(s) for s in tab["shares"]], 32)
+        tok = P.keygen([W.eq_pred(0, 0, 0, 5)], 32, bytes(16))
+        c.test_fail_next_alloc()
+        tk = c.submit(tok)
+        with pytest.raises(P.OblivgmError) as e:
+            c.poll(tk, 60000)
+        assert e.value.status == P.ECUDA and "refused" in str(e.value)
+        c.release(tk)
+        tk = c.submit(tok)                 # the next batch allocates normally
+        assert c.poll(tk, 60000) is not None
+        c.release(tk)

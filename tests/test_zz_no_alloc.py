@@ -62,3 +62,55 @@ def test_no_alloc_rejects_a_query_larger_than_its_array(ctx):
     with pytest.raises(P.OblivgmError) as e:
         ctx.filter_and_combine_noalloc(1, toks, outs)
     assert e.value.status == P.ERANGE
+
+
+def test_no_alloc_calls_back_to_back_on_one_stream(ctx):
+    """Two calls with different queries issued one after the other on one stream, with a
+    single synchronisation at the end: the second call's workspace upload is ordered after the
+    first call's kernel on that stream, so both results equal the ordinary entry point's."""
+    graph = W.edge_graph(10007, 30011, 4, 2, seed=56)
+    load_tables(ctx, graph)
+    queries = [W.bulk_vertex_filter(n_vertices=10007, seed=57)["preds"], W.query_mix(graph, 1, seed=58)[0]["preds"]]
+    toks = [P.keygen(q, 32, bytes([call + 7]) * 16) for call, q in enumerate(queries)]
+    want = [alloc_outs(graph, preds=q) for q in queries]
+    for call, q in enumerate(queries):
+        ctx.filter_and_combine(60 + call, toks[call], want[call])
+    got = [alloc_outs(graph, preds=q) for q in queries]
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    for call in range(2):
+        ctx.filter_and_combine_noalloc(60 + call, toks[call], got[call], stream=s)
+    s.synchronize()
+    ctx.sync(s)
+    torch.cuda.synchronize()
+    for call in range(2):
+        assert _equal(got[call], want[call]), call
+
+
+def test_no_alloc_refuses_a_stream_under_capture(ctx):
+    """The call uploads its workspace from a host buffer that lives only for the call, so a
+    captured call would replay a copy of freed memory: on a capturing stream it must return
+    EINVAL before launching anything, and the context stays usable."""
+    graph = W.edge_graph(1000, 3000, 4, 2, seed=59)
+    load_tables(ctx, graph)
+    preds = [W.eq_pred(0, 0, 0, 5)]
+    toks = P.keygen(preds, 32, bytes(16))
+    outs = alloc_outs(graph, preds=preds)
+    torch.cuda.synchronize()
+    launches = ctx.launch_count()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    caught = None
+    with torch.cuda.graph(g, stream=s):
+        try:
+            ctx.filter_and_combine_noalloc(1, toks, outs, stream=s)
+        except P.OblivgmError as err:
+            caught = err
+    assert caught is not None and caught.status == P.EINVAL
+    assert ctx.launch_count() == launches
+    want = alloc_outs(graph, preds=preds)
+    ctx.filter_and_combine(1, toks, want)
+    ctx.filter_and_combine_noalloc(1, toks, outs)
+    torch.cuda.synchronize()
+    ctx.sync()
+    assert _equal(outs, want)
