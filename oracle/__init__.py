@@ -101,6 +101,10 @@ def lib():
             l.orc_fresh_direct.argtypes = [ctypes.POINTER(_Pred), u32, ctypes.c_int, u8p, u32, u8p, u32, u8p,
                                            ctypes.POINTER(_Table), u32, u8p, u64, u8p]
             l.orc_aes_blocks.restype = u64
+            l.orc_test_plant.argtypes = [ctypes.c_int]
+            l.orc_test_plant.restype = None
+            l.orc_sbox.argtypes = [u32]
+            l.orc_sbox.restype = u32
             l.orc_init()
             _lib = l
     return _lib
@@ -132,6 +136,21 @@ def aes_blocks() -> int:
     """AES-128 blocks the oracle has encrypted on the calling thread since the last reset
     (test instrumentation: the benchmark's algorithmic block counts are checked against it)."""
     return int(lib().orc_aes_blocks())
+
+
+def sbox(x: int) -> int:
+    """The oracle's AES S-box entry for byte x (built from the GF(2^8) inverse and the affine map)."""
+    return int(lib().orc_sbox(x))
+
+
+PLANT_NONE, PLANT_CONST, PLANT_CLEARED_BIT, PLANT_MASK_OVERLAP = 0, 1, 2, 3
+
+
+def test_plant(mode: int) -> None:
+    """Plant a deliberate mistake in the calling thread's oracle (test instrumentation, so a test
+    can show that its pin fails on it): 1 constant Converts and mask words, 2 Converts reading the
+    cleared control bit, 3 <r>_1 read from r's bytes; 0 removes it."""
+    lib().orc_test_plant(mode)
 
 
 def prg(which: int, seed: bytes) -> bytes:

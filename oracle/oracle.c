@@ -142,6 +142,20 @@ static __thread uint64_t AES_BLOCKS;
 uint64_t orc_aes_blocks(void) { return AES_BLOCKS; }
 void orc_aes_blocks_reset(void) { AES_BLOCKS = 0; }
 
+/* Test instrumentation: a mistake the tests plant on purpose in the calling thread, so that
+ * they can show that their uniformity pins fail on it (it never changes results otherwise).
+ *   0  none (the default);
+ *   1  every Convert and every mask word is the constant 0;
+ *   2  Converts read the cleared control bit: a seed's Convert takes bytes 0..3 (Z_{2^32}) or
+ *      bit 0 of byte 0 (Z_2), and a DCF value word is taken from the child seed block
+ *      (whose bit 0 is cleared) instead of the value block;
+ *   3  the mask share <r>_1 is read from the bytes of r itself. */
+static __thread int PLANTED;
+void orc_test_plant(int mode) { PLANTED = mode; }
+
+/* S-box entry (test accessor; the table is built by orc_init) */
+uint32_t orc_sbox(uint32_t x) { return SBOX[x & 0xFFu]; }
+
 static void aes_encrypt(const aes_ks* ks, const uint8_t in[16], uint8_t out[16])
 {
     uint8_t st[4][4];
@@ -215,6 +229,8 @@ static uint32_t group_mask(int group) { return group == GROUP_Z2 ? 1u : 0xFFFFFF
 
 static uint32_t convert_seed_g(const uint8_t s[16], int group)
 {
+    if (PLANTED == 1) return 0u;
+    if (PLANTED == 2) return group == GROUP_Z2 ? (uint32_t)(s[0] & 1) : le32(s);
     return group == GROUP_Z2 ? (uint32_t)((s[0] >> 1) & 1) : le32(s + 4);
 }
 
@@ -222,8 +238,22 @@ static uint32_t convert_seed_g(const uint8_t s[16], int group)
 static uint32_t value_word_g(int dir, const uint8_t s[16], int group)
 {
     uint8_t v[16];
-    prg_h(dir == 0 ? KEY_VL : KEY_VR, s, v);
+    if (PLANTED == 1) return 0u;
+    prg_h(PLANTED == 2 ? (dir == 0 ? KEY_L : KEY_R) : (dir == 0 ? KEY_VL : KEY_VR), s, v);
+    if (PLANTED == 2) v[0] &= 0xFE;   /* the child seed block, control bit cleared */
     return group == GROUP_Z2 ? (uint32_t)(v[0] & 1) : le32(v);
+}
+
+/* A predicate's mask r and its additive shares <r>_1, <r>_2, <r>_3 (mod 2^n) from one random
+ * block: r = bytes 0..3, <r>_1 = bytes 4..7, <r>_2 = bytes 8..11, <r>_3 = r - <r>_1 - <r>_2. */
+static uint32_t mask_words(const uint8_t blk[16], uint32_t m, uint32_t rs[3])
+{
+    uint32_t r = le32(blk) & m;
+    rs[0] = le32(blk + (PLANTED == 3 ? 0 : 4)) & m;
+    rs[1] = le32(blk + 8) & m;
+    if (PLANTED == 1) r = rs[0] = rs[1] = 0u;
+    rs[2] = (r - rs[0] - rs[1]) & m;
+    return r;
 }
 
 /* i-th input bit, i = 1..n, most significant first */
@@ -538,10 +568,7 @@ static int keygen_impl(const orc_pred* preds, uint32_t n_preds, int n, const uin
         if (!onehot) {
             uint8_t blk[16];
             rng_block(&g, blk);
-            r = le32(blk) & m;
-            rs[0] = le32(blk + 4) & m;
-            rs[1] = le32(blk + 8) & m;
-            rs[2] = (r - rs[0] - rs[1]) & m;
+            r = mask_words(blk, m, rs);
         }
         const uint32_t beta = onehot ? 1u : BETA_PRIME;
         /* the functions of the three pairs */
@@ -1018,10 +1045,7 @@ static void fresh_element(const aes_ks* K, const orc_pred* q, uint32_t p, int n,
     uint32_t m = mask_n(n);
     uint8_t blk[16];
     client_block(K, c, p, 1, 0, blk);
-    uint32_t r = le32(blk) & m;
-    rs[0] = le32(blk + 4) & m;
-    rs[1] = le32(blk + 8) & m;
-    rs[2] = (r - rs[0] - rs[1]) & m;
+    uint32_t r = mask_words(blk, m, rs);
     *cbeta = 0;
     for (int pair = 0; pair < 3; pair++) {
         uint8_t s0[16], s1[16];
