@@ -1,19 +1,28 @@
 #!/usr/bin/env python3
-"""Throughput of OblivGM's secure predicate evaluation (secEval, Alg. 3) on GB300.
+"""Throughput and latency of OblivGM's secure predicate evaluation (secEval, Alg. 3) on GB300.
 
 One step = one fused evaluation of the bulk vertex filter: 1,048,576 vertices
 with 4 uint32 attributes (uniform), secret-shared three ways and resident in
 HBM; 8 predicates (4 equality / DPF, 4 range / 2 DCF each) at n = 32, each
 evaluated by all three simulated servers (6 key halves), re-shared to RSS and
 ANDed.  Metric: element-predicate evaluations per second (one unit = one
-predicate on one element, all three servers, re-share included).
+predicate on one element, all three servers, re-share included), beside the
+plain one-query-per-launch GPU path and query p50/p99 latency.
+
+The same JSON line carries, under "workloads", one record per other workload
+of the metric, each timed on its own with its own clocks, roofline, plain-path
+comparison and oracle leg: the 1k/4k path query (n = 16), the triangle +
+pendant query on a 1M-vertex / 10M-edge graph, 256 mixed queries in one
+persistent launch replayed from a CUDA graph, and the serving loop on a
+4M-vertex / 40M-edge graph under Poisson arrivals.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Under torchrun every rank evaluates its own replica of the workload (weak
 scaling; the element filter needs no exchange between GPUs), timed between
-barriers, max over ranks.  --impl reference times the CPU oracle on the host
-cores on bounded samples of the same workload.
+barriers, max over ranks; the per-workload records run on rank 0 of a
+one-GPU run only.  --impl reference times the CPU oracle on the host cores on
+bounded samples of the same workload.
 """
 from __future__ import annotations
 
@@ -208,24 +217,53 @@ def run_reference(args):
     toks = oracle.keygen(wl["preds"], 32, KEY_SEED)
     cores = os.cpu_count() or 1
     per_step_s = min(10.0, max(1.0, 120.0 / max(1, args.steps + args.warmup)))
-    rates = []
-    sample_desc = None
+    rates, secs, sizes = [], [], []
     for s in range(args.warmup + args.steps):
         r, size, dt = oracle_rate(wl, toks, per_step_s, cores, rng_seed=100 + s)
         if s >= args.warmup:
             rates.append(r)
-            sample_desc = f"{size} random vertices of the 1,048,576-vertex table per step, all 8 predicates"
-    value = statistics.mean(rates)
-    units = len(wl["preds"]) * N_VERTICES
+            secs.append(dt)
+            sizes.append(size)
+    # a step is one bounded sample of the table (all 8 predicates on `size` random vertices);
+    # value = element-predicates of the timed samples over their measured seconds
+    units = len(wl["preds"]) * sum(sizes)
+    value = units / sum(secs)
+    sample_desc = (f"{min(sizes)}-{max(sizes)} random vertices of the 1,048,576-vertex table per step, all 8 "
+                   f"predicates, {statistics.mean(secs):.2f} s per step on {cores} threads")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": units / value * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(secs) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic", "config": {"workload": wl["name"], "elements": N_VERTICES, "predicates": 8,
-                                            "n_bits": 32, "servers": 3},
+            "data": "synthetic", "config": {"workload": wl["name"], "elements": N_VERTICES, "attributes": 4,
+                                            "predicates": 8, "n_bits": 32, "servers": 3,
+                                            "step": "one bounded random sample of the table (oracle, all host cores)"},
+            "measured_seconds_per_step": statistics.mean(secs),
+            "extrapolated_full_table_ms_per_step": len(wl["preds"]) * N_VERTICES / value * 1e3,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample_desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def gpu_index_of(local: int) -> int:
+    """nvidia-smi index of this process's CUDA device (honours CUDA_VISIBLE_DEVICES)."""
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        try:
+            return int(vis.split(",")[local])
+        except (ValueError, IndexError):
+            pass
+    return local
+
+
+def lookup_roofline(lookups: float, seconds: float, peak_lu: float, aes: float | None = None) -> dict:
+    """Roofline record of a filter run against the shared-memory T-table lookup ceiling."""
+    ach = lookups / seconds / 1e9
+    out = {"bound": "lds", "achieved": ach, "peak": peak_lu, "unit": "Glookup/s", "frac": ach / peak_lu,
+           "traffic": None,
+           "pipe": "shared-memory (LDS/MIO) AES T-table lookups, one 4-byte word per lane per clock per SM"}
+    if aes is not None:
+        out["aes_blocks_per_s"] = aes / seconds
+    return out
 
 
 def run_ours(args):
@@ -268,14 +306,7 @@ def run_ours(args):
     ctx.sync(stream)
     barrier()
 
-    gpu_index = local
-    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
-    if vis:
-        try:
-            gpu_index = int(vis.split(",")[local])
-        except (ValueError, IndexError):
-            pass
-    sampler = ClockSampler(gpu_index)
+    sampler = ClockSampler(gpu_index_of(local))
     sampler.start()
     launches0 = ctx.launch_count()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -294,6 +325,8 @@ def run_ours(args):
     reduce_max = make_reduce_max(pg, dev) if pg else None
     value, total_s = aggregate_ranks(sum(step_ms) / 1e3, units, args.steps, world, reduce_max)
     ms_per_step = total_s / args.steps * 1e3
+    rec = (sum(o.cpu().numpy().view(np.uint32).astype(np.uint64) for o in outs[0]) & 0xFFFFFFFF)
+    parity_ok = bool(np.array_equal(rec, plain_and(preds, wl["tables"][0]["values"])))
 
     # ---- end to end through the public API with host buffers (pinned), every step:
     # upload the three share sets and the tokens, evaluate, read the result shares back
@@ -318,22 +351,21 @@ def run_ours(args):
     max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     lookups_step = lookups_per_element(preds) * N_VERTICES
     peak_lu = sm_count * LDS_LANES_PER_CLK * max_mhz * 1e6 / 1e9
-    achieved_lu = lookups_step / (ms_per_step / 1e3) / 1e9
-    achieved_aes = aes_step / (ms_per_step / 1e3) / 1e9
-    roofline = {"bound": "alu", "achieved": achieved_lu, "peak": peak_lu, "unit": "Glookup/s",
-                "frac": achieved_lu / peak_lu, "traffic": None, "kernel": "k_filter",
-                "pipe": "shared-memory AES T-table lookups (4-byte LDS, one per lane per clock per SM)",
-                "peak_basis": f"{sm_count} SMs x {LDS_LANES_PER_CLK} lookups/clk x {max_mhz:.0f} MHz",
-                "lookups_per_step": lookups_step, "aes_blocks_per_s": achieved_aes * 1e9}
-    traffic = os.path.join(ROOT, "profiles", "k_filter_traffic.json")
-    if os.path.exists(traffic):
-        try:
-            with open(traffic) as f:
-                tr = json.load(f)
-            if tr.get("kernel_source_hash") == kernel_hash():
-                roofline["traffic"] = tr.get("bytes_per_launch")
-        except (OSError, ValueError):
-            pass
+    roofline = lookup_roofline(lookups_step, ms_per_step / 1e3, peak_lu, aes_step)
+    roofline.update({"kernel": "k_filter", "peak_basis": f"{sm_count} SMs x {LDS_LANES_PER_CLK} lookups/clk x "
+                                                         f"{max_mhz:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)",
+                     "lookups_per_step": lookups_step})
+    rec_traffic = kernel_record("k_filter_traffic.json")
+    if rec_traffic:
+        roofline["traffic"] = rec_traffic.get("bytes_per_launch")
+    rec_issue = kernel_record("k_filter_issue.json")
+    if rec_issue:
+        # every instruction the kernel issues, per AES block (ncu), against the SMs' issue slots
+        # for 32-bit integer work: 128 lanes per clock per SM
+        ipb = float(rec_issue["thread_inst_per_aes_block"])
+        roofline["int32_issue_frac"] = roofline["aes_blocks_per_s"] * ipb / (sm_count * 128 * max_mhz * 1e6)
+        roofline["int32_issue_basis"] = (f"AES blocks/s x {ipb:.1f} thread-instructions per block (ncu, "
+                                         f"{rec_issue['source']}) / ({sm_count} SMs x 128 lanes x {max_mhz:.0f} MHz)")
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -341,8 +373,13 @@ def run_ours(args):
             "config": {"workload": wl["name"], "elements": N_VERTICES, "attributes": 4, "predicates": 8,
                        "predicate_mix": "4 equality (DPF) + 4 range (2 DCF)", "n_bits": 32, "ring": "Z_2^32",
                        "servers": 3, "combine": "RSS AND of all 8", "l2": "flushed between timed steps",
-                       "schedule": {"threads": threads, "elems_per_thread": ept},
-                       "aes_blocks_per_step": aes_step, "parallelism": f"replica x{world}"},
+                       "schedule": {"threads": threads, "elems_per_thread": ept,
+                                    "vector_width": "32-bit coalesced share loads and output stores: the "
+                                                    "one-element-per-thread shape the autotuner picks; the "
+                                                    "128-bit four-element shape spills and runs 1.5x slower, "
+                                                    "and shares are ~1e-5 of the kernel's time"},
+                       "aes_blocks_per_step": aes_step, "parallelism": f"replica x{world}",
+                       "reconstructs_to_plaintext": parity_ok},
             "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},
@@ -352,7 +389,7 @@ def run_ours(args):
             "secondary_units": {
                 "key_half_walks_per_s": sum(6 if p["kind"] == W.PRED_EQ else 12 for p in preds) * N_VERTICES
                 / (ms_per_step / 1e3),
-                "aes_blocks_per_s": achieved_aes * 1e9}}
+                "aes_blocks_per_s": roofline["aes_blocks_per_s"]}}
     # ---- the plain per-query GPU path on the same step (same shares, parity-tested)
     if not args.no_compare:
         l0 = ctx.launch_count()
@@ -365,32 +402,8 @@ def run_ours(args):
                               "what": "per predicate: open + one launch per key half (6 DPF / 12 DCF walks, "
                                       "global-memory AES tables) + sum/re-share + AND launches",
                               "fused_speedup": value / (units / plain_s)}
-        # ---- query latency under Poisson arrivals at half the fused path's measured capacity:
-        # 32 queries of 1-8 predicates (one AND-group) on the resident table, served by the
-        # serving loop (continuous batching) and by the plain path (FIFO)
-        g = W.rng(77)
-        tabs = wl["tables"]
-        qlist = []
-        for _ in range(32):
-            q = W.random_query(g, tabs, 32, int(g.integers(1, 9)), 1, vertex_table=0, edge_table=0)
-            qlist.append(q["preds"])
-        toks_q = [P.keygen(q, 32, bytes([i % 256]) * 16) for i, q in enumerate(qlist)]
-        table_n = {0: N_VERTICES}
-        svc = [query_aes(q, table_n) / (achieved_aes * 1e9) for q in qlist]
-        rate = 0.5 / float(np.mean(svc))
-        arrivals = np.cumsum(g.exponential(1.0 / rate, len(qlist)))
-        arrivals -= arrivals[0]
-        lat, tot, rej = serve_latency(ctx, toks_q, arrivals, P)
-        plain_outs = [query_outs(torch, dev, q, table_n) for q in qlist]
-        plat, ptot = plain_latency(ctx, toks_q, plain_outs, arrivals, stream)
-        del plain_outs
-        line["latency"] = {"queries": len(qlist), "arrival": "Poisson", "rate_qps": rate,
-                           "offered_load": "50% of fused capacity",
-                           "predicates_per_query": "1-8 (uniform), one AND-group on the resident table",
-                           "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "completed_qps": len(qlist) / tot,
-                           "rejected": rej,
-                           "plain_p50_ms": pct(plat, 50), "plain_p99_ms": pct(plat, 99),
-                           "plain_completed_qps": len(qlist) / ptot}
+        line["latency"] = latency_leg(ctx, P, torch, dev, wl, roofline["aes_blocks_per_s"], stream,
+                                      args.latency_queries, args.latency_plain)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
@@ -405,12 +418,58 @@ def run_ours(args):
     line["paper_context"] = {"secEval_10000_candidates_eq_s": 2.6, "candidate_predicates_per_s": 10000 / 2.6,
                              "hardware": "3 x Tesla V100 (one per server), 2.5 Gbps network",
                              "note": "not the same workload or metric; not used for vs_baseline"}
+    ctx.close()
+    del outs, shares_dev, flush
+    torch.cuda.empty_cache()
+    # ---- the metric's other workloads, one record each (one GPU only: they are not replicated)
+    if not args.no_compare and world == 1 and args.workloads:
+        line["workloads"] = {}
+        for name in [w for w in args.workloads.split(",") if w]:
+            t0 = time.perf_counter()
+            line["workloads"][name] = WORKLOAD_RECORDS[name](P, torch, args, (threads, ept))
+            line["workloads"][name]["wall_s"] = time.perf_counter() - t0
+            torch.cuda.empty_cache()
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
     if pg:
         pg.destroy_process_group()
     return 0
+
+
+def latency_leg(ctx, P, torch, dev, wl, aes_per_s, stream, n_queries: int, plain_k: int) -> dict:
+    """Query latency under Poisson arrivals at half the fused path's measured capacity: queries
+    of 1-8 predicates (one AND-group) on the resident 1,048,576-vertex table, served by the
+    serving loop (continuous batching); the plain path serves the first plain_k arrivals as a
+    FIFO at the same arrival times."""
+    g = W.rng(77)
+    tabs = wl["tables"]
+    qlist = []
+    for _ in range(n_queries):
+        q = W.random_query(g, tabs, 32, int(g.integers(1, 9)), 1, vertex_table=0, edge_table=0)
+        qlist.append(q["preds"])
+    toks_q = [P.keygen(q, 32, struct_seed(i)) for i, q in enumerate(qlist)]
+    table_n = {0: N_VERTICES}
+    svc = [query_aes(q, table_n) / aes_per_s for q in qlist]
+    rate = 0.5 / float(np.mean(svc))
+    arrivals = np.cumsum(g.exponential(1.0 / rate, len(qlist)))
+    arrivals -= arrivals[0]
+    lat, tot, rej = serve_latency(ctx, toks_q, arrivals, P)
+    k = min(plain_k, n_queries)
+    plain_outs = [query_outs(torch, dev, q, table_n) for q in qlist[:k]]
+    plat, ptot = plain_latency(ctx, toks_q[:k], plain_outs, arrivals[:k], stream)
+    del plain_outs
+    return {"queries": len(qlist), "arrival": "Poisson", "rate_qps": rate, "offered_load": "50% of fused capacity",
+            "predicates_per_query": "1-8 (uniform), one AND-group on the resident table",
+            "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "max_ms": float(np.max(lat) * 1e3),
+            "completed_qps": len(qlist) / tot, "rejected": rej,
+            "plain_queries": k, "plain_p50_ms": pct(plat, 50), "plain_p99_ms": pct(plat, 99),
+            "fused_p50_ms_same_queries": pct(lat[:k], 50), "fused_p99_ms_same_queries": pct(lat[:k], 99),
+            "plain_completed_qps": k / ptot}
+
+
+def struct_seed(i: int) -> bytes:
+    """16-byte client seed of query i."""
+    return bytes([i % 256, (i >> 8) % 256]) + bytes(14)
 
 
 def run_profile_case(args):
@@ -437,7 +496,7 @@ def run_profile_case(args):
 def kernel_hash() -> str:
     """Hash of the k_filter source: the device AES/FSS and async-copy headers and the kernel's
     part of oblivgm.cu (from the PTX helpers to the raw-batch section), so host-code edits
-    elsewhere do not invalidate a traffic capture."""
+    elsewhere do not invalidate a capture."""
     import hashlib
     h = hashlib.sha256()
     for hdr in ("device_fss.cuh", "ptx_async.cuh"):
@@ -449,6 +508,17 @@ def kernel_hash() -> str:
     b = src.index(b"// ------------------------------------------------------------------ raw batches")
     h.update(src[a:b])
     return h.hexdigest()[:16]
+
+
+def kernel_record(name: str):
+    """An ncu record under profiles/ taken on the current k_filter source, else None."""
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    return rec if rec.get("kernel_source_hash") == kernel_hash() else None
 
 
 def query_aes(preds, table_n, n_bits=32):
@@ -573,8 +643,9 @@ def _load_graph(ctx, torch, dev, graph):
 
 
 def _timed_graph(torch, ctx, plan, stream, warmup, steps):
-    """Capture one plan launch in a CUDA graph, replay it warmup + steps times, time the steps."""
-    for _ in range(max(1, warmup)):
+    """Launch a plan `warmup` times, capture one launch in a CUDA graph and time `steps` replays,
+    each after an L2 flush."""
+    for _ in range(warmup):
         ctx.plan_launch(plan, stream)
     stream.synchronize()
     g = torch.cuda.CUDAGraph()
@@ -592,6 +663,229 @@ def _timed_graph(torch, ctx, plan, stream, warmup, steps):
         b.synchronize()
         ms.append(a.elapsed_time(b))
     return ms
+
+
+def sampled_parity(torch, graph, queries, outs, k_elems=4096, seed=21) -> bool:
+    """Every group of the given queries: the three output share sets, read back at k_elems random
+    elements plus the first and the last, reconstruct to the plaintext AND of the group's
+    predicates (Def. 2) at those elements."""
+    g = W.rng(seed)
+    ok = True
+    for q, out in zip(queries, outs):
+        groups = {}
+        for p in q["preds"]:
+            groups.setdefault(p["group"], []).append(p)
+        for grp, gp in groups.items():
+            vals = graph["tables"][gp[0]["table"]]["values"]
+            n = vals.shape[1]
+            idx = np.unique(np.concatenate([g.integers(0, n, min(k_elems, n)), [0, n - 1]]))
+            it = torch.from_numpy(idx.astype(np.int64)).to(out[grp][0].device)
+            rec = sum(o.index_select(0, it).cpu().numpy().view(np.uint32).astype(np.uint64) for o in out[grp])
+            ok &= bool(np.array_equal(rec & 0xFFFFFFFF, plain_and(gp, vals[:, idx])))
+    return ok
+
+
+def oracle_query_leg(graph, toks_o, preds, seconds: float, what: str, seed: int = 31) -> dict:
+    """The oracle as it stands, on all host cores, on random elements of every group of one query
+    (the same number per group), sized to take about `seconds`; element-predicates/s."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    tabs = [(t["shares"], t["bits"]) for t in graph["tables"]]
+    groups = {}
+    for p in preds:
+        groups.setdefault(p["group"], []).append(p)
+    g = W.rng(seed)
+
+    def run(m):
+        units, t0 = 0, time.perf_counter()
+        for grp, gp in groups.items():
+            n = graph["tables"][gp[0]["table"]]["values"].shape[1]
+            elems = g.integers(0, n, m)
+            oracle.filter_group(toks_o, 1, PRF, tabs, grp, elems, threads=cores)
+            units += m * len(gp)
+        return units, time.perf_counter() - t0
+
+    u, dt = run(2 * cores)
+    m = max(2 * cores, int(2 * cores * seconds / max(dt, 1e-6)))
+    u, dt = run(m)
+    return {"value": u / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{m} random elements of each of the query's {len(groups)} groups ({what}), "
+                      f"{dt:.1f} s on {cores} threads"}
+
+
+def filter_workload_record(P, torch, name: str, graph, queries, sched, steps: int, warmup: int, plain_k: int,
+                           cpu_seconds: float, no_cpu: bool, plain_reps: int = 1) -> dict:
+    """One filter workload, timed on its own: the queries as one prepared batch (one persistent
+    launch) captured in a CUDA graph and replayed, L2 flushed before every replay; the plain
+    per-query path on the first plain_k queries beside the fused launch on the same queries;
+    sampled reconstruction against plaintext; the oracle on a bounded sample of query 0."""
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    peaks = measured_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_lu = sm_count * LDS_LANES_PER_CLK * max_mhz / 1e3
+    n_bits = graph["n_bits"]
+    ctx = P.Context(0, prf_keys=PRF)
+    ctx.set_schedule(*sched)
+    table_n = _load_graph(ctx, torch, dev, graph)
+    toks = [P.keygen(q["preds"], n_bits, struct_seed(i)) for i, q in enumerate(queries)]
+    outs = [query_outs(torch, dev, q["preds"], table_n) for q in queries]
+    qids = list(range(1, len(queries) + 1))
+    units = sum(query_units(q["preds"], table_n) for q in queries)
+    aes = sum(query_aes(q["preds"], table_n, n_bits) for q in queries)
+    lookups = sum(query_lookups(q["preds"], table_n, n_bits) for q in queries)
+    # the plain per-query path on the first plain_k queries, beside the fused launch of the same
+    # queries; those fused launches also warm the kernel up before the timed replays
+    plain = None
+    if plain_k:
+        k = min(plain_k, len(queries))
+        sub = list(range(k))
+        plan = ctx.plan_create([qids[i] for i in sub], [toks[i] for i in sub], [outs[i] for i in sub])
+        fms = _timed_graph(torch, ctx, plan, stream, 1, 2)
+        ctx.plan_destroy(plan)
+        l0 = ctx.launch_count()
+        ps = time_plain(ctx, [toks[i] for i in sub], [outs[i] for i in sub], stream, reps=plain_reps)
+        plain_launches = (ctx.launch_count() - l0) // plain_reps
+        u = sum(query_units(queries[i]["preds"], table_n) for i in sub)
+        pl = sum(query_lookups(queries[i]["preds"], table_n, n_bits) for i in sub)
+        plain = {"queries": k, "value": u / ps, "unit": UNIT, "ms": ps * 1e3, "gpu_launches": plain_launches,
+                 "fused_value_same_queries": u / (np.mean(fms) / 1e3), "fused_speedup": ps / (np.mean(fms) / 1e3),
+                 "frac_of_lookup_ceiling": pl / ps / 1e9 / peak_lu}
+    plan = ctx.plan_create(qids, toks, outs)
+    shape = ctx.plan_describe(plan)
+    sampler = ClockSampler(gpu_index_of(0))
+    sampler.start()
+    ms = _timed_graph(torch, ctx, plan, stream, warmup, steps)
+    clocks = sampler.stop()
+    ctx.plan_destroy(plan)
+    step_s = float(np.mean(ms)) / 1e3
+    k_check = min(8, len(queries))
+    rec = {"metric": METRIC, "value": units / step_s, "unit": UNIT, "ms_per_step": step_s * 1e3,
+           "steps": steps, "warmup": warmup, "gpu_launches": steps,
+           "config": {"workload": name, "queries": len(queries), "element_predicates_per_step": units,
+                      "aes_blocks_per_step": aes, "tables": {str(k): v for k, v in table_n.items()},
+                      "n_bits": n_bits, "l2": "flushed between timed steps",
+                      "launch": f"one persistent {shape['kernel']} launch ({shape['grid']} CTAs x "
+                                f"{shape['threads']} threads, {shape['items']} tiles of {shape['tile']} "
+                                "elements) replayed from a CUDA graph",
+                      "warmup_launches": f"{warmup} of this plan" + (
+                          f", after 3 of the first {plain['queries']} queries' plan (same kernel)" if plain else ""),
+                      "reconstructs_to_plaintext_sampled": sampled_parity(torch, graph, queries[:k_check],
+                                                                          outs[:k_check]),
+                      "parity_queries_checked": k_check},
+           "roofline": lookup_roofline(lookups, step_s, peak_lu, aes),
+           "clocks": clocks}
+    rec["roofline"]["kernel"] = shape["kernel"]
+    if plain:
+        rec["plain_path"] = plain
+    ctx.close()
+    del outs
+    if not no_cpu:
+        import oracle
+        toks_o = oracle.keygen(queries[0]["preds"], n_bits, struct_seed(0))
+        rec["cpu_baseline"] = oracle_query_leg(graph, toks_o, queries[0]["preds"], cpu_seconds, "query 0")
+    return rec
+
+
+def record_tiny(P, torch, args, sched) -> dict:
+    """1,000 vertices / 4,000 edges, 3-vertex path query, one equality + one range predicate, n = 16."""
+    wl = W.tiny_path(seed=1)
+    graph = {"tables": wl["tables"], "n_bits": 16}
+    return filter_workload_record(P, torch, wl["name"], graph, [{"preds": wl["preds"]}], sched,
+                                  steps=args.sub_steps or 20, warmup=3, plain_k=1, cpu_seconds=4.0,
+                                  no_cpu=args.no_cpu_baseline, plain_reps=5)
+
+
+def record_edges(P, torch, args, sched) -> dict:
+    """Triangle + pendant (4 vertices, 4 edges, 6 mixed predicates) on a 1M-vertex / 10M-edge graph."""
+    graph = W.edge_graph(1_000_000, 10_000_000, 2, 2, seed=3)
+    return filter_workload_record(P, torch, "triangle_pendant_1Mv_10Me_6pred_n32", graph,
+                                  [W.triangle_pendant(graph, seed=3)], sched, steps=args.sub_steps or 3, warmup=1,
+                                  plain_k=1, cpu_seconds=4.0, no_cpu=args.no_cpu_baseline)
+
+
+def record_batch(P, torch, args, sched) -> dict:
+    """256 queries (2-8 vertices, 1-6 predicates) on the 1M / 10M graph with 4 vertex attributes,
+    one persistent launch replayed from a CUDA graph; plain path on the first 8 queries."""
+    graph = W.edge_graph(1_000_000, 10_000_000, 4, 2, seed=4)
+    return filter_workload_record(P, torch, "query_mix_256q_1Mv_10Me_n32", graph, W.query_mix(graph, 256, seed=4),
+                                  sched, steps=args.sub_steps or 1, warmup=0, plain_k=8, cpu_seconds=4.0,
+                                  no_cpu=args.no_cpu_baseline)
+
+
+def record_serve(P, torch, args, sched) -> dict:
+    """The serving loop on a 4M-vertex / 40M-edge graph resident in HBM: Poisson arrivals of mixed
+    queries at 50, 200 and 1000 queries/s and at half the estimated capacity, args.serve_queries
+    arrivals per rate; the plain path serves the first args.plain_queries arrivals of each rate as
+    a FIFO at the same arrival times."""
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    peaks = measured_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_lu = sm_count * LDS_LANES_PER_CLK * float(peaks.get("sm_max_mhz", 2070.0)) / 1e3
+    peak_aes = peak_lu / LOOKUPS_PER_AES
+    graph = W.edge_graph(4_000_000, 40_000_000, 4, 2, seed=5)
+    ctx = P.Context(0, prf_keys=PRF)
+    ctx.set_schedule(*sched)
+    table_n = _load_graph(ctx, torch, dev, graph)
+    n_arr = args.serve_queries
+    queries = W.query_mix(graph, n_arr, seed=5)
+    toks = [P.keygen(q["preds"], 32, struct_seed(i)) for i, q in enumerate(queries)]
+    svc = [query_aes(q["preds"], table_n) / (peak_aes * 0.95e9) for q in queries]
+    capacity = 1.0 / float(np.mean(svc))
+    rates = [50.0, 200.0, 1000.0, 0.5 * capacity]
+    units = sum(query_units(q["preds"], table_n) for q in queries)
+    lookups = sum(query_lookups(q["preds"], table_n) for q in queries)
+    aes = sum(query_aes(q["preds"], table_n) for q in queries)
+    runs = []
+    g = W.rng(55)
+    sampler = ClockSampler(gpu_index_of(0))
+    sampler.start()
+    l0 = ctx.launch_count()
+    for rate in rates:
+        arrivals = np.cumsum(g.exponential(1.0 / rate, n_arr))
+        arrivals -= arrivals[0]
+        lat, tot, rej = serve_latency(ctx, toks, arrivals, P)
+        run = {"rate_qps": rate, "queries": n_arr, "completed_qps": n_arr / tot, "wall_s": tot,
+               "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "max_ms": float(np.max(lat) * 1e3),
+               "rejected": rej, "element_predicates_per_s": units / tot,
+               "frac_of_lookup_ceiling": lookups / tot / 1e9 / peak_lu}
+        if args.plain_queries:
+            k = min(args.plain_queries, n_arr)
+            pouts = [query_outs(torch, dev, queries[i]["preds"], table_n) for i in range(k)]
+            plat, ptot = plain_latency(ctx, toks[:k], pouts, arrivals[:k], stream)
+            del pouts
+            run.update({"plain_queries": k, "plain_p50_ms": pct(plat, 50), "plain_p99_ms": pct(plat, 99),
+                        "fused_p50_ms_same_queries": pct(lat[:k], 50),
+                        "fused_p99_ms_same_queries": pct(lat[:k], 99)})
+        runs.append(run)
+    launches = ctx.launch_count() - l0
+    clocks = sampler.stop()
+    ctx.close()
+    sat = runs[:3]
+    sat_s = sum(r["wall_s"] for r in sat)
+    rec = {"metric": METRIC + " and query p50/p99 latency", "value": 3 * units / sat_s, "unit": UNIT,
+           "ms_per_query": sat_s / (3 * n_arr) * 1e3, "steps": 3 * n_arr, "warmup": 0,
+           "gpu_launches": launches,
+           "config": {"workload": "serve_4Mv_40Me_mixed_queries_n32", "tables": {str(k): v for k, v in table_n.items()},
+                      "queries": "2-8 vertices, 1-6 predicates (uniform)", "arrivals_per_rate": n_arr,
+                      "estimated_capacity_qps": capacity,
+                      "value": "element-predicates completed per second over the three overloaded rates "
+                               "(50, 200, 1000 q/s)",
+                      "launches": "the serving loop's fused batches on two streams (continuous batching); "
+                                  "plain path FIFO on the same arrival prefix"},
+           "roofline": lookup_roofline(3 * lookups, sat_s, peak_lu, 3 * aes),
+           "serving": runs, "clocks": clocks}
+    if not args.no_cpu_baseline:
+        import oracle
+        toks_o = oracle.keygen(queries[0]["preds"], 32, struct_seed(0))
+        rec["cpu_baseline"] = oracle_query_leg(graph, toks_o, queries[0]["preds"], 4.0, "query 0 of the mix")
+    return rec
+
+
+WORKLOAD_RECORDS = {"tiny": record_tiny, "edges": record_edges, "batch": record_batch, "serve": record_serve}
 
 
 def run_workload(args):
@@ -952,92 +1246,14 @@ def run_workload(args):
         print(json.dumps(line), flush=True)
         return 0
 
-    if args.workload in ("tiny", "edges", "batch"):
-        if args.workload == "tiny":
-            wl = W.tiny_path(seed=1)
-            graph = {"tables": wl["tables"], "n_bits": 16}
-            queries = [{"preds": wl["preds"]}]
-            name = wl["name"]
-        elif args.workload == "edges":
-            graph = W.edge_graph(1_000_000, 10_000_000, 2, 2, seed=3)
-            queries = [W.triangle_pendant(graph, seed=3)]
-            name = "triangle_pendant_1Mv_10Me_6pred_n32"
-        else:
-            graph = W.edge_graph(1_000_000, 10_000_000, 4, 2, seed=4)
-            queries = W.query_mix(graph, 256, seed=4)
-            name = "query_mix_256q_1Mv_10Me_n32"
-        table_n = _load_graph(ctx, torch, dev, graph)
-        n_bits = graph["n_bits"]
-        toks = [P.keygen(q["preds"], n_bits, bytes([i % 256, i // 256]) + bytes(14)) for i, q in enumerate(queries)]
-        outs = [query_outs(torch, dev, q["preds"], table_n) for q in queries]
-        qids = list(range(1, len(queries) + 1))
-        units = sum(query_units(q["preds"], table_n) for q in queries)
-        aes = sum(query_aes(q["preds"], table_n, n_bits) for q in queries)
-        lookups = sum(query_lookups(q["preds"], table_n, n_bits) for q in queries)
-        plan = ctx.plan_create(qids, toks, outs)
-        shape = ctx.plan_describe(plan)
-        ms = _timed_graph(torch, ctx, plan, stream, args.warmup, args.steps)
-        ctx.plan_destroy(plan)
-        step_s = float(np.mean(ms)) / 1e3
-        t0 = time.perf_counter()
-        ctx.filter_batch(qids, toks, outs, stream)        # end to end: tokens from the host
-        stream.synchronize()
-        e2e_s = time.perf_counter() - t0
-        line.update({"value": units / step_s, "ms_per_step": step_s * 1e3, "steps": args.steps,
-                     "warmup": args.warmup,
-                     "config": {"l2": "flushed between timed steps", "workload": name, "queries": len(queries), "element_predicates_per_step": units,
-                                "aes_blocks_per_step": aes, "tables": {str(k): v for k, v in table_n.items()},
-                                "launch": f"one persistent {shape['kernel']} launch ({shape['grid']} CTAs x "
-                                          f"{shape['threads']} threads, {shape['items']} tiles of {shape['tile']} "
-                                          "elements) replayed from a CUDA graph"},
-                     "roofline": {"bound": "alu", "achieved": lookups / step_s / 1e9, "peak": peak_lu,
-                                  "unit": "Glookup/s", "frac": lookups / step_s / 1e9 / peak_lu,
-                                  "aes_blocks_per_s": aes / step_s},
-                     "e2e": {"value": units / e2e_s, "unit": UNIT, "what": "filter_batch from host tokens, "
-                             "outputs left on the device"}})
-        if not args.no_compare:
-            k = min(8, len(queries))
-            sub = list(range(k))
-            plan = ctx.plan_create([qids[i] for i in sub], [toks[i] for i in sub], [outs[i] for i in sub])
-            fms = _timed_graph(torch, ctx, plan, stream, 1, 2)
-            ctx.plan_destroy(plan)
-            ps = time_plain(ctx, [toks[i] for i in sub], [outs[i] for i in sub], stream)
-            u = sum(query_units(queries[i]["preds"], table_n) for i in sub)
-            line["plain_path"] = {"queries": k, "value": u / ps, "fused_value": u / (np.mean(fms) / 1e3),
-                                  "fused_speedup": ps / (np.mean(fms) / 1e3)}
-    else:
-        graph = W.edge_graph(4_000_000, 40_000_000, 4, 2, seed=5)
-        table_n = _load_graph(ctx, torch, dev, graph)
-        n_arr = args.serve_queries
-        queries = W.query_mix(graph, n_arr, seed=5)
-        toks = [P.keygen(q["preds"], 32, bytes([i % 256, i // 256]) + bytes(14)) for i, q in enumerate(queries)]
-        svc = [query_aes(q["preds"], table_n) / (peak_aes * 0.95e9) for q in queries]
-        capacity = 1.0 / float(np.mean(svc))
-        rates = [50.0, 200.0, 1000.0, 0.5 * capacity]
-        runs = []
-        g = W.rng(55)
-        for rate in rates:
-            arrivals = np.cumsum(g.exponential(1.0 / rate, n_arr))
-            arrivals -= arrivals[0]
-            lat, tot, rej = serve_latency(ctx, toks, arrivals, P)
-            units = sum(query_units(q["preds"], table_n) for q in queries)
-            run = {"rate_qps": rate, "queries": n_arr, "completed_qps": n_arr / tot, "p50_ms": pct(lat, 50),
-                   "p99_ms": pct(lat, 99), "rejected": rej, "element_predicates_per_s": units / tot}
-            if not args.no_compare:
-                k = min(args.plain_queries, n_arr)
-                pouts = [query_outs(torch, dev, queries[i]["preds"], table_n) for i in range(k)]
-                plat, ptot = plain_latency(ctx, toks[:k], pouts, arrivals[:k], stream)
-                del pouts
-                run.update({"plain_queries": k, "plain_p50_ms": pct(plat, 50), "plain_p99_ms": pct(plat, 99),
-                            "fused_p99_ms_same_queries": pct(lat[:k], 99)})
-            runs.append(run)
-        line.update({"value": runs[-1]["element_predicates_per_s"], "config": {
-            "workload": "serve_4Mv_40Me_mixed_queries_n32", "tables": {str(k): v for k, v in table_n.items()},
-            "queries": "2-8 vertices, 1-6 predicates", "estimated_capacity_qps": capacity},
-            "serving": runs})
+    if args.workload in WORKLOAD_RECORDS:
+        ctx.close()
+        args.sub_steps = args.sub_steps or args.steps
+        line.update(WORKLOAD_RECORDS[args.workload](P, torch, args, sched))
+        print(json.dumps(line), flush=True)
+        return 0
     ctx.close()
-    print(json.dumps(line), flush=True)
-    return 0
+    raise ValueError(f"unknown workload {args.workload}")
 
 
 def main():
@@ -1048,9 +1264,19 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--no-compare", action="store_true", help="skip the plain-path and latency comparisons")
-    ap.add_argument("--serve-queries", type=int, default=48, help="arrivals per rate in --workload serve")
-    ap.add_argument("--plain-queries", type=int, default=6, help="plain-path queries per rate in --workload serve")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="the headline step only: skip the plain-path and latency comparisons and the other "
+                         "workloads' records")
+    ap.add_argument("--workloads", default="tiny,edges,batch,serve",
+                    help="records of the other workloads in the default line (comma list of tiny, edges, batch, "
+                         "serve; empty for none)")
+    ap.add_argument("--sub-steps", type=int, default=0, help="timed replays per workload record (0: its default)")
+    ap.add_argument("--latency-queries", type=int, default=200, help="Poisson arrivals of the headline latency leg")
+    ap.add_argument("--latency-plain", type=int, default=100,
+                    help="arrivals of the latency leg that the plain path also serves (a prefix)")
+    ap.add_argument("--serve-queries", type=int, default=200, help="arrivals per rate of the serving record")
+    ap.add_argument("--plain-queries", type=int, default=12,
+                    help="plain-path arrivals per rate of the serving record (a prefix)")
     ap.add_argument("--workload", choices=["bulk", "tiny", "edges", "batch", "serve", "onehot", "fetch", "keygen", "fresh", "shuffle"],
                     default="bulk",
                     help="bulk (default, the headline line); the others print their own line")

@@ -314,6 +314,39 @@ def test_full_size_bulk_filter_sampled(ctx):
     assert np.array_equal(got[:, sample], want)
 
 
+def test_full_size_wide_ranges_many_positives(ctx):
+    """A full-size group whose predicates are wide ranges only, so that most elements match:
+    2^20 vertices, three 32-bit ranges ANDed (about 62 % of the elements reconstruct to 1).
+    Every element against the plaintext, and 1,024 random elements plus the first, the last
+    and the elements on both sides of every tile boundary the launch uses near the start and
+    the end, share for share against the oracle."""
+    n = 1 << 20
+    g = W.rng(71)
+    vals = W.uniform_attrs(g, 3, n, 32)
+    wl = {"tables": [W.table(vals, 32, g)], "preds": [
+        W.range_pred(0, 0, 0, 0x10000000, 0xF0000000),
+        W.range_pred(0, 1, 0, 0x20000000, 0xFFFFFFFF),     # the domain's last value included
+        W.range_pred(0, 2, 0, 0, 0xD0000000)]}             # and its first
+    load_tables(ctx, wl)
+    ctx.autotune()
+    toks = P.keygen(wl["preds"], 32, bytes(range(3, 19)))
+    got = _filter(ctx, wl, toks, 5)[0]
+    rec = oracle.reconstruct(got)
+    plain = oracle.plain_group(wl["preds"], 0, vals)
+    assert np.array_equal(rec, plain)
+    assert 0.55 < plain.mean() < 0.70
+    outs = alloc_outs(wl)
+    plan = ctx.plan_create([5], [toks], [outs])
+    tile = ctx.plan_describe(plan)["tile"]
+    ctx.plan_destroy(plan)
+    edges = [t * tile + d for t in (1, 2, 3, n // tile - 1, n // tile) for d in (-1, 0, 1)]
+    sample = np.unique(np.concatenate([[0, n - 1], [e for e in edges if 0 <= e < n],
+                                       W.rng(72).integers(0, n, 1024)]))
+    assert len(sample) >= 1024
+    want = oracle_group(oracle, wl, toks, 5, 0, sample, threads=16)
+    assert np.array_equal(got[:, sample], want)
+
+
 def test_plain_path_equals_fused_and_oracle(ctx):
     """The plain per-query path (one launch per key half, global-memory AES tables) gives the
     same shares as the fused kernel and the oracle."""
