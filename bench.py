@@ -793,8 +793,9 @@ def record_tiny(P, torch, args, sched) -> dict:
     """1,000 vertices / 4,000 edges, 3-vertex path query, one equality + one range predicate, n = 16."""
     wl = W.tiny_path(seed=1)
     graph = {"tables": wl["tables"], "n_bits": 16}
+    # a step is ~0.06 ms: 3,000 timed replays keep the clock sampler (200 ms period) in the region
     return filter_workload_record(P, torch, wl["name"], graph, [{"preds": wl["preds"]}], sched,
-                                  steps=args.sub_steps or 20, warmup=3, plain_k=1, cpu_seconds=4.0,
+                                  steps=args.sub_steps or 3000, warmup=3, plain_k=1, cpu_seconds=4.0,
                                   no_cpu=args.no_cpu_baseline, plain_reps=5)
 
 

@@ -457,10 +457,11 @@ oblivgm_status oblivgm_fetch_multi(oblivgm_ctx* ctx, uint32_t table_id, const ui
  * 0, no re-share needed) and of each listed attribute
  * (sum_c [[v_c]] (x) [[x_c]] with one re-share; counter element = attribute
  * index, step = 256 + group, table, query), the attribute values reducing
- * mod 2^n of the table.  out is cleared and then accumulated into (each
- * word is a sum mod 2^32), so it must not be read or written by other work
- * until the call's stream work completes.  n_attrs <= 64.  Asynchronous on
- * stream.  Errors: EINVAL, ENOENT (table), ECUDA. */
+ * mod 2^n of the table.  Every word of out is written once, by the call's
+ * last kernel, so out must not be read or written by other work until the
+ * call's stream work completes.  The per-CTA partial sums live in a
+ * stream-ordered workspace (cudaMallocAsync).  n_attrs <= 64.  Asynchronous
+ * on stream.  Errors: EINVAL, ENOENT (table), ENOMEM, ECUDA. */
 oblivgm_status oblivgm_fetch_unique(oblivgm_ctx* ctx, uint32_t query_id, uint32_t group, uint32_t table_id,
                                     const uint32_t* const x[3], uint32_t n_attrs, const uint32_t* attrs,
                                     uint32_t* out, void* stream);
