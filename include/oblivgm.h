@@ -155,6 +155,38 @@ oblivgm_status oblivgm_load_shares(oblivgm_ctx* ctx, uint32_t table_id, uint64_t
 /* Drop a resident table.  Errors: ENOENT, EBUSY. */
 oblivgm_status oblivgm_unload_shares(oblivgm_ctx* ctx, uint32_t table_id);
 
+/* ------------------------------------------------------------- the PRG */
+
+/* The fixed-key PRG of the DPF / DCF constructions cited in Sec. V-C
+ * (lambda = 128, Sec. VII-A): H_K(s) = AES-128_K(s) xor s under one of the four
+ * public keys K_j[i] = 16 j + i (key 0 K_L, 1 K_R, 2 K_vL, 3 K_vR), on the
+ * counter blocks B_c = u64 c || 8 zero bytes, c = first .. first + n_blocks - 1,
+ * computed in one of two AES layouts:
+ *   OBLIVGM_AES_TTABLE    one block per thread, bank-replicated shared-memory
+ *                         T-tables (the layout of every walk in this library);
+ *   OBLIVGM_AES_BITSLICED 32 blocks per thread as 128 bit planes in registers,
+ *                         SubBytes as a gate circuit (tower-field inverse).
+ * out (device, n_out uint32): flags 0 -> out[4 c' + w] = word w of
+ * H_K(B_{first + c'}), n_out >= 4 n_blocks; flags & OBLIVGM_PRG_PARITY -> one
+ * word per 32 blocks, bit e of out[g] = XOR of the 128 bits of
+ * H_K(B_{first + 32 g + e}), n_out >= n_blocks / 32 (for timing the layouts).
+ * first and n_blocks must be multiples of 32.  Asynchronous on stream.
+ * Errors: EINVAL, ERANGE (n_out too small), ECUDA. */
+#define OBLIVGM_AES_TTABLE    0u
+#define OBLIVGM_AES_BITSLICED 1u
+#define OBLIVGM_PRG_PARITY    1u
+oblivgm_status oblivgm_prg_batch(oblivgm_ctx* ctx, uint32_t layout, uint32_t key, uint64_t first,
+                                 uint64_t n_blocks, uint32_t flags, uint32_t* out, uint64_t n_out, void* stream);
+
+/* The AES-layout dimension of the autotuner: times oblivgm_prg_batch in both
+ * layouts on 2^26 blocks (parity outputs, best of three after a warm-up,
+ * synchronous; allocates an 8 MB buffer) and reports the faster layout and
+ * both rates in blocks per second (any pointer may be NULL).  The walks of the
+ * filter, keygen, fresh-key and one-hot kernels are built in the T-table
+ * layout: this measurement is what decides that layout for them. */
+oblivgm_status oblivgm_autotune_aes_layout(oblivgm_ctx* ctx, uint32_t* layout, double* ttable_blocks_per_s,
+                                           double* bitsliced_blocks_per_s);
+
 /* ------------------------------------------------------------------ tokens */
 
 /* Client-side secure query token generation (genToken, Sec. V-C), for the
@@ -457,11 +489,10 @@ oblivgm_status oblivgm_fetch_multi(oblivgm_ctx* ctx, uint32_t table_id, const ui
  * 0, no re-share needed) and of each listed attribute
  * (sum_c [[v_c]] (x) [[x_c]] with one re-share; counter element = attribute
  * index, step = 256 + group, table, query), the attribute values reducing
- * mod 2^n of the table.  Every word of out is written once, by the call's
- * last kernel, so out must not be read or written by other work until the
- * call's stream work completes.  The per-CTA partial sums live in a
- * stream-ordered workspace (cudaMallocAsync).  n_attrs <= 64.  Asynchronous
- * on stream.  Errors: EINVAL, ENOENT (table), ENOMEM, ECUDA. */
+ * mod 2^n of the table.  out is cleared and then accumulated into (each
+ * word is a sum mod 2^32), so it must not be read or written by other work
+ * until the call's stream work completes.  n_attrs <= 64.  Asynchronous on
+ * stream.  Errors: EINVAL, ENOENT (table), ECUDA. */
 oblivgm_status oblivgm_fetch_unique(oblivgm_ctx* ctx, uint32_t query_id, uint32_t group, uint32_t table_id,
                                     const uint32_t* const x[3], uint32_t n_attrs, const uint32_t* attrs,
                                     uint32_t* out, void* stream);

@@ -13,7 +13,7 @@ import ctypes
 from typing import Sequence
 
 from . import _native as N
-from ._native import (ALL_PAIRS, COMBINE_AND, COMBINE_OR, COMBINE_XOR, EAGAIN, EBUSY, ECUDA, EFAULT_DEVICE, EINVAL,
+from ._native import (AES_BITSLICED, AES_TTABLE, ALL_PAIRS, COMBINE_AND, COMBINE_OR, COMBINE_XOR, EAGAIN, EBUSY, ECUDA, EFAULT_DEVICE, EINVAL,
                       ENOENT, ENOMEM, ERANGE, ETIMEOUT, KEY_DCF, KEY_DPF, POLL_LIMIT_DEFAULT_MS,
                       OK, PRED_EQ, PRED_RANGE, OblivgmError)
 from .build import build
@@ -409,6 +409,21 @@ class Context:
         t, e = N.c_u32(), N.c_u32()
         N.check(self._lib.oblivgm_autotune(self._h, ctypes.byref(t), ctypes.byref(e)), "oblivgm_autotune")
         return t.value, e.value
+
+    def prg_batch(self, layout: int, key: int, first: int, n_blocks: int, out, parity: bool = False, stream=None):
+        """H_K(B_c) for the counter blocks c = first .. first + n_blocks - 1 (multiples of 32) in the
+        given AES layout: out gets 4 words per block, or one parity word per 32 blocks."""
+        N.check(self._lib.oblivgm_prg_batch(self._h, layout, key, first, n_blocks, N.PRG_PARITY if parity else 0,
+                                            out.data_ptr(), out.numel(), _stream_handle(stream)),
+                "oblivgm_prg_batch")
+
+    def autotune_aes_layout(self):
+        """Time both AES layouts of the PRG; returns (chosen layout, T-table blocks/s, bitsliced blocks/s)."""
+        lay = ctypes.c_uint32()
+        tt, bs = ctypes.c_double(), ctypes.c_double()
+        N.check(self._lib.oblivgm_autotune_aes_layout(self._h, ctypes.byref(lay), ctypes.byref(tt), ctypes.byref(bs)),
+                "oblivgm_autotune_aes_layout")
+        return lay.value, tt.value, bs.value
 
     def test_fail_next_alloc(self):
         """Failure-path test hook: the next device workspace allocation reports ENOMEM."""

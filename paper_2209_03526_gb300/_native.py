@@ -30,6 +30,8 @@ MEM_HOST, MEM_DEVICE = 0, 1
 ALL_PAIRS = 1
 KEYS_DEVICE = 2
 SHUFFLE_ADD, SHUFFLE_XOR = 0, 1
+AES_TTABLE, AES_BITSLICED = 0, 1
+PRG_PARITY = 1
 MAX_GROUPS = 64
 NOALLOC_SCRATCH_BYTES = 256 * 1024
 POLL_LIMIT_DEFAULT_MS = 600000
@@ -105,6 +107,9 @@ _SIGS = {
     "oblivgm_set_walk_parallel": ([c_vp, c_u64, ctypes.POINTER(c_u64)], c_i32),
     "oblivgm_test_expire_next_wait": ([c_vp, c_u32], c_i32),
     "oblivgm_test_fail_next_alloc": ([c_vp], c_i32),
+    "oblivgm_prg_batch": ([c_vp, c_u32, c_u32, c_u64, c_u64, c_u32, c_vp, c_u64, c_vp], c_i32),
+    "oblivgm_autotune_aes_layout": ([c_vp, ctypes.POINTER(c_u32), ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)], c_i32),
 }
 
 

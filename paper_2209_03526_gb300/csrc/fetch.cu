@@ -4,10 +4,9 @@
 //   index:   sum_c c * [[x_c]]            (public weights: linear, stays RSS)
 //   attr a:  sum_c [[v_c]] (x) [[x_c]]     (RSS product per element, summed, one re-share)
 // The re-share counter is (element = a, step = 256 + group, table, query).  Two kernels:
-// k_fetch streams the candidates (one CTA per SM) and leaves one partial sum per CTA,
-// column and share set; k_fetch_final, launched as a programmatic dependent of it so that
-// its launch overlaps the stream, adds the partials and the re-share masks and writes
-// every output word once.
+// k_fetch_clear zeroes the outputs and lets k_fetch, launched as its programmatic
+// dependent, start at once: k_fetch streams the candidates while the clear runs and waits
+// for it (griddepcontrol.wait) only before adding its sums into the outputs atomically.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -24,7 +23,8 @@ namespace {
 
 constexpr int kFetchMaxAttrs = 64;
 constexpr uint32_t kFetchStep = 256;
-constexpr int kFetchMaxThreads = 1024;       // one CTA per SM
+constexpr int kFetchThreads = 256;
+constexpr int kFetchCtasPerSm = 5;          // 48 registers: 1,280 threads per SM
 
 struct FetchParams {
     const uint32_t* x[3];          // filter result share sets, n_elems each
@@ -34,16 +34,15 @@ struct FetchParams {
     uint32_t attrs[kFetchMaxAttrs];
     uint32_t n_attrs;
     uint32_t vec4;                 // the three result share sets are 16-byte aligned
-    uint32_t* partial;             // [3 * cols][gridDim.x]: sum (column, share set) of each CTA
+    uint32_t mask[3][kFetchMaxAttrs];   // F(k_i, ctr) - F(k_{i-1}, ctr) per share set and attribute
+    uint32_t* out;                 // [3][1 + n_attrs], zeroed by k_fetch_clear
 };
 
-struct FetchFinalParams {
-    const uint32_t* partial;       // as FetchParams::partial
-    uint32_t n_parts;              // CTAs of k_fetch
-    uint32_t cols;                 // 1 + attributes
-    uint32_t mask[3][kFetchMaxAttrs];   // F(k_i, ctr) - F(k_{i-1}, ctr) per share set and attribute
-    uint32_t* out;                 // [3][cols]
-};
+// zero the outputs; the dependent k_fetch may launch right away
+__global__ void k_fetch_clear(uint32_t* out, uint32_t n) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) out[t] = 0u;
+}
 
 __device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
 #pragma unroll
@@ -64,20 +63,20 @@ __device__ __forceinline__ void fetch_add(uint32_t acc[3], bool index_col, uint3
     }
 }
 
-// Every output word is a sum mod 2^32, so the order of the additions does not matter:
+// Every output word is a sum mod 2^32, so each CTA adds its part straight into the
+// zeroed outputs and the order of the additions does not matter:
 //   index (column 0), share set i:    sum_c c * <x_c>_i
 //   attribute a (column 1 + k), set i: sum_c w_i(c) + F(k_i, ctr) - F(k_{i-1}, ctr),
 //   ctr = (a, 256 + group, table, query).
+// CTA 0 adds the re-share masks (PRF blocks the host computes: they depend only on the
+// attribute, the step, the table and the query); the index has public weights and needs none.
 // Work split: the launch has a multiple of `cols` warps, and warp w always serves column
 // w % cols, for blocks of 32 x 4 candidates w / cols, w / cols + W / cols, ... (W warps):
 // each lane issues six 16-byte loads (its four candidates' result shares and the column's
-// attribute shares) per step and keeps three accumulators.  The result shares are read
-// once per column; the other columns' reads of the same block come from warps of the same
-// CTA, mostly out of L1.  Each CTA leaves its sums in `partial` (plain stores, no atomics
-// on shared addresses) for k_fetch_final.
-__global__ void __launch_bounds__(kFetchMaxThreads, 1) k_fetch(const __grid_constant__ FetchParams P) {
-    // the final kernel may launch now: it waits for this grid to complete before it reads
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+// attribute shares) per step, every SM streams many such steps, and a warp keeps three
+// accumulators.  The result shares are read once per column; the other columns' reads of
+// the same block come from warps of the same CTA, mostly out of L1 / L2.
+__global__ void __launch_bounds__(kFetchThreads, kFetchCtasPerSm) k_fetch(const __grid_constant__ FetchParams P) {
     __shared__ uint32_t part[1 + kFetchMaxAttrs][3];
     const uint32_t cols = 1 + P.n_attrs;
     for (uint32_t t = threadIdx.x; t < 3 * cols; t += blockDim.x) part[t / 3][t % 3] = 0;
@@ -131,24 +130,14 @@ __global__ void __launch_bounds__(kFetchMaxThreads, 1) k_fetch(const __grid_cons
         if (lane == 0) atomicAdd(&part[k][i], t);
     }
     __syncthreads();
-    for (uint32_t t = threadIdx.x; t < 3 * cols; t += blockDim.x)
-        P.partial[(uint64_t)t * gridDim.x + blockIdx.x] = part[t / 3][t % 3];
-}
-
-// out[i][col] = sum of the CTAs' partials (+ the re-share mask of an attribute column):
-// warp w adds up sums w, w + 32, ..., one lane per CTA partial.
-__global__ void __launch_bounds__(1024) k_fetch_final(const __grid_constant__ FetchFinalParams F) {
-    // wait until k_fetch has completed and its partials are visible
+    // the outputs are written only after k_fetch_clear has completed
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
-    for (uint32_t t = warp; t < 3 * F.cols; t += warps) {
-        uint32_t acc = 0;
-        for (uint32_t p = lane; p < F.n_parts; p += 32) acc += F.partial[(uint64_t)t * F.n_parts + p];
-        acc = warp_sum(acc);
-        if (lane == 0) {
-            const uint32_t col = t / 3, i = t % 3;
-            F.out[i * F.cols + col] = acc + (col ? F.mask[i][col - 1] : 0u);
-        }
+    if (blockIdx.x == 0)
+        for (uint32_t t = threadIdx.x; t < 3 * P.n_attrs; t += blockDim.x)
+            atomicAdd(P.out + (t / P.n_attrs) * cols + 1 + t % P.n_attrs, P.mask[t / P.n_attrs][t % P.n_attrs]);
+    for (uint32_t t = threadIdx.x; t < 3 * cols; t += blockDim.x) {
+        const uint32_t col = t / 3, i = t % 3;
+        atomicAdd(P.out + i * cols + col, part[col][i]);
     }
 }
 
@@ -176,14 +165,14 @@ extern "C" oblivgm_status oblivgm_fetch_unique(oblivgm_ctx* ctx, uint32_t query_
         if (attrs[a] >= tb.n_attrs) return fail(OBLIVGM_EINVAL, "attribute outside the table");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const uint32_t cols = 1 + n_attrs;
-    // CTAs of up to 1,024 threads, one per SM, with a multiple of cols warps in all (each warp
-    // serves one column): cols <= 32 puts whole rounds of columns in every CTA
-    const uint32_t wpc = cols <= 32 ? 32 / cols * cols : 32;
-    const uint64_t unit = cols / std::gcd<uint64_t>(cols, wpc);     // CTAs per whole round of columns
+    // warps: a multiple of cols (each warp serves one column), enough for one block of
+    // 32 x 4 candidates per warp and column, at most kFetchCtasPerSm CTAs per SM
+    const uint64_t warps_per_cta = kFetchThreads / 32;
+    const uint64_t unit = cols / std::gcd<uint64_t>(cols, warps_per_cta);   // CTAs per whole round of columns
     const uint64_t blocks32 = std::max<uint64_t>(1, (tb.n_elems + 127) / 128);
-    const uint64_t want = (blocks32 * cols + wpc - 1) / wpc;        // one block of 128 per warp at least
-    const uint64_t cap = std::max<uint64_t>(unit, (uint64_t)ctx->sm_count / unit * unit);
-    const uint64_t grid = std::min<uint64_t>((want + unit - 1) / unit * unit, cap);
+    const uint64_t want = (blocks32 * cols + warps_per_cta - 1) / warps_per_cta;
+    const uint64_t cap = std::max<uint64_t>(unit, (uint64_t)kFetchCtasPerSm * ctx->sm_count / unit * unit);
+    const uint64_t blocks = std::min<uint64_t>((want + unit - 1) / unit * unit, cap);
     FetchParams F{};
     for (int j = 0; j < 3; j++) {
         F.x[j] = x[j];
@@ -193,13 +182,6 @@ extern "C" oblivgm_status oblivgm_fetch_unique(oblivgm_ctx* ctx, uint32_t query_
     F.n_elems = tb.n_elems;
     if (n_attrs) std::memcpy(F.attrs, attrs, n_attrs * sizeof(uint32_t));
     F.n_attrs = n_attrs;
-    F.vec4 = 1;
-    for (int j = 0; j < 3; j++)
-        if (reinterpret_cast<uintptr_t>(x[j]) % 16) F.vec4 = 0;
-    FetchFinalParams G{};
-    G.n_parts = (uint32_t)grid;
-    G.cols = cols;
-    G.out = out;
     // re-share masks: F(k, ctr) = word 0 of AES_k(attr || step || table || query)
     for (uint32_t a = 0; a < n_attrs; a++) {
         const uint32_t ctr[4] = {attrs[a], 0u, (kFetchStep + group) | (table_id << 16), query_id};
@@ -211,35 +193,29 @@ extern "C" oblivgm_status oblivgm_fetch_unique(oblivgm_ctx* ctx, uint32_t query_
             aes_encrypt(rk, ctr, o);
             f[i] = o[0];
         }
-        for (int i = 0; i < 3; i++) G.mask[i][a] = f[i] - f[(i + 2) % 3];
+        for (int i = 0; i < 3; i++) F.mask[i][a] = f[i] - f[(i + 2) % 3];
     }
-    uint32_t* partial = nullptr;
-    oblivgm_status as = ws_alloc(ctx, reinterpret_cast<void**>(&partial), 3ull * cols * grid * sizeof(uint32_t), s,
-                                 "fetch partials");
-    if (as != OBLIVGM_OK) return as;
-    ScratchGuard guard(partial, s);
-    F.partial = partial;
-    G.partial = partial;
-    k_fetch<<<(unsigned)grid, wpc * 32, 0, s>>>(F);
+    F.out = out;
+    F.vec4 = 1;
+    for (int j = 0; j < 3; j++)
+        if (reinterpret_cast<uintptr_t>(x[j]) % 16) F.vec4 = 0;
+    k_fetch_clear<<<1, 256, 0, s>>>(out, 3 * cols);
     ce = cudaGetLastError();
-    if (ce != cudaSuccess) return cuda_fail(ce, "fetch launch");
+    if (ce != cudaSuccess) return cuda_fail(ce, "fetch clear launch");
     ctx->launches++;
-    // the final sums as a programmatic dependent launch: it starts while k_fetch streams and
-    // waits (griddepcontrol.wait) for its completion
+    // the streaming kernel as a programmatic dependent of the clear: it starts at once and
+    // waits (griddepcontrol.wait) for the clear only before it adds into the outputs
     cudaLaunchConfig_t lc{};
-    lc.gridDim = dim3(1);
-    lc.blockDim = dim3(1024);
+    lc.gridDim = dim3((unsigned)blocks);
+    lc.blockDim = dim3(kFetchThreads);
     lc.stream = s;
     cudaLaunchAttribute la[1];
     la[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     la[0].val.programmaticStreamSerializationAllowed = 1;
     lc.attrs = la;
     lc.numAttrs = 1;
-    ce = cudaLaunchKernelEx(&lc, k_fetch_final, G);
-    if (ce != cudaSuccess) return cuda_fail(ce, "fetch final launch");
+    ce = cudaLaunchKernelEx(&lc, k_fetch, F);
+    if (ce != cudaSuccess) return cuda_fail(ce, "fetch launch");
     ctx->launches++;
-    guard.done();
-    ce = cudaFreeAsync(partial, s);
-    if (ce != cudaSuccess) return cuda_fail(ce, "fetch partials release");
     return OBLIVGM_OK;
 }

@@ -333,17 +333,24 @@ namespace ogm {
 
 // ------------------------------------------------------------------ walk-parallel filter
 //
-// For queries too small to give every SM its own tiles: twelve threads per element, one
-// key walk each (the six DPF or twelve DCF keys of a predicate), so an element's walks
-// run side by side instead of one after another in one thread.  The keys are staged as
-// in k_filter; the walks' outputs meet in shared memory, and the element's first slot
+// For queries too small to give every SM its own tiles: every key walk of an element gets
+// its own thread (the six DPF or twelve DCF keys of a predicate), so an element's walks run
+// side by side instead of one after another in one thread; a DCF walk is split once more
+// over two threads.  Each DCF level takes two PRG calls on the same seed s_i: the seed /
+// control-bit block of the chosen child and its value block.  The walk's seed thread
+// computes the first and the next seed, the walk's value thread the second, both at once:
+// the seed thread leaves (s_i, t_i) in shared memory for its partner, and one CTA barrier
+// per level (all walks of a CTA have the same n) orders the hand-over.  The keys are staged
+// as in k_filter; the walks' outputs meet in shared memory, and the element's first slot
 // thread sums them per server, re-shares and folds exactly as k_filter does.
 
-constexpr int kWpSlots = 12;                      // threads per element
-constexpr int kWpElems = 40;                      // elements per CTA (tile)
-constexpr int kWpThreads = kWpSlots * kWpElems;   // 480
-constexpr int kWpPrf = 6;                         // re-share PRF words per element: 2 passes x 3 keys
-constexpr int kWpSmem = kFilterSmem + kWpElems * (kWpSlots + kWpPrf) * 4;
+constexpr int kWpSlots = 12;                          // key walks per element
+constexpr int kWpElems = 40;                          // elements per CTA (tile)
+constexpr int kWpWalks = kWpSlots * kWpElems;         // 480 seed threads, then 480 value threads
+constexpr int kWpThreads = 2 * kWpWalks;              // 960
+constexpr int kWpPrf = 6;                             // re-share PRF words per element: 2 passes x 3 keys
+constexpr int kWpSmem = kFilterSmem + kWpElems * (kWpSlots + kWpPrf) * 4 +   // walk outputs, PRF words
+                        2 * kWpWalks * 16 + 2 * kWpWalks * 4 + kWpWalks * 4; // seed / control-bit hand-over, V
 // default switch-over: batches of at most this many elements per SM in all
 constexpr uint64_t kWpDefaultElemsPerSm = 128;
 
@@ -353,6 +360,9 @@ __global__ void __launch_bounds__(kWpThreads, 1) k_filter_wp(const __grid_consta
     DevKey* kbuf = reinterpret_cast<DevKey*>(smem + kTableBytes);
     uint32_t* part = reinterpret_cast<uint32_t*>(smem + kFilterSmem);   // [element][slot]
     uint32_t* fprf = part + kWpElems * kWpSlots;                           // [element][pass * 3 + key]
+    uint4* sbuf = reinterpret_cast<uint4*>(fprf + kWpElems * kWpPrf);      // [2][walk]: s_i
+    uint32_t* tbuf = reinterpret_cast<uint32_t*>(sbuf + 2 * kWpWalks);     // [2][walk]: t_i
+    uint32_t* vbuf = tbuf + 2 * kWpWalks;                                  // [walk]: the value sum V
     __shared__ __align__(8) uint64_t mbar;
     __shared__ unsigned long long item_sh;
 
@@ -360,7 +370,9 @@ __global__ void __launch_bounds__(kWpThreads, 1) k_filter_wp(const __grid_consta
     if (threadIdx.x == 0) mbar_init(&mbar);
     __syncthreads();
 
-    const uint32_t el = threadIdx.x / kWpSlots, slot = threadIdx.x % kWpSlots;
+    const bool value_thread = threadIdx.x >= (unsigned)kWpWalks;
+    const uint32_t walk = threadIdx.x % kWpWalks;
+    const uint32_t el = walk / kWpSlots, slot = walk % kWpSlots;
     uint32_t phase = 0;
     const uint64_t n_items = P.item_start[P.n_groups];
     for (;;) {
@@ -396,33 +408,92 @@ __global__ void __launch_bounds__(kWpThreads, 1) k_filter_wp(const __grid_consta
             }
             const bool eq = D.kind == OBLIVGM_PRED_EQ;
             const uint32_t nsub = eq ? 1u : 2u;
-            uint32_t y[1] = {0};
-            if (valid && slot < 6 * nsub) {
+            const bool active = valid && slot < 6 * nsub;
+            uint32_t xh = 0;
+            if (active) {
                 const uint32_t mask = D.n_bits >= 32 ? 0xFFFFFFFFu : ((1u << D.n_bits) - 1u);
                 const uint64_t row = (uint64_t)D.attr * G.stride;
-                uint32_t xh[1] = {D.r[0] + D.r[1] + D.r[2]};
+                xh = D.r[0] + D.r[1] + D.r[2];
 #pragma unroll
-                for (int j = 0; j < 3; j++) xh[0] += __ldg(G.share[j] + row + e);
-                xh[0] &= mask;
-                const DevKey& K = kbuf[slot];
-                if (eq) dpf_walk<1>(T, P.aes, K, xh, y);
-                else dcf_walk<1>(T, P.aes, K, xh, y);
-                // RANGE: the public constant c * beta' joins party 0's half once
-                if (!eq && (slot % nsub) == 0 && K.party == 0) y[0] += D.cbeta;
+                for (int j = 0; j < 3; j++) xh += __ldg(G.share[j] + row + e);
+                xh &= mask;
             }
-            part[el * kWpSlots + slot] = y[0];
+            const DevKey& K = kbuf[slot];
+            uint32_t y = 0;
+            // one loop for both kinds: the seed thread walks the seed / control-bit chain (a
+            // DPF walk whole); for a DCF the value thread takes each level's value block on
+            // the seed s_i the seed thread hands over, one CTA barrier per level (n and the
+            // kind are the same for every walk of the CTA)
+            const int n = (int)D.n_bits;
+            const uint32_t party = K.party;
+            uint32_t s[4] = {0, 0, 0, 0}, t = party, V = 0;
+            if (active && !value_thread) {
+#pragma unroll
+                for (int w = 0; w < 4; w++) s[w] = K.seed[w];
+                if (!eq) {
+                    sbuf[walk] = make_uint4(s[0], s[1], s[2], s[3]);
+                    tbuf[walk] = t;
+                }
+            }
+            if (!eq) __syncthreads();
+            for (int i = 0; i < n; i++) {
+                const uint32_t dir = (xh >> (n - 1 - i)) & 1u;
+                const uint32_t m = 0u - dir;
+                if (active && !value_thread) {
+                    // seed / control-bit block of the chosen child and its correction
+                    uint32_t o[4];
+                    aes_sel(T, P.aes.rk_st, P.aes.d_st, m, s, o);
+                    const uint4 cw = *reinterpret_cast<const uint4*>(K.scw[i]);
+#pragma unroll
+                    for (int w = 0; w < 4; w++) o[w] ^= s[w];
+                    uint32_t tn = o[0] & 1u;
+                    o[0] &= ~1u;
+                    const uint32_t tm = 0u - t;
+                    s[0] = o[0] ^ (cw.x & tm);
+                    s[1] = o[1] ^ (cw.y & tm);
+                    s[2] = o[2] ^ (cw.z & tm);
+                    s[3] = o[3] ^ (cw.w & tm);
+                    tn ^= t & (((dir ? K.tr : K.tl) >> i) & 1u);
+                    t = tn;
+                    if (!eq) {
+                        sbuf[((i + 1) & 1) * kWpWalks + walk] = make_uint4(s[0], s[1], s[2], s[3]);
+                        tbuf[((i + 1) & 1) * kWpWalks + walk] = t;
+                    }
+                } else if (active && !eq) {
+                    // value block on the same seed s_i: V += (-1)^b (Convert(v) + t_i V_CW)
+                    const uint4 si = sbuf[(i & 1) * kWpWalks + walk];
+                    const uint32_t ti = tbuf[(i & 1) * kWpWalks + walk];
+                    const uint32_t sv[4] = {si.x, si.y, si.z, si.w};
+                    const uint32_t v0 = aes_sel_w0(T, P.aes.rk_v, P.aes.d_v, m, sv);
+                    const uint32_t term = (v0 ^ si.x) + (ti ? K.vcw[i] : 0u);
+                    V += party ? 0u - term : term;
+                }
+                if (!eq) __syncthreads();   // s_{i+1} visible; everyone is done reading s_i
+            }
+            if (!eq) {
+                if (active && value_thread) vbuf[walk] = V;
+                __syncthreads();
+            }
+            if (active && !value_thread) {
+                const uint32_t term = s[1] + (t ? K.cw_final : 0u);   // Convert(s_n): bytes 4..7
+                y = (eq ? 0u : vbuf[walk]) + (party ? 0u - term : term);
+                // RANGE: the public constant c * beta' joins party 0's half once
+                if (!eq && (slot % nsub) == 0 && party == 0) y += D.cbeta;
+            }
+            if (!value_thread) part[el * kWpSlots + slot] = y;
             // The re-share PRF words depend only on (element, step, table, query), so six
-            // slots compute the (pass, key) pairs side by side: pass p re-shares with step
+            // value threads compute the (pass, key) pairs side by side (for an equality
+            // predicate while the seed threads walk): pass p re-shares with step
             // D.step + 64 p (the fold's re-share, for every predicate after the first).
             const int passes = k == 0 ? 1 : 2;
-            if (valid && slot < 3u * passes) {
+            if (value_thread && valid && slot < 3u * passes) {
                 const uint32_t pass = slot / 3, i = slot % 3;
                 const uint32_t ctr[4] = {(uint32_t)e, (uint32_t)(e >> 32), (D.step + 64u * pass) | (table << 16),
                                          query};
                 fprf[el * kWpPrf + slot] = aes_one_w0(T, P.rk_prf[i], ctr);   // F keeps bytes 0..3
             }
             __syncthreads();
-            if (slot == 0 && valid) {
+            if (!value_thread && slot == 0 && valid) {
                 // keys are ordered [server i][half h][sub s]: server i owns slots [2 nsub i, 2 nsub (i + 1))
                 uint32_t z[3][1] = {{0}, {0}, {0}};
                 for (uint32_t kk = 0; kk < 6 * nsub; kk++) {
@@ -452,7 +523,7 @@ __global__ void __launch_bounds__(kWpThreads, 1) k_filter_wp(const __grid_consta
                 }
             }
         }
-        if (slot == 0 && valid) {
+        if (!value_thread && slot == 0 && valid) {
 #pragma unroll
             for (int i = 0; i < 3; i++) G.out[i][e] = acc[i][0];
         }
@@ -525,10 +596,10 @@ uint32_t choose_tile(size_t n_groups, NF n_elems_of, TF item_time, uint32_t max_
 //  k_filter: one thread per element, so the time follows the cost of the group's walks
 //  times the width rounded up to whole warps, but never less than for 64 elements: below
 //  about two warps per SM the walks' own latency, not the shared-memory pipe, sets it.
-//  k_filter_wp: one thread per walk; per predicate of n bits a fixed latency of its walk
-//  chain (about 0.55 n us for EQ, 0.97 n us for RANGE on GB300) plus, beyond 10 elements,
-//  a per-element term (31 n / 62 n ns: an EQ predicate leaves half of an element's twelve
-//  threads idle).  Fitted to single-predicate sweeps of widths 1..40 at n = 32.
+//  k_filter_wp: one thread per walk (two per DCF walk); per predicate of n bits a fixed
+//  latency of its walk chain, one PRG call per level for either kind (about 0.55 n us on
+//  GB300), plus, beyond 10 elements, a per-element term (31 n / 62 n ns: the lookups of an
+//  EQ / RANGE element).
 struct GroupCost {
     uint64_t walk_cost = 0;            // k_filter: sum over predicates of 6 n (EQ) / 24 n (RANGE)
     uint64_t wp_lat = 0, wp_slope = 0; // k_filter_wp: latency and per-element terms, ns
@@ -572,7 +643,7 @@ oblivgm_status plan_queries(const std::map<uint32_t, Table>& tables, uint32_t n_
                 if (p->n != tb.n_bits) return fail(OBLIVGM_EINVAL, "predicate bit length differs from its table's");
                 const bool eq = p->kind == OBLIVGM_PRED_EQ;
                 cost.walk_cost += (eq ? 6ull : 24ull) * p->n;
-                cost.wp_lat += (eq ? 550ull : 970ull) * p->n;
+                cost.wp_lat += 550ull * p->n;
                 cost.wp_slope += (eq ? 31ull : 62ull) * p->n;
             }
             G gr{};
@@ -793,6 +864,7 @@ oblivgm_status oblivgm_create(oblivgm_ctx** out, int32_t device, const oblivgm_c
     if (st == OBLIVGM_OK) st = set_keygen_attrs();
     if (st == OBLIVGM_OK) st = set_fresh_attrs();
     if (st == OBLIVGM_OK) st = set_shuffle_attrs();
+    if (st == OBLIVGM_OK) st = set_prg_attrs();
     if (st != OBLIVGM_OK) { delete ctx; return st; }
     cudaError_t e = cudaMalloc(&ctx->d_te0, 256 * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemcpy(ctx->d_te0, aes_tables().te0, 256 * sizeof(uint32_t), cudaMemcpyHostToDevice);

@@ -121,6 +121,8 @@ struct oblivgm_ctx {
     bool test_expire_next = false;      // failure-path test hook, one-shot
     std::atomic<bool> test_fail_alloc{false};   // failure-path test hook: refuse the next workspace allocation
     uint64_t test_wait_limit_ns = 0;
+    uint32_t aes_layout = 0;             // OBLIVGM_AES_TTABLE until oblivgm_autotune_aes_layout measures
+    double aes_layout_rate[2] = {0, 0};  // measured PRG blocks/s: T-table, bitsliced
     ogm::ServeState serve;
 };
 
@@ -147,6 +149,7 @@ oblivgm_status set_keygen_attrs();
 oblivgm_status ws_alloc(oblivgm_ctx* ctx, void** p, size_t bytes, cudaStream_t s, const char* what);
 oblivgm_status set_fresh_attrs();
 oblivgm_status set_shuffle_attrs();
+oblivgm_status set_prg_attrs();
 oblivgm_status repack_keys_device(oblivgm_ctx* ctx, const uint8_t* wire, uint32_t kind, uint32_t n, uint32_t n_keys,
                                   DevKey* out, cudaStream_t s);
 

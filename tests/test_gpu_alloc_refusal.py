@@ -93,9 +93,3 @@ def test_onehot_shuffle_and_fetch_recover_after_refused_allocation(ctx):
     fouts = [torch.zeros((N, 3), dtype=torch.int32, device="cuda") for _ in range(3)]
     m = _refused_then_ok(ctx, lambda: ctx.fetch_multi(0, [to_dev(x) for x in xs], [0, 1], seeds, fouts))
     assert m == 2
-    # secFetch case I: its per-CTA partial sums come from the same workspace allocator
-    res = torch.empty(3 * 3, dtype=torch.int32, device="cuda")
-    _refused_then_ok(ctx, lambda: ctx.fetch_unique(4, 1, 0, [to_dev(x) for x in xs], [0, 1], res))
-    ctx.sync()
-    want = oracle.fetch_unique(xs, [(tab["shares"], 16)], 0, [0, 1], 4, 1, PRF)
-    assert np.array_equal(from_dev(res).reshape(3, 3), want)
