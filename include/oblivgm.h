@@ -594,6 +594,12 @@ oblivgm_status oblivgm_set_schedule(oblivgm_ctx* ctx, uint32_t threads, uint32_t
  * the serving loop.  Errors: EINVAL for a NULL context. */
 oblivgm_status oblivgm_set_walk_parallel(oblivgm_ctx* ctx, uint64_t max_elems, uint64_t* previous);
 
+/* Elements per work item of the walk-parallel kernel: 1..40 fixes it, 0 (the
+ * default) lets each launch choose it by simulating its schedule over the SMs.
+ * For tuning and measurement.  `previous` (may be NULL) receives the setting it
+ * replaces.  Errors: EINVAL (NULL context, tile above 40). */
+oblivgm_status oblivgm_set_walk_parallel_tile(oblivgm_ctx* ctx, uint32_t tile, uint32_t* previous);
+
 /* Synchronise `stream` and report device-side faults recorded since the last
  * check: EFAULT_DEVICE if a bounded device wait (key staging) expired in a
  * kernel of this context, ECUDA on a CUDA error; the flag is cleared. */

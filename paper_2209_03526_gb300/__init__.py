@@ -436,6 +436,14 @@ class Context:
     def set_schedule(self, threads: int = 0, elems_per_thread: int = 0):
         N.check(self._lib.oblivgm_set_schedule(self._h, threads, elems_per_thread), "oblivgm_set_schedule")
 
+    def set_walk_parallel_tile(self, tile: int) -> int:
+        """Fix the walk-parallel kernel's elements per tile (1..40; 0: chosen per launch).
+        Returns the setting it replaces."""
+        prev = ctypes.c_uint32(0)
+        N.check(self._lib.oblivgm_set_walk_parallel_tile(self._h, tile, ctypes.byref(prev)),
+                "oblivgm_set_walk_parallel_tile")
+        return prev.value
+
     def set_walk_parallel(self, max_elems: int) -> int:
         """Batches of at most max_elems elements in all run the walk-parallel kernel (0: never,
         2**64 - 1: always).  Returns the setting it replaces."""

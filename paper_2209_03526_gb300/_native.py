@@ -105,6 +105,7 @@ _SIGS = {
     "oblivgm_plan_describe": ([c_vp, ctypes.POINTER(c_u32), ctypes.POINTER(c_u32), ctypes.POINTER(c_u32),
                                ctypes.POINTER(c_u64), ctypes.POINTER(c_u32)], c_i32),
     "oblivgm_set_walk_parallel": ([c_vp, c_u64, ctypes.POINTER(c_u64)], c_i32),
+    "oblivgm_set_walk_parallel_tile": ([c_vp, c_u32, ctypes.POINTER(c_u32)], c_i32),
     "oblivgm_test_expire_next_wait": ([c_vp, c_u32], c_i32),
     "oblivgm_test_fail_next_alloc": ([c_vp], c_i32),
     "oblivgm_prg_batch": ([c_vp, c_u32, c_u32, c_u64, c_u64, c_u32, c_vp, c_u64, c_vp], c_i32),

@@ -597,14 +597,14 @@ uint32_t choose_tile(size_t n_groups, NF n_elems_of, TF item_time, uint32_t max_
 //  times the width rounded up to whole warps, but never less than for 64 elements: below
 //  about two warps per SM the walks' own latency, not the shared-memory pipe, sets it.
 //  k_filter_wp: one thread per walk (two per DCF walk); per predicate of n bits a fixed
-//  latency of its walk chain, one PRG call per level for either kind (about 0.55 n us on
-//  GB300), plus, beyond 10 elements, a per-element term (31 n / 62 n ns: the lookups of an
-//  EQ / RANGE element).
+//  cost (the key staging, the walk chain of one PRG call per level, the combine: about
+//  656 n ns for EQ, 719 n ns for RANGE on GB300) plus a per-element term (20 n / 54 n ns:
+//  the shared-memory lookups of an EQ / RANGE element).  Fitted to sweeps of tiles of 1..40
+//  elements, one and two items per SM, n = 16 and 32.
 struct GroupCost {
     uint64_t walk_cost = 0;            // k_filter: sum over predicates of 6 n (EQ) / 24 n (RANGE)
     uint64_t wp_lat = 0, wp_slope = 0; // k_filter_wp: latency and per-element terms, ns
 };
-constexpr uint64_t kWpKnee = 10;
 
 double filter_item_time(const GroupCost& c, uint64_t width) {
     const uint64_t busy = std::max<uint64_t>((width + 31) / 32 * 32, 64);
@@ -612,7 +612,7 @@ double filter_item_time(const GroupCost& c, uint64_t width) {
 }
 
 double wp_item_time(const GroupCost& c, uint64_t width) {
-    return (double)c.wp_lat + (double)c.wp_slope * (double)(width > kWpKnee ? width - kWpKnee : 0);
+    return (double)c.wp_lat + (double)c.wp_slope * (double)width;
 }
 
 oblivgm_status plan_queries(const std::map<uint32_t, Table>& tables, uint32_t n_queries, const uint32_t* query_ids,
@@ -643,8 +643,8 @@ oblivgm_status plan_queries(const std::map<uint32_t, Table>& tables, uint32_t n_
                 if (p->n != tb.n_bits) return fail(OBLIVGM_EINVAL, "predicate bit length differs from its table's");
                 const bool eq = p->kind == OBLIVGM_PRED_EQ;
                 cost.walk_cost += (eq ? 6ull : 24ull) * p->n;
-                cost.wp_lat += 550ull * p->n;
-                cost.wp_slope += (eq ? 31ull : 62ull) * p->n;
+                cost.wp_lat += (eq ? 656ull : 719ull) * p->n;
+                cost.wp_slope += (eq ? 20ull : 54ull) * p->n;
             }
             G gr{};
             for (int j = 0; j < 3; j++) {
@@ -710,7 +710,9 @@ oblivgm_status plan_filter(oblivgm_ctx* ctx, const std::map<uint32_t, Table>& ta
     uint64_t total = 0;
     for (const GroupDesc& g : plan->groups) total += g.n_elems;
     if (total == 0 || total > ctx->wp_max_elems) return OBLIVGM_OK;
-    s = plan_queries(tables, n_queries, query_ids, parsed, n_groups, outs, kWpElems, 1, true, ctx->sm_count, plan);
+    // a forced tile (oblivgm_set_walk_parallel_tile) skips the search: step 0
+    s = plan_queries(tables, n_queries, query_ids, parsed, n_groups, outs, ctx->wp_tile ? ctx->wp_tile : kWpElems,
+                     ctx->wp_tile ? 0 : 1, true, ctx->sm_count, plan);
     if (s != OBLIVGM_OK) return s;
     plan->wp = true;
     plan->threads = kWpThreads;
@@ -1196,6 +1198,15 @@ oblivgm_status oblivgm_set_schedule(oblivgm_ctx* ctx, uint32_t threads, uint32_t
     if (t % 32 || t < 32 || t > tmax) return fail(OBLIVGM_EINVAL, "threads must be a multiple of 32, at most 1024 (E = 1) or 512 (E = 2, 4)");
     ctx->threads = t;
     ctx->elems_per_thread = e;
+    return OBLIVGM_OK;
+}
+
+oblivgm_status oblivgm_set_walk_parallel_tile(oblivgm_ctx* ctx, uint32_t tile, uint32_t* previous) {
+    oblivgm_status st = check_ctx(ctx);
+    if (st) return st;
+    if (tile > (uint32_t)kWpElems) return fail(OBLIVGM_EINVAL, "the walk-parallel tile is at most 40 elements");
+    if (previous) *previous = ctx->wp_tile;
+    ctx->wp_tile = tile;
     return OBLIVGM_OK;
 }
 

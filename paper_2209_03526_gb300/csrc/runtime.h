@@ -117,6 +117,7 @@ struct oblivgm_ctx {
     uint32_t threads = 768;          // the autotuner's pick on GB300 (256 x 4 spills)
     uint32_t elems_per_thread = 1;
     uint64_t wp_max_elems = 0;       // batches with at most this many elements in all run walk-parallel
+    uint32_t wp_tile = 0;            // walk-parallel elements per tile; 0 = chosen per launch
     std::atomic<uint64_t> launches{0};
     bool test_expire_next = false;      // failure-path test hook, one-shot
     std::atomic<bool> test_fail_alloc{false};   // failure-path test hook: refuse the next workspace allocation
