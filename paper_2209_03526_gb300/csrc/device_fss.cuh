@@ -18,12 +18,18 @@ constexpr int kTableBytes = 131072;
 
 __device__ __forceinline__ uint32_t lane_offset() { return (threadIdx.x & 31u) * 4u; }
 
-// Fill the replicated tables from the compact Te0 (256 words in global memory).
+// Fill the replicated tables from the compact Te0 (256 words in global memory).  Each of
+// the 1,024 (table, entry) pairs is one word replicated for the 32 lanes (128 bytes): eight
+// threads write a pair with one 16-byte store each, so a warp's store covers four whole
+// 128-byte rows (four wavefronts, no bank conflict).
 __device__ __forceinline__ void fill_tables(uint32_t* tab, const uint32_t* __restrict__ te0) {
-    for (int i = threadIdx.x; i < 4 * 256 * 32; i += blockDim.x) {
-        const int k = i >> 13, rem = i & 8191, idx = rem >> 5, lane = rem & 31;
-        const uint32_t v = te0[idx];
-        tab[(k >> 1) * 16384 + idx * 64 + (k & 1) * 32 + lane] = __funnelshift_l(v, v, 8 * k);
+#pragma unroll 4
+    for (int i = threadIdx.x; i < 4 * 256 * 8; i += blockDim.x) {
+        const int pair = i >> 3, chunk = i & 7;
+        const int k = pair >> 8, idx = pair & 255;
+        const uint32_t w = __ldg(te0 + idx);
+        const uint32_t v = __funnelshift_l(w, w, 8 * k);
+        reinterpret_cast<uint4*>(tab + (k >> 1) * 16384 + idx * 64 + (k & 1) * 32)[chunk] = make_uint4(v, v, v, v);
     }
 }
 

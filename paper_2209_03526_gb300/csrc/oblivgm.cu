@@ -87,6 +87,7 @@ struct FilterParams {
     const DevKey* keys;
     const uint64_t* item_start;   // n_groups + 1 prefix sums of element tiles
     unsigned long long* counter;  // work queue head
+    uint32_t* done;               // CTAs of the walk-parallel kernel that have finished (it resets both)
     uint32_t* error;              // context fault flags
     uint32_t n_groups;
     uint32_t tile;                // elements per item (a multiple of 32 E, at most blockDim.x * E)
@@ -374,6 +375,7 @@ __global__ void __launch_bounds__(kWpThreads, 1) k_filter_wp(const __grid_consta
     const uint32_t walk = threadIdx.x % kWpWalks;
     const uint32_t el = walk / kWpSlots, slot = walk % kWpSlots;
     uint32_t phase = 0;
+    bool failed = false;
     const uint64_t n_items = P.item_start[P.n_groups];
     for (;;) {
         if (threadIdx.x == 0) item_sh = atomicAdd(P.counter, 1ull);
@@ -404,7 +406,8 @@ __global__ void __launch_bounds__(kWpThreads, 1) k_filter_wp(const __grid_consta
             if (__syncthreads_or(!ok)) {
                 if (threadIdx.x == 0) atomicOr(P.error, kErrKeyWait);
                 mbar_wait_bounded(&mbar, phase ^ 1u, P.wait_limit_ns);   // let an in-flight copy land
-                return;
+                failed = true;
+                break;
             }
             const bool eq = D.kind == OBLIVGM_PRED_EQ;
             const uint32_t nsub = eq ? 1u : 2u;
@@ -523,11 +526,21 @@ __global__ void __launch_bounds__(kWpThreads, 1) k_filter_wp(const __grid_consta
                 }
             }
         }
+        if (failed) break;   // the CTA records the fault and leaves its outputs alone
         if (!value_thread && slot == 0 && valid) {
 #pragma unroll
             for (int i = 0; i < 3; i++) G.out[i][e] = acc[i][0];
         }
         __syncthreads();
+    }
+    // the last CTA to finish resets the work counter and this count, so that the next launch
+    // of a prepared plan finds them at zero without a separate clear
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(P.done, 1u) == gridDim.x - 1) {
+            *P.counter = 0ull;
+            *P.done = 0u;
+        }
     }
 }
 
@@ -736,9 +749,9 @@ cudaError_t launch_filter_kernel(const FilterParams& P, uint64_t n_items, int sm
     return cudaGetLastError();
 }
 
-// Device workspace of one fused launch: work counter | groups | preds | keys | tile offsets,
-// each part 256-byte aligned.  The image is built on the host; its first 8 bytes (the work
-// counter) are zero.
+// Device workspace of one fused launch: work counter (and the walk-parallel kernel's count
+// of finished CTAs at byte 8) | groups | preds | keys | tile offsets, each part 256-byte
+// aligned.  The image is built on the host; its first 256 bytes are zero.
 struct WsImage {
     size_t off_groups = 0, off_preds = 0, off_keys = 0, off_items = 0, total = 0;
     std::vector<unsigned char> bytes;
@@ -771,6 +784,7 @@ FilterParams filter_params(const oblivgm_ctx* ctx, const Plan& plan, const WsIma
     P.keys = reinterpret_cast<const DevKey*>(ws + im.off_keys);
     P.item_start = reinterpret_cast<const uint64_t*>(ws + im.off_items);
     P.counter = reinterpret_cast<unsigned long long*>(ws);
+    P.done = reinterpret_cast<uint32_t*>(ws + 8);
     P.error = error_flag;
     P.n_groups = (uint32_t)plan.groups.size();
     P.tile = plan.tile;
@@ -1365,7 +1379,9 @@ extern "C" oblivgm_status oblivgm_plan_launch(oblivgm_plan* p, void* stream) {
     if (!p) return fail(OBLIVGM_EINVAL, "NULL plan");
     if (p->n_items == 0) return OBLIVGM_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    OGM_CUDA(cudaMemsetAsync(p->ws, 0, sizeof(unsigned long long), s), "plan counter reset");
+    // the walk-parallel kernel leaves its counters at zero when it ends; the per-element
+    // kernel's counter is cleared before each launch
+    if (!p->wp) OGM_CUDA(cudaMemsetAsync(p->ws, 0, sizeof(unsigned long long), s), "plan counter reset");
     const cudaError_t e = launch_filter_kernel(p->params, p->n_items, p->ctx->sm_count, p->threads, p->E, p->wp, s);
     if (e != cudaSuccess) return cuda_fail(e, "k_filter launch (plan)");
     p->ctx->launches++;
