@@ -340,8 +340,8 @@ namespace ogm {
 // over two threads.  Each DCF level takes two PRG calls on the same seed s_i: the seed /
 // control-bit block of the chosen child and its value block.  The walk's seed thread
 // computes the first and the next seed, the walk's value thread the second, both at once:
-// the seed thread leaves (s_i, t_i) in shared memory for its partner, and one CTA barrier
-// per level (all walks of a CTA have the same n) orders the hand-over.  The keys are staged
+// the seed thread leaves (s_i, t_i) in shared memory for its partner, and one barrier of
+// the two threads' warps per level (all walks of a CTA have the same n) orders the hand-over.  The keys are staged
 // as in k_filter; the walks' outputs meet in shared memory, and the element's first slot
 // thread sums them per server, re-shares and folds exactly as k_filter does.
 
@@ -349,11 +349,19 @@ constexpr int kWpSlots = 12;                          // key walks per element
 constexpr int kWpElems = 40;                          // elements per CTA (tile)
 constexpr int kWpWalks = kWpSlots * kWpElems;         // 480 seed threads, then 480 value threads
 constexpr int kWpThreads = 2 * kWpWalks;              // 960
+static_assert(kWpWalks % 32 == 0 && kWpWalks / 32 <= 15, "one named barrier (1..15) per walk pair of warps");
 constexpr int kWpPrf = 6;                             // re-share PRF words per element: 2 passes x 3 keys
 constexpr int kWpSmem = kFilterSmem + kWpElems * (kWpSlots + kWpPrf) * 4 +   // walk outputs, PRF words
                         2 * kWpWalks * 16 + 2 * kWpWalks * 4 + kWpWalks * 4; // seed / control-bit hand-over, V
 // default switch-over: batches of at most this many elements per SM in all
 constexpr uint64_t kWpDefaultElemsPerSm = 128;
+
+// The seed warp w (< 15) and the value warp 15 + w of a walk pair meet at named barrier
+// 1 + w (64 threads): the per-level hand-over needs only the two of them, so pairs do not
+// wait for one another and drift apart, which keeps the lookup and logic pipes busy.
+__device__ __forceinline__ void wp_pair_sync(uint32_t walk) {
+    asm volatile("bar.sync %0, 64;" ::"r"(1u + walk / 32u) : "memory");
+}
 
 __global__ void __launch_bounds__(kWpThreads, 1) k_filter_wp(const __grid_constant__ FilterParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -425,8 +433,8 @@ __global__ void __launch_bounds__(kWpThreads, 1) k_filter_wp(const __grid_consta
             uint32_t y = 0;
             // one loop for both kinds: the seed thread walks the seed / control-bit chain (a
             // DPF walk whole); for a DCF the value thread takes each level's value block on
-            // the seed s_i the seed thread hands over, one CTA barrier per level (n and the
-            // kind are the same for every walk of the CTA)
+            // the seed s_i the seed thread hands over, one barrier of the walk pair per level
+            // (n and the kind are the same for every walk of the CTA)
             const int n = (int)D.n_bits;
             const uint32_t party = K.party;
             uint32_t s[4] = {0, 0, 0, 0}, t = party, V = 0;
@@ -438,7 +446,7 @@ __global__ void __launch_bounds__(kWpThreads, 1) k_filter_wp(const __grid_consta
                     tbuf[walk] = t;
                 }
             }
-            if (!eq) __syncthreads();
+            if (!eq) wp_pair_sync(walk);
             for (int i = 0; i < n; i++) {
                 const uint32_t dir = (xh >> (n - 1 - i)) & 1u;
                 const uint32_t m = 0u - dir;
@@ -471,11 +479,11 @@ __global__ void __launch_bounds__(kWpThreads, 1) k_filter_wp(const __grid_consta
                     const uint32_t term = (v0 ^ si.x) + (ti ? K.vcw[i] : 0u);
                     V += party ? 0u - term : term;
                 }
-                if (!eq) __syncthreads();   // s_{i+1} visible; everyone is done reading s_i
+                if (!eq) wp_pair_sync(walk);   // s_{i+1} visible; the partner is done reading s_i
             }
             if (!eq) {
                 if (active && value_thread) vbuf[walk] = V;
-                __syncthreads();
+                wp_pair_sync(walk);
             }
             if (active && !value_thread) {
                 const uint32_t term = s[1] + (t ? K.cw_final : 0u);   // Convert(s_n): bytes 4..7

@@ -493,3 +493,24 @@ def test_fetch_unique_column_groups_and_sizes(ctx, n_el, attrs, offset):
     got = from_dev(res).reshape(3, 1 + len(attrs))
     want = oracle.fetch_unique(xs, [(wl["tables"][0]["shares"], bits)], 0, attrs, 8, 5, PRF)
     assert np.array_equal(got, want)
+
+
+def test_fetch_unique_calls_back_to_back(ctx):
+    """secFetch case I leaves the context's accumulators at zero for the next call: three calls
+    on one stream with different attribute lists and outputs, one synchronisation at the end,
+    each equal to the oracle."""
+    g = W.rng(74)
+    n_el, bits = 30011, 32
+    vals = W.uniform_attrs(g, 5, n_el, bits)
+    wl = {"tables": [W.table(vals, bits, g)]}
+    load_tables(ctx, wl)
+    xs = [g.integers(0, 1 << 32, n_el, dtype=np.uint64).astype(np.uint32) for _ in range(3)]
+    dx = [to_dev(x) for x in xs]
+    calls = [[0, 1, 2, 3, 4], [2], []]
+    res = [torch.empty(3 * (1 + len(a)), dtype=torch.int32, device="cuda") for a in calls]
+    for q, (attrs, r) in enumerate(zip(calls, res)):
+        ctx.fetch_unique(20 + q, q, 0, dx, attrs, r)
+    ctx.sync()
+    for q, (attrs, r) in enumerate(zip(calls, res)):
+        want = oracle.fetch_unique(xs, [(wl["tables"][0]["shares"], bits)], 0, attrs, 20 + q, q, PRF)
+        assert np.array_equal(from_dev(r).reshape(3, 1 + len(attrs)), want), q
