@@ -93,6 +93,8 @@ struct FilterParams {
     uint32_t tile;                // elements per item (a multiple of 32 E, at most blockDim.x * E)
     uint64_t wait_limit_ns;       // bound of every key-staging wait
     uint32_t expect_extra;        // failure-path test only: bytes expected beyond the copy (0 normally)
+    uint32_t resident_bytes;      // walk-parallel kernel: nonzero when the workspace from `groups` to the
+                                  // end of `item_start` (this many bytes) fits its shared memory whole
 };
 
 constexpr int kMaxKeysPerPred = 12;
@@ -351,8 +353,11 @@ constexpr int kWpWalks = kWpSlots * kWpElems;         // 480 seed threads, then 
 constexpr int kWpThreads = 2 * kWpWalks;              // 960
 static_assert(kWpWalks % 32 == 0 && kWpWalks / 32 <= 15, "one named barrier (1..15) per walk pair of warps");
 constexpr int kWpPrf = 6;                             // re-share PRF words per element: 2 passes x 3 keys
-constexpr int kWpSmem = kFilterSmem + kWpElems * (kWpSlots + kWpPrf) * 4 +   // walk outputs, PRF words
-                        2 * kWpWalks * 16 + 2 * kWpWalks * 4 + kWpWalks * 4; // seed / control-bit hand-over, V
+constexpr int kWpResidentOff = kFilterSmem + kWpElems * (kWpSlots + kWpPrf) * 4 +   // walk outputs, PRF words
+                               2 * kWpWalks * 16 + 2 * kWpWalks * 4 + kWpWalks * 4; // seed / control-bit hand-over, V
+constexpr int kWpResidentBytes = 48 * 1024;   // descriptors, keys and tile offsets of a small launch
+constexpr int kWpSmem = kWpResidentOff + kWpResidentBytes;
+static_assert(kWpResidentOff % 16 == 0, "bulk copies need 16-byte aligned destinations");
 // default switch-over: batches of at most this many elements per SM in all
 constexpr uint64_t kWpDefaultElemsPerSm = 128;
 
@@ -372,51 +377,84 @@ __global__ void __launch_bounds__(kWpThreads, 1) k_filter_wp(const __grid_consta
     uint4* sbuf = reinterpret_cast<uint4*>(fprf + kWpElems * kWpPrf);      // [2][walk]: s_i
     uint32_t* tbuf = reinterpret_cast<uint32_t*>(sbuf + 2 * kWpWalks);     // [2][walk]: t_i
     uint32_t* vbuf = tbuf + 2 * kWpWalks;                                  // [walk]: the value sum V
+    unsigned char* wsm = smem + kWpResidentOff;                            // resident copy of the workspace
     __shared__ __align__(8) uint64_t mbar;
     __shared__ unsigned long long item_sh;
 
+    // A small launch's descriptors, keys and tile offsets come into shared memory with one
+    // bulk copy that runs while the tables fill; the items then read no global descriptor
+    // and stage no keys.  Otherwise they are read from global memory and each predicate's
+    // keys are staged as k_filter does.
+    const bool resident = P.resident_bytes != 0;
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar);
+        if (resident) {
+            mbar_expect_tx(&mbar, P.resident_bytes + P.expect_extra);
+            bulk_g2s(wsm, P.groups, P.resident_bytes, &mbar);
+        }
+    }
     fill_tables(reinterpret_cast<uint32_t*>(smem), P.te0);
-    if (threadIdx.x == 0) mbar_init(&mbar);
     __syncthreads();
+    uint32_t phase = 0;
+    bool failed = false;
+    if (resident) {
+        const bool ok = mbar_wait_bounded(&mbar, phase, P.wait_limit_ns);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) atomicOr(P.error, kErrKeyWait);
+            mbar_wait_bounded(&mbar, phase ^ 1u, P.wait_limit_ns);   // let an in-flight copy land
+            failed = true;
+        }
+    }
+    const auto rel = [&](const void* p) {
+        return wsm + (reinterpret_cast<const unsigned char*>(p) - reinterpret_cast<const unsigned char*>(P.groups));
+    };
+    const GroupDesc* groups = resident ? reinterpret_cast<const GroupDesc*>(wsm) : P.groups;
+    const PredDesc* preds = resident ? reinterpret_cast<const PredDesc*>(rel(P.preds)) : P.preds;
+    const DevKey* rkeys = reinterpret_cast<const DevKey*>(rel(P.keys));
+    const uint64_t* item_start = resident ? reinterpret_cast<const uint64_t*>(rel(P.item_start)) : P.item_start;
 
     const bool value_thread = threadIdx.x >= (unsigned)kWpWalks;
     const uint32_t walk = threadIdx.x % kWpWalks;
     const uint32_t el = walk / kWpSlots, slot = walk % kWpSlots;
-    uint32_t phase = 0;
-    bool failed = false;
-    const uint64_t n_items = P.item_start[P.n_groups];
-    for (;;) {
-        if (threadIdx.x == 0) item_sh = atomicAdd(P.counter, 1ull);
+    const uint64_t n_items = failed ? 0 : item_start[P.n_groups];
+    // the first item of CTA b is item b (the grid has at most n_items CTAs); later ones come
+    // from the work counter, past the first gridDim.x
+    for (uint32_t round = 0;; round++) {
+        if (threadIdx.x == 0) item_sh = round == 0 ? blockIdx.x : gridDim.x + atomicAdd(P.counter, 1ull);
         __syncthreads();
         const uint64_t item = item_sh;
         if (item >= n_items) break;
         int lo = 0, hi = (int)P.n_groups - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (P.item_start[mid] <= item) lo = mid; else hi = mid - 1;
+            if (item_start[mid] <= item) lo = mid; else hi = mid - 1;
         }
-        const GroupDesc& G = P.groups[lo];
-        const uint64_t e = (item - P.item_start[lo]) * P.tile + el;
+        const GroupDesc& G = groups[lo];
+        const uint64_t e = (item - item_start[lo]) * P.tile + el;
         const uint64_t n_elems = G.n_elems;
         const bool valid = el < P.tile && e < n_elems;
         const uint32_t table = G.table_id, query = G.query_id;
         uint32_t acc[3][1] = {{0}, {0}, {0}};
         for (uint32_t k = 0; k < G.n_preds; k++) {
-            const PredDesc& D = P.preds[G.pred_begin + k];
-            __syncthreads();   // everyone is done with the previous predicate's keys
-            if (threadIdx.x == 0) {
-                const uint32_t bytes = D.n_keys * (uint32_t)sizeof(DevKey);
-                mbar_expect_tx(&mbar, bytes + P.expect_extra);
-                bulk_g2s(kbuf, P.keys + D.key_begin, bytes, &mbar);
+            const PredDesc& D = preds[G.pred_begin + k];
+            __syncthreads();   // everyone is done with the previous predicate's keys and outputs
+            if (!resident) {
+                if (threadIdx.x == 0) {
+                    const uint32_t bytes = D.n_keys * (uint32_t)sizeof(DevKey);
+                    mbar_expect_tx(&mbar, bytes + P.expect_extra);
+                    bulk_g2s(kbuf, P.keys + D.key_begin, bytes, &mbar);
+                }
+                const bool ok = mbar_wait_bounded(&mbar, phase, P.wait_limit_ns);
+                phase ^= 1u;
+                if (__syncthreads_or(!ok)) {
+                    if (threadIdx.x == 0) atomicOr(P.error, kErrKeyWait);
+                    mbar_wait_bounded(&mbar, phase ^ 1u, P.wait_limit_ns);   // let an in-flight copy land
+                    failed = true;
+                    break;
+                }
             }
-            const bool ok = mbar_wait_bounded(&mbar, phase, P.wait_limit_ns);
-            phase ^= 1u;
-            if (__syncthreads_or(!ok)) {
-                if (threadIdx.x == 0) atomicOr(P.error, kErrKeyWait);
-                mbar_wait_bounded(&mbar, phase ^ 1u, P.wait_limit_ns);   // let an in-flight copy land
-                failed = true;
-                break;
-            }
+            const DevKey* pkeys = resident ? rkeys + D.key_begin : kbuf;
             const bool eq = D.kind == OBLIVGM_PRED_EQ;
             const uint32_t nsub = eq ? 1u : 2u;
             const bool active = valid && slot < 6 * nsub;
@@ -429,7 +467,7 @@ __global__ void __launch_bounds__(kWpThreads, 1) k_filter_wp(const __grid_consta
                 for (int j = 0; j < 3; j++) xh += __ldg(G.share[j] + row + e);
                 xh &= mask;
             }
-            const DevKey& K = kbuf[slot];
+            const DevKey& K = pkeys[slot];
             uint32_t y = 0;
             // one loop for both kinds: the seed thread walks the seed / control-bit chain (a
             // DPF walk whole); for a DCF the value thread takes each level's value block on
@@ -771,7 +809,7 @@ WsImage build_ws_image(const Plan& plan) {
     im.off_preds = im.off_groups + (plan.groups.size() * sizeof(GroupDesc) + 255) / 256 * 256;
     im.off_keys = im.off_preds + (plan.preds.size() * sizeof(PredDesc) + 255) / 256 * 256;
     im.off_items = im.off_keys + (plan.keys.size() * sizeof(DevKey) + 255) / 256 * 256;
-    im.total = im.off_items + plan.item_start.size() * sizeof(uint64_t);
+    im.total = (im.off_items + plan.item_start.size() * sizeof(uint64_t) + 255) / 256 * 256;
     im.bytes.assign(im.total, 0);
     std::memcpy(im.bytes.data() + im.off_groups, plan.groups.data(), plan.groups.size() * sizeof(GroupDesc));
     std::memcpy(im.bytes.data() + im.off_preds, plan.preds.data(), plan.preds.size() * sizeof(PredDesc));
@@ -797,6 +835,10 @@ FilterParams filter_params(const oblivgm_ctx* ctx, const Plan& plan, const WsIma
     P.n_groups = (uint32_t)plan.groups.size();
     P.tile = plan.tile;
     P.wait_limit_ns = kWaitLimitNs;
+    // the walk-parallel kernel keeps a small launch's workspace (from the groups on) in its
+    // shared memory; the image is padded to 256 bytes, so the copy stays inside it
+    const size_t res = im.total - im.off_groups;
+    P.resident_bytes = plan.wp && res <= (size_t)kWpResidentBytes ? (uint32_t)res : 0u;
     return P;
 }
 
