@@ -904,7 +904,7 @@ def run_workload(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     ctx = P.Context(0, prf_keys=PRF)
-    if args.workload in ("fresh", "keygen", "fetch", "onehot", "shuffle"):
+    if args.workload in ("fresh", "keygen", "fetch", "onehot", "shuffle", "aes-layouts", "wp-sweep"):
         sched = ()                       # these modes do not launch k_filter
     else:
         sched = tuple(int(v) for v in args.schedule.split(",")) if args.schedule else ctx.autotune()
@@ -1252,6 +1252,68 @@ def run_workload(args):
         print(json.dumps(line), flush=True)
         return 0
 
+    if args.workload == "aes-layouts":
+        # the autotuner's AES-layout dimension: the PRG on 2^26 counter blocks in both layouts
+        runs = [ctx.autotune_aes_layout() for _ in range(max(1, args.steps))]
+        mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        tt = statistics.median(r[1] for r in runs)
+        bs = statistics.median(r[2] for r in runs)
+        line.update({"metric": "fixed-key PRG blocks/s by AES layout", "unit": "blocks/s", "value": max(tt, bs),
+                     "steps": len(runs), "warmup": 1,
+                     "config": {"workload": "prg_2pow26_counter_blocks_K_L", "blocks_per_timing": 1 << 26,
+                                "chosen_layout": "bitsliced" if runs[-1][0] == P.AES_BITSLICED else "T-table"},
+                     "ttable": {"blocks_per_s": tt, "blocks_per_clk_per_sm": tt / (sm_count * mhz * 1e6)},
+                     "bitsliced": {"blocks_per_s": bs, "blocks_per_clk_per_sm": bs / (sm_count * mhz * 1e6)},
+                     "roofline": {"bound": "lds", "achieved": tt * LOOKUPS_PER_AES / 1e9, "peak": peak_lu,
+                                  "unit": "Glookup/s", "frac": tt * LOOKUPS_PER_AES / 1e9 / peak_lu,
+                                  "what": "the T-table layout against the shared-memory lookup ceiling"}})
+        ctx.close()
+        print(json.dumps(line), flush=True)
+        return 0
+
+    if args.workload == "wp-sweep":
+        # the walk-parallel kernel's item time by tile width: one predicate of each kind at n = 16
+        # and 32 on a table of 152 x w (one item per SM) or 304 x w (two) elements, tile forced
+        ctx.set_walk_parallel((1 << 64) - 1)
+        rows = []
+        for n in (16, 32):
+            for kind in ("eq", "range"):
+                for waves in (1, 2):
+                    for w in (1, 4, 8, 12, 16, 20, 24, 28, 32, 36, 40):
+                        N = sm_count * w * waves
+                        g = W.rng(w)
+                        tab = W.table(W.uniform_attrs(g, 1, N, n), n, g)
+                        ctx.load_shares(0, [torch.from_numpy(x.view(np.int32)).to(dev) for x in tab["shares"]], n)
+                        pred = W.eq_pred(0, 0, 0, 5) if kind == "eq" else W.range_pred(0, 0, 0, 7, ((1 << n) - 1) // 2)
+                        toks = P.keygen([pred], n, KEY_SEED)
+                        outs = [[torch.empty(N, dtype=torch.int32, device=dev) for _ in range(3)]]
+                        ctx.set_walk_parallel_tile(w)
+                        plan = ctx.plan_create([1], [toks], [outs])
+                        ms = _timed_graph(torch, ctx, plan, stream, 3, max(5, args.steps))
+                        ctx.plan_destroy(plan)
+                        rows.append({"n": n, "kind": kind, "items_per_sm": waves, "tile": w,
+                                     "us": float(np.median(ms)) * 1e3})
+        wl = W.tiny_path(seed=1)
+        for tid, t in enumerate(wl["tables"]):
+            ctx.load_shares(tid, [torch.from_numpy(x.view(np.int32)).to(dev) for x in t["shares"]], 16)
+        toks = P.keygen(wl["preds"], 16, KEY_SEED)
+        outs = [[torch.empty(t["values"].shape[1], dtype=torch.int32, device=dev) for _ in range(3)]
+                for t in wl["tables"]]
+        tiny = []
+        for w in [0] + list(range(20, 41, 2)):
+            ctx.set_walk_parallel_tile(w)
+            plan = ctx.plan_create([1], [toks], [outs])
+            shape = ctx.plan_describe(plan)
+            ms = _timed_graph(torch, ctx, plan, stream, 3, max(50, args.steps))
+            ctx.plan_destroy(plan)
+            tiny.append({"forced_tile": w, "tile": shape["tile"], "items": shape["items"],
+                         "us": float(np.median(ms)) * 1e3})
+        line.update({"metric": "walk-parallel item time", "unit": "us", "higher_is_better": False,
+                     "config": {"workload": "walk_parallel_tile_sweep"}, "sweep": rows, "tiny_path_by_tile": tiny})
+        ctx.close()
+        print(json.dumps(line), flush=True)
+        return 0
+
     if args.workload in WORKLOAD_RECORDS:
         ctx.close()
         args.sub_steps = args.sub_steps or args.steps
@@ -1283,7 +1345,8 @@ def main():
     ap.add_argument("--serve-queries", type=int, default=200, help="arrivals per rate of the serving record")
     ap.add_argument("--plain-queries", type=int, default=12,
                     help="plain-path arrivals per rate of the serving record (a prefix)")
-    ap.add_argument("--workload", choices=["bulk", "tiny", "edges", "batch", "serve", "onehot", "fetch", "keygen", "fresh", "shuffle"],
+    ap.add_argument("--workload", choices=["bulk", "tiny", "edges", "batch", "serve", "onehot", "fetch", "keygen", "fresh",
+                                           "shuffle", "aes-layouts", "wp-sweep"],
                     default="bulk",
                     help="bulk (default, the headline line); the others print their own line")
     ap.add_argument("--elems", type=int, default=0, help="--workload fresh: vertices (default 1,048,576)")
