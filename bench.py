@@ -297,6 +297,8 @@ def run_ours(args):
         ctx.set_schedule(threads, ept)
     else:
         threads, ept = ctx.autotune()
+    # the autotuner's AES-layout dimension: the walks are built in the layout it measures faster
+    lay, tt_rate, bs_rate = (None, None, None) if args.no_compare else ctx.autotune_aes_layout()
     outs = [[torch.empty(N_VERTICES, dtype=torch.int32, device=dev) for _ in range(3)]]
     stream = torch.cuda.current_stream(dev)
     flush = L2Flush(torch, dev, stream)
@@ -374,6 +376,9 @@ def run_ours(args):
                        "predicate_mix": "4 equality (DPF) + 4 range (2 DCF)", "n_bits": 32, "ring": "Z_2^32",
                        "servers": 3, "combine": "RSS AND of all 8", "l2": "flushed between timed steps",
                        "schedule": {"threads": threads, "elems_per_thread": ept,
+                                    "aes_layout": None if lay is None else {
+                                        "chosen": "bitsliced" if lay == P.AES_BITSLICED else "T-table",
+                                        "ttable_prg_blocks_per_s": tt_rate, "bitsliced_prg_blocks_per_s": bs_rate},
                                     "vector_width": "32-bit coalesced share loads and output stores: the "
                                                     "one-element-per-thread shape the autotuner picks; the "
                                                     "128-bit four-element shape spills and runs 1.5x slower, "
