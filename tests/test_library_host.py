@@ -116,3 +116,18 @@ def test_fresh_token_size_matches_oracle_layout():
         P.fresh_token_size([W.range_pred(0, 0, 0, 9, 2)], 8, [10])
     with pytest.raises(P.OblivgmError):
         P.fresh_token_size(preds, 33, [10, 10])
+
+
+def test_bitsliced_sbox_header_is_the_checked_circuit():
+    # the bitsliced layout's S-box is a gate circuit derived from the tower-field inverse; the
+    # generator checks it on all 256 inputs against the S-box's definition before emitting it,
+    # and the committed header must be exactly what it emits
+    import importlib.util
+    path = os.path.join(ROOT, "paper_2209_03526_gb300", "csrc", "gen_aes_bitsliced.py")
+    spec = importlib.util.spec_from_file_location("gen_aes_bitsliced", path)
+    gen = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(gen)
+    assert gen.SBOX[0x53] == 0xED and gen.SBOX[0] == 0x63
+    assert [gen.SBOX[a] for a in range(256)] == [oracle.sbox(a) for a in range(256)]
+    with open(os.path.join(ROOT, "paper_2209_03526_gb300", "csrc", "aes_bitsliced_sbox.cuh")) as f:
+        assert f.read() == gen.header_text()
