@@ -27,6 +27,7 @@
 #include <utility>
 #include <vector>
 
+#include "aes_byte0.cuh"
 #include "device_fss.cuh"
 #include "host_crypto.h"
 #include "oblivgm.h"
@@ -59,14 +60,15 @@ struct EvalAllParams {
 
 // One tree level of DPF / DCF Eval (Z_2 outputs) in direction dir, as in the walks of the
 // masked mode: the selected child's seed and control bit (and, for the DCF, the value
-// term V += Convert(v) + t * V_CW, taken mod 2).
+// term V += Convert(v) + t * V_CW, taken mod 2; Convert(v) is bit 0 of byte 0, so the
+// value block is computed as far as byte 0 only).
 __device__ __forceinline__ void level_step(const SmemTab& T, const AesParams& A, const DevKey& K, int i, uint32_t dir,
                                            bool dcf, uint32_t s[4], uint32_t& t, uint32_t& V) {
     const uint32_t m = 0u - dir;
     uint32_t o[4];
     aes_sel(T, A.rk_st, A.d_st, m, s, o);
     if (dcf) {
-        const uint32_t v0 = aes_sel_w0(T, A.rk_v, A.d_v, m, s);
+        const uint32_t v0 = aes_sel_b0(T, A.rk_v, A.d_v, m, s);
         V ^= ((v0 ^ s[0]) & 1u) ^ (t & K.vcw[i] & 1u);
     }
 #pragma unroll
@@ -96,7 +98,7 @@ __device__ __forceinline__ void level_step_fixed(const SmemTab& T, const FixedKe
     uint32_t o[4];
     aes_one(T, F.st[DIR], s, o);
     if (dcf) {
-        const uint32_t v0 = aes_one_w0(T, F.v[DIR], s);
+        const uint32_t v0 = aes_one_b0(T, F.v[DIR], s);
         V ^= ((v0 ^ s[0]) & 1u) ^ (t & K.vcw[i] & 1u);
     }
 #pragma unroll
@@ -600,7 +602,7 @@ template <class Tab>
 __device__ __forceinline__ uint32_t prf_bit(const Tab& T, const uint32_t* rk, uint64_t el, uint32_t step,
                                             uint32_t table, uint32_t query) {
     const uint32_t ctr[4] = {(uint32_t)el, (uint32_t)(el >> 32), step | (table << 16), query};
-    return aes_one_w0(T, rk, ctr) & 1u;
+    return aes_one_b0(T, rk, ctr) & 1u;   // F into Z_2: bit 0 of byte 0
 }
 
 // binary re-share: r_i = z_i xor F(k_i) xor F(k_{i-1})
