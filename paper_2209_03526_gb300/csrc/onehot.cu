@@ -296,6 +296,7 @@ struct DotParams {
     uint64_t n_elems;
     uint32_t words;
     uint32_t n_preds;
+    uint32_t pow2[32];            // pow2[i] = 2^i (read at run time by the staged pass)
 };
 
 // The unstaged pass, launched for domains below 2^12 and general in W.  One CTA per 32
@@ -439,8 +440,18 @@ __device__ __forceinline__ void load_halves(const DotParams& P, uint32_t W, uint
     }
 }
 
+// acc ^ (a & b) in one instruction
+__device__ __forceinline__ uint32_t xor_and(uint32_t acc, uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, 0x78;" : "=r"(d) : "r"(acc), "r"(a), "r"(b));
+    return d;
+}
+
 __global__ void __launch_bounds__(512) k_onehot_dots_pipe(const __grid_constant__ DotParams P) {
     extern __shared__ __align__(16) unsigned char dsmem[];
+    // 2^i for i < 32 from the launch parameters: a runtime factor, so that shifts into place
+    // are multiply-adds on the FMA pipe and leave the ALU pipe to the AND / XOR work
+    const uint32_t* pw = P.pow2;
     __shared__ uint32_t zs[2][16][kDotPreds][3][2];    // by word parity: per warp, masks per (pred, share, half)
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
     const uint32_t W = P.words, np = P.n_preds;
@@ -508,16 +519,19 @@ __global__ void __launch_bounds__(512) k_onehot_dots_pipe(const __grid_constant_
                     uint32_t cnt[kDotBatch / 4] = {};
 #pragma unroll
                     for (int b = 0; b < kDotBatch; b++) {
-                        const uint32_t a = (v[b][0] & h[k][hh][0]) ^ (v[b][1] & h[k][hh][1]) ^
-                                           (v[b][2] & h[k][hh][2]) ^ (v[b][3] & h[k][hh][3]);
-                        cnt[b / 4] += (uint32_t)__popc(a) << (8 * (b % 4));
+                        uint32_t a = v[b][0] & h[k][hh][0];
+                        a = xor_and(a, v[b][1], h[k][hh][1]);
+                        a = xor_and(a, v[b][2], h[k][hh][2]);
+                        a = xor_and(a, v[b][3], h[k][hh][3]);
+                        // popcount into byte b % 4 by a multiply-add (the FMA pipe, not the ALU)
+                        cnt[b / 4] = (uint32_t)__popc(a) * pw[8 * (b % 4)] + cnt[b / 4];
                     }
-                    // bit 8 f + q, q = cb * (kDotBatch / 4) + (b / 4), a compile-time shift
+                    // bit 8 f + q, q = cb * (kDotBatch / 4) + (b / 4): shifted by a multiply
 #pragma unroll
                     for (int q = 0; q < kDotBatch / 4; q++) {
                         constexpr uint32_t M = 0x01010101u;
                         const int sh = cb * (kDotBatch / 4) + q;
-                        pl[k][hh] ^= (cnt[q] << sh) & (M << sh);
+                        pl[k][hh] = xor_and(pl[k][hh], cnt[q] * pw[sh], M << sh);
                     }
                 }
             }
@@ -909,6 +923,7 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
             }
             D.n_elems = tb.n_elems;
             D.words = words;
+            for (int i = 0; i < 32; i++) D.pow2[i] = 1u << i;
             launch_dots(D, nwords, ctx->sm_count, s);
             ctx->launches++;
         }

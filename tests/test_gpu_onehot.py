@@ -2,10 +2,11 @@
 
 Every compared share bit is equal; the reconstruction equals the plaintext
 predicates; domains cover one partial word (n = 3), a few words (n = 6),
-whole warps of words (n = 10), the staged path with one warp per 32 elements
-(n = 12), with two warps and more words than the persistent grid has CTAs
-(n = 13, 70,001 elements), and the bench's domain (n = 16) with a ragged last
-word and CTAs that each take two words."""
+half a warp of words (n = 9), whole warps of words (n = 10), the staged path
+with one warp per 32 elements (n = 12), with two warps and more words than the
+persistent grid has CTAs (n = 13, 70,001 elements), and the bench's domain
+(n = 16) with a ragged last word and CTAs that each take two words; and a table
+loaded from host memory."""
 import numpy as np
 import pytest
 
@@ -46,7 +47,7 @@ def _run(ctx, toks, n_groups, sizes, qid):
     return [np.stack([_unpack(from_dev(t), sizes[g]) for t in outs[g]]) for g in range(n_groups)], outs
 
 
-@pytest.mark.parametrize("n,n_elems", [(3, 77), (6, 1000), (10, 333), (12, 129)])
+@pytest.mark.parametrize("n,n_elems", [(3, 77), (6, 1000), (9, 1025), (10, 333), (12, 129)])
 def test_onehot_parity(ctx, n, n_elems):
     g = W.rng(100 + n)
     top = (1 << n) - 1
@@ -145,3 +146,23 @@ def test_onehot_many_predicates_on_one_column(ctx):
         want = oracle.filter_onehot(toks, 29, PRF, tabs, grp, np.arange(n_elems))
         assert np.array_equal(got[grp], want), grp
         assert np.array_equal(oracle.reconstruct_bits(got[grp]), oracle.plain_group(preds, grp, vals))
+
+
+def test_onehot_host_loaded_table_equals_device_loaded(ctx):
+    """A table loaded from host memory gives the same shares as the same table loaded
+    from device memory, with predicates on both attributes."""
+    n, n_elems = 12, 3001
+    g = W.rng(77)
+    top = (1 << n) - 1
+    vals = W.uniform_attrs(g, 2, n_elems, n)
+    tab = W.onehot_table(vals, n, g)
+    preds = [W.eq_pred(0, 1, 0, int(vals[1, 7])), W.range_pred(0, 0, 1, top // 3, top // 2)]
+    toks = P.keygen_onehot(preds, n, bytes([9]) * 16)
+    _load(ctx, 0, tab)
+    want, _ = _run(ctx, toks, 2, [n_elems] * 2, 23)
+    host = [torch.from_numpy(np.ascontiguousarray(s_, dtype=np.uint32).view(np.int32)) for s_ in tab["shares"]]
+    ctx.load_onehot(0, host, n)
+    got, _ = _run(ctx, toks, 2, [n_elems] * 2, 23)
+    for grp in range(2):
+        assert np.array_equal(got[grp], want[grp]), grp
+        assert np.array_equal(oracle.reconstruct_bits(got[grp]), oracle.plain_group(preds, grp, vals)), grp
