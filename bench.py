@@ -775,7 +775,7 @@ def filter_workload_record(P, torch, name: str, graph, queries, sched, steps: in
                       "aes_blocks_per_step": aes, "tables": {str(k): v for k, v in table_n.items()},
                       "n_bits": n_bits, "l2": "flushed between timed steps",
                       "launch": f"one persistent {shape['kernel']} launch ({shape['grid']} CTAs x "
-                                f"{shape['threads']} threads, {shape['items']} tiles of {shape['tile']} "
+                                f"{shape['threads']} threads, {shape['items']} tiles of up to {shape['tile']} "
                                 "elements) replayed from a CUDA graph",
                       "warmup_launches": f"{warmup} of this plan" + (
                           f", after 3 of the first {plain['queries']} queries' plan (same kernel)" if plain else ""),

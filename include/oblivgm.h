@@ -301,8 +301,10 @@ oblivgm_status oblivgm_plan_destroy(oblivgm_plan* plan);
 
 /* The launch a plan fixed: walk_parallel = 1 for the walk-parallel kernel
  * (one thread per key walk), 0 for the per-element kernel; threads per CTA;
- * elements per work item (tile); work items; CTAs launched (one per SM at
- * most).  Any output pointer may be NULL.  Errors: EINVAL for a NULL plan. */
+ * elements per work item (tile: for the walk-parallel kernel, which may give
+ * each of a few groups its own width, the widest); work items; CTAs launched
+ * (one per SM at most).  Any output pointer may be NULL.  Errors: EINVAL for a
+ * NULL plan. */
 oblivgm_status oblivgm_plan_describe(const oblivgm_plan* plan, uint32_t* walk_parallel, uint32_t* threads,
                                      uint32_t* tile, uint64_t* n_items, uint32_t* grid);
 
@@ -594,9 +596,10 @@ oblivgm_status oblivgm_set_schedule(oblivgm_ctx* ctx, uint32_t threads, uint32_t
  * the serving loop.  Errors: EINVAL for a NULL context. */
 oblivgm_status oblivgm_set_walk_parallel(oblivgm_ctx* ctx, uint64_t max_elems, uint64_t* previous);
 
-/* Elements per work item of the walk-parallel kernel: 1..40 fixes it, 0 (the
- * default) lets each launch choose it by simulating its schedule over the SMs.
- * For tuning and measurement.  `previous` (may be NULL) receives the setting it
+/* Elements per work item of the walk-parallel kernel: 1..40 fixes it for every
+ * group, 0 (the default) lets each launch choose it by simulating its schedule
+ * over the SMs (one width for all groups, then, in a launch of at most 4
+ * groups, a width per group).  For tuning and measurement.  `previous` (may be NULL) receives the setting it
  * replaces.  Errors: EINVAL (NULL context, tile above 40). */
 oblivgm_status oblivgm_set_walk_parallel_tile(oblivgm_ctx* ctx, uint32_t tile, uint32_t* previous);
 

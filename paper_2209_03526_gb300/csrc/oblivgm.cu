@@ -66,7 +66,8 @@ struct GroupDesc {
     uint64_t n_elems;
     uint32_t query_id, table_id, pred_begin, n_preds;
     uint32_t vec_out;           // out pointers are 16-byte aligned
-    uint32_t pad[3];
+    uint32_t tile;              // elements per work item of this group (k_filter_wp; k_filter uses the launch's)
+    uint32_t pad[2];
 };
 
 struct PredDesc {
@@ -360,6 +361,8 @@ constexpr int kWpSmem = kWpResidentOff + kWpResidentBytes;
 static_assert(kWpResidentOff % 16 == 0, "bulk copies need 16-byte aligned destinations");
 // default switch-over: batches of at most this many elements per SM in all
 constexpr uint64_t kWpDefaultElemsPerSm = 128;
+// launches of at most this many groups get a tile width per group (walk-parallel kernel)
+constexpr size_t kWpTileGroups = 4;
 
 // The seed warp w (< 15) and the value warp 15 + w of a walk pair meet at named barrier
 // 1 + w (64 threads): the per-level hand-over needs only the two of them, so pairs do not
@@ -431,9 +434,10 @@ __global__ void __launch_bounds__(kWpThreads, 1) k_filter_wp(const __grid_consta
             if (item_start[mid] <= item) lo = mid; else hi = mid - 1;
         }
         const GroupDesc& G = groups[lo];
-        const uint64_t e = (item - item_start[lo]) * P.tile + el;
+        const uint32_t tile = G.tile;
+        const uint64_t e = (item - item_start[lo]) * tile + el;
         const uint64_t n_elems = G.n_elems;
-        const bool valid = el < P.tile && e < n_elems;
+        const bool valid = el < tile && e < n_elems;
         const uint32_t table = G.table_id, query = G.query_id;
         uint32_t acc[3][1] = {{0}, {0}, {0}};
         for (uint32_t k = 0; k < G.n_preds; k++) {
@@ -625,6 +629,24 @@ struct Plan {
 // greedy schedule, with item_time(group, width) as an item's time, and the width with
 // the shortest makespan wins (the widest on ties).  Large item counts skip the search:
 // their tail is already a small fraction.
+// Makespan of the greedy schedule: items (group, tile) in group order, each taken by the CTA
+// that is free first (one persistent CTA per SM); tile_of(g) is group g's width.
+template <typename NF, typename WF, typename TF>
+double simulate_makespan(size_t n_groups, NF n_elems_of, WF tile_of, TF item_time, int sm_count,
+                         std::vector<double>& finish) {
+    finish.assign((size_t)sm_count, 0.0);
+    std::make_heap(finish.begin(), finish.end(), std::greater<double>());
+    for (size_t g = 0; g < n_groups; g++) {
+        const uint64_t n = n_elems_of(g), t = tile_of(g);
+        for (uint64_t e = 0; e < n; e += t) {
+            std::pop_heap(finish.begin(), finish.end(), std::greater<double>());
+            finish.back() += item_time(g, std::min<uint64_t>(t, n - e));
+            std::push_heap(finish.begin(), finish.end(), std::greater<double>());
+        }
+    }
+    return *std::max_element(finish.begin(), finish.end());
+}
+
 template <typename NF, typename TF>
 uint32_t choose_tile(size_t n_groups, NF n_elems_of, TF item_time, uint32_t max_tile, uint32_t step, int sm_count) {
     uint64_t items_at_max = 0;
@@ -634,21 +656,66 @@ uint32_t choose_tile(size_t n_groups, NF n_elems_of, TF item_time, uint32_t max_
     double best = -1.0;
     std::vector<double> finish;
     for (uint32_t t = max_tile; t >= step; t -= step) {
-        finish.assign((size_t)sm_count, 0.0);
-        std::make_heap(finish.begin(), finish.end(), std::greater<double>());
-        for (size_t g = 0; g < n_groups; g++) {
-            const uint64_t n = n_elems_of(g);
-            for (uint64_t e = 0; e < n; e += t) {
-                std::pop_heap(finish.begin(), finish.end(), std::greater<double>());
-                finish.back() += item_time(g, std::min<uint64_t>(t, n - e));
-                std::push_heap(finish.begin(), finish.end(), std::greater<double>());
+        if (best >= 0) {
+            // skip a width whose work, spread evenly over the SMs, already takes longer
+            double total = 0;
+            for (size_t g = 0; g < n_groups; g++) {
+                const uint64_t n = n_elems_of(g);
+                total += (double)(n / t) * item_time(g, t) + (n % t ? item_time(g, n % t) : 0.0);
+            }
+            if (total / sm_count > best) {
+                if (t < 2 * step) break;
+                continue;
             }
         }
-        const double makespan = *std::max_element(finish.begin(), finish.end());
+        const double makespan =
+            simulate_makespan(n_groups, n_elems_of, [&](size_t) { return (uint64_t)t; }, item_time, sm_count, finish);
         if (best < 0 || makespan < best * (1.0 - 1e-9)) { best = makespan; best_tile = t; }
         if (t < 2 * step) break;
     }
     return best_tile;
+}
+
+// Per-group widths for a small launch of a few groups (the walk-parallel kernel): starting
+// from the common width, each group's width in turn is set to the one (max_tile down to 1)
+// that shortens the simulated makespan most (the widest on a tie), the others held, in two
+// rounds.  An equality group's items are cheaper than a range group's, so the two kinds
+// balance best at different widths, and fitting all items into one wave avoids a CTA
+// taking two.
+template <typename NF, typename TF>
+void choose_group_tiles(size_t n_groups, NF n_elems_of, TF item_time, uint32_t max_tile, int sm_count,
+                        std::vector<uint32_t>& tiles) {
+    std::vector<double> finish;
+    auto makespan = [&]() {
+        return simulate_makespan(n_groups, n_elems_of, [&](size_t g) { return (uint64_t)tiles[g]; }, item_time,
+                                 sm_count, finish);
+    };
+    // no schedule beats the work spread evenly over the SMs, nor its longest item
+    auto lower_bound = [&]() {
+        double total = 0, longest = 0;
+        for (size_t g = 0; g < n_groups; g++) {
+            const uint64_t n = n_elems_of(g), t = tiles[g];
+            if (n == 0) continue;
+            const double full = item_time(g, std::min<uint64_t>(t, n));
+            total += (double)(n / t) * item_time(g, t) + (n % t ? item_time(g, n % t) : 0.0);
+            longest = std::max(longest, full);
+        }
+        return std::max(total / sm_count, longest);
+    };
+    double best = makespan();
+    for (int round = 0; round < 2; round++)
+        for (size_t g = 0; g < n_groups; g++) {
+            const uint32_t keep = tiles[g];
+            uint32_t pick = keep;
+            for (uint32_t t = max_tile; t >= 1; t--) {
+                tiles[g] = t;
+                if (lower_bound() > best * (1.0 + 1e-9)) continue;
+                const double m = makespan();
+                // on a tie the wider tile: fewer items leave more of the wave to the other groups
+                if (m < best * (1.0 - 1e-9) || (m <= best * (1.0 + 1e-9) && t > pick)) { best = std::min(best, m); pick = t; }
+            }
+            tiles[g] = pick;
+        }
 }
 
 // Item-time models (arbitrary units; only their ratios matter).
@@ -724,14 +791,24 @@ oblivgm_status plan_queries(const std::map<uint32_t, Table>& tables, uint32_t n_
         }
     }
     std::stable_sort(all.begin(), all.end(), [](const G& a, const G& b) { return a.cost.walk_cost > b.cost.walk_cost; });
-    tile = choose_tile(
-        all.size(), [&](size_t i) { return all[i].d.n_elems; },
-        [&](size_t i, uint64_t w) { return wp ? wp_item_time(all[i].cost, w) : filter_item_time(all[i].cost, w); },
-        tile, step, sm_count);
+    const uint32_t max_tile = tile;
+    const auto n_of = [&](size_t i) { return all[i].d.n_elems; };
+    const auto time_of = [&](size_t i, uint64_t w) {
+        return wp ? wp_item_time(all[i].cost, w) : filter_item_time(all[i].cost, w);
+    };
+    tile = choose_tile(all.size(), n_of, time_of, max_tile, step, sm_count);
+    std::vector<uint32_t> tiles(all.size(), tile);
+    if (wp && step != 0 && all.size() > 1 && all.size() <= kWpTileGroups) {
+        uint64_t items_at_max = 0;
+        for (const G& g : all) items_at_max += (g.d.n_elems + max_tile - 1) / max_tile;
+        if (items_at_max <= 4ull * (uint64_t)sm_count) choose_group_tiles(all.size(), n_of, time_of, max_tile, sm_count, tiles);
+    }
     plan->groups.clear(); plan->preds.clear(); plan->keys.clear(); plan->item_start.clear();
-    plan->tile = tile;
+    plan->tile = *std::max_element(tiles.begin(), tiles.end());
     uint64_t items = 0;
-    for (G& g : all) {
+    for (size_t gi = 0; gi < all.size(); gi++) {
+        G& g = all[gi];
+        g.d.tile = tiles[gi];
         g.d.pred_begin = (uint32_t)plan->preds.size();
         g.d.n_preds = (uint32_t)g.preds.size();
         for (const ParsedPred* p : g.preds) {
@@ -747,7 +824,7 @@ oblivgm_status plan_queries(const std::map<uint32_t, Table>& tables, uint32_t n_
         }
         plan->groups.push_back(g.d);
         plan->item_start.push_back(items);
-        items += (g.d.n_elems + tile - 1) / tile;
+        items += (g.d.n_elems + g.d.tile - 1) / g.d.tile;
     }
     plan->item_start.push_back(items);
     return OBLIVGM_OK;
