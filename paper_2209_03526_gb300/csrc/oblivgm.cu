@@ -67,7 +67,8 @@ struct GroupDesc {
     uint32_t query_id, table_id, pred_begin, n_preds;
     uint32_t vec_out;           // out pointers are 16-byte aligned
     uint32_t tile;              // elements per work item of this group (k_filter_wp; k_filter uses the launch's)
-    uint32_t pad[2];
+    uint32_t slots;             // k_filter_wp: walk threads per element, 6 (equality predicates only) or 12
+    uint32_t pad;
 };
 
 struct PredDesc {
@@ -351,10 +352,12 @@ namespace ogm {
 constexpr int kWpSlots = 12;                          // key walks per element
 constexpr int kWpElems = 40;                          // elements per CTA (tile)
 constexpr int kWpWalks = kWpSlots * kWpElems;         // 480 seed threads, then 480 value threads
+constexpr int kWpEqSlots = 6;                         // walk threads per element of a group of equality predicates
+constexpr int kWpEqElems = kWpWalks / kWpEqSlots;     // such a group's tile: up to 80 elements
 constexpr int kWpThreads = 2 * kWpWalks;              // 960
 static_assert(kWpWalks % 32 == 0 && kWpWalks / 32 <= 15, "one named barrier (1..15) per walk pair of warps");
 constexpr int kWpPrf = 6;                             // re-share PRF words per element: 2 passes x 3 keys
-constexpr int kWpResidentOff = kFilterSmem + kWpElems * (kWpSlots + kWpPrf) * 4 +   // walk outputs, PRF words
+constexpr int kWpResidentOff = kFilterSmem + (kWpWalks + kWpEqElems * kWpPrf) * 4 +   // walk outputs, PRF words
                                2 * kWpWalks * 16 + 2 * kWpWalks * 4 + kWpWalks * 4; // seed / control-bit hand-over, V
 constexpr int kWpResidentBytes = 48 * 1024;   // descriptors, keys and tile offsets of a small launch
 constexpr int kWpSmem = kWpResidentOff + kWpResidentBytes;
@@ -376,8 +379,8 @@ __global__ void __launch_bounds__(kWpThreads, 1) k_filter_wp(const __grid_consta
     const SmemTab T{reinterpret_cast<const char*>(smem), lane_offset()};
     DevKey* kbuf = reinterpret_cast<DevKey*>(smem + kTableBytes);
     uint32_t* part = reinterpret_cast<uint32_t*>(smem + kFilterSmem);   // [element][slot]
-    uint32_t* fprf = part + kWpElems * kWpSlots;                           // [element][pass * 3 + key]
-    uint4* sbuf = reinterpret_cast<uint4*>(fprf + kWpElems * kWpPrf);      // [2][walk]: s_i
+    uint32_t* fprf = part + kWpWalks;                                      // [element][pass * 3 + key]
+    uint4* sbuf = reinterpret_cast<uint4*>(fprf + kWpEqElems * kWpPrf);    // [2][walk]: s_i
     uint32_t* tbuf = reinterpret_cast<uint32_t*>(sbuf + 2 * kWpWalks);     // [2][walk]: t_i
     uint32_t* vbuf = tbuf + 2 * kWpWalks;                                  // [walk]: the value sum V
     unsigned char* wsm = smem + kWpResidentOff;                            // resident copy of the workspace
@@ -419,7 +422,6 @@ __global__ void __launch_bounds__(kWpThreads, 1) k_filter_wp(const __grid_consta
 
     const bool value_thread = threadIdx.x >= (unsigned)kWpWalks;
     const uint32_t walk = threadIdx.x % kWpWalks;
-    const uint32_t el = walk / kWpSlots, slot = walk % kWpSlots;
     const uint64_t n_items = failed ? 0 : item_start[P.n_groups];
     // the first item of CTA b is item b (the grid has at most n_items CTAs); later ones come
     // from the work counter, past the first gridDim.x
@@ -434,7 +436,8 @@ __global__ void __launch_bounds__(kWpThreads, 1) k_filter_wp(const __grid_consta
             if (item_start[mid] <= item) lo = mid; else hi = mid - 1;
         }
         const GroupDesc& G = groups[lo];
-        const uint32_t tile = G.tile;
+        const uint32_t tile = G.tile, sw = G.slots;   // elements per item, walk threads per element
+        const uint32_t el = walk / sw, slot = walk % sw;
         const uint64_t e = (item - item_start[lo]) * tile + el;
         const uint64_t n_elems = G.n_elems;
         const bool valid = el < tile && e < n_elems;
@@ -533,7 +536,7 @@ __global__ void __launch_bounds__(kWpThreads, 1) k_filter_wp(const __grid_consta
                 // RANGE: the public constant c * beta' joins party 0's half once
                 if (!eq && (slot % nsub) == 0 && party == 0) y += D.cbeta;
             }
-            if (!value_thread) part[el * kWpSlots + slot] = y;
+            if (!value_thread) part[el * sw + slot] = y;
             // The re-share PRF words depend only on (element, step, table, query), so six
             // value threads compute the (pass, key) pairs side by side (for an equality
             // predicate while the seed threads walk): pass p re-shares with step
@@ -550,7 +553,7 @@ __global__ void __launch_bounds__(kWpThreads, 1) k_filter_wp(const __grid_consta
                 // keys are ordered [server i][half h][sub s]: server i owns slots [2 nsub i, 2 nsub (i + 1))
                 uint32_t z[3][1] = {{0}, {0}, {0}};
                 for (uint32_t kk = 0; kk < 6 * nsub; kk++) {
-                    const uint32_t v = part[el * kWpSlots + kk], i = kk / (2 * nsub);
+                    const uint32_t v = part[el * sw + kk], i = kk / (2 * nsub);
                     z[0][0] += i == 0 ? v : 0u;
                     z[1][0] += i == 1 ? v : 0u;
                     z[2][0] += i == 2 ? v : 0u;
@@ -677,13 +680,13 @@ uint32_t choose_tile(size_t n_groups, NF n_elems_of, TF item_time, uint32_t max_
 }
 
 // Per-group widths for a small launch of a few groups (the walk-parallel kernel): starting
-// from the common width, each group's width in turn is set to the one (max_tile down to 1)
+// from the common width, each group's width in turn is set to the one (its maximum down to 1)
 // that shortens the simulated makespan most (the widest on a tie), the others held, in two
 // rounds.  An equality group's items are cheaper than a range group's, so the two kinds
 // balance best at different widths, and fitting all items into one wave avoids a CTA
 // taking two.
-template <typename NF, typename TF>
-void choose_group_tiles(size_t n_groups, NF n_elems_of, TF item_time, uint32_t max_tile, int sm_count,
+template <typename NF, typename TF, typename MF>
+void choose_group_tiles(size_t n_groups, NF n_elems_of, TF item_time, MF max_tile_of, int sm_count,
                         std::vector<uint32_t>& tiles) {
     std::vector<double> finish;
     auto makespan = [&]() {
@@ -707,7 +710,7 @@ void choose_group_tiles(size_t n_groups, NF n_elems_of, TF item_time, uint32_t m
         for (size_t g = 0; g < n_groups; g++) {
             const uint32_t keep = tiles[g];
             uint32_t pick = keep;
-            for (uint32_t t = max_tile; t >= 1; t--) {
+            for (uint32_t t = max_tile_of(g); t >= 1; t--) {
                 tiles[g] = t;
                 if (lower_bound() > best * (1.0 + 1e-9)) continue;
                 const double m = makespan();
@@ -783,6 +786,11 @@ oblivgm_status plan_queries(const std::map<uint32_t, Table>& tables, uint32_t n_
                 if (reinterpret_cast<uintptr_t>(gr.d.out[j]) % 16) gr.d.vec_out = 0;
             gr.d.stride = tb.stride;
             gr.d.n_elems = tb.n_elems;
+            // a group of equality predicates only needs 6 walk threads per element (k_filter_wp)
+            gr.d.slots = (uint32_t)kWpSlots;
+            bool all_eq = true;
+            for (const ParsedPred* p : members[g]) all_eq = all_eq && p->kind == OBLIVGM_PRED_EQ;
+            if (all_eq) gr.d.slots = (uint32_t)kWpEqSlots;
             gr.d.query_id = query_ids[q];
             gr.d.table_id = tid;
             gr.preds = members[g];
@@ -801,7 +809,10 @@ oblivgm_status plan_queries(const std::map<uint32_t, Table>& tables, uint32_t n_
     if (wp && step != 0 && all.size() > 1 && all.size() <= kWpTileGroups) {
         uint64_t items_at_max = 0;
         for (const G& g : all) items_at_max += (g.d.n_elems + max_tile - 1) / max_tile;
-        if (items_at_max <= 4ull * (uint64_t)sm_count) choose_group_tiles(all.size(), n_of, time_of, max_tile, sm_count, tiles);
+        if (items_at_max <= 4ull * (uint64_t)sm_count)
+            choose_group_tiles(all.size(), n_of, time_of,
+                               [&](size_t i) { return all[i].d.slots == (uint32_t)kWpEqSlots ? (uint32_t)kWpEqElems : max_tile; },
+                               sm_count, tiles);
     }
     plan->groups.clear(); plan->preds.clear(); plan->keys.clear(); plan->item_start.clear();
     plan->tile = *std::max_element(tiles.begin(), tiles.end());
