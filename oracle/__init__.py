@@ -84,6 +84,15 @@ def lib():
                 g.argtypes = [ctypes.c_int, u32, u32, u8p, u8p, u8p, u8p, ctypes.c_int]
                 g.restype = None
             l.orc_keygen_onehot.argtypes = l.orc_keygen.argtypes
+            l.orc_token_len_onehot.argtypes = l.orc_token_len.argtypes
+            l.orc_token_len_onehot.restype = ctypes.c_size_t
+            l.orc_key_len_et.argtypes = [ctypes.c_int, ctypes.c_int]
+            l.orc_key_len_et.restype = ctypes.c_size_t
+            for g in (l.orc_dpf_gen_et, l.orc_dcf_gen_et):
+                g.argtypes = [ctypes.c_int, u32, u8p, u8p, u8p, u8p]
+                g.restype = None
+            l.orc_eval_et.argtypes = [u8p, u32]
+            l.orc_eval_et.restype = u32
             l.orc_filter_onehot.argtypes = [u8p, u8p, u8p, ctypes.POINTER(ctypes.c_size_t), u32, u8p,
                                             ctypes.POINTER(_Table), u32, u32, u8p, u64, u8p]
             l.orc_reshare.argtypes = [u8p, u8p, u8p, u64, u32, u32, u32]
@@ -197,6 +206,33 @@ def dcf_gen_z2(n: int, alpha: int, s0: bytes, s1: bytes):
     return k0.raw, k1.raw
 
 
+def key_len_et(kind: int, n: int) -> int:
+    """Length of an early-terminated Z_2 key (the one-hot mode's keys)."""
+    return lib().orc_key_len_et(kind, n)
+
+
+def _gen_et(fn, kind, n, alpha, s0, s1):
+    L = key_len_et(kind, n)
+    k0, k1 = ctypes.create_string_buffer(L), ctypes.create_string_buffer(L)
+    fn(n, alpha & MASK32, _addr(_buf(s0)), _addr(_buf(s1)), _addr(k0), _addr(k1))
+    return k0.raw, k1.raw
+
+
+def dpf_gen_et(n: int, alpha: int, s0: bytes, s1: bytes):
+    """DPF Gen for [x == alpha] over Z_2 with early termination (2^min(n,7) outputs per leaf seed)."""
+    return _gen_et(lib().orc_dpf_gen_et, KIND_DPF, n, alpha, s0, s1)
+
+
+def dcf_gen_et(n: int, alpha: int, s0: bytes, s1: bytes):
+    """DCF Gen for [x < alpha] over Z_2 with early termination."""
+    return _gen_et(lib().orc_dcf_gen_et, KIND_DCF, n, alpha, s0, s1)
+
+
+def eval_et(key: bytes, x: int) -> int:
+    """Eval of an early-terminated Z_2 key (DPF or DCF, from its header) at x: 0 or 1."""
+    return lib().orc_eval_et(_addr(_buf(key)), x & MASK32)
+
+
 def dpf_eval(key: bytes, x: int) -> int:
     return lib().orc_dpf_eval(_addr(_buf(key)), x & MASK32)
 
@@ -243,9 +279,10 @@ def keygen(preds, n: int, seed: bytes):
 
 
 def keygen_onehot(preds, n: int, seed: bytes):
-    """Tokens of the one-hot mode (Sec. V-C as written): no mask, Z_2 keys with beta = 1."""
+    """Tokens of the one-hot mode (Sec. V-C as written): no mask, early-terminated Z_2 keys
+    with beta = 1."""
     arr = _preds(preds)
-    L = token_len(preds, n)
+    L = lib().orc_token_len_onehot(arr, len(preds), n)
     bufs = [ctypes.create_string_buffer(L) for _ in range(3)]
     rc = lib().orc_keygen_onehot(arr, len(preds), n, _addr(_buf(seed)), *[_addr(b) for b in bufs], L)
     if rc != 0:

@@ -444,6 +444,205 @@ uint32_t orc_dcf_eval(const uint8_t* key, uint32_t x)
     return v & group_mask(group);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Z_2 keys with early termination (the one-hot mode's keys)                 */
+/* ------------------------------------------------------------------------ */
+/*
+ * BGI16 (the DPF the paper cites in Sec. IV-B) stops the tree early when the output
+ * group is small: a leaf seed of lambda = 128 bits expands into the outputs of many
+ * consecutive inputs.  Over Z_2 the last m = min(n, 7) input bits index a vector of
+ * 2^m <= 128 output bits, so the tree has nu = n - m levels, walked with the high
+ * bits x_hi = x >> m; the low bits x_lo pick the output bit.
+ *
+ * Vectors of 2^m bits sit in 16 bytes, bit j at byte j / 8, bit j % 8; bits from 2^m
+ * up are zero.  A leaf seed s converts to Conv(s) = H_{K_vL}(s) (the value block a
+ * further level would compute; a leaf seed is never expanded, so the block is used
+ * nowhere else), and a DCF value block to H_{K_vdir}(s), both cut to 2^m bits.
+ *
+ * DPF, f(x) = [x == alpha]: the nu levels on alpha_hi as in the full-depth DPF; the
+ * final word CW = e_{alpha_lo} xor Conv(s_0) xor Conv(s_1), so that the parties'
+ * leaf vectors Conv(s_b) xor t_b CW differ exactly in bit alpha_lo on alpha_hi's leaf
+ * and agree everywhere else.
+ *
+ * DCF, f(x) = [x < alpha]: the BCG+21 tree over the vector group Z_2^(2^m) with
+ * beta = the all-ones vector on the nu levels of alpha_hi (so a leaf left of
+ * alpha_hi's carries all ones), and the final word chosen so that alpha_hi's own leaf
+ * carries L_{alpha_lo} (bits j < alpha_lo set):
+ *   V_CW  = v^lose_0 xor v^lose_1 xor V_alpha xor [lose = L] 1,
+ *   V_alpha <- V_alpha xor v^keep_0 xor v^keep_1 xor V_CW,
+ *   CW    = Conv(s_0) xor Conv(s_1) xor V_alpha xor L_{alpha_lo}.
+ * Over Z_2 every sign of BCG+21 is +.  Key layout (group byte 1):
+ *   header 8 B, seed 16 B, per level s_CW[16], u8 t^L_CW, u8 t^R_CW, u16 0,
+ *   [DCF: V_CW[16]], final CW[16].
+ */
+static int et_low_bits(int n) { return n < 7 ? n : 7; }
+
+static size_t et_level_bytes(int kind) { return kind == KIND_DPF ? 20u : 36u; }
+
+size_t orc_key_len_et(int kind, int n)
+{
+    return 24u + (size_t)(n - et_low_bits(n)) * et_level_bytes(kind) + 16u;
+}
+
+static void vec_cut(uint8_t v[16], int m)
+{
+    int bits = 1 << m;
+    for (int j = 0; j < 128; j++)
+        if (j >= bits) v[j / 8] &= (uint8_t)~(1u << (j % 8));
+}
+
+static int vec_bit(const uint8_t v[16], uint32_t j) { return (v[j / 8] >> (j % 8)) & 1; }
+
+/* Conv(s) of a leaf seed, 2^m bits */
+static void leaf_vec(const uint8_t s[16], int m, uint8_t out[16])
+{
+    if (PLANTED == 1) { memset(out, 0, 16); return; }
+    if (PLANTED == 2) memcpy(out, s, 16);       /* the seed itself, control bit cleared */
+    else prg_h(KEY_VL, s, out);
+    vec_cut(out, m);
+}
+
+/* value vector of child dir of node s (DCF), 2^m bits */
+static void value_vec(int dir, const uint8_t s[16], int m, uint8_t out[16])
+{
+    if (PLANTED == 1) { memset(out, 0, 16); return; }
+    prg_h(dir == 0 ? KEY_VL : KEY_VR, s, out);
+    vec_cut(out, m);
+}
+
+static void et_header(uint8_t* k, int kind, int n, int b, const uint8_t seed[16])
+{
+    write_header(k, kind, n, b, seed, GROUP_Z2);
+}
+
+/* the nu tree levels shared by both kinds: seeds, control bits and, for the DCF, V_alpha */
+static void et_levels(int kind, int n, uint32_t a_hi, uint8_t s[2][16], int t[2], uint8_t v_alpha[16],
+                      uint8_t* k0, uint8_t* k1)
+{
+    const int m = et_low_bits(n), nu = n - m;
+    for (int i = 1; i <= nu; i++) {
+        uint8_t sc[2][2][16], vc[2][2][16];
+        int tc[2][2];
+        for (int b = 0; b < 2; b++)
+            for (int dir = 0; dir < 2; dir++) {
+                child(dir, s[b], sc[b][dir], &tc[b][dir]);
+                if (kind == KIND_DCF) value_vec(dir, s[b], m, vc[b][dir]);
+            }
+        int a = bit_of(a_hi, nu, i);
+        int keep = a, lose = 1 - a;
+        uint8_t s_cw[16], v_cw[16];
+        for (int j = 0; j < 16; j++) s_cw[j] = (uint8_t)(sc[0][lose][j] ^ sc[1][lose][j]);
+        int tl_cw = tc[0][0] ^ tc[1][0] ^ a ^ 1;
+        int tr_cw = tc[0][1] ^ tc[1][1] ^ a;
+        if (kind == KIND_DCF) {
+            for (int j = 0; j < 16; j++) v_cw[j] = (uint8_t)(vc[0][lose][j] ^ vc[1][lose][j] ^ v_alpha[j]);
+            if (lose == 0)
+                for (int j = 0; j < 16; j++) v_cw[j] ^= 0xFF;
+            vec_cut(v_cw, m);
+            for (int j = 0; j < 16; j++) v_alpha[j] ^= (uint8_t)(vc[0][keep][j] ^ vc[1][keep][j] ^ v_cw[j]);
+        }
+        size_t off = 24 + (size_t)(i - 1) * et_level_bytes(kind);
+        for (int p = 0; p < 2; p++) {
+            uint8_t* k = p ? k1 : k0;
+            memcpy(k + off, s_cw, 16);
+            k[off + 16] = (uint8_t)tl_cw;
+            k[off + 17] = (uint8_t)tr_cw;
+            k[off + 18] = 0; k[off + 19] = 0;
+            if (kind == KIND_DCF) memcpy(k + off + 20, v_cw, 16);
+        }
+        int t_keep_cw = keep == 0 ? tl_cw : tr_cw;
+        for (int b = 0; b < 2; b++) {
+            for (int j = 0; j < 16; j++) s[b][j] = (uint8_t)(sc[b][keep][j] ^ (t[b] ? s_cw[j] : 0));
+            t[b] = tc[b][keep] ^ (t[b] & t_keep_cw);
+        }
+    }
+}
+
+/* DPF Gen with early termination, f = [x == alpha] over Z_2 */
+void orc_dpf_gen_et(int n, uint32_t alpha, const uint8_t s0[16], const uint8_t s1[16], uint8_t* k0, uint8_t* k1)
+{
+    const int m = et_low_bits(n);
+    uint8_t s[2][16], unused[16] = {0};
+    int t[2] = {0, 1};
+    memcpy(s[0], s0, 16);
+    memcpy(s[1], s1, 16);
+    et_header(k0, KIND_DPF, n, 0, s0);
+    et_header(k1, KIND_DPF, n, 1, s1);
+    et_levels(KIND_DPF, n, alpha >> m, s, t, unused, k0, k1);
+    uint8_t c0[16], c1[16], cw[16] = {0};
+    leaf_vec(s[0], m, c0);
+    leaf_vec(s[1], m, c1);
+    uint32_t a_lo = alpha & ((1u << m) - 1u);
+    cw[a_lo / 8] = (uint8_t)(1u << (a_lo % 8));
+    for (int j = 0; j < 16; j++) cw[j] ^= (uint8_t)(c0[j] ^ c1[j]);
+    size_t off = 24 + (size_t)(n - m) * et_level_bytes(KIND_DPF);
+    memcpy(k0 + off, cw, 16);
+    memcpy(k1 + off, cw, 16);
+}
+
+/* DCF Gen with early termination, f = [x < alpha] over Z_2 */
+void orc_dcf_gen_et(int n, uint32_t alpha, const uint8_t s0[16], const uint8_t s1[16], uint8_t* k0, uint8_t* k1)
+{
+    const int m = et_low_bits(n);
+    uint8_t s[2][16], v_alpha[16] = {0};
+    int t[2] = {0, 1};
+    memcpy(s[0], s0, 16);
+    memcpy(s[1], s1, 16);
+    et_header(k0, KIND_DCF, n, 0, s0);
+    et_header(k1, KIND_DCF, n, 1, s1);
+    et_levels(KIND_DCF, n, alpha >> m, s, t, v_alpha, k0, k1);
+    uint8_t c0[16], c1[16], cw[16] = {0};
+    leaf_vec(s[0], m, c0);
+    leaf_vec(s[1], m, c1);
+    uint32_t a_lo = alpha & ((1u << m) - 1u);
+    for (uint32_t j = 0; j < a_lo; j++) cw[j / 8] |= (uint8_t)(1u << (j % 8));
+    for (int j = 0; j < 16; j++) cw[j] ^= (uint8_t)(c0[j] ^ c1[j] ^ v_alpha[j]);
+    size_t off = 24 + (size_t)(n - m) * et_level_bytes(KIND_DCF);
+    memcpy(k0 + off, cw, 16);
+    memcpy(k1 + off, cw, 16);
+}
+
+/* Eval of an early-terminated key: the 2^m-bit leaf vector of x_hi = x >> m
+ * (the DCF's value terms included), of which the caller takes bit x_lo. */
+static void et_leaf(const uint8_t* key, uint32_t x_hi, uint8_t y[16])
+{
+    int kind = key[0], n = key[1], b = key[2];
+    const int m = et_low_bits(n), nu = n - m;
+    uint8_t s[16], v[16] = {0};
+    int t = b;
+    memcpy(s, key + 8, 16);
+    for (int i = 1; i <= nu; i++) {
+        const uint8_t* cw = key + 24 + (size_t)(i - 1) * et_level_bytes(kind);
+        int dir = bit_of(x_hi, nu, i);
+        uint8_t ns[16];
+        int nt;
+        child(dir, s, ns, &nt);
+        if (kind == KIND_DCF) {
+            uint8_t vw[16];
+            value_vec(dir, s, m, vw);
+            for (int j = 0; j < 16; j++) v[j] ^= (uint8_t)(vw[j] ^ (t ? cw[20 + j] : 0));
+        }
+        if (t) {
+            for (int j = 0; j < 16; j++) ns[j] ^= cw[j];
+            nt ^= dir == 0 ? cw[16] : cw[17];
+        }
+        memcpy(s, ns, 16);
+        t = nt;
+    }
+    const uint8_t* fin = key + 24 + (size_t)nu * et_level_bytes(kind);
+    uint8_t c[16];
+    leaf_vec(s, m, c);
+    for (int j = 0; j < 16; j++) y[j] = (uint8_t)(v[j] ^ c[j] ^ (t ? fin[j] : 0));
+}
+
+uint32_t orc_eval_et(const uint8_t* key, uint32_t x)
+{
+    const int m = et_low_bits(key[1]);
+    uint8_t y[16];
+    et_leaf(key, x >> m, y);
+    return (uint32_t)vec_bit(y, x & ((1u << m) - 1u));
+}
+
 void orc_aes128(const uint8_t key[16], const uint8_t in[16], uint8_t out[16])
 {
     aes_ks ks;
@@ -512,15 +711,30 @@ static void rng_block(ctr_rng* g, uint8_t out[16])
 
 static uint32_t mask_n(int n) { return n >= 32 ? 0xFFFFFFFFu : ((1u << n) - 1u); }
 
-size_t orc_token_len(const orc_pred* preds, uint32_t n_preds, int n)
+size_t orc_key_len_et(int kind, int n);
+
+/* key length of the mode: full depth over Z_{2^32} (masked), early terminated over Z_2 (one-hot) */
+static size_t key_len_mode(int kind, int n, int onehot)
+{
+    return onehot ? orc_key_len_et(kind, n) : orc_key_len(kind, n);
+}
+
+static size_t token_len_mode(const orc_pred* preds, uint32_t n_preds, int n, int onehot)
 {
     size_t len = 16;
     for (uint32_t p = 0; p < n_preds; p++) {
         len += 24;
-        if (preds[p].kind == PRED_EQ) len += 2 * orc_key_len(KIND_DPF, n);
-        else len += 4 * orc_key_len(KIND_DCF, n);
+        if (preds[p].kind == PRED_EQ) len += 2 * key_len_mode(KIND_DPF, n, onehot);
+        else len += 4 * key_len_mode(KIND_DCF, n, onehot);
     }
     return len;
+}
+
+size_t orc_token_len(const orc_pred* preds, uint32_t n_preds, int n) { return token_len_mode(preds, n_preds, n, 0); }
+
+size_t orc_token_len_onehot(const orc_pred* preds, uint32_t n_preds, int n)
+{
+    return token_len_mode(preds, n_preds, n, 1);
 }
 
 /*
@@ -547,12 +761,12 @@ static int keygen_impl(const orc_pred* preds, uint32_t n_preds, int n, const uin
         if (q->table > 0xFFFF || q->attr > 0xFFFF || q->group > 0xFFFF) return -1;
         if (q->combine > COMBINE_OR || (first_of_group(preds, p) && q->combine != COMBINE_AND)) return -1;
     }
-    size_t total = orc_token_len(preds, n_preds, n);
+    size_t total = token_len_mode(preds, n_preds, n, onehot);
     if (cap < total) return -2;
     ctr_rng g;
     key_expansion(seed, &g.ks);
     g.ctr = 0;
-    size_t dpf_len = orc_key_len(KIND_DPF, n), dcf_len = orc_key_len(KIND_DCF, n);
+    size_t dpf_len = key_len_mode(KIND_DPF, n, onehot), dcf_len = key_len_mode(KIND_DCF, n, onehot);
     for (int i = 0; i < 3; i++) {
         uint8_t* h = tok[i];
         memset(h, 0, 16);
@@ -588,15 +802,19 @@ static int keygen_impl(const orc_pred* preds, uint32_t n_preds, int n, const uin
                 uint8_t s0[16], s1[16];
                 rng_block(&g, s0);
                 rng_block(&g, s1);
-                orc_dpf_gen_g(n, a_eq, beta, s0, s1, keys[j][0], keys[j][1], group);
+                if (onehot) orc_dpf_gen_et(n, a_eq, s0, s1, keys[j][0], keys[j][1]);
+                else orc_dpf_gen_g(n, a_eq, beta, s0, s1, keys[j][0], keys[j][1], group);
             } else {
                 uint8_t s0[16], s1[16];
                 rng_block(&g, s0);
                 rng_block(&g, s1);
-                orc_dcf_gen_g(n, a1, beta, s0, s1, keys[j][0], keys[j][1], group);
+                if (onehot) orc_dcf_gen_et(n, a1, s0, s1, keys[j][0], keys[j][1]);
+                else orc_dcf_gen_g(n, a1, beta, s0, s1, keys[j][0], keys[j][1], group);
                 rng_block(&g, s0);
                 rng_block(&g, s1);
-                orc_dcf_gen_g(n, a0, 0u - beta, s0, s1, keys[j][0] + dcf_len, keys[j][1] + dcf_len, group);
+                /* over Z_2, -beta = beta = 1 */
+                if (onehot) orc_dcf_gen_et(n, a0, s0, s1, keys[j][0] + dcf_len, keys[j][1] + dcf_len);
+                else orc_dcf_gen_g(n, a0, 0u - beta, s0, s1, keys[j][0] + dcf_len, keys[j][1] + dcf_len, group);
             }
         }
         for (int i = 0; i < 3; i++) {
@@ -663,7 +881,9 @@ static int parse_tokens(const uint8_t* const tok[3], const size_t tok_len[3], pr
     }
     if (np <= 0 || np > max_preds || n < 1 || n > 32) return -1;
     size_t off = 16;
-    size_t dpf_len = orc_key_len(KIND_DPF, n), dcf_len = orc_key_len(KIND_DCF, n);
+    const int onehot = tok[0][7] == GROUP_Z2;
+    if (onehot && n > 16) return -1;
+    size_t dpf_len = key_len_mode(KIND_DPF, n, onehot), dcf_len = key_len_mode(KIND_DCF, n, onehot);
     for (int p = 0; p < np; p++) {
         if (off + 24 > tok_len[0]) return -1;
         const uint8_t* r0 = tok[0] + off;
@@ -882,12 +1102,12 @@ static void reshare_bin(const aes_ks prf_ks[3], const uint32_t z[3], uint32_t ou
 /* value of server i's key half h at public position l (0/1) */
 static uint32_t half_at(const pred_view* pv, int server, int h, uint32_t l)
 {
-    size_t dpf_len = orc_key_len(KIND_DPF, pv->n), dcf_len = orc_key_len(KIND_DCF, pv->n);
+    size_t dpf_len = orc_key_len_et(KIND_DPF, pv->n), dcf_len = orc_key_len_et(KIND_DCF, pv->n);
     const uint8_t* rec = pv->rec[server];
-    if (pv->kind == PRED_EQ) return orc_dpf_eval(rec + 24 + (size_t)h * dpf_len, l);
+    if (pv->kind == PRED_EQ) return orc_eval_et(rec + 24 + (size_t)h * dpf_len, l);
     const uint8_t* k_hi = rec + 24 + (size_t)h * 2 * dcf_len;
     const uint8_t* k_lo = k_hi + dcf_len;
-    uint32_t y = orc_dcf_eval(k_hi, l) ^ orc_dcf_eval(k_lo, l);
+    uint32_t y = orc_eval_et(k_hi, l) ^ orc_eval_et(k_lo, l);
     if (k_hi[2] == 0) y ^= le32(rec + 16) & 1u;
     return y;
 }

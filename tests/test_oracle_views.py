@@ -23,10 +23,12 @@ PRF = bytes(range(48))
 
 
 def _key_spans(tok, n):
-    """(start, length) of every key in a masked-mode token, after its 8-byte header."""
+    """(start, length) of every key in a token, after its 8-byte header (a one-hot token,
+    group byte 1, holds early-terminated keys)."""
     spans = []
     off = 16
-    dpf, dcf = oracle.key_len(oracle.KIND_DPF, n), oracle.key_len(oracle.KIND_DCF, n)
+    klen = oracle.key_len_et if tok[7] == 1 else oracle.key_len
+    dpf, dcf = klen(oracle.KIND_DPF, n), klen(oracle.KIND_DCF, n)
     while off < len(tok):
         kind = tok[off]
         keys = [dpf, dpf] if kind == oracle.PRED_EQ else [dcf] * 4
