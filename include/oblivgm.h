@@ -513,7 +513,18 @@ oblivgm_status oblivgm_fetch_unique(oblivgm_ctx* ctx, uint32_t query_id, uint32_
  * alpha; RANGE [lo, hi]: DCFs at hi + 1 and lo, plus the constant 1 for
  * party 0 when hi is the domain's last value).  Same token layout as
  * oblivgm_keygen with header byte 7 = 1 and all <r> fields 0; the random
- * stream has no mask block.  n_bits 1..16.  Errors as oblivgm_keygen. */
+ * stream has no mask block.  The keys stop their trees early (BGI16's early
+ * termination for small output groups, the DPF cited in Sec. IV-B; the DCF
+ * the same over the vector group Z_2^(2^m)): with m = min(n, 7) a leaf seed s
+ * expands into the outputs of the 2^m positions sharing x >> m, as the 2^m
+ * low bits of H_{K_vL}(s) (bit j in byte j / 8, bit j % 8), so a key has
+ * n - m levels, walked with x >> m:
+ *   key: u8 kind (1 DPF, 2 DCF), u8 n, u8 party b, u8 1, u32 0, seed[16],
+ *     per level i = 1..n-m: s_CW[16], u8 t^L_CW, u8 t^R_CW, u16 0 and for DCF
+ *     V_CW[16] (a 2^m-bit vector); then CW[16] (2^m bits).
+ * Eval at x: walk the levels; y = V ^ H_{K_vL}(s) ^ t CW, with V the XOR of
+ * H_{K_vdir}(s_parent) ^ t V_CW over the DCF's levels; the output is bit
+ * x mod 2^m of y.  n_bits 1..16.  Errors as oblivgm_keygen. */
 oblivgm_status oblivgm_keygen_onehot(const oblivgm_pred* preds, uint32_t n_preds, uint32_t n_bits,
                                      const uint8_t seed[16], uint8_t* const tok[3], size_t cap, size_t out_len[3]);
 

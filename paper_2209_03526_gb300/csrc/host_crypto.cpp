@@ -248,6 +248,139 @@ void dcf_gen(int n, uint32_t alpha, uint32_t beta, const uint8_t s0[16], const u
     st32(k1 + 24 + (size_t)n * 24, cw);
 }
 
+namespace {
+
+// A 2^m-bit vector as four words (bit j in word j / 32); bits from 2^m up cleared.
+struct Vec { uint32_t w[4]; };
+
+Vec vec_keep_low(Vec v, int m) {
+    const int bits = 1 << m;
+    for (int w = 0; w < 4; w++) {
+        const int lo = 32 * w;
+        if (bits <= lo) v.w[w] = 0;
+        else if (bits < lo + 32) v.w[w] &= (1u << (bits - lo)) - 1u;
+    }
+    return v;
+}
+
+// H_{K_vdir}(s) cut to 2^m bits: a DCF level's value vector of child dir, and (dir 0)
+// Conv of a leaf seed, the value block a further level would have computed.
+Vec value_vec(int dir, const Seed& s, int m) {
+    const Seed o = prg(2 + dir, s);
+    Vec v;
+    for (int w = 0; w < 4; w++) v.w[w] = o.w[w];
+    return vec_keep_low(v, m);
+}
+
+Vec vec_xor(const Vec& a, const Vec& b) {
+    Vec r;
+    for (int w = 0; w < 4; w++) r.w[w] = a.w[w] ^ b.w[w];
+    return r;
+}
+
+void store_vec(uint8_t* p, const Vec& v) { for (int w = 0; w < 4; w++) st32(p + 4 * w, v.w[w]); }
+
+}  // namespace
+
+// BGI16's early termination over Z_2 (the DPF the paper cites, Sec. IV-B), and the same
+// for the BCG+21 DCF over the vector group Z_2^(2^m): the nu = n - m levels walk the high
+// bits of alpha; a DCF level's lost branch carries the all-ones vector when alpha's bit is
+// 1 (inputs there are smaller than alpha), and the final word puts e_{alpha_lo} (DPF) or
+// the bits below alpha_lo (DCF) on alpha_hi's leaf.  Over Z_2 every sign is +.
+void gen_et(uint32_t kind, int n, uint32_t alpha, const uint8_t s0[16], const uint8_t s1[16], uint8_t* k0,
+            uint8_t* k1) {
+    const bool dcf = kind == OBLIVGM_KEY_DCF;
+    const int m = et_low_bits(n), nu = n - m;
+    const size_t lb = dcf ? 36 : 20;
+    put_header(k0, kind, n, 0, s0, 1);
+    put_header(k1, kind, n, 1, s1, 1);
+    Seed s[2] = {load_seed(s0), load_seed(s1)};
+    uint32_t t[2] = {0, 1};
+    Vec valpha{};
+    const Vec ones = vec_keep_low(Vec{{~0u, ~0u, ~0u, ~0u}}, m);
+    const uint32_t hi = alpha >> m, lo = alpha & ((1u << m) - 1u);
+    for (int i = 1; i <= nu; i++) {
+        Seed c[2][2];
+        uint32_t tc[2][2];
+        Vec v[2][2];
+        for (int b = 0; b < 2; b++)
+            for (int dir = 0; dir < 2; dir++) {
+                expand(dir, s[b], &c[b][dir], &tc[b][dir]);
+                if (dcf) v[b][dir] = value_vec(dir, s[b], m);
+            }
+        const uint32_t a = input_bit(hi, nu, i);
+        const int keep = (int)a, lose = 1 - (int)a;
+        Seed scw;
+        for (int w = 0; w < 4; w++) scw.w[w] = c[0][lose].w[w] ^ c[1][lose].w[w];
+        const uint32_t tlcw = tc[0][0] ^ tc[1][0] ^ a ^ 1u;
+        const uint32_t trcw = tc[0][1] ^ tc[1][1] ^ a;
+        const size_t off = 24 + (size_t)(i - 1) * lb;
+        Vec vcw{};
+        if (dcf) {
+            vcw = vec_xor(vec_xor(v[0][lose], v[1][lose]), valpha);
+            if (a) vcw = vec_xor(vcw, ones);
+            valpha = vec_xor(vec_xor(valpha, vcw), vec_xor(v[0][keep], v[1][keep]));
+        }
+        for (uint8_t* k : {k0, k1}) {
+            store_seed(k + off, scw);
+            k[off + 16] = (uint8_t)tlcw;
+            k[off + 17] = (uint8_t)trcw;
+            k[off + 18] = k[off + 19] = 0;
+            if (dcf) store_vec(k + off + 20, vcw);
+        }
+        const uint32_t tkeep = keep ? trcw : tlcw;
+        for (int b = 0; b < 2; b++) {
+            const uint32_t msk = 0u - t[b];
+            for (int w = 0; w < 4; w++) s[b].w[w] = c[b][keep].w[w] ^ (scw.w[w] & msk);
+            t[b] = tc[b][keep] ^ (t[b] & tkeep);
+        }
+    }
+    Vec point{};
+    if (dcf) {
+        for (uint32_t j = 0; j < lo; j++) point.w[j / 32] |= 1u << (j % 32);
+        point = vec_xor(point, valpha);
+    } else {
+        point.w[lo / 32] = 1u << (lo % 32);
+    }
+    const Vec cw = vec_xor(point, vec_xor(value_vec(0, s[0], m), value_vec(0, s[1], m)));
+    store_vec(k0 + 24 + (size_t)nu * lb, cw);
+    store_vec(k1 + 24 + (size_t)nu * lb, cw);
+}
+
+bool repack_key_et(const uint8_t* wire, size_t avail, uint32_t want_kind, int want_n, EtKey* out, std::string* err) {
+    if (avail < 40) { *err = "key truncated"; return false; }
+    const uint32_t kind = wire[0];
+    const int n = wire[1];
+    const uint32_t party = wire[2];
+    if ((kind != OBLIVGM_KEY_DPF && kind != OBLIVGM_KEY_DCF) || (want_kind && kind != want_kind)) {
+        *err = "unexpected key kind";
+        return false;
+    }
+    if (n < 1 || n > kMaxOnehotBits || (want_n && n != want_n)) { *err = "key bit length mismatch"; return false; }
+    if (party > 1 || wire[3] != 1) { *err = "bad key header"; return false; }
+    if (avail < et_key_bytes(kind, n)) { *err = "key truncated"; return false; }
+    std::memset(out, 0, sizeof *out);
+    const int m = et_low_bits(n), nu = n - m;
+    const size_t lb = kind == OBLIVGM_KEY_DPF ? 20 : 36;
+    for (int w = 0; w < 4; w++) out->seed[w] = ld32(wire + 8 + 4 * w);
+    for (int i = 0; i < nu; i++) {
+        const uint8_t* lv = wire + 24 + i * lb;
+        for (int w = 0; w < 4; w++) out->scw[i][w] = ld32(lv + 4 * w);
+        if (lv[16] > 1 || lv[17] > 1) { *err = "bad control-bit correction"; return false; }
+        out->tl |= (uint32_t)lv[16] << i;
+        out->tr |= (uint32_t)lv[17] << i;
+        if (kind == OBLIVGM_KEY_DCF)
+            for (int w = 0; w < 4; w++) out->vcw[i][w] = ld32(lv + 20 + 4 * w);
+    }
+    for (int w = 0; w < 4; w++) out->cw_final[w] = ld32(wire + 24 + nu * lb + 4 * w);
+    out->party = party;
+    out->n = (uint32_t)n;
+    out->kind = kind;
+    out->low_bits = (uint32_t)m;
+    out->levels = (uint32_t)nu;
+    return true;
+}
+
 bool repack_key(const uint8_t* wire, size_t avail, uint32_t want_kind, int want_n, DevKey* out, std::string* err) {
     if (avail < 28) { *err = "key truncated"; return false; }
     const uint32_t kind = wire[0];
@@ -293,6 +426,9 @@ oblivgm_status parse_tokens(const uint8_t* const tok[3], const size_t tok_len[3]
         else if (tn != n || tnp != np) { *err = "tokens disagree on n or predicate count"; return OBLIVGM_EINVAL; }
     }
     if (n < 1 || n > kMaxBits || np < 1 || np > kMaxPreds) { *err = "token n or predicate count out of range"; return OBLIVGM_EINVAL; }
+    const bool onehot = tok[0][7] == 1;
+    if (onehot && n > kMaxOnehotBits) { *err = "one-hot token n above 16"; return OBLIVGM_EINVAL; }
+    auto kbytes = [onehot](uint32_t kind, int nb) { return onehot ? et_key_bytes(kind, nb) : key_bytes(kind, nb); };
     q->n_bits = (uint32_t)n;
     q->out_group = tok[0][7];
     q->preds.clear();
@@ -313,7 +449,7 @@ oblivgm_status parse_tokens(const uint8_t* const tok[3], const size_t tok_len[3]
         }
         const uint32_t kkind = pp.kind == OBLIVGM_PRED_EQ ? OBLIVGM_KEY_DPF : OBLIVGM_KEY_DCF;
         const int nsub = pp.kind == OBLIVGM_PRED_EQ ? 1 : 2;
-        const size_t half = nsub * key_bytes(kkind, n);
+        const size_t half = nsub * kbytes(kkind, n);
         const size_t rec_len = 24 + 2 * half;
         for (int i = 0; i < 3; i++) {
             if (off + rec_len > tok_len[i]) { *err = "token truncated"; return OBLIVGM_EINVAL; }
@@ -336,13 +472,20 @@ oblivgm_status parse_tokens(const uint8_t* const tok[3], const size_t tok_len[3]
             *err = "a group's first predicate must combine with AND";
             return OBLIVGM_EINVAL;
         }
-        pp.keys.resize(6 * nsub);
+        if (onehot) pp.et_keys.resize(6 * nsub);
+        else pp.keys.resize(6 * nsub);
         for (int i = 0; i < 3; i++)
             for (int h = 0; h < 2; h++)
                 for (int s = 0; s < nsub; s++) {
-                    const uint8_t* kw = tok[i] + off + 24 + h * half + s * key_bytes(kkind, n);
+                    const uint8_t* kw = tok[i] + off + 24 + h * half + s * kbytes(kkind, n);
+                    const size_t avail = tok_len[i] - (size_t)(kw - tok[i]);
+                    if (onehot) {
+                        if (!repack_key_et(kw, avail, kkind, n, &pp.et_keys[(i * 2 + h) * nsub + s], err))
+                            return OBLIVGM_EINVAL;
+                        continue;
+                    }
                     DevKey& dk = pp.keys[(i * 2 + h) * nsub + s];
-                    if (!repack_key(kw, tok_len[i] - (size_t)(kw - tok[i]), kkind, n, &dk, err))
+                    if (!repack_key(kw, avail, kkind, n, &dk, err))
                         return OBLIVGM_EINVAL;
                     if (dk.group != q->out_group) { *err = "key output group differs from the token's"; return OBLIVGM_EINVAL; }
                 }
@@ -378,7 +521,8 @@ oblivgm_status keygen(const oblivgm_pred* preds, uint32_t n_preds, uint32_t n_bi
     const int group = onehot ? 1 : 0;
     const int n = (int)n_bits;
     const uint32_t m = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
-    const size_t dpf = key_bytes(OBLIVGM_KEY_DPF, n), dcf = key_bytes(OBLIVGM_KEY_DCF, n);
+    const size_t dpf = onehot ? et_key_bytes(OBLIVGM_KEY_DPF, n) : key_bytes(OBLIVGM_KEY_DPF, n);
+    const size_t dcf = onehot ? et_key_bytes(OBLIVGM_KEY_DCF, n) : key_bytes(OBLIVGM_KEY_DCF, n);
     size_t total = 16;
     for (uint32_t p = 0; p < n_preds; p++) {
         const oblivgm_pred& q = preds[p];
@@ -452,12 +596,16 @@ oblivgm_status keygen(const oblivgm_pred* preds, uint32_t n_preds, uint32_t n_bi
             next_block(s0);
             next_block(s1);
             if (eq) {
-                dpf_gen(n, a_eq, beta, s0, s1, kp0, kp1, group);
+                if (onehot) gen_et(OBLIVGM_KEY_DPF, n, a_eq, s0, s1, kp0, kp1);
+                else dpf_gen(n, a_eq, beta, s0, s1, kp0, kp1, group);
             } else {
-                dcf_gen(n, a1, beta, s0, s1, kp0, kp1, group);
+                if (onehot) gen_et(OBLIVGM_KEY_DCF, n, a1, s0, s1, kp0, kp1);
+                else dcf_gen(n, a1, beta, s0, s1, kp0, kp1, group);
                 next_block(s0);
                 next_block(s1);
-                dcf_gen(n, a0, 0u - beta, s0, s1, kp0 + dcf, kp1 + dcf, group);
+                // over Z_2, -beta = beta = 1
+                if (onehot) gen_et(OBLIVGM_KEY_DCF, n, a0, s0, s1, kp0 + dcf, kp1 + dcf);
+                else dcf_gen(n, a0, 0u - beta, s0, s1, kp0 + dcf, kp1 + dcf, group);
             }
         }
         for (int i = 0; i < 3; i++) {

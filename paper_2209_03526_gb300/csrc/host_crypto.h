@@ -56,6 +56,37 @@ struct alignas(16) DevKey {
 static_assert(sizeof(DevKey) == 688, "DevKey layout");
 static_assert(sizeof(DevKey) % 16 == 0, "bulk copies need 16-byte multiples");
 
+// One-hot mode keys (outputs in Z_2) stop the tree early: the last m = min(n, 7) input
+// bits index a vector of 2^m <= 128 output bits that a leaf seed expands into, so a key
+// has nu = n - m levels.  Wire layout: header 8 B, seed 16 B, per level s_CW 16 B,
+// t^L_CW, t^R_CW, 2 zero bytes, (DCF) V_CW 16 B; the final CW 16 B.
+constexpr int kEtLowBits = 7;
+constexpr int kMaxEtLevels = kMaxOnehotBits - kEtLowBits;
+inline int et_low_bits(int n) { return n < kEtLowBits ? n : kEtLowBits; }
+inline size_t et_key_bytes(uint32_t kind, int n) {
+    return 40u + (size_t)(n - et_low_bits(n)) * (kind == OBLIVGM_KEY_DPF ? 20u : 36u);
+}
+
+// Device form of an early-terminated key.  Vectors of 2^m bits are four 32-bit words,
+// bit j in word j / 32 at bit j % 32.
+struct alignas(16) EtKey {
+    uint32_t seed[4];
+    uint32_t scw[kMaxEtLevels][4];
+    uint32_t vcw[kMaxEtLevels][4];   // DCF value corrections (2^m-bit vectors)
+    uint32_t cw_final[4];
+    uint32_t tl, tr;                 // bit i-1: t^L_CW / t^R_CW of level i
+    uint32_t party, n, kind, low_bits, levels, pad;
+};
+static_assert(sizeof(EtKey) == 352, "EtKey layout");
+
+// Gen of an early-terminated Z_2 key pair (beta = 1): [x == alpha] for a DPF,
+// [x < alpha] for a DCF, in the wire layout above.
+void gen_et(uint32_t kind, int n, uint32_t alpha, const uint8_t s0[16], const uint8_t s1[16], uint8_t* k0,
+            uint8_t* k1);
+
+// Wire key (early terminated) -> EtKey.  Returns false on a malformed key.
+bool repack_key_et(const uint8_t* wire, size_t avail, uint32_t want_kind, int want_n, EtKey* out, std::string* err);
+
 // Wire key -> DevKey.  Returns false on a malformed key.
 bool repack_key(const uint8_t* wire, size_t avail, uint32_t want_kind, int want_n, DevKey* out, std::string* err);
 
@@ -65,7 +96,8 @@ struct ParsedPred {
     uint32_t combine = 0;       // OBLIVGM_COMBINE_*: how the result joins the group's
     uint32_t r[3];        // <r>_1, <r>_2, <r>_3 (each server's own share)
     uint32_t cbeta;
-    std::vector<DevKey> keys;   // [server][half][sub]: 6 (EQ) or 12 (RANGE)
+    std::vector<DevKey> keys;   // [server][half][sub]: 6 (EQ) or 12 (RANGE); masked mode
+    std::vector<EtKey> et_keys; // the same order, one-hot mode
 };
 
 // Fold of a group's result a with a predicate's result b (Sec. V-D), over 0/1 values in

@@ -8,9 +8,10 @@
 // in binary RSS and the query element's predicates are folded (AND, XOR or OR) in binary RSS.
 //
 // Three steps per query:
-//  * EvalAll, every key half at every position: k_onehot_evalall32 (n >= 5) walks the
-//    shared top levels once per block of 32 positions and expands the last 5 depth
-//    first; k_onehot_evalall (n < 5) covers blocks of up to 8 positions;
+//  * EvalAll, every key half at every position: the keys stop their trees early (a
+//    leaf seed expands into the outputs of 2^min(n,7) consecutive positions, BGI16's
+//    early termination for small output groups), and k_onehot_evalall_et gives each
+//    (key, leaf) a thread that walks the n - 7 levels and writes the leaf's 128 bits;
 //  * the dot pass, one streaming pass over an attribute column's three share rows for
 //    up to 4 predicates on that column: k_onehot_dots_pipe (D >= 2^12, persistent,
 //    rows staged by per-lane cp.async, warps splitting the rows, each lane holding its
@@ -46,190 +47,6 @@ struct HalfDesc {
     uint32_t kind;         // OBLIVGM_KEY_DPF / OBLIVGM_KEY_DCF
 };
 
-struct EvalAllParams {
-    AesParams aes;
-    const uint32_t* te0;
-    const DevKey* keys;
-    const HalfDesc* halves;
-    uint32_t* hv;          // [half][words], zeroed before the launch
-    uint32_t domain;       // D = 2^n
-    uint32_t words;        // max(1, D / 32)
-    uint32_t n_halves;
-    int log_block;         // m = min(3, n): positions per work item = 2^m
-};
-
-// One tree level of DPF / DCF Eval (Z_2 outputs) in direction dir, as in the walks of the
-// masked mode: the selected child's seed and control bit (and, for the DCF, the value
-// term V += Convert(v) + t * V_CW, taken mod 2; Convert(v) is bit 0 of byte 0, so the
-// value block is computed as far as byte 0 only).
-__device__ __forceinline__ void level_step(const SmemTab& T, const AesParams& A, const DevKey& K, int i, uint32_t dir,
-                                           bool dcf, uint32_t s[4], uint32_t& t, uint32_t& V) {
-    const uint32_t m = 0u - dir;
-    uint32_t o[4];
-    aes_sel(T, A.rk_st, A.d_st, m, s, o);
-    if (dcf) {
-        const uint32_t v0 = aes_sel_b0(T, A.rk_v, A.d_v, m, s);
-        V ^= ((v0 ^ s[0]) & 1u) ^ (t & K.vcw[i] & 1u);
-    }
-#pragma unroll
-    for (int w = 0; w < 4; w++) o[w] ^= s[w];
-    uint32_t tn = o[0] & 1u;
-    o[0] &= ~1u;
-    const uint32_t tm = 0u - t;
-#pragma unroll
-    for (int w = 0; w < 4; w++) s[w] = o[w] ^ (K.scw[i][w] & tm);
-    tn ^= t & (((dir ? K.tr : K.tl) >> i) & 1u);
-    t = tn;
-}
-
-// The fixed PRG round keys of both directions, for level steps whose direction the whole
-// warp shares (the depth-first part of EvalAll): st[dir] for the seed / control-bit
-// block, v[dir] for the DCF value block.
-struct FixedKeys {
-    uint32_t st[2][44];
-    uint32_t v[2][44];
-};
-
-// level_step with the direction DIR known at compile time: plain AES under fixed round
-// keys instead of a per-lane key selection in every round.
-template <uint32_t DIR>
-__device__ __forceinline__ void level_step_fixed(const SmemTab& T, const FixedKeys& F, const DevKey& K, int i,
-                                                 bool dcf, uint32_t s[4], uint32_t& t, uint32_t& V) {
-    uint32_t o[4];
-    aes_one(T, F.st[DIR], s, o);
-    if (dcf) {
-        const uint32_t v0 = aes_one_b0(T, F.v[DIR], s);
-        V ^= ((v0 ^ s[0]) & 1u) ^ (t & K.vcw[i] & 1u);
-    }
-#pragma unroll
-    for (int w = 0; w < 4; w++) o[w] ^= s[w];
-    uint32_t tn = o[0] & 1u;
-    o[0] &= ~1u;
-    const uint32_t tm = 0u - t;
-#pragma unroll
-    for (int w = 0; w < 4; w++) s[w] = o[w] ^ (K.scw[i][w] & tm);
-    tn ^= t & (((DIR ? K.tr : K.tl) >> i) & 1u);
-    t = tn;
-}
-
-// Eval of one key at the 2^m consecutive positions prefix * 2^m + j, j < 2^m (m <= 3):
-// walk the n - m shared levels once, then expand the last m levels depth first
-// (2^(m+1) - 2 more levels instead of m per position).  Bit j of the result is
-// position prefix * 2^m + j.
-__device__ __forceinline__ uint32_t eval_block(const SmemTab& T, const AesParams& A, const DevKey& K, uint32_t prefix,
-                                               int m) {
-    const int n = (int)K.n;
-    const bool dcf = K.kind == OBLIVGM_KEY_DCF;
-    uint32_t s[4] = {K.seed[0], K.seed[1], K.seed[2], K.seed[3]};
-    uint32_t t = K.party, V = 0;
-    for (int i = 0; i < n - m; i++) level_step(T, A, K, i, (prefix >> (n - m - 1 - i)) & 1u, dcf, s, t, V);
-    uint32_t bits = 0;
-    const uint32_t cwf = K.cw_final & 1u;
-    if (m == 0) {
-        return V ^ ((s[0] >> 1) & 1u) ^ (t & cwf);
-    }
-    // depth-first over the last m levels (m = 1, 2 or 3), keeping one node per level
-    uint32_t s1[4], t1, V1, s2[4], t2, V2;
-    const int L1 = n - m;            // level index of the first expanded level
-    for (uint32_t b1 = 0; b1 < 2; b1++) {
-#pragma unroll
-        for (int w = 0; w < 4; w++) s1[w] = s[w];
-        t1 = t; V1 = V;
-        level_step(T, A, K, L1, b1, dcf, s1, t1, V1);
-        if (m == 1) { bits |= (V1 ^ ((s1[0] >> 1) & 1u) ^ (t1 & cwf)) << b1; continue; }
-        for (uint32_t b2 = 0; b2 < 2; b2++) {
-#pragma unroll
-            for (int w = 0; w < 4; w++) s2[w] = s1[w];
-            t2 = t1; V2 = V1;
-            level_step(T, A, K, L1 + 1, b2, dcf, s2, t2, V2);
-            if (m == 2) { bits |= (V2 ^ ((s2[0] >> 1) & 1u) ^ (t2 & cwf)) << (b1 * 2 + b2); continue; }
-            for (uint32_t b3 = 0; b3 < 2; b3++) {
-                uint32_t s3[4] = {s2[0], s2[1], s2[2], s2[3]}, t3 = t2, V3 = V2;
-                level_step(T, A, K, L1 + 2, b3, dcf, s3, t3, V3);
-                bits |= (V3 ^ ((s3[0] >> 1) & 1u) ^ (t3 & cwf)) << (b1 * 4 + b2 * 2 + b3);
-            }
-        }
-    }
-    return bits;
-}
-
-// Every key half at every position.  Work item = (half, block of 2^m positions); the
-// items are spread over one persistent CTA per SM.  hv must be zeroed: each item ORs
-// its 2^m bits into place.
-__global__ void __launch_bounds__(1024, 1) k_onehot_evalall(const __grid_constant__ EvalAllParams P) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    fill_tables(reinterpret_cast<uint32_t*>(smem), P.te0);
-    __syncthreads();
-    const SmemTab T{reinterpret_cast<const char*>(smem), lane_offset()};
-    const int m = P.log_block;
-    const uint32_t per_half = P.domain >> m;
-    const uint64_t items = (uint64_t)P.n_halves * per_half;
-    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < items;
-         idx += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t half = (uint32_t)(idx / per_half), prefix = (uint32_t)(idx % per_half);
-        const HalfDesc H = P.halves[half];
-        uint32_t bits = eval_block(T, P.aes, P.keys[H.key0], prefix, m);
-        if (H.key1 != kNoKey) bits ^= eval_block(T, P.aes, P.keys[H.key1], prefix, m);
-        if (H.cbit) bits ^= (m == 5 ? 0xFFFFFFFFu : ((1u << (1u << m)) - 1u));
-        const uint32_t pos = prefix << m;
-        atomicOr(P.hv + (uint64_t)half * P.words + pos / 32, bits << (pos % 32));
-    }
-}
-
-// ---- n >= 5: one work item per (key, 32 positions), one output word each
-
-#ifndef OGM_DFS_DEPTH
-#define OGM_DFS_DEPTH 5
-#endif
-constexpr int kDfsDepth = OGM_DFS_DEPTH;   // positions per work item: 2^kDfsDepth (at most 5)
-constexpr int kNodeWords = 6;              // seed, control bit, DCF value bit
-
-// Eval of one key at the 2^D positions prefix * 2^D + j: the n - D shared levels once,
-// then the last D levels depth first, 2^(D+1) - 2 level steps for the 2^D positions.
-// The depth-first order keeps, for each depth below the block's root, the node on the
-// current path in a per-thread stack in shared memory (word w of depth d of thread x at
-// stack[(d * kNodeWords + w) * blockDim.x + x]), so one level step serves every depth.
-// Leaf j recomputes the levels below the highest bit in which j differs from j - 1.
-__device__ __forceinline__ uint32_t eval_block_d(const SmemTab& T, const AesParams& A, const FixedKeys& F,
-                                                 const DevKey& K, uint32_t prefix, bool dcf, uint32_t* stack) {
-    const int n = (int)K.n;
-    const uint32_t nt = blockDim.x;
-    uint32_t s[4] = {K.seed[0], K.seed[1], K.seed[2], K.seed[3]};
-    uint32_t t = K.party, V = 0;
-    for (int i = 0; i < n - kDfsDepth; i++)
-        level_step(T, A, K, i, (prefix >> (n - kDfsDepth - 1 - i)) & 1u, dcf, s, t, V);
-    const int lv0 = n - kDfsDepth;
-    const uint32_t cwf = K.cw_final & 1u;
-    auto save = [&](int d) {
-#pragma unroll
-        for (int w = 0; w < 4; w++) stack[(d * kNodeWords + w) * nt] = s[w];
-        stack[(d * kNodeWords + 4) * nt] = t;
-        stack[(d * kNodeWords + 5) * nt] = V;
-    };
-    auto load = [&](int d) {
-#pragma unroll
-        for (int w = 0; w < 4; w++) s[w] = stack[(d * kNodeWords + w) * nt];
-        t = stack[(d * kNodeWords + 4) * nt];
-        V = stack[(d * kNodeWords + 5) * nt];
-    };
-    save(0);
-    uint32_t bits = 0;
-#pragma unroll 1
-    for (uint32_t leaf = 0; leaf < (1u << kDfsDepth); leaf++) {
-        const int d0 = leaf == 0 ? 0 : kDfsDepth - 1 - (31 - __clz(leaf ^ (leaf - 1)));
-        if (leaf != 0) load(d0);
-#pragma unroll 1
-        for (int d = d0; d < kDfsDepth; d++) {
-            // the same leaf sequence in every lane: the direction is warp-uniform here
-            if ((leaf >> (kDfsDepth - 1 - d)) & 1u) level_step_fixed<1>(T, F, K, lv0 + d, dcf, s, t, V);
-            else level_step_fixed<0>(T, F, K, lv0 + d, dcf, s, t, V);
-            if (d + 1 < kDfsDepth) save(d + 1);
-        }
-        bits |= (V ^ ((s[0] >> 1) & 1u) ^ (t & cwf)) << leaf;
-    }
-    return bits;
-}
-
 struct KeySlot {
     uint32_t key;       // index into the keys
     uint32_t half;      // the half vector it is XORed into
@@ -237,48 +54,73 @@ struct KeySlot {
     uint32_t dcf;
 };
 
-struct EvalWordParams {
+struct EvalEtParams {
     AesParams aes;
-    FixedKeys fixed;
     const uint32_t* te0;
-    const DevKey* keys;
+    const EtKey* keys;
     const KeySlot* slots;
     uint32_t* hv;          // [half][words], zeroed before the launch
-    uint32_t words;        // 2^n / 32
-    uint32_t blocks;       // 2^(n - kDfsDepth) blocks of positions per key
+    uint32_t words;        // max(1, 2^n / 32)
+    uint32_t leaves;       // 2^nu leaf seeds per key
     uint32_t n_slots;
 };
 
-// Every key at every position, n >= 5.  Work item = (key slot, block of 2^D positions);
-// a range half's two DCF keys are separate items XORed into the same word.
-#ifndef OGM_EVALALL32_THREADS
-#define OGM_EVALALL32_THREADS 768
-#endif
-constexpr int kEvalAll32Threads = OGM_EVALALL32_THREADS;
-constexpr int kEvalAll32Smem = kTableBytes + kDfsDepth * kNodeWords * kEvalAll32Threads * 4;
+// One tree level of an early-terminated key in direction dir: the selected child's seed
+// and control bit and, for a DCF, the value term V ^= H_{K_vdir}(s) ^ t V_CW (a 2^m-bit
+// vector; bits from 2^m up are never stored, so they need no clearing here).
+__device__ __forceinline__ void et_level(const SmemTab& T, const AesParams& A, const EtKey& K, int i,
+                                         uint32_t dir, bool dcf, uint32_t s[4], uint32_t& t, uint32_t V[4]) {
+    const uint32_t msk = 0u - dir, tm = 0u - t;
+    uint32_t o[4];
+    aes_sel(T, A.rk_st, A.d_st, msk, s, o);
+    if (dcf) {
+        uint32_t v[4];
+        aes_sel(T, A.rk_v, A.d_v, msk, s, v);
+#pragma unroll
+        for (int w = 0; w < 4; w++) V[w] ^= v[w] ^ s[w] ^ (K.vcw[i][w] & tm);
+    }
+#pragma unroll
+    for (int w = 0; w < 4; w++) o[w] ^= s[w];
+    uint32_t tn = o[0] & 1u;
+    o[0] &= ~1u;
+#pragma unroll
+    for (int w = 0; w < 4; w++) s[w] = o[w] ^ (K.scw[i][w] & tm);
+    tn ^= t & (((dir ? K.tr : K.tl) >> i) & 1u);
+    t = tn;
+}
 
-// The key kind is a runtime value: with it fixed at compile time the compiler keeps far
-// more state live in the DCF walk and spills.  Slots are ordered DPF first, so warps mix
-// kinds only at the boundary.
-__global__ void __launch_bounds__(kEvalAll32Threads, 1) k_onehot_evalall32(const __grid_constant__ EvalWordParams P) {
+// Every key at every position.  Work item = (key slot, leaf): walk the nu levels to the
+// leaf, expand its seed into the 2^m output bits of positions leaf * 2^m + j,
+//   y = V ^ H_{K_vL}(s) ^ t CW,
+// and XOR them into the slot's half vector (a range half's two DCF keys land in the same
+// words).  At n = 16 a key has 512 leaves of 9 levels: 36 keys are 18,432 items.
+constexpr int kEvalEtMaxThreads = 512;
+
+__global__ void __launch_bounds__(kEvalEtMaxThreads, 1) k_onehot_evalall_et(const __grid_constant__ EvalEtParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
     fill_tables(reinterpret_cast<uint32_t*>(smem), P.te0);
     __syncthreads();
     const SmemTab T{reinterpret_cast<const char*>(smem), lane_offset()};
-    uint32_t* stack = reinterpret_cast<uint32_t*>(smem + kTableBytes) + threadIdx.x;
-    constexpr uint32_t kBits = 1u << kDfsDepth;
-    constexpr uint32_t kMask = kBits == 32 ? 0xFFFFFFFFu : ((1u << kBits) - 1u);
-    // Item x goes to thread x / gridDim.x of CTA x % gridDim.x, which spreads the items,
-    // and the DPF / DCF mix, evenly over the SMs.
-    const uint64_t items = (uint64_t)P.n_slots * P.blocks;
-    for (uint64_t idx = (uint64_t)threadIdx.x * gridDim.x + blockIdx.x; idx < items;
+    const uint64_t items = (uint64_t)P.n_slots * P.leaves;
+    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < items;
          idx += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t slot = (uint32_t)(idx / P.blocks), b = (uint32_t)(idx % P.blocks);
+        const uint32_t slot = (uint32_t)(idx / P.leaves), leaf = (uint32_t)(idx % P.leaves);
         const KeySlot S = P.slots[slot];
-        const DevKey& K = P.keys[S.key];
-        const uint32_t bits = (eval_block_d(T, P.aes, P.fixed, K, b, S.dcf != 0, stack) ^ S.cmask) & kMask;
-        const uint32_t pos = b * kBits;
-        atomicXor(P.hv + (uint64_t)S.half * P.words + pos / 32, bits << (pos % 32));
+        const EtKey& K = P.keys[S.key];
+        const int nu = (int)K.levels, m = (int)K.low_bits;
+        uint32_t s[4] = {K.seed[0], K.seed[1], K.seed[2], K.seed[3]};
+        uint32_t t = K.party, V[4] = {0u, 0u, 0u, 0u};
+        for (int i = 0; i < nu; i++) et_level(T, P.aes, K, i, (leaf >> (nu - 1 - i)) & 1u, S.dcf != 0, s, t, V);
+        uint32_t c[4];
+        aes_sel(T, P.aes.rk_v, P.aes.d_v, 0u, s, c);
+        const uint32_t tm = 0u - t;
+        const uint32_t bits = 1u << m;
+        const uint32_t nw = bits >= 32 ? bits / 32 : 1u;
+        const uint32_t keep = bits >= 32 ? 0xFFFFFFFFu : ((1u << bits) - 1u);
+        uint32_t* dst = P.hv + (uint64_t)S.half * P.words + (uint64_t)leaf * nw;
+#pragma unroll
+        for (uint32_t w = 0; w < 4; w++)
+            if (w < nw) atomicXor(dst + w, (V[w] ^ c[w] ^ s[w] ^ (K.cw_final[w] & tm) ^ S.cmask) & keep);
     }
 }
 
@@ -772,18 +614,18 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
     }
     const uint32_t n = q.n_bits, domain = 1u << n, words = n >= 5 ? domain / 32 : 1u;
     // device keys and half descriptors: six halves per predicate, [server][half]
-    std::vector<DevKey> keys;
+    std::vector<EtKey> keys;
     std::vector<HalfDesc> halves;
     for (const ParsedPred& pp : q.preds) {
         const bool eq = pp.kind == OBLIVGM_PRED_EQ;
         const uint32_t nsub = eq ? 1 : 2, k0 = (uint32_t)keys.size();
-        keys.insert(keys.end(), pp.keys.begin(), pp.keys.end());
+        keys.insert(keys.end(), pp.et_keys.begin(), pp.et_keys.end());
         for (uint32_t hh = 0; hh < 6; hh++) {
             HalfDesc h{};
             h.key0 = k0 + hh * nsub;
             h.key1 = eq ? kNoKey : k0 + hh * nsub + 1;
             h.kind = eq ? OBLIVGM_KEY_DPF : OBLIVGM_KEY_DCF;
-            h.cbit = (!eq && pp.keys[hh * nsub].party == 0) ? (pp.cbeta & 1u) : 0u;
+            h.cbit = (!eq && pp.et_keys[hh * nsub].party == 0) ? (pp.cbeta & 1u) : 0u;
             halves.push_back(h);
         }
     }
@@ -829,7 +671,7 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
     // scratch: keys | halves | group offsets | group steps | key slots | fold groups | half vectors |
     // predicate bits
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t off_h = up(keys.size() * sizeof(DevKey));
+    const size_t off_h = up(keys.size() * sizeof(EtKey));
     const size_t off_o = off_h + up(halves.size() * sizeof(HalfDesc));
     const size_t off_s = off_o + up(np * sizeof(uint64_t));
     std::vector<KeySlot> slots;             // DPF keys first, then DCF keys
@@ -847,7 +689,7 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
     const size_t off_z = off_v + up(halves.size() * words * sizeof(uint32_t));
     const size_t total = off_z + zwords * sizeof(uint32_t);
     std::vector<unsigned char> img(off_v, 0);
-    std::memcpy(img.data(), keys.data(), keys.size() * sizeof(DevKey));
+    std::memcpy(img.data(), keys.data(), keys.size() * sizeof(EtKey));
     std::memcpy(img.data() + off_h, halves.data(), halves.size() * sizeof(HalfDesc));
     std::memcpy(img.data() + off_o, gzoff.data(), np * sizeof(uint64_t));
     std::memcpy(img.data() + off_s, gstep.data(), np * sizeof(uint32_t));
@@ -863,44 +705,26 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
     ce = cudaMemcpyAsync(ws, img.data(), off_v, cudaMemcpyHostToDevice, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "one-hot descriptor upload");
     uint32_t* zbase = reinterpret_cast<uint32_t*>(ws + off_z);
-    EvalAllParams E{};
-    E.aes = ctx->aes;
-    E.te0 = ctx->d_te0;
-    E.keys = reinterpret_cast<const DevKey*>(ws);
-    E.halves = reinterpret_cast<const HalfDesc*>(ws + off_h);
-    E.hv = reinterpret_cast<uint32_t*>(ws + off_v);
-    E.domain = domain;
-    E.words = words;
-    E.n_halves = (uint32_t)halves.size();
-    E.log_block = (int)std::min<uint32_t>(3, n);
-    ce = cudaMemsetAsync(E.hv, 0, halves.size() * words * sizeof(uint32_t), s);
+    uint32_t* hv = reinterpret_cast<uint32_t*>(ws + off_v);
+    ce = cudaMemsetAsync(hv, 0, halves.size() * words * sizeof(uint32_t), s);
     if (ce != cudaSuccess) return cuda_fail(ce, "half-vector clear");
-    if (n >= (uint32_t)kDfsDepth && n >= 5) {
-        EvalWordParams EW{};
-        EW.aes = ctx->aes;
-        for (int w = 0; w < 44; w++) {
-            EW.fixed.st[0][w] = ctx->aes.rk_st[w];
-            EW.fixed.st[1][w] = ctx->aes.rk_st[w] ^ ctx->aes.d_st[w];
-            EW.fixed.v[0][w] = ctx->aes.rk_v[w];
-            EW.fixed.v[1][w] = ctx->aes.rk_v[w] ^ ctx->aes.d_v[w];
-        }
-        EW.te0 = ctx->d_te0;
-        EW.keys = E.keys;
-        EW.slots = reinterpret_cast<const KeySlot*>(ws + off_k);
-        EW.hv = E.hv;
-        EW.words = words;
-        EW.blocks = domain >> kDfsDepth;
-        EW.slots = reinterpret_cast<const KeySlot*>(ws + off_k);
-        EW.n_slots = (uint32_t)slots.size();
-        const uint64_t items = (uint64_t)EW.n_slots * EW.blocks;
-        // every SM, each with an equal share of the items (at least a warp's worth)
-        const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((items + 31) / 32,
+    {
+        EvalEtParams E{};
+        E.aes = ctx->aes;
+        E.te0 = ctx->d_te0;
+        E.keys = reinterpret_cast<const EtKey*>(ws);
+        E.slots = reinterpret_cast<const KeySlot*>(ws + off_k);
+        E.hv = hv;
+        E.words = words;
+        E.leaves = 1u << (n - (uint32_t)et_low_bits((int)n));
+        E.n_slots = (uint32_t)slots.size();
+        const uint64_t items = (uint64_t)E.n_slots * E.leaves;
+        // one CTA per SM (the tables take 128 KiB), as many threads as give every item a thread
+        const uint64_t per_sm = (items + ctx->sm_count - 1) / ctx->sm_count;
+        const unsigned threads = (unsigned)std::min<uint64_t>(kEvalEtMaxThreads, std::max<uint64_t>(64, (per_sm + 31) / 32 * 32));
+        const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((items + threads - 1) / threads,
                                                                                  (uint64_t)ctx->sm_count));
-        k_onehot_evalall32<<<grid, kEvalAll32Threads, kEvalAll32Smem, s>>>(EW);
-    } else {
-        const uint64_t items = (uint64_t)halves.size() * (domain >> E.log_block);
-        const unsigned grid = (unsigned)std::min<uint64_t>((items + 1023) / 1024, (uint64_t)ctx->sm_count);
-        k_onehot_evalall<<<grid, 1024, kTableBytes, s>>>(E);
+        k_onehot_evalall_et<<<grid, threads, kTableBytes, s>>>(E);
     }
     ctx->launches++;
     // one streaming pass per (table, attribute) for up to kDotPreds predicates on it
@@ -915,7 +739,7 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
         for (size_t c0 = 0; c0 < ps.size(); c0 += kDotPreds) {
             DotParams D{};
             for (int j = 0; j < 3; j++) D.share[j] = tb.dev + j * set_words + (size_t)col.first.second * tb.n_elems * tb.words;
-            D.hv = E.hv;
+            D.hv = hv;
             D.n_preds = (uint32_t)std::min<size_t>(kDotPreds, ps.size() - c0);
             for (uint32_t k = 0; k < D.n_preds; k++) {
                 D.half_base[k] = 6 * ps[c0 + k];
@@ -956,9 +780,7 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
 namespace ogm {
 
 oblivgm_status set_onehot_attrs() {
-    cudaError_t e = cudaFuncSetAttribute(k_onehot_evalall, cudaFuncAttributeMaxDynamicSharedMemorySize, kTableBytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_onehot_evalall32, cudaFuncAttributeMaxDynamicSharedMemorySize, kEvalAll32Smem);
+    cudaError_t e = cudaFuncSetAttribute(k_onehot_evalall_et, cudaFuncAttributeMaxDynamicSharedMemorySize, kTableBytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_onehot_dots_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 * kPipeSmemPerWarp);
     if (e == cudaSuccess)
