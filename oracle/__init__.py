@@ -91,6 +91,8 @@ def lib():
             for g in (l.orc_dpf_gen_et, l.orc_dcf_gen_et):
                 g.argtypes = [ctypes.c_int, u32, u8p, u8p, u8p, u8p]
                 g.restype = None
+            l.orc_prf_bit.argtypes = [u8p, u64, u32, u32, u32]
+            l.orc_prf_bit.restype = u32
             l.orc_eval_et.argtypes = [u8p, u32]
             l.orc_eval_et.restype = u32
             l.orc_filter_onehot.argtypes = [u8p, u8p, u8p, ctypes.POINTER(ctypes.c_size_t), u32, u8p,
@@ -231,6 +233,11 @@ def dcf_gen_et(n: int, alpha: int, s0: bytes, s1: bytes):
 def eval_et(key: bytes, x: int) -> int:
     """Eval of an early-terminated Z_2 key (DPF or DCF, from its header) at x: 0 or 1."""
     return lib().orc_eval_et(_addr(_buf(key)), x & MASK32)
+
+
+def prf_bit(key: bytes, elem: int, step: int, table: int, query: int) -> int:
+    """The one-hot mode's re-share PRF into Z_2 (bit elem mod 128 of one AES block)."""
+    return lib().orc_prf_bit(_addr(_buf(key)), elem, step, table, query)
 
 
 def dpf_eval(key: bytes, x: int) -> int:

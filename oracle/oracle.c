@@ -1076,7 +1076,7 @@ void orc_reshare(const uint8_t prf_keys[48], const uint32_t z[3], uint32_t out[3
  * Server CS_i evaluates its key halves at every public position l and computes
  *   x = XOR_l Eval(k, l) AND <e>_j[l]
  * with j = i for its first half and j = i + 1 for its second (pair j meets share j),
- * XORs its two results, re-shares in binary RSS (F = bit 0 of AES_k(ctr)) and the
+ * XORs its two results, re-shares in binary RSS (F = prf_bit below) and the
  * group's predicates are ANDed with binary RSS multiplication.
  */
 typedef struct {
@@ -1086,9 +1086,31 @@ typedef struct {
     const uint32_t* share[3];
 } orc_onehot_table;
 
+/* F(k, ctr) into Z_2: one AES block serves 128 consecutive elements.  The bit of element
+ * e is bit e mod 128 (byte (e mod 128) / 8, bit e mod 8) of AES_k(c) with
+ * c = u64 (e div 128) | 2^63 || u16 step || u16 table || u32 query; bit 63 of c keeps
+ * these blocks apart from the masked mode's, whose element field stays below 2^63.
+ * Distinct (e, step, table, query) read distinct bits of distinct blocks, so F stays a
+ * PRF (Sec. III-B needs only that). */
 static uint32_t prf_bit(const aes_ks* k, uint64_t elem, uint32_t step, uint32_t table, uint32_t query)
 {
-    return prf(k, elem, step, table, query) & 1u;
+    uint8_t c[16], o[16];
+    uint64_t blk = (elem >> 7) | (1ull << 63);
+    uint32_t j = (uint32_t)(elem & 127u);
+    for (int i = 0; i < 8; i++) c[i] = (uint8_t)(blk >> (8 * i));
+    c[8] = (uint8_t)step; c[9] = (uint8_t)(step >> 8);
+    c[10] = (uint8_t)table; c[11] = (uint8_t)(table >> 8);
+    put32(c + 12, query);
+    aes_encrypt(k, c, o);
+    if (PLANTED == 1) return 0u;
+    return (uint32_t)((o[j / 8] >> (j % 8)) & 1u);
+}
+
+uint32_t orc_prf_bit(const uint8_t key[16], uint64_t elem, uint32_t step, uint32_t table, uint32_t query)
+{
+    aes_ks ks;
+    key_expansion(key, &ks);
+    return prf_bit(&ks, elem, step, table, query);
 }
 
 static void reshare_bin(const aes_ks prf_ks[3], const uint32_t z[3], uint32_t out[3],
