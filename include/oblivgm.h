@@ -540,8 +540,10 @@ oblivgm_status oblivgm_load_onehot(oblivgm_ctx* ctx, uint32_t table_id, uint64_t
 /* One-hot secEval of one query: per predicate each server evaluates its two
  * key halves at all 2^n positions (EvalAll) and takes the parity of their AND
  * with the binary share its key pair is tied to (CS_i: shares i and i+1);
- * it XORs its two bits, re-shares in binary RSS (F = bit 0 of AES_k(ctr),
- * same counters as the masked mode) and the group's predicates are folded
+ * it XORs its two bits, re-shares in binary RSS (F into Z_2: the bit of
+ * element e is bit e mod 128 of AES_k(c), c = u64 (e div 128) | 2^63 || u16
+ * step || u16 table || u32 query, bit j of a block in byte j / 8 at bit
+ * j % 8; steps as in the masked mode) and the group's predicates are folded
  * in binary RSS (AND, XOR or OR per predicate).  out[3 g + i] receives share set i+1 of group g packed 32
  * elements per word (element e in bit e % 32 of word e / 32; ceil(n_elems / 32)
  * words; bits past n_elems are 0).  Asynchronous on stream.  Errors as

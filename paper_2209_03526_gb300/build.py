@@ -14,7 +14,7 @@ LIB = os.path.join(OUT_DIR, "liboblivgm.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["oblivgm.cu", "plain.cu", "onehot.cu", "fetch.cu", "keygen_dev.cu", "fresh.cu", "shuffle.cu", "aes_layouts.cu", "host_crypto.cpp", "serve.cpp"]
-HEADERS = ["aes_bitsliced_sbox.cuh", "aes_byte0.cuh", "device_fss.cuh", "gen_device.cuh", "host_crypto.h", "ptx_async.cuh", "runtime.h"]
+HEADERS = ["aes_bitsliced_sbox.cuh", "device_fss.cuh", "gen_device.cuh", "host_crypto.h", "ptx_async.cuh", "runtime.h"]
 
 
 def _nvcc() -> str:

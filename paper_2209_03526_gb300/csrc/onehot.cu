@@ -28,7 +28,6 @@
 #include <utility>
 #include <vector>
 
-#include "aes_byte0.cuh"
 #include "device_fss.cuh"
 #include "host_crypto.h"
 #include "oblivgm.h"
@@ -429,13 +428,18 @@ void launch_dots(const DotParams& D, uint64_t nwords, int sm_count, cudaStream_t
 }
 
 // All groups of a query in one launch: each element's predicate bits are re-shared in
-// binary RSS and folded in token order.  A warp takes one (group, 32-element word) item
-// at a time, one lane per element, results packed by warp ballots.  The PRF's AES reads
-// the bank-replicated shared-memory T-tables (one persistent CTA per SM).
+// binary RSS and folded in token order.  The re-share PRF gives the bits of 128
+// consecutive elements from one AES block (bit e mod 128 of AES_k(c), c = u64 (e div 128)
+// | 2^63 || u16 step || u16 table || u32 query), and word q of that block holds the bits
+// of the block's output word q, so a warp takes one (group, 128 elements) item and
+// works on whole 32-element words: lane 4 b + q (b < 6) computes PRF block b (the three
+// servers' keys at the predicate's step, then at its fold step) and keeps word q; shuffles
+// bring each word's six PRF words to lane q, which re-shares, folds and stores word q.
+// The AES reads the bank-replicated shared-memory T-tables (one persistent CTA per SM).
 struct FoldGroup {
     uint32_t* out[3];
     uint64_t n_elems;
-    uint64_t word_begin;     // first item of the group in the launch's item space
+    uint64_t item_begin;     // first item (128-element block) of the group in the launch
     uint32_t first;          // index of the group's first predicate in zoff / steps
     uint32_t n_preds;
     uint32_t table_id;
@@ -449,31 +453,13 @@ struct FoldParams {
     const uint64_t* zoff;              // per predicate (group order): word offset of its [3][nwords] block
     const uint32_t* steps;             // per predicate: its index in the token | combine << 16
     const FoldGroup* groups;
-    uint64_t total_words;
+    uint64_t total_items;
     uint32_t n_groups;
     uint32_t query_id;
 };
 
-template <class Tab>
-__device__ __forceinline__ uint32_t prf_bit(const Tab& T, const uint32_t* rk, uint64_t el, uint32_t step,
-                                            uint32_t table, uint32_t query) {
-    const uint32_t ctr[4] = {(uint32_t)el, (uint32_t)(el >> 32), step | (table << 16), query};
-    return aes_one_b0(T, rk, ctr) & 1u;   // F into Z_2: bit 0 of byte 0
-}
-
-// binary re-share: r_i = z_i xor F(k_i) xor F(k_{i-1})
-template <class Tab>
-__device__ __forceinline__ void reshare_bits(const Tab& T, const FoldParams& P, uint32_t table, const uint32_t z[3],
-                                             uint32_t out[3], uint64_t el, uint32_t step) {
-    uint32_t f[3];
-#pragma unroll 1
-    for (int i = 0; i < 3; i++) f[i] = prf_bit(T, P.rk_prf[i], el, step, table, P.query_id);
-    out[0] = z[0] ^ f[0] ^ f[2];
-    out[1] = z[1] ^ f[1] ^ f[0];
-    out[2] = z[2] ^ f[2] ^ f[1];
-}
-
 constexpr int kFoldThreads = 768;
+constexpr uint32_t kFoldBlockElems = 128;
 
 __global__ void __launch_bounds__(kFoldThreads, 1) k_onehot_fold(const __grid_constant__ FoldParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -481,44 +467,63 @@ __global__ void __launch_bounds__(kFoldThreads, 1) k_onehot_fold(const __grid_co
     __syncthreads();
     const SmemTab T{reinterpret_cast<const char*>(smem), lane_offset()};
     const uint32_t lane = threadIdx.x & 31, warps = blockDim.x >> 5;
-    for (uint64_t item = (uint64_t)blockIdx.x * warps + (threadIdx.x >> 5); item < P.total_words;
+    // this lane's PRF block: b = 0..2 server b's key at the step, 3..5 at the fold step
+    // (lanes 24..31 repeat lanes 16..23; they keep a word nobody reads)
+    const uint32_t b = lane < 24 ? lane >> 2 : (lane >> 2) - 2, q = lane & 3;
+    const uint32_t* rk = P.rk_prf[b % 3];
+    for (uint64_t item = (uint64_t)blockIdx.x * warps + (threadIdx.x >> 5); item < P.total_items;
          item += (uint64_t)gridDim.x * warps) {
         uint32_t g = 0;
-        while (g + 1 < P.n_groups && P.groups[g + 1].word_begin <= item) g++;
+        while (g + 1 < P.n_groups && P.groups[g + 1].item_begin <= item) g++;
         const FoldGroup& G = P.groups[g];
         const uint64_t nwords = (G.n_elems + 31) / 32;
-        const uint64_t wd = item - G.word_begin;
-        const uint64_t e = wd * 32 + lane;
-        const bool valid = e < G.n_elems;
+        const uint64_t blk = item - G.item_begin;
+        const uint64_t wd = blk * 4 + q;                  // this lane's output word
+        const bool have = wd < nwords;
+        const uint64_t rem = have ? G.n_elems - wd * 32 : 0;
+        const uint32_t valid = rem >= 32 ? 0xFFFFFFFFu : ((1u << rem) - 1u);
+        const uint32_t c0 = (uint32_t)blk, c1 = (uint32_t)(blk >> 32) | 0x80000000u;
         uint32_t acc[3] = {0, 0, 0};
         for (uint32_t k = 0; k < G.n_preds; k++) {
             const uint64_t zo = P.zoff[G.first + k];
             const uint32_t sc = P.steps[G.first + k];
-            uint32_t z[3], b[3];
-#pragma unroll
-            for (int i = 0; i < 3; i++) z[i] = (P.zbase[zo + (uint64_t)i * nwords + wd] >> lane) & 1u;
             const uint32_t step = sc & 0xFFFFu, combine = sc >> 16;
-            reshare_bits(T, P, G.table_id, z, b, e, step);
+            uint32_t f = 0;
+            if (b < 3 || k > 0) {
+                const uint32_t ctr[4] = {c0, c1, (b < 3 ? step : 64u + step) | (G.table_id << 16), P.query_id};
+                uint32_t o[4];
+                aes_one(T, rk, ctr, o);
+                f = q == 0 ? o[0] : q == 1 ? o[1] : q == 2 ? o[2] : o[3];
+            }
+            uint32_t F[6];
+#pragma unroll
+            for (int s = 0; s < 6; s++) F[s] = __shfl_sync(0xFFFFFFFFu, f, 4 * s + (int)q);
+            uint32_t z[3], r[3];
+#pragma unroll
+            for (int i = 0; i < 3; i++) z[i] = have ? P.zbase[zo + (uint64_t)i * nwords + wd] : 0u;
+            // binary re-share: r_i = z_i xor F(k_i) xor F(k_{i-1})
+#pragma unroll
+            for (int i = 0; i < 3; i++) r[i] = z[i] ^ F[i] ^ F[(i + 2) % 3];
             if (k == 0) {
-                acc[0] = b[0]; acc[1] = b[1]; acc[2] = b[2];
+                acc[0] = r[0]; acc[1] = r[1]; acc[2] = r[2];
             } else {
                 // fold over Z_2 (Sec. V-D): AND = a b, XOR = a ^ b, OR = a ^ b ^ a b
-                const uint32_t lin = combine == OBLIVGM_COMBINE_AND ? 0u : 1u;
-                const uint32_t prod = combine == OBLIVGM_COMBINE_XOR ? 0u : 1u;
+                const uint32_t lin = combine == OBLIVGM_COMBINE_AND ? 0u : 0xFFFFFFFFu;
+                const uint32_t prod = combine == OBLIVGM_COMBINE_XOR ? 0u : 0xFFFFFFFFu;
                 uint32_t w[3];
 #pragma unroll
                 for (int i = 0; i < 3; i++) {
                     const int i1 = (i + 1) % 3;
-                    const uint32_t pr = (acc[i] & b[i]) ^ (acc[i] & b[i1]) ^ (acc[i1] & b[i]);
-                    w[i] = ((acc[i] ^ b[i]) & (0u - lin)) ^ (pr & (0u - prod));
+                    const uint32_t pr = (acc[i] & r[i]) ^ (acc[i] & r[i1]) ^ (acc[i1] & r[i]);
+                    w[i] = ((acc[i] ^ r[i]) & lin) ^ (pr & prod);
                 }
-                reshare_bits(T, P, G.table_id, w, acc, e, 64u + step);
+#pragma unroll
+                for (int i = 0; i < 3; i++) acc[i] = w[i] ^ F[3 + i] ^ F[3 + (i + 2) % 3];
             }
         }
+        if (lane < 4 && have) {
 #pragma unroll
-        for (int i = 0; i < 3; i++) {
-            const uint32_t word = __ballot_sync(0xFFFFFFFFu, valid && (acc[i] & 1u));
-            if (lane == 0) G.out[i][wd] = word;
+            for (int i = 0; i < 3; i++) G.out[i][wd] = acc[i] & valid;
         }
     }
 }
@@ -661,12 +666,12 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
             if (!G.out[j]) return fail(OBLIVGM_EINVAL, "NULL output pointer");
         }
         G.n_elems = tb.n_elems;
-        G.word_begin = fold_items;
+        G.item_begin = fold_items;
         G.first = (uint32_t)gbegin[g];
         G.n_preds = (uint32_t)members[g].size();
         G.table_id = q.preds[members[g][0]].table;
         fg.push_back(G);
-        fold_items += (tb.n_elems + 31) / 32;
+        fold_items += (tb.n_elems + kFoldBlockElems - 1) / kFoldBlockElems;
     }
     // scratch: keys | halves | group offsets | group steps | key slots | fold groups | half vectors |
     // predicate bits
@@ -761,7 +766,7 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
         F.zoff = reinterpret_cast<const uint64_t*>(ws + off_o);
         F.steps = reinterpret_cast<const uint32_t*>(ws + off_s);
         F.groups = reinterpret_cast<const FoldGroup*>(ws + off_g);
-        F.total_words = fold_items;
+        F.total_items = fold_items;
         F.n_groups = (uint32_t)fg.size();
         F.query_id = query_id;
         const uint64_t warps = kFoldThreads / 32;
