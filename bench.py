@@ -13,8 +13,9 @@ The same JSON line carries, under "workloads", one record per other workload
 of the metric, each timed on its own with its own clocks, roofline, plain-path
 comparison and oracle leg: the 1k/4k path query (n = 16), the triangle +
 pendant query on a 1M-vertex / 10M-edge graph, 256 mixed queries in one
-persistent launch replayed from a CUDA graph, and the serving loop on a
-4M-vertex / 40M-edge graph under Poisson arrivals.
+persistent launch replayed from a CUDA graph, the serving loop on a
+4M-vertex / 40M-edge graph under Poisson arrivals, and the paper's one-hot
+secEval on 107,614 vertices with 2^16-position one-hot vectors.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -900,7 +901,91 @@ def record_serve(P, torch, args, sched) -> dict:
     return rec
 
 
-WORKLOAD_RECORDS = {"tiny": record_tiny, "edges": record_edges, "batch": record_batch, "serve": record_serve}
+def record_onehot(P, torch, args, sched, ctx=None, steps=None, warmup=None) -> dict:
+    """The paper's secEval as written (one-hot mode): one 16-bit attribute of 107,614 vertices
+    (the size of the paper's graph) as binary-RSS one-hot vectors of 2^16 positions (2.64 GB
+    resident), four predicates on that column in three AND-groups, one filter_onehot call per
+    step with the L2 flushed before it."""
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    own = ctx is None
+    if own:
+        ctx = P.Context(0, prf_keys=PRF)
+    steps = steps or args.sub_steps or 1000
+    warmup = max(3, warmup or 3)
+    n_v, n = 107_614, 16
+    g = W.rng(6)
+    vals = W.uniform_attrs(g, 1, n_v, n)
+    tab = W.onehot_table(vals, n, g)
+    ctx.load_onehot(0, [torch.from_numpy(x.view(np.int32)).to(dev) for x in tab["shares"]], n)
+    del tab
+    v0, v1 = int(vals[0, 11]), int(vals[0, 22])
+    preds = [W.eq_pred(0, 0, 0, v0), W.range_pred(0, 0, 1, v1 // 2, min((1 << n) - 1, v1 + 9000)),
+             W.eq_pred(0, 0, 2, v1), W.range_pred(0, 0, 2, v1 // 3, (1 << n) - 1)]
+    toks = P.keygen_onehot(preds, n, KEY_SEED)
+    words_out = (n_v + 31) // 32
+    outs = [[torch.empty(words_out, dtype=torch.int32, device=dev) for _ in range(3)] for _ in range(3)]
+    for _ in range(warmup):
+        ctx.filter_onehot(1, toks, outs, stream)
+    ctx.sync(stream)
+    flush = L2Flush(torch, dev, stream)
+    l0 = ctx.launch_count()
+    sampler = ClockSampler(gpu_index_of(0))
+    sampler.start()
+    ms = []
+    for k in range(steps):
+        flush()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.filter_onehot(2 + k, toks, outs, stream)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    clocks = sampler.stop()
+    launches = (ctx.launch_count() - l0) // steps
+    ctx.sync(stream)
+    # the last step's bits reconstruct to the plaintext predicates (every element)
+    got = [np.stack([np.unpackbits(t.cpu().numpy().view(np.uint8), bitorder="little")[:n_v] for t in outs[gr]])
+           for gr in range(3)]
+    parity = all(np.array_equal((got[gr][0] ^ got[gr][1] ^ got[gr][2]).astype(np.uint64),
+                                plain_and([q for q in preds if q["group"] == gr], vals))
+                 for gr in range(3))
+    step_s = float(np.mean(ms)) / 1e3
+    units = len(preds) * n_v
+    row_bytes = 3 * ((1 << n) // 32) * 4                   # the three share rows of one element
+    columns = len({(p["table"], p["attr"]) for p in preds})
+    # every share row of each column the query reads, once, plus the packed outputs
+    algo_bytes = columns * n_v * row_bytes + 3 * 3 * words_out * 4
+    peak_bw = float(measured_peaks().get("hbm_gbs", 6800.0))
+    rec = {"metric": METRIC, "unit": UNIT, "value": units / step_s, "ms_per_step": step_s * 1e3, "steps": steps,
+           "warmup": warmup, "gpu_launches": launches,
+           "config": {"l2": "flushed between timed steps", "workload": "onehot_107614v_n16_4pred", "elements": n_v,
+                      "one_hot_bits": 1 << n, "groups": "EQ | RANGE | EQ AND RANGE",
+                      "element_predicates_per_step": units, "share_row_bytes_per_element": row_bytes,
+                      "columns_read": columns, "reconstructs_to_plaintext": parity},
+           "roofline": {"bound": "hbm", "achieved": algo_bytes / step_s / 1e9, "peak": peak_bw,
+                        "unit": "GB/s", "frac": algo_bytes / step_s / 1e9 / peak_bw,
+                        "what": "whole step (EvalAll + dot-product + fold launches) against the share "
+                                "rows of each column read (once for all predicates on it) and the packed "
+                                "outputs"},
+           "clocks": clocks}
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        m = 4096
+        sub = W.onehot_table(vals[:, :m], n, W.rng(16))["shares"]
+        # group 0 (one equality predicate): its EvalAll over the 2^16 positions, then m vertices
+        rec["cpu_baseline"] = oracle_leg(
+            lambda k: [oracle.filter_onehot(toks, 1, PRF, [(sub, n)], 0, np.arange(m)) for _ in range(k)],
+            m, UNIT, 1, f"oracle one-hot secEval of group 0 (1 predicate) on {m} vertices", target_s=4.0)
+    del outs, flush
+    if own:
+        ctx.close()
+    return rec
+
+
+WORKLOAD_RECORDS = {"tiny": record_tiny, "edges": record_edges, "batch": record_batch, "serve": record_serve,
+                    "onehot": record_onehot}
 
 
 def run_workload(args):
@@ -1207,60 +1292,7 @@ def run_workload(args):
         return 0
 
     if args.workload == "onehot":
-        # the paper's secEval as written: one-hot vectors of 2^16 positions in binary RSS,
-        # 107,614 vertices (the size of the paper's graph), one 16-bit attribute
-        n_v, n = 107_614, 16
-        g = W.rng(6)
-        vals = W.uniform_attrs(g, 1, n_v, n)
-        tab = W.onehot_table(vals, n, g)
-        ctx.load_onehot(0, [torch.from_numpy(x.view(np.int32)).to(dev) for x in tab["shares"]], n)
-        del tab
-        v0, v1 = int(vals[0, 11]), int(vals[0, 22])
-        preds = [W.eq_pred(0, 0, 0, v0), W.range_pred(0, 0, 1, v1 // 2, min((1 << n) - 1, v1 + 9000)),
-                 W.eq_pred(0, 0, 2, v1), W.range_pred(0, 0, 2, v1 // 3, (1 << n) - 1)]
-        toks = P.keygen_onehot(preds, n, KEY_SEED)
-        words_out = (n_v + 31) // 32
-        outs = [[torch.empty(words_out, dtype=torch.int32, device=dev) for _ in range(3)] for _ in range(3)]
-        for _ in range(max(1, args.warmup)):
-            ctx.filter_onehot(1, toks, outs, stream)
-        ctx.sync(stream)
-        flush = L2Flush(torch, dev, stream)
-        ms = []
-        for k in range(args.steps):
-            flush()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            ctx.filter_onehot(2 + k, toks, outs, stream)
-            b.record(stream)
-            b.synchronize()
-            ms.append(a.elapsed_time(b))
-        ctx.sync(stream)
-        step_s = float(np.mean(ms)) / 1e3
-        units = len(preds) * n_v
-        row_bytes = 3 * ((1 << n) // 32) * 4                   # the three share rows of one element
-        columns = len({(p["table"], p["attr"]) for p in preds})
-        # every share row of each column the query reads, once, plus the packed outputs
-        algo_bytes = columns * n_v * row_bytes + 3 * 3 * words_out * 4
-        peak_bw = float(peaks.get("hbm_gbs", 6800.0))
-        line.update({"value": units / step_s, "ms_per_step": step_s * 1e3, "steps": args.steps,
-                     "warmup": args.warmup,
-                     "config": {"l2": "flushed between timed steps", "workload": "onehot_107614v_n16_4pred", "elements": n_v, "one_hot_bits": 1 << n,
-                                "groups": "EQ | RANGE | EQ AND RANGE", "element_predicates_per_step": units,
-                                "share_row_bytes_per_element": row_bytes, "columns_read": columns},
-                     "roofline": {"bound": "hbm", "achieved": algo_bytes / step_s / 1e9, "peak": peak_bw,
-                                  "unit": "GB/s", "frac": algo_bytes / step_s / 1e9 / peak_bw,
-                                  "what": "whole step (EvalAll + dot-product + fold launches) against the share "
-                                          "rows of each column read (once for all predicates on it) and the packed "
-                                          "outputs"}})
-        if not args.no_cpu_baseline:
-            import oracle
-            oracle.build()
-            m = 4096
-            sub = W.onehot_table(vals[:, :m], n, W.rng(16))["shares"]
-            # group 0 (one equality predicate): its EvalAll over the 2^16 positions, then m vertices
-            line["cpu_baseline"] = oracle_leg(
-                lambda k: [oracle.filter_onehot(toks, 1, PRF, [(sub, n)], 0, np.arange(m)) for _ in range(k)],
-                m, UNIT, 1, f"oracle one-hot secEval of group 0 (1 predicate) on {m} vertices", target_s=4.0)
+        line.update(record_onehot(P, torch, args, sched, ctx=ctx, steps=args.steps, warmup=args.warmup))
         print(json.dumps(line), flush=True)
         return 0
 
@@ -1347,9 +1379,9 @@ def main():
     ap.add_argument("--no-compare", action="store_true",
                     help="the headline step only: skip the plain-path and latency comparisons and the other "
                          "workloads' records")
-    ap.add_argument("--workloads", default="tiny,edges,batch,serve",
+    ap.add_argument("--workloads", default="tiny,edges,batch,serve,onehot",
                     help="records of the other workloads in the default line (comma list of tiny, edges, batch, "
-                         "serve; empty for none)")
+                         "serve, onehot; empty for none)")
     ap.add_argument("--sub-steps", type=int, default=0, help="timed replays per workload record (0: its default)")
     ap.add_argument("--latency-queries", type=int, default=200, help="Poisson arrivals of the headline latency leg")
     ap.add_argument("--latency-plain", type=int, default=100,

@@ -1,7 +1,10 @@
 """GPU parity of the one-hot mode (the paper's secEval as written) against the oracle.
 
 Every compared share bit is equal; the reconstruction equals the plaintext
-predicates; domains cover one partial word (n = 3), a few words (n = 6),
+predicates.  The keys stop their trees 7 levels early (a leaf seed gives 2^min(n,7)
+bits), so the domains cover the leaf-only keys (n = 1, a 2-bit leaf; n = 5, one
+word; n = 6, two words; n = 7, one 128-bit leaf) and the first levels (n = 8, 9);
+as to the dot pass they cover one partial word (n = 3), a few words (n = 6),
 half a warp of words (n = 9), whole warps of words (n = 10), the staged path
 with one warp per 32 elements (n = 12), with two warps and more words than the
 persistent grid has CTAs (n = 13, 70,001 elements), and the bench's domain
@@ -47,7 +50,8 @@ def _run(ctx, toks, n_groups, sizes, qid):
     return [np.stack([_unpack(from_dev(t), sizes[g]) for t in outs[g]]) for g in range(n_groups)], outs
 
 
-@pytest.mark.parametrize("n,n_elems", [(3, 77), (6, 1000), (9, 1025), (10, 333), (12, 129)])
+@pytest.mark.parametrize("n,n_elems", [(1, 40), (3, 77), (5, 64), (6, 1000), (7, 500), (8, 257), (9, 1025),
+                                        (10, 333), (12, 129)])
 def test_onehot_parity(ctx, n, n_elems):
     g = W.rng(100 + n)
     top = (1 << n) - 1
