@@ -15,7 +15,9 @@ comparison and oracle leg: the 1k/4k path query (n = 16), the triangle +
 pendant query on a 1M-vertex / 10M-edge graph, 256 mixed queries in one
 persistent launch replayed from a CUDA graph, the serving loop on a
 4M-vertex / 40M-edge graph under Poisson arrivals, and the paper's one-hot
-secEval on 107,614 vertices with 2^16-position one-hot vectors.
+secEval on 107,614 vertices with 2^16-position one-hot vectors; then one record
+each of secFetch case I (1,048,576 candidates, 4 attributes), secShuffle
+(1,048,576 records) and the GPU keygen (2^20 key pairs of each kind).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -988,7 +990,7 @@ WORKLOAD_RECORDS = {"tiny": record_tiny, "edges": record_edges, "batch": record_
                     "onehot": record_onehot}
 
 
-def run_workload(args):
+def workload_line(args) -> dict:
     """The other configurations, one JSON line each (not the headline line):
     tiny   -- 1,000-vertex / 4,000-edge path query, n = 16 (parity-sized);
     edges  -- 1,000,000 vertices / 10,000,000 edges, triangle + pendant, 6 predicates;
@@ -1080,8 +1082,7 @@ def run_workload(args):
                            for _ in range(k)], n_v, "candidates/s", 1,
                 f"oracle secFetch case I over all {n_v} candidates, 4 attributes (numpy)")
         ctx.close()
-        print(json.dumps(line), flush=True)
-        return 0
+        return line
 
     if args.workload == "fresh":
         # the headline workload (1,048,576 vertices, 4 equality + 4 range predicates, n = 32)
@@ -1149,8 +1150,7 @@ def run_workload(args):
                 m * len(preds), UNIT, cores,
                 f"servers' filter on the oracle's fresh tokens for {m} vertices of the table, all 8 predicates")
         ctx.close()
-        print(json.dumps(line), flush=True)
-        return 0
+        return line
 
     if args.workload == "shuffle":
         # secShuffle of 1,048,576 records of 6 words (x, id and 4 attributes: the records of
@@ -1216,8 +1216,7 @@ def run_workload(args):
             line["cpu_baseline"] = oracle_leg(lambda k: [oracle.shuffle(osh, seeds, 0) for _ in range(k)], m,
                                               "records/s", 1, f"oracle secShuffle of {m} records x {width} words")
         ctx.close()
-        print(json.dumps(line), flush=True)
-        return 0
+        return line
 
     if args.workload == "keygen":
         # batched Gen on the device: 1,048,576 DPF pairs and 1,048,576 DCF pairs with n = 32
@@ -1288,13 +1287,12 @@ def run_workload(args):
             line["cpu_baseline"] = oracle_leg(gen_pairs, 2 * len(al), "key-pairs/s", 1,
                                               "oracle DPF and DCF Gen at n = 32, 64 pairs of each, one thread")
         ctx.close()
-        print(json.dumps(line), flush=True)
-        return 0
+        return line
 
     if args.workload == "onehot":
         line.update(record_onehot(P, torch, args, sched, ctx=ctx, steps=args.steps, warmup=args.warmup))
-        print(json.dumps(line), flush=True)
-        return 0
+        ctx.close()
+        return line
 
     if args.workload == "aes-layouts":
         # the autotuner's AES-layout dimension: the PRG on 2^26 counter blocks in both layouts
@@ -1312,8 +1310,7 @@ def run_workload(args):
                                   "unit": "Glookup/s", "frac": tt * LOOKUPS_PER_AES / 1e9 / peak_lu,
                                   "what": "the T-table layout against the shared-memory lookup ceiling"}})
         ctx.close()
-        print(json.dumps(line), flush=True)
-        return 0
+        return line
 
     if args.workload == "wp-sweep":
         # the walk-parallel kernel's item time by tile width: one predicate of each kind at n = 16
@@ -1355,17 +1352,40 @@ def run_workload(args):
         line.update({"metric": "walk-parallel item time", "unit": "us", "higher_is_better": False,
                      "config": {"workload": "walk_parallel_tile_sweep"}, "sweep": rows, "tiny_path_by_tile": tiny})
         ctx.close()
-        print(json.dumps(line), flush=True)
-        return 0
+        return line
 
     if args.workload in WORKLOAD_RECORDS:
         ctx.close()
         args.sub_steps = args.sub_steps or args.steps
         line.update(WORKLOAD_RECORDS[args.workload](P, torch, args, sched))
-        print(json.dumps(line), flush=True)
-        return 0
+        return line
     ctx.close()
     raise ValueError(f"unknown workload {args.workload}")
+
+
+def run_workload(args):
+    print(json.dumps(workload_line(args)), flush=True)
+    return 0
+
+
+def mode_record(mode: str, steps: int):
+    """A default-line record of one of the single-operation modes (fetch, shuffle, keygen): the
+    mode's own measurement, its clocks sampled over the whole record (setup included)."""
+    def rec(P, torch, args, sched) -> dict:
+        a = argparse.Namespace(**vars(args))
+        a.workload, a.steps, a.warmup, a.schedule = mode, args.sub_steps or steps, 3, ""
+        sampler = ClockSampler(gpu_index_of(0))
+        sampler.start()
+        line = workload_line(a)
+        line["clocks"] = dict(sampler.stop(), over="the whole record, setup included")
+        for k in ("n_gpus", "higher_is_better", "dtype", "data", "workload_mode", "schedule"):
+            line.pop(k, None)
+        return line
+    return rec
+
+
+WORKLOAD_RECORDS.update({"fetch": mode_record("fetch", 200), "shuffle": mode_record("shuffle", 20),
+                         "keygen": mode_record("keygen", 5)})
 
 
 def main():
@@ -1379,9 +1399,9 @@ def main():
     ap.add_argument("--no-compare", action="store_true",
                     help="the headline step only: skip the plain-path and latency comparisons and the other "
                          "workloads' records")
-    ap.add_argument("--workloads", default="tiny,edges,batch,serve,onehot",
+    ap.add_argument("--workloads", default="tiny,edges,batch,serve,onehot,fetch,shuffle,keygen",
                     help="records of the other workloads in the default line (comma list of tiny, edges, batch, "
-                         "serve, onehot; empty for none)")
+                         "serve, onehot, fetch, shuffle, keygen; empty for none)")
     ap.add_argument("--sub-steps", type=int, default=0, help="timed replays per workload record (0: its default)")
     ap.add_argument("--latency-queries", type=int, default=200, help="Poisson arrivals of the headline latency leg")
     ap.add_argument("--latency-plain", type=int, default=100,
