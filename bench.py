@@ -258,12 +258,14 @@ def gpu_index_of(local: int) -> int:
     return local
 
 
+LDS_PIPE = "shared-memory (LDS/MIO) AES T-table lookups, one 4-byte word per lane per clock per SM"
+
+
 def lookup_roofline(lookups: float, seconds: float, peak_lu: float, aes: float | None = None) -> dict:
     """Roofline record of a filter run against the shared-memory T-table lookup ceiling."""
     ach = lookups / seconds / 1e9
     out = {"bound": "lds", "achieved": ach, "peak": peak_lu, "unit": "Glookup/s", "frac": ach / peak_lu,
-           "traffic": None,
-           "pipe": "shared-memory (LDS/MIO) AES T-table lookups, one 4-byte word per lane per clock per SM"}
+           "traffic": None, "pipe": LDS_PIPE}
     if aes is not None:
         out["aes_blocks_per_s"] = aes / seconds
     return out
@@ -1131,7 +1133,7 @@ def workload_line(args) -> dict:
                                 "token_bytes_per_server": L, "element_predicates_per_step": units,
                                 "reconstructs_to_plaintext": ok,
                                 "launch": "one k_filter_fresh launch (servers); one k_keygen_fresh launch (client)"},
-                     "roofline": {"bound": "alu", "achieved": lookups / step_s / 1e9, "peak": peak_lu,
+                     "roofline": {"bound": "lds", "pipe": LDS_PIPE, "achieved": lookups / step_s / 1e9, "peak": peak_lu,
                                   "unit": "Glookup/s", "frac": lookups / step_s / 1e9 / peak_lu,
                                   "token_GB_per_s": key_bytes / step_s / 1e9,
                                   "token_frac_of_hbm": key_bytes / step_s / 1e9 / peak_bw},
@@ -1202,7 +1204,7 @@ def workload_line(args) -> dict:
                      "ms_per_step": shuf_s * 1e3, "steps": args.steps, "warmup": args.warmup,
                      "config": {"l2": "flushed between timed steps", "workload": "shuffle_1048576x6_add", "records": n_v, "words_per_record": width,
                                 "launch": "k_feistel_tab + k_perms + one kernel per server (k_shuf_cs1..3)"},
-                     "roofline": {"bound": "alu", "achieved": lookups / shuf_s / 1e9, "peak": peak_lu,
+                     "roofline": {"bound": "lds", "pipe": LDS_PIPE, "achieved": lookups / shuf_s / 1e9, "peak": peak_lu,
                                   "unit": "Glookup/s", "frac": lookups / shuf_s / 1e9 / peak_lu},
                      "fetch_case_ii": {"candidates": n_v, "matches": int(m), "ms_host_clock": float(np.mean(fms)) * 1e3,
                                        "candidates_per_s": n_v / float(np.mean(fms)),
@@ -1269,7 +1271,7 @@ def workload_line(args) -> dict:
                      "config": {"l2": "flushed between timed steps", "workload": "keygen_1048576_dpf_1048576_dcf_n32", "pairs_per_kind": m,
                                 "launch": "one k_keygen launch per kind"},
                      "kinds": kinds,
-                     "roofline": {"bound": "alu", "achieved": total_lu / total_s / 1e9, "peak": peak_lu,
+                     "roofline": {"bound": "lds", "pipe": LDS_PIPE, "achieved": total_lu / total_s / 1e9, "peak": peak_lu,
                                   "unit": "Glookup/s", "frac": total_lu / total_s / 1e9 / peak_lu},
                      "table1_host_gentoken": table1})
         if not args.no_cpu_baseline:
@@ -1385,7 +1387,7 @@ def mode_record(mode: str, steps: int):
 
 
 WORKLOAD_RECORDS.update({"fetch": mode_record("fetch", 200), "shuffle": mode_record("shuffle", 20),
-                         "keygen": mode_record("keygen", 5)})
+                         "keygen": mode_record("keygen", 5), "fresh": mode_record("fresh", 3)})
 
 
 def main():
@@ -1399,9 +1401,9 @@ def main():
     ap.add_argument("--no-compare", action="store_true",
                     help="the headline step only: skip the plain-path and latency comparisons and the other "
                          "workloads' records")
-    ap.add_argument("--workloads", default="tiny,edges,batch,serve,onehot,fetch,shuffle,keygen",
+    ap.add_argument("--workloads", default="tiny,edges,batch,serve,onehot,fetch,shuffle,keygen,fresh",
                     help="records of the other workloads in the default line (comma list of tiny, edges, batch, "
-                         "serve, onehot, fetch, shuffle, keygen; empty for none)")
+                         "serve, onehot, fetch, shuffle, keygen, fresh; empty for none)")
     ap.add_argument("--sub-steps", type=int, default=0, help="timed replays per workload record (0: its default)")
     ap.add_argument("--latency-queries", type=int, default=200, help="Poisson arrivals of the headline latency leg")
     ap.add_argument("--latency-plain", type=int, default=100,

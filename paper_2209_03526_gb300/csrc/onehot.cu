@@ -64,34 +64,35 @@ struct EvalEtParams {
     uint32_t n_slots;
 };
 
-// One tree level of an early-terminated key in direction dir: the selected child's seed
-// and control bit and, for a DCF, the value term V ^= H_{K_vdir}(s) ^ t V_CW (a 2^m-bit
-// vector; bits from 2^m up are never stored, so they need no clearing here).
-__device__ __forceinline__ void et_level(const SmemTab& T, const AesParams& A, const EtKey& K, int i,
-                                         uint32_t dir, bool dcf, uint32_t s[4], uint32_t& t, uint32_t V[4]) {
-    const uint32_t msk = 0u - dir, tm = 0u - t;
-    uint32_t o[4];
-    aes_sel(T, A.rk_st, A.d_st, msk, s, o);
-    if (dcf) {
-        uint32_t v[4];
-        aes_sel(T, A.rk_v, A.d_v, msk, s, v);
+// AES-128 whose round keys depend on the lane: key A (rkA ^ (m & dA)) where r = 0, key B
+// (rkB ^ (m & dB)) where r = ~0.  The four schedules are launch parameters (uniform
+// operands); the per-lane choice costs three LOP3s per round-key word.
+template <class Tab>
+__device__ __forceinline__ void aes_two_keys(const Tab& T, const uint32_t* rkA, const uint32_t* dA,
+                                             const uint32_t* rkB, const uint32_t* dB, uint32_t m, uint32_t r,
+                                             const uint32_t in[4], uint32_t out[4]) {
+    auto key = [&](int w) {
+        const uint32_t a = rkA[w] ^ (m & dA[w]), b = rkB[w] ^ (m & dB[w]);
+        return a ^ ((a ^ b) & r);
+    };
+    uint32_t c[4];
 #pragma unroll
-        for (int w = 0; w < 4; w++) V[w] ^= v[w] ^ s[w] ^ (K.vcw[i][w] & tm);
-    }
+    for (int j = 0; j < 4; j++) c[j] = in[j] ^ key(j);
 #pragma unroll
-    for (int w = 0; w < 4; w++) o[w] ^= s[w];
-    uint32_t tn = o[0] & 1u;
-    o[0] &= ~1u;
+    for (int rd = 1; rd < 10; rd++) aes_round(T, c, key(4 * rd), key(4 * rd + 1), key(4 * rd + 2), key(4 * rd + 3));
+    aes_last(T, c, key(40), key(41), key(42), key(43));
 #pragma unroll
-    for (int w = 0; w < 4; w++) s[w] = o[w] ^ (K.scw[i][w] & tm);
-    tn ^= t & (((dir ? K.tr : K.tl) >> i) & 1u);
-    t = tn;
+    for (int j = 0; j < 4; j++) out[j] = c[j];
 }
 
-// Every key at every position.  Work item = (key slot, leaf): walk the nu levels to the
-// leaf, expand its seed into the 2^m output bits of positions leaf * 2^m + j,
+// Every key at every position.  Work item = (key slot, leaf), taken by a pair of lanes:
+// at each of the nu levels the even lane computes the chosen child's seed block and the
+// odd lane, for a DCF, its value block H_{K_vdir}(s) on the same seed (for a DPF its
+// block is not used); the new seed and control bit reach the odd lane by shuffles.  The
+// odd lane then expands the leaf seed into the 2^m output bits of positions
+// leaf * 2^m + j,
 //   y = V ^ H_{K_vL}(s) ^ t CW,
-// and XOR them into the slot's half vector (a range half's two DCF keys land in the same
+// and XORs them into the slot's half vector (a range half's two DCF keys land in the same
 // words).  At n = 16 a key has 512 leaves of 9 levels: 36 keys are 18,432 items.
 constexpr int kEvalEtMaxThreads = 512;
 
@@ -100,16 +101,39 @@ __global__ void __launch_bounds__(kEvalEtMaxThreads, 1) k_onehot_evalall_et(cons
     fill_tables(reinterpret_cast<uint32_t*>(smem), P.te0);
     __syncthreads();
     const SmemTab T{reinterpret_cast<const char*>(smem), lane_offset()};
+    const uint32_t lane = threadIdx.x & 31, role = lane & 1u, rmask = 0u - role, even = lane & ~1u;
     const uint64_t items = (uint64_t)P.n_slots * P.leaves;
-    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < items;
-         idx += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t slot = (uint32_t)(idx / P.leaves), leaf = (uint32_t)(idx % P.leaves);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x / 2;
+    // the warp's first pair: the loop bound is the same for every lane of the warp, so the
+    // shuffles below always have all 32 lanes; a pair past the end repeats the last item
+    // and writes nothing
+    const uint64_t warp_first = ((uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u)) / 2;
+    for (uint64_t wf = warp_first; wf < items; wf += stride) {
+        const uint64_t idx = wf + lane / 2;
+        const bool live = idx < items;
+        const uint64_t it = live ? idx : items - 1;
+        const uint32_t slot = (uint32_t)(it / P.leaves), leaf = (uint32_t)(it % P.leaves);
         const KeySlot S = P.slots[slot];
         const EtKey& K = P.keys[S.key];
         const int nu = (int)K.levels, m = (int)K.low_bits;
+        const uint32_t vmask = S.dcf ? rmask : 0u;    // the value chain runs on the odd lane of a DCF pair
         uint32_t s[4] = {K.seed[0], K.seed[1], K.seed[2], K.seed[3]};
         uint32_t t = K.party, V[4] = {0u, 0u, 0u, 0u};
-        for (int i = 0; i < nu; i++) et_level(T, P.aes, K, i, (leaf >> (nu - 1 - i)) & 1u, S.dcf != 0, s, t, V);
+        for (int i = 0; i < nu; i++) {
+            const uint32_t dir = (leaf >> (nu - 1 - i)) & 1u, dm = 0u - dir, tm = 0u - t;
+            uint32_t o[4];
+            aes_two_keys(T, P.aes.rk_st, P.aes.d_st, P.aes.rk_v, P.aes.d_v, dm, rmask, s, o);
+#pragma unroll
+            for (int w = 0; w < 4; w++) {
+                o[w] ^= s[w];
+                V[w] ^= (o[w] ^ (K.vcw[i][w] & tm)) & vmask;
+            }
+            uint32_t tn = (o[0] & 1u) ^ (t & (((dir ? K.tr : K.tl) >> i) & 1u));
+            o[0] &= ~1u;
+#pragma unroll
+            for (int w = 0; w < 4; w++) s[w] = __shfl_sync(0xFFFFFFFFu, o[w] ^ (K.scw[i][w] & tm), even);
+            t = __shfl_sync(0xFFFFFFFFu, tn, even);
+        }
         uint32_t c[4];
         aes_sel(T, P.aes.rk_v, P.aes.d_v, 0u, s, c);
         const uint32_t tm = 0u - t;
@@ -117,9 +141,11 @@ __global__ void __launch_bounds__(kEvalEtMaxThreads, 1) k_onehot_evalall_et(cons
         const uint32_t nw = bits >= 32 ? bits / 32 : 1u;
         const uint32_t keep = bits >= 32 ? 0xFFFFFFFFu : ((1u << bits) - 1u);
         uint32_t* dst = P.hv + (uint64_t)S.half * P.words + (uint64_t)leaf * nw;
+        if (live && role) {
 #pragma unroll
-        for (uint32_t w = 0; w < 4; w++)
-            if (w < nw) atomicXor(dst + w, (V[w] ^ c[w] ^ s[w] ^ (K.cw_final[w] & tm) ^ S.cmask) & keep);
+            for (uint32_t w = 0; w < 4; w++)
+                if (w < nw) atomicXor(dst + w, (V[w] ^ c[w] ^ s[w] ^ (K.cw_final[w] & tm) ^ S.cmask) & keep);
+        }
     }
 }
 
@@ -724,10 +750,10 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
         E.leaves = 1u << (n - (uint32_t)et_low_bits((int)n));
         E.n_slots = (uint32_t)slots.size();
         const uint64_t items = (uint64_t)E.n_slots * E.leaves;
-        // one CTA per SM (the tables take 128 KiB), as many threads as give every item a thread
-        const uint64_t per_sm = (items + ctx->sm_count - 1) / ctx->sm_count;
+        // one CTA per SM (the tables take 128 KiB), as many threads as give every item a lane pair
+        const uint64_t per_sm = (2 * items + ctx->sm_count - 1) / ctx->sm_count;
         const unsigned threads = (unsigned)std::min<uint64_t>(kEvalEtMaxThreads, std::max<uint64_t>(64, (per_sm + 31) / 32 * 32));
-        const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((items + threads - 1) / threads,
+        const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((2 * items + threads - 1) / threads,
                                                                                  (uint64_t)ctx->sm_count));
         k_onehot_evalall_et<<<grid, threads, kTableBytes, s>>>(E);
     }
