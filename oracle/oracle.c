@@ -1,5 +1,5 @@
 /*
- * oracle.c -- plain, slow CPU oracle for the masked FSS predicate-evaluation path.
+ * oracle.c -- plain, slow CPU oracle for the FSS predicate-evaluation path.
  *
  * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
  * cpu_baseline / reference legs of bench.py load this code.  The product
@@ -22,6 +22,11 @@
  *     Sec. III-B and the aggregation of a target's predicates of Sec. V-D
  *     (all hold: the RSS product; "one of": the paper's XOR; or the inclusive
  *     OR), all over Z_{2^32}.
+ *   - the one-hot mode of Sec. V-B/V-C: keys over Z_2 with beta = 1 that stop
+ *     their trees early (BGI16's early termination for small output groups; the
+ *     DCF the same over the vector group Z_2^(2^m)), evaluated at every position
+ *     of a binary-RSS one-hot vector, re-shared with a PRF bit per element (one
+ *     AES block per 128 elements) and folded in binary RSS.
  *
  * Every step is written in the order the construction states it; nothing is
  * blocked, fused or reordered.  Eval computes only the child the input bit
@@ -31,8 +36,9 @@
  * Parity unpinned (conventions the paper leaves open; they fix individual share
  * values, while every reconstructed result is pinned by the tests): the fixed
  * keys K_R, K_vL, K_vR (K_L is FIPS-pinned), the token byte layout, the keygen
- * random streams, the PRF counter layout, and secShuffle's derivation of each
- * pair's permutation and masks from its seed.
+ * random streams, the PRF counter layouts (the one-hot PRF's is pinned against
+ * the FIPS-pinned AES), and secShuffle's derivation of each pair's permutation
+ * and masks from its seed.
  */
 #include <stdint.h>
 #include <stddef.h>
