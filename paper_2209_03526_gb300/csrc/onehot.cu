@@ -514,6 +514,10 @@ __global__ void __launch_bounds__(kFoldThreads, 1) k_onehot_fold(const __grid_co
             const uint64_t zo = P.zoff[G.first + k];
             const uint32_t sc = P.steps[G.first + k];
             const uint32_t step = sc & 0xFFFFu, combine = sc >> 16;
+            // the predicate's bits of this word, loaded before the PRF's AES so the loads overlap it
+            uint32_t z[3], r[3];
+#pragma unroll
+            for (int i = 0; i < 3; i++) z[i] = have ? P.zbase[zo + (uint64_t)i * nwords + wd] : 0u;
             uint32_t f = 0;
             if (b < 3 || k > 0) {
                 const uint32_t ctr[4] = {c0, c1, (b < 3 ? step : 64u + step) | (G.table_id << 16), P.query_id};
@@ -524,9 +528,6 @@ __global__ void __launch_bounds__(kFoldThreads, 1) k_onehot_fold(const __grid_co
             uint32_t F[6];
 #pragma unroll
             for (int s = 0; s < 6; s++) F[s] = __shfl_sync(0xFFFFFFFFu, f, 4 * s + (int)q);
-            uint32_t z[3], r[3];
-#pragma unroll
-            for (int i = 0; i < 3; i++) z[i] = have ? P.zbase[zo + (uint64_t)i * nwords + wd] : 0u;
             // binary re-share: r_i = z_i xor F(k_i) xor F(k_{i-1})
 #pragma unroll
             for (int i = 0; i < 3; i++) r[i] = z[i] ^ F[i] ^ F[(i + 2) % 3];
@@ -795,9 +796,11 @@ extern "C" oblivgm_status oblivgm_filter_onehot(oblivgm_ctx* ctx, uint32_t query
         F.total_items = fold_items;
         F.n_groups = (uint32_t)fg.size();
         F.query_id = query_id;
-        const uint64_t warps = kFoldThreads / 32;
+        // a warp per item: as many warps per CTA as spread the items over every SM (at least 4)
+        const uint64_t warps = std::min<uint64_t>(kFoldThreads / 32, std::max<uint64_t>(
+                                                      4, (fold_items + ctx->sm_count - 1) / ctx->sm_count));
         const unsigned grid = (unsigned)std::min<uint64_t>((fold_items + warps - 1) / warps, (uint64_t)ctx->sm_count);
-        k_onehot_fold<<<grid, kFoldThreads, kTableBytes, s>>>(F);
+        k_onehot_fold<<<grid, (unsigned)(warps * 32), kTableBytes, s>>>(F);
         ctx->launches++;
     }
     ce = cudaGetLastError();
