@@ -11,15 +11,17 @@
 //  * EvalAll, every key half at every position: the keys stop their trees early (a
 //    leaf seed expands into the outputs of 2^min(n,7) consecutive positions, BGI16's
 //    early termination for small output groups), and k_onehot_evalall_et gives each
-//    (key, leaf) a thread that walks the n - 7 levels and writes the leaf's 128 bits;
+//    (key, leaf) a lane pair that walks the n - 7 levels (seed chain and DCF value
+//    chain side by side) and writes the leaf's 128 bits;
 //  * the dot pass, one streaming pass over an attribute column's three share rows for
 //    up to 4 predicates on that column: k_onehot_dots_pipe (D >= 2^12, persistent,
 //    rows staged by per-lane cp.async, warps splitting the rows, each lane holding its
 //    slice of the half vectors in registers) or k_onehot_dots (smaller D); parities
 //    are XOR-reduced over the warp and each server's bit written packed;
 //  * k_onehot_fold: every group in one launch, each element's bits re-shared in
-//    binary RSS and folded in token order (PRF AES from shared-memory T-tables);
-//    results are packed 32 elements per word.
+//    binary RSS and folded in token order on whole 32-element words (one PRF AES
+//    block from the shared-memory T-tables serves 128 elements); results are packed
+//    32 elements per word.
 #include <cuda_runtime.h>
 
 #include <algorithm>
