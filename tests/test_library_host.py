@@ -95,7 +95,7 @@ def test_keygen_buffer_too_small_reports_size():
     assert st == N.ERANGE and lens[0] == P.token_len(preds, 8)
 
 
-@pytest.mark.parametrize("n", [1, 3, 8, 12, 16])
+@pytest.mark.parametrize("n", [1, 3, 5, 6, 7, 8, 12, 16])
 def test_onehot_keygen_byte_identical_to_oracle(n):
     g = np.random.default_rng(50 + n)
     for trial in range(2):
